@@ -1,0 +1,350 @@
+"""Benchmark of the SEIRD backward-Euler Newton-Krylov-Schwarz step on GB300.
+
+Metric: implicit DOF*steps/s at a 1e-8 relative Newton residual (DOF = 5 x
+nodes), on the Southern-Ontario-like workload: a seeded 24-gon meshed to 2.0M
+P1 nodes (10M unknowns), urban-Gaussian density, 5 infection seeds, dt = 0.5
+day, RAS with 512 uneven subdomains, overlap 2, plus the constant coarse space.
+A "step" is one backward-Euler time step (assembly, preconditioner set-up,
+GMRES, line search) of that whole mesh.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (test infrastructure, not the product)
+on the host cores, on a bounded sample of the same workload.  Under torchrun
+(N > 1) every rank runs an independent replica of the workload (the path is one
+coupled solve; it is not sharded across GPUs) and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SEIRD implicit DOF·steps/s at 1e-8 Newton resid (FP64 vs mixed); BSR SpMV GB/s"
+UNIT = "DOF·steps/s"
+FALLBACK_HBM_GBS = 6800.0
+
+# dram__bytes_read.sum + dram__bytes_write.sum per launch from the committed ncu
+# capture of each kernel class at this workload (profiles/); None until captured
+# or after the kernel changed.
+NCU_TRAFFIC = {}
+
+# kernel classes with one kernel launch per timed call, and their algorithmic
+# bytes per launch ("Algorithmic bytes")
+SINGLE_KERNEL = ("spmv", "ilu_solve", "ilu_factor")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--nodes", type=int, default=2_000_000)
+    ap.add_argument("--subdomains", type=int, default=512)
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-sample", type=str, default=None, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+def workload_config(wl, args):
+    return {
+        "workload": "%s (Southern-Ontario-like 24-gon, %d P1 nodes, %d unknowns)" % (wl.name, wl.n, 5 * wl.n),
+        "n_nodes": wl.n, "n_tris": int(len(wl.tri)), "dof": 5 * wl.n, "dt_days": wl.dt,
+        "subdomains": args.subdomains, "overlap": 2, "coarse": "additive, constant per subdomain and compartment",
+        "subdomain_solver": "block ILU(0)", "krylov": "FGMRES(30) right-preconditioned, CGS2, rtol 1e-5",
+        "newton_rtol": 1e-8, "quadrature": "degree-5 seven-point", "seed": args.seed,
+        "l2": "inputs larger than L2 (the FP64 Jacobian alone is > 2.7 GB)",
+    }
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample (run in a child process with one BLAS thread)
+# ---------------------------------------------------------------------------
+
+SAMPLE_NODES = 20_000
+
+
+def oracle_sample_child(spec):
+    """Times the oracle (as it stands) on the same generator at SAMPLE_NODES."""
+    from oracle import seird_oracle as O
+    from paper_2208_01839_gb300 import inputs as I
+    d = json.loads(spec)
+    wl = I.ontario_workload(d["nodes"], seed=d["seed"])
+    U = wl.U0
+    times = []
+    for k in range(d["warmup"] + d["steps"]):
+        t0 = time.perf_counter()
+        U, info = O.newton_step(wl.xy, wl.tri, wl.params, wl.dt, U, rtol=1e-8)
+        if k >= d["warmup"]:
+            times.append(time.perf_counter() - t0)
+    print(json.dumps({"n": wl.n, "dof": 5 * wl.n, "times": times}))
+
+
+def run_oracle_sample(nodes, steps, warmup, seed):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[k] = "1"
+    spec = json.dumps({"nodes": nodes, "steps": steps, "warmup": warmup, "seed": seed})
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", spec], env=env,
+                       capture_output=True, text=True, cwd=ROOT)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed: %s" % r.stderr[-2000:])
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    tot = sum(out["times"])
+    return {"value": out["dof"] * len(out["times"]) / tot, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d steps of the same generator at %d nodes (%d DOF), Newton to 1e-8 with a SuperLU "
+                      "direct solve, one thread" % (len(out["times"]), out["n"], out["dof"]),
+            "s_per_step": tot / len(out["times"])}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", "seird_clocks_%d_%d.csv" % (os.getpid(), index))
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def algorithmic_bytes(cls, info):
+    """Bytes each launch of a kernel class must move at least."""
+    n, nnzb = info["n_nodes"], info["nnzb"]
+    nl, nlb = info["subdomain_rows"], info["subdomain_blocks"]
+    if cls == "spmv":  # values + column indices + row pointers + x once + y once
+        return nnzb * (25 * 8 + 4) + (n + 1) * 4 + 2 * 5 * n * 8
+    if cls == "ilu_solve":  # factor blocks + columns + inverse diagonals + r gathered + z written
+        return nlb * (25 * 8 + 4) + nl * (25 * 8 + 8 + 16) + nl * 5 * 8 + 5 * n * 8
+    if cls == "ilu_factor":  # J blocks gathered, factor blocks written, inverse diagonals written
+        return nlb * (25 * 8 * 2 + 4 + 4) + nl * 25 * 8
+    return None
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2208_01839_gb300 import build as B
+    B.build()
+    from paper_2208_01839_gb300 import inputs as I
+    from paper_2208_01839_gb300 import seird as S
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+
+    t_setup = time.perf_counter()
+    wl = I.ontario_workload(args.nodes, seed=args.seed, n_subdomains=args.subdomains)
+    t_gen = time.perf_counter() - t_setup
+    sv = S.Solver(wl.xy, wl.tri, wl.params, stream=stream, dt=wl.dt, n_subdomains=args.subdomains, overlap=2,
+                  coarse=1, newton_rtol=1e-8, gmres_rtol=1e-5, gmres_restart=30, gmres_maxit=200,
+                  precision=1 if args.precision == "mixed" else 0, seed=args.seed, timing=1)
+    t_create = time.perf_counter() - t_setup - t_gen
+    info = sv.info()
+    sv.set_state(torch.tensor(wl.U0, device="cuda"))
+    for _ in range(args.warmup):
+        sv.step()
+    torch.cuda.synchronize()
+
+    # ---- device-timed region: K steps, inputs resident in HBM
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    launches0 = S.launch_count()
+    stats = []
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            stats.append(sv.step())
+        e1.record(stream)
+        torch.cuda.synchronize()
+    launches = S.launch_count() - launches0
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        dist.barrier()
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    dof = 5 * wl.n
+    value = world * dof * args.steps / (ms * 1e-3)
+
+    # kernel classes over the timed region
+    kms = {k: sum(s["kernel_ms"][k] for s in stats) for k in S.KERNEL_CLASSES}
+    kcalls = {k: sum(s["kernel_calls"][k] for s in stats) for k in S.KERNEL_CLASSES}
+    peak, peak_kind = hbm_peak()
+    dom = max(SINGLE_KERNEL, key=lambda k: kms[k])
+    ab = algorithmic_bytes(dom, info)
+    avg_ms = kms[dom] / max(kcalls[dom], 1)
+    achieved = ab / (avg_ms * 1e-3) / 1e9
+    sp_ab = algorithmic_bytes("spmv", info)
+    sp_ms = kms["spmv"] / max(kcalls["spmv"], 1)
+    sp_gbs = sp_ab / (sp_ms * 1e-3) / 1e9 if kcalls["spmv"] else None
+
+    # ---- end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        hbuf = torch.empty((wl.n, 5), dtype=torch.float64, pin_memory=True)
+        sv.get_state(hbuf.numpy())
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            sv.set_state(hbuf.numpy())
+            sv.step()
+            sv.get_state(hbuf.numpy())
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([wall], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            wall = float(t.item())
+        e2e = {"value": world * dof * args.steps / wall, "unit": UNIT, "h2d_bytes_per_step": dof * 8,
+               "d2h_bytes_per_step": dof * 8}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            cpu = run_oracle_sample(SAMPLE_NODES, 2, 0, args.seed)
+        except Exception as ex:  # reported, never fatal
+            cpu = {"error": str(ex)[:300]}
+
+    if rank == 0:
+        nits = [s["newton_its"] for s in stats]
+        gits = [s["gmres_its"] for s in stats]
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
+            "data": "synthetic (seeded Southern-Ontario-like mesh, density and infection seeds)",
+            "config": dict(workload_config(wl, args), parallelism="replicas" if world > 1 else "single GPU"),
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind,
+                         "traffic": NCU_TRAFFIC.get(dom), "algorithmic_bytes_per_launch": ab,
+                         "avg_launch_ms": avg_ms, "launches": kcalls[dom]},
+            "spmv": {"gbs": sp_gbs, "frac_of_hbm": (sp_gbs / peak) if sp_gbs else None,
+                     "avg_launch_ms": sp_ms, "launches": kcalls["spmv"], "algorithmic_bytes": sp_ab},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
+            "kernel_ms": {k: round(v, 3) for k, v in kms.items()}, "kernel_calls": kcalls,
+            "newton_its_per_step": sum(nits) / len(nits), "gmres_its_per_step": sum(gits) / len(gits),
+            "setup_s": {"generate": round(t_gen, 2), "create": round(t_create, 2)},
+            "device_bytes": info["device_bytes"],
+        }
+        print(json.dumps(line))
+    sv.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    res = run_oracle_sample(SAMPLE_NODES, args.steps, args.warmup, args.seed)
+    line = {
+        "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * res["s_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": "Southern-Ontario-like 24-gon, %d P1 nodes (timed on a %d-node sample)"
+                               % (args.nodes, SAMPLE_NODES), "dt_days": 0.5, "newton_rtol": 1e-8},
+        "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": res["sample"], "value": res["value"], "unit": UNIT},
+        "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.oracle_sample:
+        oracle_sample_child(args.oracle_sample)
+        return
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,241 @@
+/*
+ * seird.h -- C ABI of the GB300 backward-Euler Newton-Krylov-Schwarz step for
+ * the five-compartment SEIRD reaction-diffusion model (arXiv 2208.01839).
+ *
+ * The method (all references are to the paper):
+ *   - PDE: Eq. seird1-5 with N = s+e+i+r+d (Eq. N), vector form Eq.
+ *     vec_component1/2, homogeneous Neumann (no-flux) boundary.
+ *   - Time discretisation: backward Euler, Eq. timediscrete.
+ *   - Space: P1 triangles, weak form Eq. weakform.  Consistent mass, exact
+ *     diffusion integral (mean_T(N) |T| grad u . grad phi), reaction term by
+ *     Radon's degree-5 seven-point rule (or the three-vertex rule).
+ *   - Nonlinear solve: Newton with the exact Jacobian and backtracking on
+ *     ||F||_2 (Section 2.2 names Newton as the coupled alternative to its
+ *     Picard iteration; both converge to the root of Eq. weakform).
+ *   - Linear solve: right-preconditioned restarted (F)GMRES with classical
+ *     Gram-Schmidt and one re-orthogonalisation (CGS2); stopping rules of
+ *     Section 3.2 (rtol, atol, dtol against ||b||_2).
+ *   - Preconditioner: restricted additive Schwarz (Eq. RAS) with overlapping
+ *     subdomains and block-ILU(0) subdomain solves, plus (optionally) the
+ *     additive coarse correction M_2^{-1} = M_RAS^{-1} + Z A_c^{-1} Z^T
+ *     (Section 3.1) with Z the per-subdomain, per-compartment constant space.
+ *
+ * Layouts.  A state is node-major: u[node*5 + c], c = 0..4 = s, e, i, r, d,
+ * float64, in the caller's node numbering.  Internally the library renumbers
+ * nodes by (subdomain, caller index); every entry point below that takes or
+ * returns a state uses the caller's numbering.  Block-sparse matrices are
+ * 5x5-block BSR: row_ptr int32[n_rows+1], col int32[nnzb] (sorted within each
+ * block row), val float64[nnzb][5][5] row-major inside a block.
+ *
+ * Ownership.  seird_create copies everything it needs (mesh, parameters,
+ * optional fields and partition) to the device; the caller keeps ownership of
+ * its arrays.  Pointers passed with on_device = 1 are device pointers that the
+ * call reads or writes on the context's stream and never retains; with
+ * on_device = 0 they are host pointers and the call returns after the copy.
+ *
+ * Errors.  Every int-returning call returns SEIRD_OK (0) or a negative
+ * SEIRD_E* code; seird_last_error() gives a message.  The library never traps
+ * or aborts, never waits without bound, and leaves the state at u^n when a
+ * step fails.  A context is used by one host thread at a time.
+ */
+#ifndef SEIRD_H
+#define SEIRD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SEIRD_OK 0
+#define SEIRD_EINVAL (-1)           /* bad argument or mesh */
+#define SEIRD_ENOMEM (-2)           /* device or host allocation failed */
+#define SEIRD_ECUDA (-3)            /* a CUDA runtime call failed */
+#define SEIRD_ENEWTON_DIVERGED (-4) /* line search could not decrease ||F|| */
+#define SEIRD_ENEWTON_MAXIT (-5)    /* Newton iteration limit reached */
+#define SEIRD_EGMRES (-6)           /* GMRES diverged (dtol) or hit its limit */
+#define SEIRD_ENONFINITE (-7)       /* non-finite value, or N <= 0 where 1/N is needed */
+#define SEIRD_ETIMEOUT (-8)         /* a bounded device wait gave up */
+#define SEIRD_ESINGULAR (-9)        /* a 5x5 pivot block is singular */
+
+/* Mesh (Section 2.2: P1 triangles).  Host arrays. */
+typedef struct {
+  int64_t n_nodes;
+  int64_t n_tris;
+  const double* xy;    /* [n_nodes][2] */
+  const int32_t* tri;  /* [n_tris][3], counter-clockwise, 0-based */
+} seird_mesh;
+
+/* Rates of Eq. seird1-5 and the diffusion coefficients of Eq. vec_component1. */
+typedef struct {
+  double A;        /* Allee parameter in (1 - A/N) */
+  double beta_i;   /* transmission by infected */
+  double beta_e;   /* transmission by exposed */
+  double sigma;    /* exposed -> infected */
+  double gamma_e;  /* exposed -> recovered */
+  double gamma_r;  /* infected -> recovered */
+  double gamma_d;  /* infected -> deceased */
+  double alpha;    /* births (the paper uses 0) */
+  double mu;       /* natural deaths (the paper uses 0) */
+  double nu[4];    /* nubar_S, nubar_E, nubar_I, nubar_R ; nubar_D = 0 */
+  const double* beta_field; /* optional host [n_nodes] P1 multiplier of beta_i and beta_e
+                               (Eq. beta_ie/beta_x frozen in time); NULL means 1 */
+} seird_params;
+
+/* Solver options.  seird_default_options() fills the values quoted per field. */
+typedef struct {
+  double dt;              /* time step (1.0) */
+  double newton_rtol;     /* stop when ||F|| <= rtol ||F(u^n)|| + atol (1e-8) */
+  double newton_atol;     /* (0) */
+  int32_t newton_maxit;   /* (20) */
+  int32_t ls_maxit;       /* backtracking halvings (10) */
+  int32_t gmres_restart;  /* Krylov vectors per cycle, <= 64 (30) */
+  int32_t gmres_maxit;    /* total iterations per linear solve (200, Section 3.2) */
+  double gmres_rtol;      /* (1e-5, Section 3.2) */
+  double gmres_atol;      /* (1e-50, Section 3.2) */
+  double gmres_dtol;      /* (1e5, Section 3.2) */
+  int32_t n_subdomains;   /* RAS subdomains when owner == NULL (4) */
+  int32_t overlap;        /* graph layers of overlap (1; Section 3.2 uses a minimal one) */
+  int32_t coarse;         /* 0: one-level RAS; 1: additive constant coarse space (0) */
+  int32_t precision;      /* 0: FP64 throughout; 1: FP32 matrix copy and FP32 subdomain
+                             factors inside the FP64 outer FGMRES (0) */
+  int32_t quadrature;     /* 0: degree-5 seven-point rule; 1: three-vertex rule (0) */
+  int32_t pc_lag;         /* rebuild the preconditioner every pc_lag Newton iterations
+                             (the first iteration of every step always rebuilds) (1) */
+  const int32_t* owner;   /* optional host [n_nodes]: subdomain of each node, values
+                             0..n_subdomains-1 all used; NULL: seeded recursive
+                             coordinate bisection into n_subdomains parts */
+  uint64_t seed;          /* seed of the bisection's uneven split fractions (0) */
+  void* stream;           /* cudaStream_t the context runs on; NULL: a private stream */
+  int32_t timing;         /* 1: time every kernel class with CUDA events on the stream and
+                             report it in seird_stats.kernel_ms (0) */
+} seird_options;
+
+/* Kernel classes of seird_stats.kernel_ms / kernel_calls. */
+enum {
+  SEIRD_K_RESIDUAL = 0,     /* residual assembly (element + gather + norm) */
+  SEIRD_K_JACOBIAN = 1,     /* Jacobian assembly (records + block gather) */
+  SEIRD_K_ILU_FACTOR = 2,   /* subdomain block-ILU(0) factorisation */
+  SEIRD_K_COARSE_SETUP = 3, /* Z^T J Z and its banded block LU */
+  SEIRD_K_SPMV = 4,         /* BSR SpMV */
+  SEIRD_K_ILU_SOLVE = 5,    /* subdomain triangular solves (RAS apply) */
+  SEIRD_K_COARSE_APPLY = 6, /* Z^T r, banded solve, Z y */
+  SEIRD_K_KRYLOV = 7,       /* CGS2, norms and vector updates */
+  SEIRD_K_COUNT = 8
+};
+
+/* Per-step statistics (the paper's iteration counts and setup/solve split,
+ * Table PC_2000_600cores and Fig. setup_hypre). */
+typedef struct {
+  int32_t newton_its;
+  int32_t gmres_its;      /* summed over the step's linear solves */
+  int32_t ls_halvings;
+  int32_t pc_setups;
+  double res0;            /* ||F(u^n)||_2 */
+  double res_final;       /* ||F(u^{n+1})||_2 */
+  double eps_update;      /* last ||u^{k+1}-u^k|| / ||u^n|| (Eq. picardtol) */
+  double ms_assemble;     /* residual + Jacobian assembly */
+  double ms_setup;        /* preconditioner setup (subdomain factors, coarse) */
+  double ms_solve;        /* GMRES */
+  double ms_total;
+  double kernel_ms[8];    /* device time per kernel class (options.timing = 1) */
+  int32_t kernel_calls[8];
+} seird_stats;
+
+/* Sizes of a created context. */
+typedef struct {
+  int64_t n_nodes, n_tris, nnzb;
+  int32_t n_subdomains;
+  int64_t subdomain_rows;      /* sum over subdomains of overlapped node counts */
+  int64_t subdomain_blocks;    /* sum over subdomains of local BSR blocks */
+  int32_t max_levels;          /* deepest ILU(0) level schedule */
+  int32_t coarse_band;         /* half bandwidth (in subdomains) of the coarse matrix */
+  int64_t device_bytes;        /* device memory held by the context */
+} seird_info;
+
+typedef struct seird_ctx seird_ctx;
+
+/* Fills *opt with the defaults listed above. */
+void seird_default_options(seird_options* opt);
+
+/* Builds a context: validates the mesh (indices in range, positive areas),
+ * partitions and renumbers nodes, builds the BSR pattern, element maps,
+ * overlapping subdomains (Eq. RAS), ILU(0) level schedules and the coarse
+ * pattern, and uploads everything.  The state is set to zero at t = 0.
+ * Returns SEIRD_EINVAL for a bad mesh/option, SEIRD_ENOMEM, SEIRD_ECUDA. */
+int seird_create(const seird_mesh* mesh, const seird_params* params, const seird_options* opt,
+                 seird_ctx** out);
+
+/* Releases every resource of the context (NULL is ignored). */
+void seird_destroy(seird_ctx* ctx);
+
+/* Message of the last error on this context (or of the last failed create
+ * when ctx is NULL).  Valid until the next call on the context. */
+const char* seird_last_error(const seird_ctx* ctx);
+
+/* Sets the state u^n (caller numbering, [n_nodes][5] float64) and time t. */
+int seird_set_state(seird_ctx* ctx, const double* u, int on_device, double t);
+
+/* Copies the current state out (caller numbering) and its time (t may be NULL). */
+int seird_get_state(const seird_ctx* ctx, double* u, int on_device, double* t);
+
+/* One backward-Euler step (Eq. timediscrete): u^{n+1} = root of Eq. weakform
+ * by Newton-Krylov-Schwarz from the guess u^n; t += dt.  stats may be NULL.
+ * On failure the state stays u^n and the code says why. */
+int seird_step(seird_ctx* ctx, seird_stats* stats);
+
+/* n_steps steps; per_step may be NULL or point to n_steps records.  Stops at
+ * the first failing step and returns its code. */
+int seird_run(seird_ctx* ctx, int32_t n_steps, seird_stats* per_step);
+
+/* Sizes of the context. */
+int seird_get_info(const seird_ctx* ctx, seird_info* info);
+
+/* ---- component entry points (kernel-level parity and measurement) ---- */
+
+/* F(u; u_prev) of Eq. weakform (caller numbering, [n_nodes][5]).  All three
+ * pointers are device pointers when on_device = 1, host pointers otherwise. */
+int seird_eval_residual(seird_ctx* ctx, const double* u, const double* u_prev, double* F, int on_device);
+
+/* Assembles the exact Jacobian dF/du at u into the context's BSR matrix. */
+int seird_eval_jacobian(seird_ctx* ctx, const double* u, int on_device);
+
+/* Copies the context's Jacobian out in caller numbering as host BSR arrays
+ * (row_ptr [n_nodes+1], col [nnzb] sorted, val [nnzb][25]). */
+int seird_get_jacobian(const seird_ctx* ctx, int32_t* row_ptr, int32_t* col, double* val);
+
+/* y = J x with the context's Jacobian (caller numbering). */
+int seird_apply_jacobian(seird_ctx* ctx, const double* x, double* y, int on_device);
+
+/* Builds the preconditioner (subdomain block-ILU(0) factors and, if enabled,
+ * the coarse matrix Z^T J Z and its factors) from the context's Jacobian. */
+int seird_precond_setup(seird_ctx* ctx);
+
+/* z = M^{-1} r with the last preconditioner built (caller numbering). */
+int seird_precond_apply(seird_ctx* ctx, const double* r, double* z, int on_device);
+
+/* Solves J x = b with the preconditioned (F)GMRES of the step (x starts at 0),
+ * using the context's Jacobian and last preconditioner.  its may be NULL. */
+int seird_linear_solve(seird_ctx* ctx, const double* b, double* x, int on_device, int32_t* its);
+
+/* y = A x for a 5x5-block BSR matrix with n_rows block rows; every pointer is a
+ * device pointer; stream is a cudaStream_t (NULL: legacy default stream).
+ * x has 5 entries per block column, y 5 per block row.  Returns SEIRD_EINVAL
+ * for n_rows < 0 or a NULL pointer with n_rows > 0, SEIRD_ECUDA if the launch fails. */
+int seird_bsr_spmv(int64_t n_rows, const int32_t* row_ptr, const int32_t* col, const double* val,
+                   const double* x, double* y, void* stream);
+
+/* The same product with float32 block values (x and y stay float64): the
+ * matrix copy of the mixed-precision path. */
+int seird_bsr_spmv_f32val(int64_t n_rows, const int32_t* row_ptr, const int32_t* col, const float* val,
+                          const double* x, double* y, void* stream);
+
+/* Number of kernels the library has launched in this process so far. */
+int64_t seird_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SEIRD_H */

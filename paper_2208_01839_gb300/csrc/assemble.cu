@@ -1,0 +1,384 @@
+// Residual and Jacobian assembly of the discrete system of Eq. weakform
+// (P1 triangles, backward Euler, Eq. timediscrete; reaction rows of Eq.
+// vec_component2).  Two phases each, atomic-free and deterministic:
+//   element phase  (one thread per triangle): element vector / Jacobian record;
+//   gather phase   (one thread per node / per 5x5 block): fixed-order sums over
+//                  the incident triangles, lists built at setup.
+// All arithmetic is FP64.
+#include <cmath>
+
+#include "kernels.cuh"
+
+namespace seird {
+
+// Quadrature tables: rule 0 = Radon's degree-5 seven-point rule (barycentric
+// points on the centroid and two three-point orbits at (6 -+ sqrt 15)/21,
+// weights 9/40 and (155 -+ sqrt 15)/1200); rule 1 = three vertices, 1/3 each.
+__constant__ double cQL[2][7][3];
+__constant__ double cQW[2][7];
+
+void upload_quadrature() {
+  double L[2][7][3] = {};
+  double W[2][7] = {};
+  const double r = std::sqrt(15.0);
+  const double a1 = (6.0 - r) / 21.0, b1 = (9.0 + 2.0 * r) / 21.0;
+  const double a2 = (6.0 + r) / 21.0, b2 = (9.0 - 2.0 * r) / 21.0;
+  const double pts[7][3] = {{1.0 / 3, 1.0 / 3, 1.0 / 3}, {b1, a1, a1}, {a1, b1, a1}, {a1, a1, b1},
+                            {b2, a2, a2}, {a2, b2, a2}, {a2, a2, b2}};
+  const double w1 = (155.0 - r) / 1200.0, w2 = (155.0 + r) / 1200.0;
+  const double wts[7] = {9.0 / 40.0, w1, w1, w1, w2, w2, w2};
+  for (int q = 0; q < 7; ++q) {
+    for (int a = 0; a < 3; ++a) L[0][q][a] = pts[q][a];
+    W[0][q] = wts[q];
+  }
+  for (int q = 0; q < 3; ++q) {
+    L[1][q][q] = 1.0;
+    W[1][q] = 1.0 / 3.0;
+  }
+  cudaMemcpyToSymbol(cQL, L, sizeof(L));
+  cudaMemcpyToSymbol(cQW, W, sizeof(W));
+}
+
+namespace {
+
+struct Tri {
+  double area, gx[3], gy[3];
+  int32_t v[3];
+};
+
+__device__ __forceinline__ Tri load_tri(const int32_t* __restrict__ tri, const double* __restrict__ xy, int64_t t) {
+  Tri T;
+  T.v[0] = tri[3 * t];
+  T.v[1] = tri[3 * t + 1];
+  T.v[2] = tri[3 * t + 2];
+  const double x0 = xy[2 * (int64_t)T.v[0]], y0 = xy[2 * (int64_t)T.v[0] + 1];
+  const double x1 = xy[2 * (int64_t)T.v[1]], y1 = xy[2 * (int64_t)T.v[1] + 1];
+  const double x2 = xy[2 * (int64_t)T.v[2]], y2 = xy[2 * (int64_t)T.v[2] + 1];
+  const double twoA = (x1 - x0) * (y2 - y0) - (x2 - x0) * (y1 - y0);
+  const double inv = 1.0 / twoA;
+  T.area = 0.5 * twoA;
+  T.gx[0] = (y1 - y2) * inv;
+  T.gy[0] = (x2 - x1) * inv;
+  T.gx[1] = (y2 - y0) * inv;
+  T.gy[1] = (x0 - x2) * inv;
+  T.gx[2] = (y0 - y1) * inv;
+  T.gy[2] = (x1 - x0) * inv;
+  return T;
+}
+
+// Element residual: consistent mass, exact diffusion, quadrature of the reaction.
+template <int RULE, bool BF>
+__global__ void __launch_bounds__(128) k_residual_elem(int64_t m, const int32_t* __restrict__ tri,
+                                                       const double* __restrict__ xy, const double* __restrict__ U,
+                                                       const double* __restrict__ Un,
+                                                       const double* __restrict__ bfield, Rates r,
+                                                       double* __restrict__ elem, int32_t* err) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= m) return;
+  const Tri T = load_tri(tri, xy, t);
+  double u[3][5], Fe[3][5];
+  double Nbar = 0.0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      u[a][c] = U[5 * (int64_t)T.v[a] + c];
+      Nbar += u[a][c];
+    }
+  Nbar *= (1.0 / 3.0);
+  // consistent mass: (phi_a, phi_b) = |T| (1 + delta_ab) / 12
+  const double m12 = T.area * (1.0 / 12.0);
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    double du[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) du[a] = u[a][c] - Un[5 * (int64_t)T.v[a] + c];
+    const double sdu = du[0] + du[1] + du[2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) Fe[a][c] = m12 * (du[a] + sdu);
+  }
+  // diffusion: dt nubar_c |T| mean_T(N) grad u_c . grad phi_a  (nubar_D = 0)
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const double gux = u[0][c] * T.gx[0] + u[1][c] * T.gx[1] + u[2][c] * T.gx[2];
+    const double guy = u[0][c] * T.gy[0] + u[1][c] * T.gy[1] + u[2][c] * T.gy[2];
+    const double coef = r.dt * r.nu[c] * Nbar * T.area;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) Fe[a][c] += coef * (gux * T.gx[a] + guy * T.gy[a]);
+  }
+  double bv[3] = {1.0, 1.0, 1.0};
+  if (BF) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) bv[a] = bfield[T.v[a]];
+  }
+  constexpr int NQ = RULE == 0 ? 7 : 3;
+  bool bad = false;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    double uq[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c)
+      uq[c] = cQL[RULE][q][0] * u[0][c] + cQL[RULE][q][1] * u[1][c] + cQL[RULE][q][2] * u[2][c];
+    const double bq = BF ? cQL[RULE][q][0] * bv[0] + cQL[RULE][q][1] * bv[1] + cQL[RULE][q][2] * bv[2] : 1.0;
+    const double N = uq[0] + uq[1] + uq[2] + uq[3] + uq[4];
+    bad |= !(N > 0.0);
+    const double kappa = 1.0 - r.A / N;
+    const double lam = (r.bi * uq[2] + r.be * uq[1]) * bq;
+    const double Tr = kappa * uq[0] * lam;  // transmission s -> e
+    double R[5];
+    R[0] = r.alpha * N - Tr - r.mu * uq[0];
+    R[1] = Tr - (r.sigma + r.ge + r.mu) * uq[1];
+    R[2] = r.sigma * uq[1] - (r.gr + r.gd + r.mu) * uq[2];
+    R[3] = r.ge * uq[1] + r.gr * uq[2] - r.mu * uq[3];
+    R[4] = r.gd * uq[2];
+    const double wq = r.dt * T.area * cQW[RULE][q];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double wa = wq * cQL[RULE][q][a];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) Fe[a][c] -= wa * R[c];
+    }
+  }
+  if (bad) atomicOr(err, 1);
+  double* out = elem + 15 * t;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int c = 0; c < 5; ++c) out[5 * a + c] = Fe[a][c];
+}
+
+// Node gather of element vectors (fixed order) plus per-CTA partial ||F||^2.
+__global__ void __launch_bounds__(256) k_residual_gather(int64_t n, const int32_t* __restrict__ inc_ptr,
+                                                         const int32_t* __restrict__ inc,
+                                                         const double* __restrict__ elem, double* __restrict__ F,
+                                                         double* __restrict__ partial) {
+  __shared__ double sh[32];
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double ss = 0.0;
+  if (i < n) {
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (int32_t k = inc_ptr[i]; k < inc_ptr[i + 1]; ++k) {
+      const double* e = elem + 5 * (int64_t)inc[k];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) acc[c] += e[c];
+    }
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      F[5 * i + c] = acc[c];
+      ss += acc[c] * acc[c];
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_down_sync(0xffffffffu, ss, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = ss;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) partial[blockIdx.x] = v;
+  }
+}
+
+// Fixed-order sum of per-CTA partials (one CTA).
+__global__ void k_sum_partials(int64_t np, const double* __restrict__ partial, double* out) {
+  __shared__ double sh[32];
+  double v = 0.0;
+  for (int64_t k = threadIdx.x; k < np; k += blockDim.x) v += partial[k];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double x = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (threadIdx.x == 0) *out = x;
+  }
+}
+
+// symmetric pair index: (0,0) (1,1) (2,2) (0,1) (0,2) (1,2)
+__device__ __forceinline__ int sym(int a, int b) {
+  return a == b ? a : (a + b + 2);
+}
+
+// Jacobian record of a triangle.
+template <int RULE, bool BF>
+__global__ void __launch_bounds__(128) k_jac_record(int64_t m, const int32_t* __restrict__ tri,
+                                                    const double* __restrict__ xy, const double* __restrict__ U,
+                                                    const double* __restrict__ bfield, Rates r,
+                                                    double* __restrict__ rec, int32_t* err) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= m) return;
+  const Tri T = load_tri(tri, xy, t);
+  double u[3][5];
+  double Nbar = 0.0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      u[a][c] = U[5 * (int64_t)T.v[a] + c];
+      Nbar += u[a][c];
+    }
+  Nbar *= (1.0 / 3.0);
+  double* out = rec + (int64_t)REC * t;
+  out[0] = T.area;
+  // N-weighted stiffness |T| mean(N) grad phi_a . grad phi_b
+  const double an = T.area * Nbar;
+  out[REC_K + 0] = an * (T.gx[0] * T.gx[0] + T.gy[0] * T.gy[0]);
+  out[REC_K + 1] = an * (T.gx[1] * T.gx[1] + T.gy[1] * T.gy[1]);
+  out[REC_K + 2] = an * (T.gx[2] * T.gx[2] + T.gy[2] * T.gy[2]);
+  out[REC_K + 3] = an * (T.gx[0] * T.gx[1] + T.gy[0] * T.gy[1]);
+  out[REC_K + 4] = an * (T.gx[0] * T.gx[2] + T.gy[0] * T.gy[2]);
+  out[REC_K + 5] = an * (T.gx[1] * T.gx[2] + T.gy[1] * T.gy[2]);
+  // G_{c,a} = |T|/3 grad u_c . grad phi_a (derivative of mean_T(N) by any u_{b,c'})
+  const double a3 = T.area * (1.0 / 3.0);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const double gux = u[0][c] * T.gx[0] + u[1][c] * T.gx[1] + u[2][c] * T.gx[2];
+    const double guy = u[0][c] * T.gy[0] + u[1][c] * T.gy[1] + u[2][c] * T.gy[2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) out[REC_G + 3 * c + a] = a3 * (gux * T.gx[a] + guy * T.gy[a]);
+  }
+  // reaction moments P^k_ab = |T| sum_q w_q phi_a phi_b rho_k(x_q):
+  //   rho_0 = A s lam / N^2 (d kappa/du_c' = A/N^2 for every c'), rho_1 = kappa lam,
+  //   rho_2 = kappa s beta_E b, rho_3 = kappa s beta_I b.
+  double P[4][6];
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int s = 0; s < 6; ++s) P[k][s] = 0.0;
+  double bv[3] = {1.0, 1.0, 1.0};
+  if (BF) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) bv[a] = bfield[T.v[a]];
+  }
+  constexpr int NQ = RULE == 0 ? 7 : 3;
+  bool bad = false;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    double uq[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c)
+      uq[c] = cQL[RULE][q][0] * u[0][c] + cQL[RULE][q][1] * u[1][c] + cQL[RULE][q][2] * u[2][c];
+    const double bq = BF ? cQL[RULE][q][0] * bv[0] + cQL[RULE][q][1] * bv[1] + cQL[RULE][q][2] * bv[2] : 1.0;
+    const double N = uq[0] + uq[1] + uq[2] + uq[3] + uq[4];
+    bad |= !(N > 0.0);
+    const double invN = 1.0 / N;
+    const double kappa = 1.0 - r.A * invN;
+    const double lam = (r.bi * uq[2] + r.be * uq[1]) * bq;
+    double rho[4];
+    rho[0] = r.A * invN * invN * uq[0] * lam;
+    rho[1] = kappa * lam;
+    rho[2] = kappa * uq[0] * r.be * bq;
+    rho[3] = kappa * uq[0] * r.bi * bq;
+    const double wq = T.area * cQW[RULE][q];
+    const double L0 = cQL[RULE][q][0], L1 = cQL[RULE][q][1], L2 = cQL[RULE][q][2];
+    const double w6[6] = {wq * L0 * L0, wq * L1 * L1, wq * L2 * L2, wq * L0 * L1, wq * L0 * L2, wq * L1 * L2};
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int s = 0; s < 6; ++s) P[k][s] += w6[s] * rho[k];
+  }
+  if (bad) atomicOr(err, 1);
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int s = 0; s < 6; ++s) out[REC_P + 6 * k + s] = P[k][s];
+  out[REC - 1] = 0.0;
+}
+
+// One thread per 5x5 block: fixed-order sums over the triangles sharing the
+// node pair, then the block of dF_i/dU_j:
+//   M delta + dt nubar_c (G_c + K delta) - dt int phi_i phi_j dR_c/du_c'.
+__global__ void __launch_bounds__(128) k_jac_gather(int64_t nnzb, const int32_t* __restrict__ inc_ptr,
+                                                    const int32_t* __restrict__ inc,
+                                                    const double* __restrict__ rec, Rates r,
+                                                    double* __restrict__ val) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= nnzb) return;
+  double M = 0, K = 0, G[4] = {0, 0, 0, 0}, P[4] = {0, 0, 0, 0};
+  for (int32_t q = inc_ptr[k]; q < inc_ptr[k + 1]; ++q) {
+    const int32_t e = inc[q];
+    const int32_t t = e / 9, ab = e - 9 * t;
+    const int a = ab / 3, b = ab - 3 * a;
+    const double* R = rec + (int64_t)REC * t;
+    const int s = sym(a, b);
+    M += R[0] * (a == b ? (2.0 / 12.0) : (1.0 / 12.0));
+    K += R[REC_K + s];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) G[c] += R[REC_G + 3 * c + a];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) P[c] += R[REC_P + 6 * c + s];
+  }
+  const double dt = r.dt;
+  double B[5][5];
+  // rows S, E: transmission derivative row  dT/du_c' = P0 + [S]P1 + [E]P2 + [I]P3
+  const double gS = dt * r.nu[0] * G[0], gE = dt * r.nu[1] * G[1], gI = dt * r.nu[2] * G[2], gR = dt * r.nu[3] * G[3];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    B[0][c] = gS - dt * r.alpha * M + dt * P[0];
+    B[1][c] = gE - dt * P[0];
+    B[2][c] = gI;
+    B[3][c] = gR;
+    B[4][c] = 0.0;
+  }
+  B[0][0] += M + dt * r.nu[0] * K + dt * P[1] + dt * r.mu * M;
+  B[0][1] += dt * P[2];
+  B[0][2] += dt * P[3];
+  B[1][0] -= dt * P[1];
+  B[1][1] += M + dt * r.nu[1] * K - dt * P[2] + dt * (r.sigma + r.ge + r.mu) * M;
+  B[1][2] -= dt * P[3];
+  B[2][1] -= dt * r.sigma * M;
+  B[2][2] += M + dt * r.nu[2] * K + dt * (r.gr + r.gd + r.mu) * M;
+  B[3][1] -= dt * r.ge * M;
+  B[3][2] -= dt * r.gr * M;
+  B[3][3] += M + dt * r.nu[3] * K + dt * r.mu * M;
+  B[4][2] -= dt * r.gd * M;
+  B[4][4] += M;
+  double* out = val + 25 * k;
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int c = 0; c < 5; ++c) out[5 * i + c] = B[i][c];
+}
+
+}  // namespace
+
+void launch_residual(int64_t n, int64_t m, const int32_t* tri, const double* xy, const double* U, const double* Un,
+                     const double* bfield, const Rates& r, int rule, double* elem, const int32_t* inc_ptr,
+                     const int32_t* inc, double* F, double* partial, int grid_red, double* out_norm2, int32_t* err,
+                     cudaStream_t s) {
+  (void)grid_red;
+  const int tb = 128;
+  const int64_t g = (m + tb - 1) / tb;
+  if (rule == 0) {
+    if (bfield) k_residual_elem<0, true><<<g, tb, 0, s>>>(m, tri, xy, U, Un, bfield, r, elem, err);
+    else k_residual_elem<0, false><<<g, tb, 0, s>>>(m, tri, xy, U, Un, bfield, r, elem, err);
+  } else {
+    if (bfield) k_residual_elem<1, true><<<g, tb, 0, s>>>(m, tri, xy, U, Un, bfield, r, elem, err);
+    else k_residual_elem<1, false><<<g, tb, 0, s>>>(m, tri, xy, U, Un, bfield, r, elem, err);
+  }
+  count_launch();
+  const int64_t g2 = (n + 255) / 256;
+  k_residual_gather<<<g2, 256, 0, s>>>(n, inc_ptr, inc, elem, F, partial);
+  count_launch();
+  k_sum_partials<<<1, 1024, 0, s>>>(g2, partial, out_norm2);
+  count_launch();
+}
+
+void launch_jacobian(int64_t nnzb, int64_t m, const int32_t* tri, const double* xy, const double* U,
+                     const double* bfield, const Rates& r, int rule, double* rec, const int32_t* inc_ptr,
+                     const int32_t* inc, double* val, int32_t* err, cudaStream_t s) {
+  const int tb = 128;
+  const int64_t g = (m + tb - 1) / tb;
+  if (rule == 0) {
+    if (bfield) k_jac_record<0, true><<<g, tb, 0, s>>>(m, tri, xy, U, bfield, r, rec, err);
+    else k_jac_record<0, false><<<g, tb, 0, s>>>(m, tri, xy, U, bfield, r, rec, err);
+  } else {
+    if (bfield) k_jac_record<1, true><<<g, tb, 0, s>>>(m, tri, xy, U, bfield, r, rec, err);
+    else k_jac_record<1, false><<<g, tb, 0, s>>>(m, tri, xy, U, bfield, r, rec, err);
+  }
+  count_launch();
+  const int64_t g2 = (nnzb + tb - 1) / tb;
+  k_jac_gather<<<g2, tb, 0, s>>>(nnzb, inc_ptr, inc, rec, r, val);
+  count_launch();
+}
+
+}  // namespace seird

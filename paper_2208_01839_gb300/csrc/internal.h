@@ -1,0 +1,163 @@
+// Internal declarations of the SEIRD library: the context, the host-side setup
+// products and the kernel launchers.  Everything here sits behind include/seird.h.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/seird.h"
+
+namespace seird {
+
+// Device error flags (bitmask written by kernels, read by the host after a phase).
+enum : int {
+  ERR_NONPOS_N = 1,    // N <= 0 at a quadrature point (1/N undefined)
+  ERR_SINGULAR = 2,    // a 5x5 pivot block is singular
+  ERR_NONFINITE = 4,   // a non-finite value in a reduction
+  ERR_TIMEOUT = 8,     // a bounded wait gave up
+};
+
+constexpr int MAX_RESTART = 64;
+
+// Host-side products of the setup phase (all indices in the internal numbering,
+// where nodes are sorted by (subdomain, caller index)).
+struct HostSetup {
+  int64_t n = 0, m = 0;
+  int32_t P = 0;
+  std::vector<int32_t> perm;     // internal -> caller
+  std::vector<int32_t> iperm;    // caller -> internal
+  std::vector<int32_t> owner;    // internal node -> subdomain
+  std::vector<int32_t> own_ptr;  // [P+1] owned nodes of p are [own_ptr[p], own_ptr[p+1])
+  std::vector<double> xy;        // [n][2] internal order
+  std::vector<int32_t> tri;      // [m][3] internal node ids (triangles sorted by min node)
+  // global 5x5 BSR pattern
+  std::vector<int32_t> row_ptr, col;  // [n+1], [nnzb]
+  // residual gather: per node, list of (t*3 + a)
+  std::vector<int32_t> node_inc_ptr, node_inc;
+  // Jacobian gather: per block, list of (t*9 + a*3 + b)
+  std::vector<int32_t> blk_inc_ptr, blk_inc;
+  // subdomains (concatenated): local rows of subdomain p are [sd_row0[p], sd_row0[p+1])
+  std::vector<int32_t> sd_row0;     // [P+1]
+  std::vector<int32_t> sd_node;     // [NL] internal node of each local row
+  std::vector<int64_t> l_row_ptr;   // [NL+1] absolute block offsets
+  std::vector<int32_t> l_col;       // [NLB] local column (row index within the subdomain)
+  std::vector<int32_t> l_gblk;      // [NLB] global J block of each local block
+  std::vector<int64_t> l_diag;      // [NL] absolute index of the diagonal block
+  std::vector<int64_t> upd_ptr;     // [NLB+1] ILU(0) update pairs of each lower block
+  std::vector<int64_t> upd;         // [2*nupd] (destination block, source block) pairs
+  std::vector<int32_t> fwd_order;   // [NL] local rows (relative) grouped by forward level
+  std::vector<int32_t> fwd_lev;     // level boundaries (relative to the subdomain's rows)
+  std::vector<int32_t> sd_fwd_lev0; // [P+1] offsets into fwd_lev (each subdomain has nlev+1 entries)
+  std::vector<int32_t> bwd_order, bwd_lev, sd_bwd_lev0;
+  int32_t max_levels = 0;
+  int32_t max_sd_rows = 0;
+  // coarse space: subdomain p sits at block row cpos[p] of the banded coarse matrix
+  std::vector<int32_t> cpos;        // [P]
+  int32_t cband = 0;                // half bandwidth in blocks
+  std::vector<int32_t> cseg_blk;    // [nnzb] J block ids ordered by (cpos p, cpos q) then id
+  std::vector<int32_t> cchunk_ptr;  // [nchunk+1] chunks of cseg_blk summed by one warp
+  std::vector<int32_t> cdst_ptr;    // [ndst+1] chunk range of each coarse block
+  std::vector<int64_t> cdst_idx;    // [ndst] block index in the band storage
+};
+
+int build_setup(const seird_mesh* mesh, const seird_options* opt, HostSetup& hs, std::string& err);
+
+template <class T>
+struct DevArray {
+  T* p = nullptr;
+  size_t n = 0;
+};
+
+struct Workspace;
+
+}  // namespace seird
+
+struct seird_ctx {
+  seird::HostSetup hs;
+  seird_params params{};
+  seird_options opt{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  double t = 0.0;
+  std::string last_error;
+  int64_t device_bytes = 0;
+  std::vector<void*> allocations;
+  // device mesh and patterns
+  double* xy = nullptr;
+  int32_t* tri = nullptr;
+  double* bfield = nullptr;
+  int32_t* perm = nullptr;
+  int32_t* row_ptr = nullptr;
+  int32_t* col = nullptr;
+  double* val = nullptr;
+  float* val32 = nullptr;
+  int32_t* node_inc_ptr = nullptr;
+  int32_t* node_inc = nullptr;
+  int32_t* blk_inc_ptr = nullptr;
+  int32_t* blk_inc = nullptr;
+  double* elem = nullptr;   // [m][15] residual element vectors
+  double* rec = nullptr;    // [m][REC] Jacobian records
+  // state and Newton vectors [n][5]
+  double* U = nullptr;
+  double* Un = nullptr;
+  double* F = nullptr;
+  double* Ft = nullptr;
+  double* dU = nullptr;
+  double* Ut = nullptr;
+  double* stage = nullptr;  // staging for caller-numbered input/output
+  double* stage2 = nullptr;
+  // Krylov
+  double* V = nullptr;      // [restart+1][5n]
+  double* Z = nullptr;      // [restart][5n]
+  double* w = nullptr;      // [5n]
+  double* partial = nullptr;  // [grid][MAX_RESTART+1]
+  double* hcol = nullptr;   // [MAX_RESTART+1] reduced dot products
+  double* gm = nullptr;     // GMRES small state: H, cs, sn, g, y
+  double* scal = nullptr;   // scalar outputs (norms)
+  double* h_scal = nullptr; // pinned host mirror
+  int32_t* err = nullptr;   // device error flags
+  int32_t* h_err = nullptr; // pinned
+  int red_grid = 0;
+  // RAS
+  int32_t* sd_row0 = nullptr;
+  int32_t* sd_node = nullptr;
+  int64_t* l_row_ptr = nullptr;
+  int32_t* l_col = nullptr;
+  int32_t* l_gblk = nullptr;
+  int64_t* l_diag = nullptr;
+  int64_t* upd_ptr = nullptr;
+  int64_t* upd = nullptr;
+  int32_t* fwd_order = nullptr;
+  int32_t* fwd_lev = nullptr;
+  int32_t* sd_fwd_lev0 = nullptr;
+  int32_t* bwd_order = nullptr;
+  int32_t* bwd_lev = nullptr;
+  int32_t* sd_bwd_lev0 = nullptr;
+  int32_t* own_ptr = nullptr;
+  int32_t* owner = nullptr;
+  double* fval = nullptr;   // [NLB][25] factor blocks
+  float* fval32 = nullptr;
+  double* dinv = nullptr;   // [NL][25] inverted U diagonal blocks
+  float* dinv32 = nullptr;
+  double* ywork = nullptr;  // [NL][5]
+  double* zwork = nullptr;  // [NL][5]
+  // coarse
+  int32_t* cpos = nullptr;
+  int32_t* cseg_blk = nullptr;
+  int32_t* cchunk_ptr = nullptr;
+  int32_t* cdst_ptr = nullptr;
+  int64_t* cdst_idx = nullptr;
+  double* cpart = nullptr;  // [nchunk][25]
+  double* cband = nullptr;  // [P][2*cband+1][25] banded coarse matrix / factors
+  double* cdinv = nullptr;  // [P][25]
+  double* crhs = nullptr;   // [5P]
+  bool pc_ready = false;
+  bool jac_ready = false;
+  // kernel-class timing (options.timing): (class, start event, end event) per launch group
+  std::vector<cudaEvent_t> evpool;
+  size_t ev_used = 0;
+  std::vector<int> ev_class;
+};

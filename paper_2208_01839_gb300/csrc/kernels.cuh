@@ -1,0 +1,110 @@
+// Device-side shared declarations: rate parameters, launch accounting, small
+// reductions.  Included by the .cu files of the library only.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace seird {
+
+// Rates of Eq. seird1-5 plus dt, packed for kernel arguments.
+struct Rates {
+  double A, bi, be, sigma, ge, gr, gd, alpha, mu;
+  double nu[4];
+  double dt;
+};
+
+// Jacobian record of one triangle (doubles): area, N-weighted stiffness (6),
+// G_{c,a} = |T|/3 grad u_c . grad phi_a (12), reaction moments P^k_ab (24), pad.
+constexpr int REC = 44;
+constexpr int REC_K = 1, REC_G = 7, REC_P = 19;
+
+void count_launch();
+int64_t launch_total();
+
+// quadrature tables are uploaded once per process (degree-5 and vertex rules)
+void upload_quadrature();
+
+// ---- launchers (defined in the .cu files) ----
+void launch_residual(int64_t n, int64_t m, const int32_t* tri, const double* xy, const double* U, const double* Un,
+                     const double* bfield, const Rates& r, int rule, double* elem, const int32_t* inc_ptr,
+                     const int32_t* inc, double* F, double* partial, int grid_red, double* out_norm2, int32_t* err,
+                     cudaStream_t s);
+void launch_jacobian(int64_t nnzb, int64_t m, const int32_t* tri, const double* xy, const double* U,
+                     const double* bfield, const Rates& r, int rule, double* rec, const int32_t* inc_ptr,
+                     const int32_t* inc, double* val, int32_t* err, cudaStream_t s);
+template <class VT>
+void launch_spmv(int64_t nrow, const int32_t* rp, const int32_t* col, const VT* val, const double* x, double* y,
+                 cudaStream_t s);
+void launch_f64_to_f32(int64_t n, const double* src, float* dst, cudaStream_t s);
+
+// vectors (length len, grid-stride)
+void launch_norm2(int64_t len, const double* x, double* partial, int grid, double* out, cudaStream_t s);
+void launch_mdot(int64_t len, int nv, const double* V, int64_t ld, const double* w, double* partial, int grid,
+                 double* out, cudaStream_t s);
+void launch_update_mdot(int64_t len, int nv, const double* V, int64_t ld, const double* h, double* w,
+                        double* partial, int grid, double* out_add, cudaStream_t s);
+void launch_update_norm(int64_t len, int nv, const double* V, int64_t ld, const double* h, double* w,
+                        double* partial, int grid, double* out, cudaStream_t s);
+void launch_scale(int64_t len, const double* x, const double* alpha_ptr, int invert, double* y, cudaStream_t s);
+void launch_axpby(int64_t len, double a, const double* x, double b, const double* y, double* out, cudaStream_t s);
+void launch_multi_axpy(int64_t len, int nv, const double* Zs, int64_t ld, const double* coef, double* x,
+                       cudaStream_t s);
+void launch_givens(int j, double* gm, const double* h1, const double* h2, const double* hnext, int ldh,
+                   double* out_res, cudaStream_t s);
+void launch_reduce_cols(int grid, int nv, const double* partial, double* out, int add, cudaStream_t s);
+void cgs_init();
+constexpr int NV_STRIDE = 65;  // row stride of the CGS partial-sum buffer
+void launch_hsolve(int k, double* gm, int ldh, cudaStream_t s);
+void launch_gather5(int64_t n, const int32_t* idx, const double* src, double* dst, cudaStream_t s);
+void launch_scatter5(int64_t n, const int32_t* idx, const double* src, double* dst, cudaStream_t s);
+void launch_check_finite(int64_t len, const double* x, int32_t* err, cudaStream_t s);
+
+// RAS and coarse space
+struct RasDev {
+  int32_t P;
+  const int32_t* sd_row0;
+  const int32_t* sd_node;
+  const int64_t* l_row_ptr;
+  const int32_t* l_col;
+  const int32_t* l_gblk;
+  const int64_t* l_diag;
+  const int64_t* upd_ptr;
+  const int64_t* upd;
+  const int32_t* fwd_order;
+  const int32_t* fwd_lev;
+  const int32_t* sd_fwd_lev0;
+  const int32_t* bwd_order;
+  const int32_t* bwd_lev;
+  const int32_t* sd_bwd_lev0;
+  const int32_t* own_ptr;
+  double* fval;
+  double* dinv;
+  double* ywork;
+  double* zwork;
+};
+void launch_ilu_factor(const RasDev& d, const double* val, int32_t* err, cudaStream_t s);
+void launch_ilu_solve(const RasDev& d, const double* r, double* z, cudaStream_t s);
+
+struct CoarseDev {
+  int32_t P, band;
+  const int32_t* cpos;
+  const int32_t* owner;
+  const int32_t* own_ptr;
+  const int32_t* cseg_blk;
+  const int32_t* cchunk_ptr;
+  int32_t nchunk;
+  const int32_t* cdst_ptr;
+  const int64_t* cdst_idx;
+  int32_t ndst;
+  double* cpart;
+  double* cband;
+  double* cdinv;
+  double* crhs;
+};
+void launch_coarse_assemble(const CoarseDev& c, const double* val, cudaStream_t s);
+void launch_coarse_factor(const CoarseDev& c, int32_t* err, cudaStream_t s);
+void launch_coarse_apply_add(const CoarseDev& c, int64_t n, const double* r, double* z, cudaStream_t s);
+
+}  // namespace seird

@@ -1,0 +1,381 @@
+// BSR SpMV and the vector kernels of restarted right-preconditioned (F)GMRES
+// with CGS2 orthogonalisation (Section 3.2: GMRES with right preconditioning;
+// FGMRES when the preconditioner varies).  FP64 accumulation throughout;
+// reductions are two-stage (per-CTA partials, then one CTA in fixed order), so
+// every result is bitwise reproducible run to run.
+#include <cmath>
+
+#include "kernels.cuh"
+
+namespace seird {
+
+namespace {
+
+constexpr int NVMAX = 65;  // restart <= 64 -> at most 65 basis vectors
+
+__device__ __forceinline__ double ld_val(const double* p) { return __ldg(p); }
+__device__ __forceinline__ double ld_val(const float* p) { return (double)__ldg(p); }
+
+// y = A x, 5x5 blocks.  One thread per scalar output row (block row i, row r):
+// all 32 lanes of every warp do useful FP64 work, 25 FMA per block per 5 threads.
+template <class VT>
+__global__ void __launch_bounds__(256) k_bsr_spmv(int64_t nrow, const int32_t* __restrict__ rp,
+                                                  const int32_t* __restrict__ col, const VT* __restrict__ val,
+                                                  const double* __restrict__ x, double* __restrict__ y) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= 5 * nrow) return;
+  const int64_t i = g / 5;
+  const int r = (int)(g - 5 * i);
+  const int32_t k0 = __ldg(rp + i), k1 = __ldg(rp + i + 1);
+  double acc = 0.0;
+  for (int32_t k = k0; k < k1; ++k) {
+    const int64_t j = __ldg(col + k);
+    const VT* v = val + 25 * (int64_t)k + 5 * r;
+    const double* xj = x + 5 * j;
+    acc = fma(ld_val(v + 0), __ldg(xj + 0), acc);
+    acc = fma(ld_val(v + 1), __ldg(xj + 1), acc);
+    acc = fma(ld_val(v + 2), __ldg(xj + 2), acc);
+    acc = fma(ld_val(v + 3), __ldg(xj + 3), acc);
+    acc = fma(ld_val(v + 4), __ldg(xj + 4), acc);
+  }
+  y[g] = acc;
+}
+
+__global__ void k_f64_to_f32(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x < 32) {
+    r = threadIdx.x < NT / 32 ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+  }
+  __syncthreads();
+  return r;  // valid in thread 0
+}
+
+// partial[cta] = sum over the CTA's slice of x^2
+__global__ void __launch_bounds__(256) k_norm2_partial(int64_t len, const double* __restrict__ x,
+                                                       double* __restrict__ partial) {
+  __shared__ double sh[8];
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = x[i];
+    s += v * v;
+  }
+  s = block_sum<256>(s, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// out[k] (+)= sum_cta partial[cta * stride + k], k < nv; fixed order
+__global__ void k_reduce_cols(int grid, int nv, int stride, const double* __restrict__ partial, double* out,
+                              int add) {
+  __shared__ double sh[8];
+  for (int k = 0; k < nv; ++k) {
+    double s = 0.0;
+    for (int c = threadIdx.x; c < grid; c += blockDim.x) s += partial[(int64_t)c * stride + k];
+    s = block_sum<256>(s, sh);
+    if (threadIdx.x == 0) out[k] = add ? out[k] + s : s;
+  }
+}
+
+// CGS2 kernels.  A CTA of 256 threads walks tiles of TILE consecutive entries
+// (grid-stride over tiles); for each tile the nv basis vectors are staged in
+// shared memory once, so every basis vector is read from HBM exactly once per
+// kernel.  Warp wp owns the dot products k = wp, wp+8, ... and keeps their
+// lane partials in registers until the end.
+constexpr int TILE = 256;
+constexpr int KPW = (NVMAX + 7) / 8;  // dot products per warp
+
+// mode 0: partial[cta][k] = sum V_k . w
+// mode 1: w -= V h, then partial[cta][k] = sum V_k . w_new
+// mode 2: w -= V h, then partial[cta][0] = sum w_new^2
+template <int MODE>
+__global__ void __launch_bounds__(256) k_cgs(int64_t len, int nv, const double* __restrict__ V, int64_t ld,
+                                             const double* __restrict__ h, double* __restrict__ w,
+                                             double* __restrict__ partial) {
+  extern __shared__ double smem[];
+  double* wt = smem;            // [TILE]
+  double* hs = smem + TILE;     // [NVMAX]
+  double* Vt = hs + NVMAX + 7;  // [nv][TILE]
+  const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+  if (MODE != 0)
+    for (int k = tid; k < nv; k += blockDim.x) hs[k] = h[k];
+  double acc[KPW];
+#pragma unroll
+  for (int q = 0; q < KPW; ++q) acc[q] = 0.0;
+  double nrm = 0.0;
+  const int64_t ntile = (len + TILE - 1) / TILE;
+  for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+    const int64_t base = tile * TILE;
+    const int64_t i = base + tid;
+    const bool in = i < len;
+    __syncthreads();  // previous tile fully consumed
+    for (int k = 0; k < nv; ++k) Vt[k * TILE + tid] = in ? V[k * ld + i] : 0.0;
+    double wi = in ? w[i] : 0.0;
+    if (MODE != 0) {
+      for (int k = 0; k < nv; ++k) wi = fma(-hs[k], Vt[k * TILE + tid], wi);
+      if (in) w[i] = wi;
+    }
+    if (MODE == 2) {
+      nrm = fma(wi, wi, nrm);
+    } else {
+      wt[tid] = wi;
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < KPW; ++q) {
+        const int k = wp + 8 * q;
+        if (k < nv) {
+          double s = acc[q];
+#pragma unroll
+          for (int e = lane; e < TILE; e += 32) s = fma(Vt[k * TILE + e], wt[e], s);
+          acc[q] = s;
+        }
+      }
+    }
+  }
+  if (MODE == 2) {
+    __shared__ double sh[8];
+    const double s = block_sum<256>(nrm, sh);
+    if (tid == 0) partial[blockIdx.x * (int64_t)NVMAX] = s;
+  } else {
+#pragma unroll
+    for (int q = 0; q < KPW; ++q) {
+      const int k = wp + 8 * q;
+      double s = acc[q];
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+      if (lane == 0 && k < nv) partial[blockIdx.x * (int64_t)NVMAX + k] = s;
+    }
+  }
+}
+
+inline size_t cgs_smem(int nv) { return sizeof(double) * (TILE + NVMAX + 7 + (size_t)nv * TILE); }
+
+// y = x * a (invert: a := 1/a), a read from device memory; a == 0 gives y = 0
+__global__ void k_scale(int64_t len, const double* __restrict__ x, const double* __restrict__ ap, int invert,
+                        double* __restrict__ y) {
+  double a = *ap;
+  if (invert) a = a != 0.0 ? 1.0 / a : 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = a * x[i];
+}
+
+__global__ void k_axpby(int64_t len, double a, const double* __restrict__ x, double b, const double* __restrict__ y,
+                        double* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = a * x[i] + b * y[i];
+}
+
+// x += sum_k coef[k] Z_k
+__global__ void k_multi_axpy(int64_t len, int nv, const double* __restrict__ Z, int64_t ld,
+                             const double* __restrict__ coef, double* __restrict__ x) {
+  __shared__ double cs[NVMAX];
+  for (int k = threadIdx.x; k < nv; k += blockDim.x) cs[k] = coef[k];
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
+    double v = x[i];
+    for (int k = 0; k < nv; ++k) v = fma(cs[k], Z[k * ld + i], v);
+    x[i] = v;
+  }
+}
+
+// GMRES small state layout in gm (ldh = restart+1):
+//   H[ldh*restart] column-major (H[row + ldh*col]), cs[restart], sn[restart], g[ldh], y[restart]
+// Column j of H gets hcol[0..j] and hnext; previous rotations are applied, a new
+// rotation annihilates H[j+1, j]; |g[j+1]| (the residual norm) goes to *out_res.
+__global__ void k_givens(int j, double* gm, const double* __restrict__ h1, const double* __restrict__ h2,
+                         const double* __restrict__ hnext_sq, int ldh, double* out_res) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int restart = ldh - 1;
+  double* H = gm;
+  double* cs = H + (int64_t)ldh * restart;
+  double* sn = cs + restart;
+  double* g = sn + restart;
+  double col[NVMAX];
+  for (int k = 0; k <= j; ++k) col[k] = h1[k] + h2[k];  // CGS2: both passes' coefficients
+  const double hn = sqrt(fmax(*hnext_sq, 0.0));
+  col[j + 1] = hn;
+  for (int k = 0; k < j; ++k) {
+    const double a = col[k], b = col[k + 1];
+    col[k] = cs[k] * a + sn[k] * b;
+    col[k + 1] = -sn[k] * a + cs[k] * b;
+  }
+  const double a = col[j], b = col[j + 1];
+  const double rr = hypot(a, b);
+  double c = 1.0, s = 0.0;
+  if (rr != 0.0) {
+    c = a / rr;
+    s = b / rr;
+  }
+  cs[j] = c;
+  sn[j] = s;
+  col[j] = rr;
+  col[j + 1] = 0.0;
+  for (int k = 0; k <= j + 1; ++k) H[k + (int64_t)ldh * j] = col[k];
+  const double gj = g[j];
+  g[j] = c * gj;
+  g[j + 1] = -s * gj;
+  out_res[0] = fabs(g[j + 1]);
+  out_res[1] = hn;
+}
+
+// y = H(0:k,0:k)^{-1} g(0:k) by back substitution (one thread)
+__global__ void k_hsolve(int k, double* gm, int ldh) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int restart = ldh - 1;
+  double* H = gm;
+  double* g = H + (int64_t)ldh * restart + 2 * restart;
+  double* y = g + ldh;
+  for (int i = k - 1; i >= 0; --i) {
+    double v = g[i];
+    for (int c = i + 1; c < k; ++c) v -= H[i + (int64_t)ldh * c] * y[c];
+    const double d = H[i + (int64_t)ldh * i];
+    y[i] = d != 0.0 ? v / d : 0.0;
+  }
+}
+
+__global__ void k_gather5(int64_t n, const int32_t* __restrict__ idx, const double* __restrict__ src,
+                          double* __restrict__ dst) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < 5 * n; g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = g / 5;
+    dst[g] = src[5 * (int64_t)idx[k] + (g - 5 * k)];
+  }
+}
+
+__global__ void k_scatter5(int64_t n, const int32_t* __restrict__ idx, const double* __restrict__ src,
+                           double* __restrict__ dst) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < 5 * n; g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = g / 5;
+    dst[5 * (int64_t)idx[k] + (g - 5 * k)] = src[g];
+  }
+}
+
+__global__ void k_check_finite(int64_t len, const double* __restrict__ x, int32_t* err) {
+  bool bad = false;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
+    bad |= !isfinite(x[i]);
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, 4);
+}
+
+inline int grid_for(int64_t len, int tb = 256, int cap = 152 * 8) {
+  int64_t g = (len + tb - 1) / tb;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace
+
+template <class VT>
+void launch_spmv(int64_t nrow, const int32_t* rp, const int32_t* col, const VT* val, const double* x, double* y,
+                 cudaStream_t s) {
+  if (nrow <= 0) return;
+  const int tb = 256;
+  const int64_t g = (5 * nrow + tb - 1) / tb;
+  k_bsr_spmv<VT><<<g, tb, 0, s>>>(nrow, rp, col, val, x, y);
+  count_launch();
+}
+template void launch_spmv<double>(int64_t, const int32_t*, const int32_t*, const double*, const double*, double*,
+                                  cudaStream_t);
+template void launch_spmv<float>(int64_t, const int32_t*, const int32_t*, const float*, const double*, double*,
+                                 cudaStream_t);
+
+void launch_f64_to_f32(int64_t n, const double* src, float* dst, cudaStream_t s) {
+  k_f64_to_f32<<<grid_for(n), 256, 0, s>>>(n, src, dst);
+  count_launch();
+}
+
+void launch_norm2(int64_t len, const double* x, double* partial, int grid, double* out, cudaStream_t s) {
+  k_norm2_partial<<<grid, 256, 0, s>>>(len, x, partial);
+  k_reduce_cols<<<1, 256, 0, s>>>(grid, 1, 1, partial, out, 0);
+  count_launch();
+  count_launch();
+}
+
+void launch_mdot(int64_t len, int nv, const double* V, int64_t ld, const double* w, double* partial, int grid,
+                 double* out, cudaStream_t s) {
+  k_cgs<0><<<grid, 256, cgs_smem(nv), s>>>(len, nv, V, ld, nullptr, const_cast<double*>(w), partial);
+  k_reduce_cols<<<1, 256, 0, s>>>(grid, nv, NVMAX, partial, out, 0);
+  count_launch();
+  count_launch();
+}
+
+// first CGS pass update fused with the second pass's dot products; the dots
+// are added to out_add (which holds the first-pass coefficients h)
+void launch_update_mdot(int64_t len, int nv, const double* V, int64_t ld, const double* h, double* w,
+                        double* partial, int grid, double* out_add, cudaStream_t s) {
+  k_cgs<1><<<grid, 256, cgs_smem(nv), s>>>(len, nv, V, ld, h, w, partial);
+  count_launch();
+  (void)out_add;
+}
+
+void launch_update_norm(int64_t len, int nv, const double* V, int64_t ld, const double* h, double* w,
+                        double* partial, int grid, double* out, cudaStream_t s) {
+  k_cgs<2><<<grid, 256, cgs_smem(nv), s>>>(len, nv, V, ld, h, w, partial);
+  k_reduce_cols<<<1, 256, 0, s>>>(grid, 1, NVMAX, partial, out, 0);
+  count_launch();
+  count_launch();
+}
+
+void cgs_init() {
+  const int mx = (int)cgs_smem(NVMAX);
+  cudaFuncSetAttribute(k_cgs<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_cgs<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_cgs<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+}
+
+void launch_reduce_cols(int grid, int nv, const double* partial, double* out, int add, cudaStream_t s) {
+  k_reduce_cols<<<1, 256, 0, s>>>(grid, nv, NVMAX, partial, out, add);
+  count_launch();
+}
+
+void launch_scale(int64_t len, const double* x, const double* alpha_ptr, int invert, double* y, cudaStream_t s) {
+  k_scale<<<grid_for(len), 256, 0, s>>>(len, x, alpha_ptr, invert, y);
+  count_launch();
+}
+
+void launch_axpby(int64_t len, double a, const double* x, double b, const double* y, double* out, cudaStream_t s) {
+  k_axpby<<<grid_for(len), 256, 0, s>>>(len, a, x, b, y, out);
+  count_launch();
+}
+
+void launch_multi_axpy(int64_t len, int nv, const double* Zs, int64_t ld, const double* coef, double* x,
+                       cudaStream_t s) {
+  k_multi_axpy<<<grid_for(len), 256, 0, s>>>(len, nv, Zs, ld, coef, x);
+  count_launch();
+}
+
+void launch_givens(int j, double* gm, const double* h1, const double* h2, const double* hnext, int ldh,
+                   double* out_res, cudaStream_t s) {
+  k_givens<<<1, 32, 0, s>>>(j, gm, h1, h2, hnext, ldh, out_res);
+  count_launch();
+}
+
+void launch_hsolve(int k, double* gm, int ldh, cudaStream_t s) {
+  k_hsolve<<<1, 32, 0, s>>>(k, gm, ldh);
+  count_launch();
+}
+
+void launch_gather5(int64_t n, const int32_t* idx, const double* src, double* dst, cudaStream_t s) {
+  k_gather5<<<grid_for(5 * n), 256, 0, s>>>(n, idx, src, dst);
+  count_launch();
+}
+
+void launch_scatter5(int64_t n, const int32_t* idx, const double* src, double* dst, cudaStream_t s) {
+  k_scatter5<<<grid_for(5 * n), 256, 0, s>>>(n, idx, src, dst);
+  count_launch();
+}
+
+void launch_check_finite(int64_t len, const double* x, int32_t* err, cudaStream_t s) {
+  k_check_finite<<<grid_for(len), 256, 0, s>>>(len, x, err);
+  count_launch();
+}
+
+}  // namespace seird

@@ -1,0 +1,803 @@
+// C ABI of the SEIRD Newton-Krylov-Schwarz step (include/seird.h) and the
+// host-side drivers: context set-up, Newton with backtracking (Section 2.2),
+// right-preconditioned restarted FGMRES with CGS2 (Section 3.2), and the
+// RAS + coarse preconditioner (Eq. RAS, Section 3.1).  Every arithmetic step
+// of the path runs in the library's CUDA kernels; the host only sequences
+// launches and reads back scalars (norms, the GMRES residual estimate).
+#include <algorithm>
+#include <atomic>
+#include <cstdio>
+#include <cstdlib>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "kernels.cuh"
+
+namespace seird {
+
+static std::atomic<int64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+int64_t launch_total() { return g_launches.load(std::memory_order_relaxed); }
+void coarse_init();
+
+}  // namespace seird
+
+using namespace seird;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+int fail(seird_ctx* ctx, int code, const std::string& msg) {
+  if (ctx) ctx->last_error = msg;
+  else g_create_error = msg;
+  return code;
+}
+
+#define CK(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(ctx, SEIRD_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define TRY(expr)          \
+  do {                     \
+    int rc_ = (expr);      \
+    if (rc_ != SEIRD_OK) { \
+      return rc_;          \
+    }                      \
+  } while (0)
+
+template <class T>
+int dalloc(seird_ctx* ctx, T** p, size_t count) {
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, sizeof(T) * count);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail(ctx, SEIRD_ENOMEM, "cudaMalloc of " + std::to_string(sizeof(T) * count) + " bytes: " +
+                                       cudaGetErrorString(e));
+  }
+  ctx->allocations.push_back((void*)*p);
+  ctx->device_bytes += (int64_t)(sizeof(T) * count);
+  return SEIRD_OK;
+}
+
+template <class T>
+int upload(seird_ctx* ctx, T** p, const std::vector<T>& v) {
+  TRY(dalloc(ctx, p, v.size()));
+  if (!v.empty()) CK(cudaMemcpy(*p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+  return SEIRD_OK;
+}
+
+Rates make_rates(const seird_ctx* ctx) {
+  Rates r;
+  const seird_params& p = ctx->params;
+  r.A = p.A;
+  r.bi = p.beta_i;
+  r.be = p.beta_e;
+  r.sigma = p.sigma;
+  r.ge = p.gamma_e;
+  r.gr = p.gamma_r;
+  r.gd = p.gamma_d;
+  r.alpha = p.alpha;
+  r.mu = p.mu;
+  for (int c = 0; c < 4; ++c) r.nu[c] = p.nu[c];
+  r.dt = ctx->opt.dt;
+  return r;
+}
+
+int64_t vlen(const seird_ctx* ctx) { return 5 * ctx->hs.n; }
+
+int check_flags(seird_ctx* ctx, const char* where) {
+  CK(cudaMemcpyAsync(ctx->h_err, ctx->err, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  const int32_t f = *ctx->h_err;
+  if (!f) return SEIRD_OK;
+  CK(cudaMemsetAsync(ctx->err, 0, sizeof(int32_t), ctx->stream));
+  *ctx->h_err = 0;
+  if (f & ERR_NONPOS_N) return fail(ctx, SEIRD_ENONFINITE, std::string(where) + ": N <= 0 at a quadrature point");
+  if (f & ERR_SINGULAR) return fail(ctx, SEIRD_ESINGULAR, std::string(where) + ": singular 5x5 pivot block");
+  if (f & ERR_TIMEOUT) return fail(ctx, SEIRD_ETIMEOUT, std::string(where) + ": bounded wait expired");
+  return fail(ctx, SEIRD_ENONFINITE, std::string(where) + ": non-finite value");
+}
+
+// ---- kernel-class timing ----------------------------------------------------
+
+// Records a start event on construction and an end event on destruction, on the
+// context's stream, when options.timing is set.
+struct KTimer {
+  seird_ctx* c;
+  size_t slot = (size_t)-1;
+  KTimer(seird_ctx* ctx, int cls) : c(ctx) {
+    if (!c->opt.timing) return;
+    if (c->ev_used + 2 > c->evpool.size()) {
+      for (int k = 0; k < 64; ++k) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return;
+        c->evpool.push_back(e);
+      }
+    }
+    slot = c->ev_used;
+    c->ev_used += 2;
+    c->ev_class.push_back(cls);
+    cudaEventRecord(c->evpool[slot], c->stream);
+  }
+  ~KTimer() {
+    if (slot != (size_t)-1) cudaEventRecord(c->evpool[slot + 1], c->stream);
+  }
+};
+
+void timing_reset(seird_ctx* ctx) {
+  ctx->ev_used = 0;
+  ctx->ev_class.clear();
+}
+
+void timing_collect(seird_ctx* ctx, seird_stats* S) {
+  for (int k = 0; k < SEIRD_K_COUNT; ++k) {
+    S->kernel_ms[k] = 0.0;
+    S->kernel_calls[k] = 0;
+  }
+  if (!ctx->opt.timing) return;
+  cudaStreamSynchronize(ctx->stream);
+  for (size_t q = 0; q < ctx->ev_class.size(); ++q) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ctx->evpool[2 * q], ctx->evpool[2 * q + 1]) == cudaSuccess) {
+      S->kernel_ms[ctx->ev_class[q]] += ms;
+      S->kernel_calls[ctx->ev_class[q]] += 1;
+    }
+  }
+  timing_reset(ctx);
+}
+
+// ---- building blocks --------------------------------------------------------
+
+// F = F(U; Un), returns ||F||_2 in *fn (synchronises)
+int residual(seird_ctx* ctx, const double* U, const double* Un, double* F, double* fn) {
+  const HostSetup& hs = ctx->hs;
+  {
+    KTimer kt_(ctx, SEIRD_K_RESIDUAL);
+    launch_residual(hs.n, hs.m, ctx->tri, ctx->xy, U, Un, ctx->bfield, make_rates(ctx), ctx->opt.quadrature,
+                    ctx->elem, ctx->node_inc_ptr, ctx->node_inc, F, ctx->partial, 0, ctx->scal, ctx->err,
+                    ctx->stream);
+  }
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(ctx->h_scal, ctx->scal, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  TRY(check_flags(ctx, "residual"));
+  const double v = ctx->h_scal[0];
+  if (!std::isfinite(v)) return fail(ctx, SEIRD_ENONFINITE, "residual: non-finite norm");
+  *fn = std::sqrt(v);
+  return SEIRD_OK;
+}
+
+int jacobian(seird_ctx* ctx, const double* U) {
+  const HostSetup& hs = ctx->hs;
+  KTimer kt_(ctx, SEIRD_K_JACOBIAN);
+  launch_jacobian((int64_t)hs.col.size(), hs.m, ctx->tri, ctx->xy, U, ctx->bfield, make_rates(ctx),
+                  ctx->opt.quadrature, ctx->rec, ctx->blk_inc_ptr, ctx->blk_inc, ctx->val, ctx->err, ctx->stream);
+  CK(cudaGetLastError());
+  ctx->jac_ready = true;
+  ctx->pc_ready = false;
+  return SEIRD_OK;
+}
+
+RasDev ras_dev(seird_ctx* ctx) {
+  RasDev d;
+  d.P = ctx->hs.P;
+  d.sd_row0 = ctx->sd_row0;
+  d.sd_node = ctx->sd_node;
+  d.l_row_ptr = ctx->l_row_ptr;
+  d.l_col = ctx->l_col;
+  d.l_gblk = ctx->l_gblk;
+  d.l_diag = ctx->l_diag;
+  d.upd_ptr = ctx->upd_ptr;
+  d.upd = ctx->upd;
+  d.fwd_order = ctx->fwd_order;
+  d.fwd_lev = ctx->fwd_lev;
+  d.sd_fwd_lev0 = ctx->sd_fwd_lev0;
+  d.bwd_order = ctx->bwd_order;
+  d.bwd_lev = ctx->bwd_lev;
+  d.sd_bwd_lev0 = ctx->sd_bwd_lev0;
+  d.own_ptr = ctx->own_ptr;
+  d.fval = ctx->fval;
+  d.dinv = ctx->dinv;
+  d.ywork = ctx->ywork;
+  d.zwork = ctx->zwork;
+  return d;
+}
+
+CoarseDev coarse_dev(seird_ctx* ctx) {
+  CoarseDev c;
+  c.P = ctx->hs.P;
+  c.band = ctx->hs.cband;
+  c.cpos = ctx->cpos;
+  c.owner = ctx->owner;
+  c.own_ptr = ctx->own_ptr;
+  c.cseg_blk = ctx->cseg_blk;
+  c.cchunk_ptr = ctx->cchunk_ptr;
+  c.nchunk = (int32_t)ctx->hs.cchunk_ptr.size() - 1;
+  c.cdst_ptr = ctx->cdst_ptr;
+  c.cdst_idx = ctx->cdst_idx;
+  c.ndst = (int32_t)ctx->hs.cdst_idx.size();
+  c.cpart = ctx->cpart;
+  c.cband = ctx->cband;
+  c.cdinv = ctx->cdinv;
+  c.crhs = ctx->crhs;
+  return c;
+}
+
+int pc_setup(seird_ctx* ctx) {
+  if (!ctx->jac_ready) return fail(ctx, SEIRD_EINVAL, "preconditioner setup needs an assembled Jacobian");
+  {
+    KTimer kt_(ctx, SEIRD_K_ILU_FACTOR);
+    launch_ilu_factor(ras_dev(ctx), ctx->val, ctx->err, ctx->stream);
+  }
+  CK(cudaGetLastError());
+  if (ctx->opt.coarse) {
+    KTimer kt_(ctx, SEIRD_K_COARSE_SETUP);
+    const CoarseDev c = coarse_dev(ctx);
+    launch_coarse_assemble(c, ctx->val, ctx->stream);
+    launch_coarse_factor(c, ctx->err, ctx->stream);
+    CK(cudaGetLastError());
+  }
+  TRY(check_flags(ctx, "preconditioner setup"));
+  ctx->pc_ready = true;
+  return SEIRD_OK;
+}
+
+// z = M^{-1} r  (every node is owned by exactly one subdomain, so the RAS part
+// writes every entry of z; the coarse part adds to it)
+int pc_apply(seird_ctx* ctx, const double* r, double* z) {
+  {
+    KTimer kt_(ctx, SEIRD_K_ILU_SOLVE);
+    launch_ilu_solve(ras_dev(ctx), r, z, ctx->stream);
+  }
+  if (ctx->opt.coarse) {
+    KTimer kt_(ctx, SEIRD_K_COARSE_APPLY);
+    launch_coarse_apply_add(coarse_dev(ctx), ctx->hs.n, r, z, ctx->stream);
+  }
+  CK(cudaGetLastError());
+  return SEIRD_OK;
+}
+
+int spmv(seird_ctx* ctx, const double* x, double* y) {
+  KTimer kt_(ctx, SEIRD_K_SPMV);
+  launch_spmv<double>(ctx->hs.n, ctx->row_ptr, ctx->col, ctx->val, x, y, ctx->stream);
+  CK(cudaGetLastError());
+  return SEIRD_OK;
+}
+
+int read_scalars(seird_ctx* ctx, int first, int count) {
+  CK(cudaMemcpyAsync(ctx->h_scal + first, ctx->scal + first, sizeof(double) * count, cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return SEIRD_OK;
+}
+
+int norm2(seird_ctx* ctx, const double* x, double* out) {
+  launch_norm2(vlen(ctx), x, ctx->partial, ctx->red_grid, ctx->scal + 4, ctx->stream);
+  CK(cudaGetLastError());
+  TRY(read_scalars(ctx, 4, 1));
+  *out = std::sqrt(std::max(ctx->h_scal[4], 0.0));
+  return SEIRD_OK;
+}
+
+// Right-preconditioned restarted FGMRES (Z_j = M^{-1} V_j kept), CGS2, x0 = 0.
+// Stops on ||r|| <= max(rtol ||b||, atol); dtol divergence and non-finite
+// estimates are errors; hitting the iteration limit returns SEIRD_OK with
+// *converged = false (Newton then takes the inexact step).
+int gmres(seird_ctx* ctx, const double* b, double* x, int* its_out, bool* converged) {
+  const int64_t len = vlen(ctx);
+  const int m = ctx->opt.gmres_restart;
+  const int ldh = m + 1;
+  const cudaStream_t s = ctx->stream;
+  double* h1 = ctx->hcol;
+  double* h2 = ctx->hcol + NV_STRIDE;
+  *its_out = 0;
+  *converged = false;
+  CK(cudaMemsetAsync(x, 0, sizeof(double) * len, s));
+  double bnorm;
+  TRY(norm2(ctx, b, &bnorm));
+  if (!std::isfinite(bnorm)) return fail(ctx, SEIRD_ENONFINITE, "gmres: non-finite right-hand side");
+  if (bnorm == 0.0) {
+    *converged = true;
+    return SEIRD_OK;
+  }
+  const double tol = std::max(ctx->opt.gmres_rtol * bnorm, ctx->opt.gmres_atol);
+  const double* r = b;
+  double rnorm = bnorm;
+  int its = 0;
+  std::vector<double> g0(ldh, 0.0);
+  double* gbuf = ctx->gm + (int64_t)ldh * m + 2 * m;  // g inside the GMRES small state
+  while (true) {
+    launch_axpby(len, 1.0 / rnorm, r, 0.0, r, ctx->V, s);
+    g0.assign(ldh, 0.0);
+    g0[0] = rnorm;
+    CK(cudaMemcpyAsync(gbuf, g0.data(), sizeof(double) * ldh, cudaMemcpyHostToDevice, s));
+    int k = 0;
+    bool done = false;
+    for (int j = 0; j < m; ++j) {
+      double* Vj = ctx->V + (int64_t)j * len;
+      double* Zj = ctx->Z + (int64_t)j * len;
+      TRY(pc_apply(ctx, Vj, Zj));
+      TRY(spmv(ctx, Zj, ctx->w));
+      {
+        KTimer kt_(ctx, SEIRD_K_KRYLOV);
+        launch_mdot(len, j + 1, ctx->V, len, ctx->w, ctx->partial, ctx->red_grid, h1, s);
+        launch_update_mdot(len, j + 1, ctx->V, len, h1, ctx->w, ctx->partial, ctx->red_grid, nullptr, s);
+        launch_reduce_cols(ctx->red_grid, j + 1, ctx->partial, h2, 0, s);
+        launch_update_norm(len, j + 1, ctx->V, len, h2, ctx->w, ctx->partial, ctx->red_grid, ctx->scal + 5, s);
+        launch_givens(j, ctx->gm, h1, h2, ctx->scal + 5, ldh, ctx->scal + 2, s);
+        launch_scale(len, ctx->w, ctx->scal + 3, 1, ctx->V + (int64_t)(j + 1) * len, s);
+      }
+      CK(cudaGetLastError());
+      TRY(read_scalars(ctx, 2, 2));
+      ++its;
+      k = j + 1;
+      const double res = ctx->h_scal[2], hn = ctx->h_scal[3];
+      if (!std::isfinite(res)) return fail(ctx, SEIRD_ENONFINITE, "gmres: non-finite residual estimate");
+      if (res > ctx->opt.gmres_dtol * bnorm) return fail(ctx, SEIRD_EGMRES, "gmres: diverged (dtol)");
+      if (res <= tol || hn == 0.0) {
+        done = true;
+        break;
+      }
+      if (its >= ctx->opt.gmres_maxit) break;
+    }
+    launch_hsolve(k, ctx->gm, ldh, s);
+    launch_multi_axpy(len, k, ctx->Z, len, gbuf + ldh, x, s);  // y lives right after g
+    CK(cudaGetLastError());
+    if (done) {
+      *converged = true;
+      break;
+    }
+    if (its >= ctx->opt.gmres_maxit) break;
+    // restart from the true residual r = b - J x
+    TRY(spmv(ctx, x, ctx->w));
+    launch_axpby(len, 1.0, b, -1.0, ctx->w, ctx->w, s);
+    TRY(norm2(ctx, ctx->w, &rnorm));
+    if (!std::isfinite(rnorm)) return fail(ctx, SEIRD_ENONFINITE, "gmres: non-finite restart residual");
+    if (rnorm <= tol) {
+      *converged = true;
+      break;
+    }
+    r = ctx->w;
+  }
+  *its_out = its;
+  return SEIRD_OK;
+}
+
+bool verbose() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = std::getenv("SEIRD_VERBOSE");
+    v = (e && e[0] && e[0] != '0') ? 1 : 0;
+  }
+  return v == 1;
+}
+
+double ms_since(std::chrono::steady_clock::time_point t0) {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+int newton_step(seird_ctx* ctx, seird_stats* st) {
+  using clk = std::chrono::steady_clock;
+  const auto t_begin = clk::now();
+  const int64_t len = vlen(ctx);
+  const cudaStream_t s = ctx->stream;
+  seird_stats S;
+  std::memset(&S, 0, sizeof(S));
+  timing_reset(ctx);
+  CK(cudaMemcpyAsync(ctx->Un, ctx->U, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
+  auto t0 = clk::now();
+  double f;
+  int rc = residual(ctx, ctx->U, ctx->Un, ctx->F, &f);
+  S.ms_assemble += ms_since(t0);
+  if (rc) return rc;
+  const double f0 = f;
+  S.res0 = f0;
+  double unorm;
+  TRY(norm2(ctx, ctx->Un, &unorm));
+  int its = 0;
+  auto restore = [&](int code) {
+    cudaMemcpyAsync(ctx->U, ctx->Un, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
+    cudaStreamSynchronize(s);
+    return code;
+  };
+  while (!(f <= ctx->opt.newton_rtol * f0 + ctx->opt.newton_atol)) {
+    if (its >= ctx->opt.newton_maxit) return restore(fail(ctx, SEIRD_ENEWTON_MAXIT, "newton: iteration limit"));
+    t0 = clk::now();
+    rc = jacobian(ctx, ctx->U);
+    if (rc) return restore(rc);
+    CK(cudaStreamSynchronize(s));
+    S.ms_assemble += ms_since(t0);
+    if (its % std::max(1, ctx->opt.pc_lag) == 0 || !ctx->pc_ready) {
+      t0 = clk::now();
+      rc = pc_setup(ctx);
+      S.ms_setup += ms_since(t0);
+      if (rc) return restore(rc);
+      S.pc_setups++;
+    }
+    // J dU = -F
+    launch_axpby(len, -1.0, ctx->F, 0.0, ctx->F, ctx->stage, s);
+    t0 = clk::now();
+    int lits = 0;
+    bool conv = false;
+    rc = gmres(ctx, ctx->stage, ctx->dU, &lits, &conv);
+    S.ms_solve += ms_since(t0);
+    S.gmres_its += lits;
+    if (rc) return restore(rc);
+    double lam = 1.0, ft = 0.0;
+    t0 = clk::now();
+    for (int ls = 0;; ++ls) {
+      launch_axpby(len, 1.0, ctx->U, lam, ctx->dU, ctx->Ut, s);
+      rc = residual(ctx, ctx->Ut, ctx->Un, ctx->Ft, &ft);
+      if (rc == SEIRD_ENONFINITE && ls < ctx->opt.ls_maxit) {  // N <= 0 on the trial point: shorten the step
+        lam *= 0.5;
+        S.ls_halvings++;
+        continue;
+      }
+      if (rc) return restore(rc);
+      if (ft <= (1.0 - 1e-4 * lam) * f || ls >= ctx->opt.ls_maxit) break;
+      lam *= 0.5;
+      S.ls_halvings++;
+    }
+    S.ms_assemble += ms_since(t0);
+    double dn;
+    TRY(norm2(ctx, ctx->dU, &dn));
+    S.eps_update = unorm > 0 ? lam * dn / unorm : 0.0;
+    if (verbose())
+      std::fprintf(stderr, "[seird] t=%g newton %d |F| %.6e -> %.6e (f0 %.6e) gmres %d conv %d lambda %g |dU| %.3e\n",
+                   ctx->t, its, f, ft, f0, lits, (int)conv, lam, dn);
+    std::swap(ctx->U, ctx->Ut);
+    std::swap(ctx->F, ctx->Ft);
+    f = ft;
+    ++its;
+  }
+  S.newton_its = its;
+  S.res_final = f;
+  ctx->t += ctx->opt.dt;
+  S.ms_total = ms_since(t_begin);
+  timing_collect(ctx, &S);
+  if (st) *st = S;
+  return SEIRD_OK;
+}
+
+// caller-numbered input -> internal vector dst
+int to_internal(seird_ctx* ctx, const double* src, int on_device, double* dst) {
+  const int64_t len = vlen(ctx);
+  const double* dsrc = src;
+  if (!on_device) {
+    CK(cudaMemcpyAsync(ctx->stage, src, sizeof(double) * len, cudaMemcpyHostToDevice, ctx->stream));
+    dsrc = ctx->stage;
+  }
+  launch_gather5(ctx->hs.n, ctx->perm, dsrc, dst, ctx->stream);
+  CK(cudaGetLastError());
+  if (!on_device) CK(cudaStreamSynchronize(ctx->stream));  // stage is reused by the next call
+  return SEIRD_OK;
+}
+
+int from_internal(seird_ctx* ctx, const double* src, double* dst, int on_device) {
+  const int64_t len = vlen(ctx);
+  if (on_device) {
+    launch_scatter5(ctx->hs.n, ctx->perm, src, dst, ctx->stream);
+    CK(cudaGetLastError());
+    return SEIRD_OK;
+  }
+  launch_scatter5(ctx->hs.n, ctx->perm, src, ctx->stage, ctx->stream);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(dst, ctx->stage, sizeof(double) * len, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return SEIRD_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+// C ABI
+// ============================================================================
+
+extern "C" {
+
+void seird_default_options(seird_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->dt = 1.0;
+  o->newton_rtol = 1e-8;
+  o->newton_atol = 0.0;
+  o->newton_maxit = 20;
+  o->ls_maxit = 10;
+  o->gmres_restart = 30;
+  o->gmres_maxit = 200;
+  o->gmres_rtol = 1e-5;
+  o->gmres_atol = 1e-50;
+  o->gmres_dtol = 1e5;
+  o->n_subdomains = 4;
+  o->overlap = 1;
+  o->coarse = 0;
+  o->precision = 0;
+  o->quadrature = 0;
+  o->pc_lag = 1;
+  o->owner = nullptr;
+  o->seed = 0;
+  o->stream = nullptr;
+}
+
+const char* seird_last_error(const seird_ctx* ctx) {
+  return ctx ? ctx->last_error.c_str() : g_create_error.c_str();
+}
+
+int64_t seird_launch_count(void) { return launch_total(); }
+
+void seird_destroy(seird_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (cudaEvent_t e : ctx->evpool) cudaEventDestroy(e);
+  for (void* p : ctx->allocations) cudaFree(p);
+  if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
+  if (ctx->h_err) cudaFreeHost(ctx->h_err);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+static int create_impl(seird_ctx* ctx, const seird_mesh* mesh, const seird_params* params) {
+  seird_options& o = ctx->opt;
+  if (!(o.dt > 0) || o.gmres_restart < 1 || o.gmres_restart > MAX_RESTART || o.gmres_maxit < 1 ||
+      o.newton_maxit < 0 || o.ls_maxit < 0 || o.overlap < 0 || (o.coarse != 0 && o.coarse != 1) ||
+      (o.quadrature != 0 && o.quadrature != 1) || (o.precision != 0 && o.precision != 1))
+    return fail(ctx, SEIRD_EINVAL, "invalid option value");
+  std::string err;
+  int rc = build_setup(mesh, &o, ctx->hs, err);
+  if (rc) return fail(ctx, rc, err);
+  HostSetup& hs = ctx->hs;
+  if (o.coarse && 5 * (int64_t)hs.P * 8 > 200 * 1024)
+    return fail(ctx, SEIRD_EINVAL, "coarse space supports at most 5120 subdomains");
+  if (o.stream) {
+    ctx->stream = (cudaStream_t)o.stream;
+  } else {
+    CK(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+    ctx->own_stream = true;
+  }
+  upload_quadrature();
+  cgs_init();
+  coarse_init();
+  CK(cudaGetLastError());
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  ctx->red_grid = std::max(1, sms) * 3;
+  const int64_t n = hs.n, m = hs.m, len = 5 * n;
+  const int64_t nnzb = (int64_t)hs.col.size();
+  const int R = o.gmres_restart;
+  // mesh, patterns, maps
+  TRY(upload(ctx, &ctx->xy, hs.xy));
+  TRY(upload(ctx, &ctx->tri, hs.tri));
+  TRY(upload(ctx, &ctx->perm, hs.perm));
+  TRY(upload(ctx, &ctx->row_ptr, hs.row_ptr));
+  TRY(upload(ctx, &ctx->col, hs.col));
+  TRY(upload(ctx, &ctx->node_inc_ptr, hs.node_inc_ptr));
+  TRY(upload(ctx, &ctx->node_inc, hs.node_inc));
+  TRY(upload(ctx, &ctx->blk_inc_ptr, hs.blk_inc_ptr));
+  TRY(upload(ctx, &ctx->blk_inc, hs.blk_inc));
+  if (params->beta_field) {
+    std::vector<double> bf(n);
+    for (int64_t k = 0; k < n; ++k) bf[k] = params->beta_field[hs.perm[k]];
+    TRY(upload(ctx, &ctx->bfield, bf));
+  }
+  TRY(dalloc(ctx, &ctx->val, 25 * nnzb));
+  TRY(dalloc(ctx, &ctx->elem, 15 * m));
+  TRY(dalloc(ctx, &ctx->rec, (size_t)REC * m));
+  double** vecs[] = {&ctx->U, &ctx->Un, &ctx->F, &ctx->Ft, &ctx->dU, &ctx->Ut, &ctx->stage, &ctx->stage2, &ctx->w};
+  for (double** v : vecs) TRY(dalloc(ctx, v, len));
+  TRY(dalloc(ctx, &ctx->V, (size_t)(R + 1) * len));
+  TRY(dalloc(ctx, &ctx->Z, (size_t)R * len));
+  const int64_t npart = std::max<int64_t>((int64_t)ctx->red_grid * NV_STRIDE, (n + 255) / 256);
+  TRY(dalloc(ctx, &ctx->partial, npart));
+  TRY(dalloc(ctx, &ctx->hcol, 2 * NV_STRIDE));
+  TRY(dalloc(ctx, &ctx->gm, (size_t)(R + 1) * R + 2 * R + (R + 1) + R));
+  TRY(dalloc(ctx, &ctx->scal, 16));
+  TRY(dalloc(ctx, &ctx->err, 1));
+  CK(cudaMemset(ctx->err, 0, sizeof(int32_t)));
+  CK(cudaMemset(ctx->U, 0, sizeof(double) * len));
+  CK(cudaMemset(ctx->gm, 0, sizeof(double) * ((size_t)(R + 1) * R + 2 * R + (R + 1) + R)));
+  CK(cudaMallocHost((void**)&ctx->h_scal, sizeof(double) * 16));
+  CK(cudaMallocHost((void**)&ctx->h_err, sizeof(int32_t)));
+  *ctx->h_err = 0;
+  // RAS
+  TRY(upload(ctx, &ctx->sd_row0, hs.sd_row0));
+  TRY(upload(ctx, &ctx->sd_node, hs.sd_node));
+  TRY(upload(ctx, &ctx->l_row_ptr, hs.l_row_ptr));
+  TRY(upload(ctx, &ctx->l_col, hs.l_col));
+  TRY(upload(ctx, &ctx->l_gblk, hs.l_gblk));
+  TRY(upload(ctx, &ctx->l_diag, hs.l_diag));
+  TRY(upload(ctx, &ctx->upd_ptr, hs.upd_ptr));
+  TRY(upload(ctx, &ctx->upd, hs.upd));
+  TRY(upload(ctx, &ctx->fwd_order, hs.fwd_order));
+  TRY(upload(ctx, &ctx->fwd_lev, hs.fwd_lev));
+  TRY(upload(ctx, &ctx->sd_fwd_lev0, hs.sd_fwd_lev0));
+  TRY(upload(ctx, &ctx->bwd_order, hs.bwd_order));
+  TRY(upload(ctx, &ctx->bwd_lev, hs.bwd_lev));
+  TRY(upload(ctx, &ctx->sd_bwd_lev0, hs.sd_bwd_lev0));
+  TRY(upload(ctx, &ctx->own_ptr, hs.own_ptr));
+  TRY(upload(ctx, &ctx->owner, hs.owner));
+  const int64_t NL = (int64_t)hs.sd_node.size();
+  const int64_t NLB = (int64_t)hs.l_col.size();
+  TRY(dalloc(ctx, &ctx->fval, 25 * NLB));
+  TRY(dalloc(ctx, &ctx->dinv, 25 * NL));
+  TRY(dalloc(ctx, &ctx->ywork, 5 * NL));
+  TRY(dalloc(ctx, &ctx->zwork, 5 * NL));
+  // coarse
+  if (o.coarse) {
+    TRY(upload(ctx, &ctx->cpos, hs.cpos));
+    TRY(upload(ctx, &ctx->cseg_blk, hs.cseg_blk));
+    TRY(upload(ctx, &ctx->cchunk_ptr, hs.cchunk_ptr));
+    TRY(upload(ctx, &ctx->cdst_ptr, hs.cdst_ptr));
+    TRY(upload(ctx, &ctx->cdst_idx, hs.cdst_idx));
+    TRY(dalloc(ctx, &ctx->cpart, 25 * (hs.cchunk_ptr.size() - 1)));
+    TRY(dalloc(ctx, &ctx->cband, 25 * (size_t)hs.P * (2 * hs.cband + 1)));
+    TRY(dalloc(ctx, &ctx->cdinv, 25 * (size_t)hs.P));
+    TRY(dalloc(ctx, &ctx->crhs, 5 * (size_t)hs.P));
+  }
+  CK(cudaDeviceSynchronize());
+  return SEIRD_OK;
+}
+
+int seird_create(const seird_mesh* mesh, const seird_params* params, const seird_options* opt, seird_ctx** out) {
+  if (!out) return fail(nullptr, SEIRD_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!mesh || !params) return fail(nullptr, SEIRD_EINVAL, "mesh and params must not be NULL");
+  seird_ctx* ctx = new (std::nothrow) seird_ctx();
+  if (!ctx) return fail(nullptr, SEIRD_ENOMEM, "host allocation failed");
+  ctx->params = *params;
+  ctx->params.beta_field = nullptr;  // copied to the device, never retained
+  if (opt) ctx->opt = *opt;
+  else seird_default_options(&ctx->opt);
+  int rc = create_impl(ctx, mesh, params);
+  ctx->opt.owner = nullptr;  // read during create only, never retained
+  if (rc) {
+    g_create_error = ctx->last_error;
+    seird_destroy(ctx);
+    return rc;
+  }
+  *out = ctx;
+  return SEIRD_OK;
+}
+
+int seird_set_state(seird_ctx* ctx, const double* u, int on_device, double t) {
+  if (!ctx || !u) return fail(ctx, SEIRD_EINVAL, "NULL argument");
+  TRY(to_internal(ctx, u, on_device, ctx->U));
+  ctx->t = t;
+  return SEIRD_OK;
+}
+
+int seird_get_state(const seird_ctx* cctx, double* u, int on_device, double* t) {
+  seird_ctx* ctx = const_cast<seird_ctx*>(cctx);
+  if (!ctx || !u) return fail(ctx, SEIRD_EINVAL, "NULL argument");
+  TRY(from_internal(ctx, ctx->U, u, on_device));
+  if (t) *t = ctx->t;
+  return SEIRD_OK;
+}
+
+int seird_step(seird_ctx* ctx, seird_stats* stats) {
+  if (!ctx) return fail(nullptr, SEIRD_EINVAL, "NULL context");
+  return newton_step(ctx, stats);
+}
+
+int seird_run(seird_ctx* ctx, int32_t n_steps, seird_stats* per_step) {
+  if (!ctx || n_steps < 0) return fail(ctx, SEIRD_EINVAL, "bad argument");
+  for (int32_t k = 0; k < n_steps; ++k) TRY(newton_step(ctx, per_step ? per_step + k : nullptr));
+  return SEIRD_OK;
+}
+
+int seird_get_info(const seird_ctx* ctx, seird_info* info) {
+  if (!ctx || !info) return SEIRD_EINVAL;
+  info->n_nodes = ctx->hs.n;
+  info->n_tris = ctx->hs.m;
+  info->nnzb = (int64_t)ctx->hs.col.size();
+  info->n_subdomains = ctx->hs.P;
+  info->subdomain_rows = (int64_t)ctx->hs.sd_node.size();
+  info->subdomain_blocks = (int64_t)ctx->hs.l_col.size();
+  info->max_levels = ctx->hs.max_levels;
+  info->coarse_band = ctx->hs.cband;
+  info->device_bytes = ctx->device_bytes;
+  return SEIRD_OK;
+}
+
+int seird_eval_residual(seird_ctx* ctx, const double* u, const double* u_prev, double* F, int on_device) {
+  if (!ctx || !u || !u_prev || !F) return fail(ctx, SEIRD_EINVAL, "NULL argument");
+  TRY(to_internal(ctx, u, on_device, ctx->Ut));
+  TRY(to_internal(ctx, u_prev, on_device, ctx->stage2));
+  double fn;
+  TRY(residual(ctx, ctx->Ut, ctx->stage2, ctx->Ft, &fn));
+  return from_internal(ctx, ctx->Ft, F, on_device);
+}
+
+int seird_eval_jacobian(seird_ctx* ctx, const double* u, int on_device) {
+  if (!ctx || !u) return fail(ctx, SEIRD_EINVAL, "NULL argument");
+  TRY(to_internal(ctx, u, on_device, ctx->Ut));
+  TRY(jacobian(ctx, ctx->Ut));
+  return check_flags(ctx, "jacobian");
+}
+
+int seird_get_jacobian(const seird_ctx* cctx, int32_t* row_ptr, int32_t* col, double* val) {
+  seird_ctx* ctx = const_cast<seird_ctx*>(cctx);
+  if (!ctx || !row_ptr || !col || !val) return fail(ctx, SEIRD_EINVAL, "NULL argument");
+  if (!ctx->jac_ready) return fail(ctx, SEIRD_EINVAL, "no Jacobian assembled");
+  const HostSetup& hs = ctx->hs;
+  const int64_t nnzb = (int64_t)hs.col.size();
+  std::vector<double> v(25 * nnzb);
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaMemcpy(v.data(), ctx->val, sizeof(double) * v.size(), cudaMemcpyDeviceToHost));
+  row_ptr[0] = 0;
+  std::vector<std::pair<int32_t, int32_t>> ent;
+  int64_t pos = 0;
+  for (int64_t i = 0; i < hs.n; ++i) {
+    const int32_t k = hs.iperm[i];
+    ent.clear();
+    for (int32_t b = hs.row_ptr[k]; b < hs.row_ptr[k + 1]; ++b) ent.push_back({hs.perm[hs.col[b]], b});
+    std::sort(ent.begin(), ent.end());
+    for (auto& e : ent) {
+      col[pos] = e.first;
+      std::memcpy(val + 25 * pos, v.data() + 25 * (int64_t)e.second, 25 * sizeof(double));
+      ++pos;
+    }
+    row_ptr[i + 1] = (int32_t)pos;
+  }
+  return SEIRD_OK;
+}
+
+int seird_apply_jacobian(seird_ctx* ctx, const double* x, double* y, int on_device) {
+  if (!ctx || !x || !y) return fail(ctx, SEIRD_EINVAL, "NULL argument");
+  if (!ctx->jac_ready) return fail(ctx, SEIRD_EINVAL, "no Jacobian assembled");
+  TRY(to_internal(ctx, x, on_device, ctx->stage2));
+  TRY(spmv(ctx, ctx->stage2, ctx->Ft));
+  return from_internal(ctx, ctx->Ft, y, on_device);
+}
+
+int seird_precond_setup(seird_ctx* ctx) {
+  if (!ctx) return fail(nullptr, SEIRD_EINVAL, "NULL context");
+  return pc_setup(ctx);
+}
+
+int seird_precond_apply(seird_ctx* ctx, const double* r, double* z, int on_device) {
+  if (!ctx || !r || !z) return fail(ctx, SEIRD_EINVAL, "NULL argument");
+  if (!ctx->pc_ready) return fail(ctx, SEIRD_EINVAL, "preconditioner not set up");
+  TRY(to_internal(ctx, r, on_device, ctx->stage2));
+  TRY(pc_apply(ctx, ctx->stage2, ctx->Ft));
+  return from_internal(ctx, ctx->Ft, z, on_device);
+}
+
+int seird_linear_solve(seird_ctx* ctx, const double* b, double* x, int on_device, int32_t* its) {
+  if (!ctx || !b || !x) return fail(ctx, SEIRD_EINVAL, "NULL argument");
+  if (!ctx->pc_ready) return fail(ctx, SEIRD_EINVAL, "preconditioner not set up");
+  TRY(to_internal(ctx, b, on_device, ctx->stage2));
+  int k = 0;
+  bool conv = false;
+  TRY(gmres(ctx, ctx->stage2, ctx->dU, &k, &conv));
+  if (its) *its = k;
+  TRY(from_internal(ctx, ctx->dU, x, on_device));
+  return conv ? SEIRD_OK : fail(ctx, SEIRD_EGMRES, "gmres: iteration limit reached");
+}
+
+int seird_bsr_spmv(int64_t n_rows, const int32_t* row_ptr, const int32_t* col, const double* val, const double* x,
+                   double* y, void* stream) {
+  if (n_rows < 0) return SEIRD_EINVAL;
+  if (n_rows == 0) return SEIRD_OK;
+  if (!row_ptr || !col || !val || !x || !y) return SEIRD_EINVAL;
+  launch_spmv<double>(n_rows, row_ptr, col, val, x, y, (cudaStream_t)stream);
+  return cudaGetLastError() == cudaSuccess ? SEIRD_OK : SEIRD_ECUDA;
+}
+
+int seird_bsr_spmv_f32val(int64_t n_rows, const int32_t* row_ptr, const int32_t* col, const float* val,
+                          const double* x, double* y, void* stream) {
+  if (n_rows < 0) return SEIRD_EINVAL;
+  if (n_rows == 0) return SEIRD_OK;
+  if (!row_ptr || !col || !val || !x || !y) return SEIRD_EINVAL;
+  launch_spmv<float>(n_rows, row_ptr, col, val, x, y, (cudaStream_t)stream);
+  return cudaGetLastError() == cudaSuccess ? SEIRD_OK : SEIRD_ECUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,420 @@
+// Host-side setup: mesh validation, seeded recursive coordinate bisection,
+// renumbering, the 5x5 BSR pattern, element gather lists, overlapping
+// subdomains (Eq. RAS) with their ILU(0) patterns and level schedules, and the
+// banded pattern of the coarse matrix Z^T J Z (Section 3.1).  Plain C++; runs
+// once per context.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <random>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace seird {
+
+namespace {
+
+// Recursive coordinate bisection: the parts [pb, pe) share the nodes idx[lo, hi)
+// in proportion to their weights; each cut is orthogonal to the longer side of
+// the nodes' bounding box.
+void rcb(const double* xy, std::vector<int32_t>& idx, int64_t lo, int64_t hi, int32_t pb, int32_t pe,
+         const std::vector<double>& w, std::vector<int32_t>& owner) {
+  if (pe - pb == 1) {
+    for (int64_t k = lo; k < hi; ++k) owner[idx[k]] = pb;
+    return;
+  }
+  const int32_t pm = pb + (pe - pb) / 2;
+  double wl = 0, wt = 0;
+  for (int32_t q = pb; q < pe; ++q) {
+    wt += w[q];
+    if (q < pm) wl += w[q];
+  }
+  const int64_t cnt = hi - lo;
+  int64_t k = lo + (int64_t)std::llround((double)cnt * wl / wt);
+  k = std::max<int64_t>(k, lo + (pm - pb));
+  k = std::min<int64_t>(k, hi - (pe - pm));
+  double mn[2] = {1e300, 1e300}, mx[2] = {-1e300, -1e300};
+  for (int64_t q = lo; q < hi; ++q)
+    for (int d = 0; d < 2; ++d) {
+      mn[d] = std::min(mn[d], xy[2 * (int64_t)idx[q] + d]);
+      mx[d] = std::max(mx[d], xy[2 * (int64_t)idx[q] + d]);
+    }
+  const int ax = (mx[0] - mn[0] >= mx[1] - mn[1]) ? 0 : 1;
+  std::nth_element(idx.begin() + lo, idx.begin() + k, idx.begin() + hi, [&](int32_t a, int32_t b) {
+    const double xa = xy[2 * (int64_t)a + ax], xb = xy[2 * (int64_t)b + ax];
+    return xa < xb || (xa == xb && a < b);
+  });
+  rcb(xy, idx, lo, k, pb, pm, w, owner);
+  rcb(xy, idx, k, hi, pm, pe, w, owner);
+}
+
+// Reverse Cuthill-McKee order of a small graph (adjacency lists).
+std::vector<int32_t> rcm(const std::vector<std::vector<int32_t>>& adj) {
+  const int32_t n = (int32_t)adj.size();
+  std::vector<int32_t> order;
+  order.reserve(n);
+  std::vector<char> seen(n, 0);
+  while ((int32_t)order.size() < n) {
+    int32_t start = -1;
+    for (int32_t v = 0; v < n; ++v)
+      if (!seen[v] && (start < 0 || adj[v].size() < adj[start].size())) start = v;
+    size_t head = order.size();
+    order.push_back(start);
+    seen[start] = 1;
+    while (head < order.size()) {
+      int32_t v = order[head++];
+      std::vector<int32_t> nb;
+      for (int32_t u : adj[v])
+        if (!seen[u]) {
+          seen[u] = 1;
+          nb.push_back(u);
+        }
+      std::sort(nb.begin(), nb.end(), [&](int32_t a, int32_t b) {
+        return adj[a].size() < adj[b].size() || (adj[a].size() == adj[b].size() && a < b);
+      });
+      order.insert(order.end(), nb.begin(), nb.end());
+    }
+  }
+  std::reverse(order.begin(), order.end());
+  return order;
+}
+
+}  // namespace
+
+int build_setup(const seird_mesh* mesh, const seird_options* opt, HostSetup& hs, std::string& err) {
+  const int64_t n = mesh->n_nodes, m = mesh->n_tris;
+  if (n < 3 || m < 1 || !mesh->xy || !mesh->tri) {
+    err = "mesh needs at least 3 nodes, 1 triangle and non-NULL arrays";
+    return SEIRD_EINVAL;
+  }
+  if (n > (int64_t)INT32_MAX / 8 || m > (int64_t)INT32_MAX / 9) {
+    err = "mesh too large for 32-bit element maps";
+    return SEIRD_EINVAL;
+  }
+  for (int64_t t = 0; t < m; ++t) {
+    const int32_t* v = mesh->tri + 3 * t;
+    for (int a = 0; a < 3; ++a)
+      if (v[a] < 0 || v[a] >= n) {
+        err = "triangle " + std::to_string(t) + " has a node index out of range";
+        return SEIRD_EINVAL;
+      }
+    const double* p0 = mesh->xy + 2 * (int64_t)v[0];
+    const double* p1 = mesh->xy + 2 * (int64_t)v[1];
+    const double* p2 = mesh->xy + 2 * (int64_t)v[2];
+    const double twoA = (p1[0] - p0[0]) * (p2[1] - p0[1]) - (p2[0] - p0[0]) * (p1[1] - p0[1]);
+    if (!(twoA > 0)) {
+      err = "triangle " + std::to_string(t) + " is not counter-clockwise or is degenerate";
+      return SEIRD_EINVAL;
+    }
+  }
+  hs.n = n;
+  hs.m = m;
+
+  // ---- partition ---------------------------------------------------------
+  std::vector<int32_t> owner_c(n);
+  int32_t P;
+  if (opt->owner) {
+    P = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      if (opt->owner[i] < 0) {
+        err = "owner values must be >= 0";
+        return SEIRD_EINVAL;
+      }
+      P = std::max(P, opt->owner[i] + 1);
+    }
+    std::vector<int64_t> cnt(P, 0);
+    for (int64_t i = 0; i < n; ++i) cnt[opt->owner[i]]++;
+    for (int32_t q = 0; q < P; ++q)
+      if (!cnt[q]) {
+        err = "subdomain " + std::to_string(q) + " owns no node";
+        return SEIRD_EINVAL;
+      }
+    std::copy(opt->owner, opt->owner + n, owner_c.begin());
+  } else {
+    P = opt->n_subdomains;
+    if (P < 1 || P > n) {
+      err = "n_subdomains must be in [1, n_nodes]";
+      return SEIRD_EINVAL;
+    }
+    std::mt19937_64 rng(opt->seed);
+    std::uniform_real_distribution<double> U(0.75, 1.5);  // uneven parts, up to 2x apart
+    std::vector<double> w(P);
+    for (auto& x : w) x = U(rng);
+    std::vector<int32_t> idx(n);
+    std::iota(idx.begin(), idx.end(), 0);
+    rcb(mesh->xy, idx, 0, n, 0, P, w, owner_c);
+  }
+  hs.P = P;
+
+  // ---- internal numbering: nodes sorted by (owner, caller index) ----------
+  hs.own_ptr.assign(P + 1, 0);
+  for (int64_t i = 0; i < n; ++i) hs.own_ptr[owner_c[i] + 1]++;
+  for (int32_t q = 0; q < P; ++q) hs.own_ptr[q + 1] += hs.own_ptr[q];
+  hs.perm.resize(n);
+  hs.iperm.resize(n);
+  hs.owner.resize(n);
+  {
+    std::vector<int32_t> fill(hs.own_ptr.begin(), hs.own_ptr.end() - 1);
+    for (int64_t i = 0; i < n; ++i) {
+      int32_t k = fill[owner_c[i]]++;
+      hs.perm[k] = (int32_t)i;
+      hs.iperm[i] = k;
+      hs.owner[k] = owner_c[i];
+    }
+  }
+  hs.xy.resize(2 * n);
+  for (int64_t k = 0; k < n; ++k) {
+    hs.xy[2 * k] = mesh->xy[2 * (int64_t)hs.perm[k]];
+    hs.xy[2 * k + 1] = mesh->xy[2 * (int64_t)hs.perm[k] + 1];
+  }
+  // triangles renumbered, then ordered by their smallest node (stable)
+  {
+    std::vector<int32_t> tri(3 * m);
+    std::vector<int32_t> key(m);
+    for (int64_t t = 0; t < m; ++t) {
+      for (int a = 0; a < 3; ++a) tri[3 * t + a] = hs.iperm[mesh->tri[3 * t + a]];
+      key[t] = std::min(tri[3 * t], std::min(tri[3 * t + 1], tri[3 * t + 2]));
+    }
+    std::vector<int32_t> ord(m);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) { return key[a] < key[b]; });
+    hs.tri.resize(3 * m);
+    for (int64_t t = 0; t < m; ++t)
+      for (int a = 0; a < 3; ++a) hs.tri[3 * t + a] = tri[3 * (int64_t)ord[t] + a];
+  }
+
+  // ---- BSR pattern --------------------------------------------------------
+  {
+    std::vector<int64_t> pairs;
+    pairs.reserve(9 * m);
+    for (int64_t t = 0; t < m; ++t)
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) pairs.push_back((int64_t)hs.tri[3 * t + a] * n + hs.tri[3 * t + b]);
+    std::sort(pairs.begin(), pairs.end());
+    pairs.erase(std::unique(pairs.begin(), pairs.end()), pairs.end());
+    hs.row_ptr.assign(n + 1, 0);
+    hs.col.resize(pairs.size());
+    for (size_t k = 0; k < pairs.size(); ++k) {
+      hs.row_ptr[pairs[k] / n + 1]++;
+      hs.col[k] = (int32_t)(pairs[k] % n);
+    }
+    for (int64_t i = 0; i < n; ++i) hs.row_ptr[i + 1] += hs.row_ptr[i];
+    for (int64_t i = 0; i < n; ++i)
+      if (hs.row_ptr[i + 1] == hs.row_ptr[i]) {
+        err = "node " + std::to_string(hs.perm[i]) + " belongs to no triangle";
+        return SEIRD_EINVAL;
+      }
+  }
+  const int64_t nnzb = hs.col.size();
+  auto find_blk = [&](int32_t i, int32_t j) -> int32_t {
+    const int32_t* b = hs.col.data() + hs.row_ptr[i];
+    const int32_t* e = hs.col.data() + hs.row_ptr[i + 1];
+    const int32_t* p = std::lower_bound(b, e, j);
+    return (int32_t)(p - hs.col.data());
+  };
+
+  // ---- element gather lists (deterministic: ordered by triangle) ---------
+  hs.node_inc_ptr.assign(n + 1, 0);
+  for (int64_t t = 0; t < m; ++t)
+    for (int a = 0; a < 3; ++a) hs.node_inc_ptr[hs.tri[3 * t + a] + 1]++;
+  for (int64_t i = 0; i < n; ++i) hs.node_inc_ptr[i + 1] += hs.node_inc_ptr[i];
+  hs.node_inc.resize(3 * m);
+  {
+    std::vector<int32_t> fill(hs.node_inc_ptr.begin(), hs.node_inc_ptr.end() - 1);
+    for (int64_t t = 0; t < m; ++t)
+      for (int a = 0; a < 3; ++a) hs.node_inc[fill[hs.tri[3 * t + a]]++] = (int32_t)(3 * t + a);
+  }
+  hs.blk_inc_ptr.assign(nnzb + 1, 0);
+  std::vector<int32_t> tblk(9 * m);
+  for (int64_t t = 0; t < m; ++t)
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        int32_t k = find_blk(hs.tri[3 * t + a], hs.tri[3 * t + b]);
+        tblk[9 * t + 3 * a + b] = k;
+        hs.blk_inc_ptr[k + 1]++;
+      }
+  for (int64_t k = 0; k < nnzb; ++k) hs.blk_inc_ptr[k + 1] += hs.blk_inc_ptr[k];
+  hs.blk_inc.resize(9 * m);
+  {
+    std::vector<int32_t> fill(hs.blk_inc_ptr.begin(), hs.blk_inc_ptr.end() - 1);
+    for (int64_t t = 0; t < m; ++t)
+      for (int ab = 0; ab < 9; ++ab) hs.blk_inc[fill[tblk[9 * t + ab]]++] = (int32_t)(9 * t + ab);
+  }
+  tblk.clear();
+  tblk.shrink_to_fit();
+
+  // ---- overlapping subdomains, local patterns, ILU(0) maps, levels --------
+  const int delta = std::max(0, opt->overlap);
+  std::vector<int32_t> loc(n, -1);   // internal node -> local row (current subdomain)
+  std::vector<int32_t> mark(n, -1);  // BFS stamp
+  hs.sd_row0.assign(P + 1, 0);
+  hs.l_row_ptr.assign(1, 0);
+  hs.sd_fwd_lev0.assign(1, 0);
+  hs.sd_bwd_lev0.assign(1, 0);
+  hs.upd_ptr.assign(1, 0);
+  std::vector<int32_t> nodes, front, next, lev, lb;
+  std::vector<int64_t> rowpos;  // local col -> absolute block index in the current row (stamp)
+  for (int32_t q = 0; q < P; ++q) {
+    nodes.clear();
+    front.clear();
+    for (int32_t i = hs.own_ptr[q]; i < hs.own_ptr[q + 1]; ++i) {
+      nodes.push_back(i);
+      front.push_back(i);
+      mark[i] = q;
+    }
+    for (int d = 0; d < delta; ++d) {
+      next.clear();
+      for (int32_t i : front)
+        for (int32_t k = hs.row_ptr[i]; k < hs.row_ptr[i + 1]; ++k) {
+          int32_t j = hs.col[k];
+          if (mark[j] != q) {
+            mark[j] = q;
+            next.push_back(j);
+            nodes.push_back(j);
+          }
+        }
+      front.swap(next);
+    }
+    std::sort(nodes.begin(), nodes.end());
+    const int32_t nl = (int32_t)nodes.size();
+    const int32_t r0 = hs.sd_row0[q];
+    hs.sd_row0[q + 1] = r0 + nl;
+    hs.max_sd_rows = std::max(hs.max_sd_rows, nl);
+    for (int32_t l = 0; l < nl; ++l) loc[nodes[l]] = l;
+    // local BSR rows (restriction of J's rows to the subdomain keeps column order)
+    const int64_t base = hs.l_row_ptr.back();
+    int64_t pos = base;
+    std::vector<int64_t> rstart(nl + 1);
+    for (int32_t l = 0; l < nl; ++l) {
+      rstart[l] = pos;
+      const int32_t g = nodes[l];
+      for (int32_t k = hs.row_ptr[g]; k < hs.row_ptr[g + 1]; ++k) {
+        int32_t j = hs.col[k];
+        if (mark[j] == q) {
+          hs.l_col.push_back(loc[j]);
+          hs.l_gblk.push_back(k);
+          if (j == g) hs.l_diag.push_back(pos);
+          ++pos;
+        }
+      }
+      hs.sd_node.push_back(g);
+      hs.l_row_ptr.push_back(pos);
+    }
+    rstart[nl] = pos;
+    // ILU(0) update pairs: for lower block (i,k): every (k,j) with j > k and (i,j) present
+    rowpos.assign(nl, -1);
+    for (int32_t i = 0; i < nl; ++i) {
+      for (int64_t a = rstart[i]; a < rstart[i + 1]; ++a) rowpos[hs.l_col[a]] = a;
+      for (int64_t a = rstart[i]; a < rstart[i + 1]; ++a) {
+        const int32_t k = hs.l_col[a];
+        if (k < i) {
+          for (int64_t b = rstart[k]; b < rstart[k + 1]; ++b) {
+            const int32_t j = hs.l_col[b];
+            if (j > k && rowpos[j] >= 0) {
+              hs.upd.push_back(rowpos[j]);
+              hs.upd.push_back(b);
+            }
+          }
+        }
+        hs.upd_ptr.push_back((int64_t)hs.upd.size() / 2);
+      }
+      for (int64_t a = rstart[i]; a < rstart[i + 1]; ++a) rowpos[hs.l_col[a]] = -1;
+    }
+    // forward levels (lower triangle) and backward levels (upper triangle)
+    for (int dir = 0; dir < 2; ++dir) {
+      lev.assign(nl, 0);
+      int32_t nlev = 0;
+      if (dir == 0) {
+        for (int32_t i = 0; i < nl; ++i) {
+          int32_t lv = 0;
+          for (int64_t a = rstart[i]; a < rstart[i + 1]; ++a)
+            if (hs.l_col[a] < i) lv = std::max(lv, lev[hs.l_col[a]] + 1);
+          lev[i] = lv;
+          nlev = std::max(nlev, lv + 1);
+        }
+      } else {
+        for (int32_t i = nl - 1; i >= 0; --i) {
+          int32_t lv = 0;
+          for (int64_t a = rstart[i]; a < rstart[i + 1]; ++a)
+            if (hs.l_col[a] > i) lv = std::max(lv, lev[hs.l_col[a]] + 1);
+          lev[i] = lv;
+          nlev = std::max(nlev, lv + 1);
+        }
+      }
+      hs.max_levels = std::max(hs.max_levels, nlev);
+      lb.assign(nlev + 1, 0);
+      for (int32_t i = 0; i < nl; ++i) lb[lev[i] + 1]++;
+      for (int32_t v = 0; v < nlev; ++v) lb[v + 1] += lb[v];
+      std::vector<int32_t>& order = dir == 0 ? hs.fwd_order : hs.bwd_order;
+      std::vector<int32_t>& levs = dir == 0 ? hs.fwd_lev : hs.bwd_lev;
+      std::vector<int32_t>& lev0 = dir == 0 ? hs.sd_fwd_lev0 : hs.sd_bwd_lev0;
+      const size_t o0 = order.size();
+      order.resize(o0 + nl);
+      std::vector<int32_t> fill(lb.begin(), lb.end() - 1);
+      if (dir == 0) {
+        for (int32_t i = 0; i < nl; ++i) order[o0 + fill[lev[i]]++] = i;
+      } else {
+        for (int32_t i = nl - 1; i >= 0; --i) order[o0 + fill[lev[i]]++] = i;
+      }
+      levs.insert(levs.end(), lb.begin(), lb.end());
+      lev0.push_back((int32_t)levs.size());
+    }
+    for (int32_t l = 0; l < nl; ++l) loc[nodes[l]] = -1;
+  }
+  if ((int64_t)hs.l_diag.size() != (int64_t)hs.sd_node.size()) {
+    err = "internal error: missing diagonal block in a subdomain";
+    return SEIRD_EINVAL;
+  }
+
+  // ---- coarse pattern: subdomain graph, RCM order, band, segment sums -----
+  {
+    std::vector<std::vector<int32_t>> adj(P);
+    std::vector<int64_t> pq;
+    pq.reserve(nnzb);
+    for (int64_t i = 0; i < n; ++i)
+      for (int32_t k = hs.row_ptr[i]; k < hs.row_ptr[i + 1]; ++k) {
+        int32_t a = hs.owner[i], b = hs.owner[hs.col[k]];
+        if (a != b) pq.push_back((int64_t)a * P + b);
+      }
+    std::sort(pq.begin(), pq.end());
+    pq.erase(std::unique(pq.begin(), pq.end()), pq.end());
+    for (int64_t v : pq) adj[v / P].push_back((int32_t)(v % P));
+    std::vector<int32_t> ord = rcm(adj);
+    hs.cpos.assign(P, 0);
+    for (int32_t k = 0; k < P; ++k) hs.cpos[ord[k]] = k;
+    int32_t band = 0;
+    for (int64_t v : pq) band = std::max(band, std::abs(hs.cpos[v / P] - hs.cpos[v % P]));
+    hs.cband = band;
+    const int64_t W = 2 * (int64_t)band + 1;
+    // J blocks ordered by (cpos[owner(row)], cpos[owner(col)], block id)
+    std::vector<int64_t> key(nnzb);
+    std::vector<int32_t> rowof(nnzb);
+    for (int64_t i = 0; i < n; ++i)
+      for (int32_t k = hs.row_ptr[i]; k < hs.row_ptr[i + 1]; ++k) rowof[k] = (int32_t)i;
+    hs.cseg_blk.resize(nnzb);
+    std::iota(hs.cseg_blk.begin(), hs.cseg_blk.end(), 0);
+    for (int64_t k = 0; k < nnzb; ++k)
+      key[k] = (int64_t)hs.cpos[hs.owner[rowof[k]]] * P + hs.cpos[hs.owner[hs.col[k]]];
+    std::stable_sort(hs.cseg_blk.begin(), hs.cseg_blk.end(), [&](int32_t a, int32_t b) { return key[a] < key[b]; });
+    const int32_t CH = 256;  // blocks per chunk
+    hs.cchunk_ptr.assign(1, 0);
+    hs.cdst_ptr.assign(1, 0);
+    int64_t s = 0;
+    while (s < nnzb) {
+      int64_t e = s;
+      const int64_t kk = key[hs.cseg_blk[s]];
+      while (e < nnzb && key[hs.cseg_blk[e]] == kk) ++e;
+      for (int64_t c = s; c < e; c += CH) hs.cchunk_ptr.push_back((int32_t)std::min<int64_t>(e, c + CH));
+      hs.cdst_ptr.push_back((int32_t)hs.cchunk_ptr.size() - 1);
+      const int64_t pr = kk / P, qc = kk % P;
+      hs.cdst_idx.push_back(pr * W + (qc - pr + band));
+      s = e;
+    }
+  }
+  return SEIRD_OK;
+}
+
+}  // namespace seird

@@ -59,13 +59,15 @@ def params_square(**over) -> Params:
     return p
 
 
-def params_ontario(mean_density: float, **over) -> Params:
-    """Table 1, "Southern Ontario" column; beta is chosen so that beta*mean(N) = 0.756/day.
+def params_ontario(max_density: float, **over) -> Params:
+    """Table 1, "Southern Ontario" column; beta is chosen so that beta*max(N) = 0.756/day.
 
     The paper fits the Ontario betas (Eq. beta_ie/beta_x) to case data it does not
-    publish; 0.756/day is the square case's beta*N (3.78e-4 * 2000).
+    publish; 0.756/day is the square case's beta*N (3.78e-4 * 2000).  Scaling by
+    the densest city makes that city grow at the square case's rate and every
+    less dense place slower (transmission is density dependent).
     """
-    beta = 0.756 / mean_density
+    beta = 0.756 / max_density
     p = Params(A=8.9e-3, beta_i=beta, beta_e=beta, sigma=1.0 / 5.0, gamma_e=1.0 / 15.0,
                gamma_r=1.0 / 11.0, gamma_d=1.0 / 750.0, alpha=0.0, mu=0.0,
                nu=(4.5e-7, 4.5e-7, 1e-9, 4.5e-7))
@@ -393,6 +395,6 @@ def ontario_workload(n_target: int = 2_000_000, seed: int = 0, n_subdomains: int
         name = "ontario_like_%dk" % (len(xy) // 1000)
     dens = urban_density(seed, poly)
     U0 = urban_ic(xy, dens, seed)
-    p = params_ontario(float(U0.sum(axis=1).mean()))
+    p = params_ontario(float(U0.sum(axis=1).max()))
     return Workload(name, xy, tri, p, U0, dt=0.5, n_steps=180, n_subdomains=n_subdomains, overlap=overlap,
                     coarse=True, owner=None, seed=seed, extra=dict(polygon=poly))

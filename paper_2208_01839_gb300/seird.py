@@ -1,0 +1,300 @@
+"""Thin ctypes binding of the C ABI declared in include/seird.h.
+
+Argument marshalling only: every step of the SEIRD Newton-Krylov-Schwarz path
+runs in the CUDA library.  Importing this module loads ``_lib/libseird.so`` and
+raises ``ImportError`` when it is missing; there is no fallback.
+
+Device buffers may be passed as torch CUDA tensors (float64, contiguous), host
+buffers as numpy arrays; the ``on_device`` flag of the C ABI is set from the
+argument's type.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libseird.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libseird.so is not built (run __graft_entry__.build() or "
+                      "python -m paper_2208_01839_gb300.build): %s" % LIB_PATH)
+_lib = C.CDLL(LIB_PATH)
+
+OK = 0
+ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENEWTON_DIVERGED", -5: "ENEWTON_MAXIT",
+          -6: "EGMRES", -7: "ENONFINITE", -8: "ETIMEOUT", -9: "ESINGULAR"}
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int32)
+
+
+class Mesh(C.Structure):
+    _fields_ = [("n_nodes", C.c_int64), ("n_tris", C.c_int64), ("xy", _dp), ("tri", _ip)]
+
+
+class Params(C.Structure):
+    _fields_ = [("A", C.c_double), ("beta_i", C.c_double), ("beta_e", C.c_double), ("sigma", C.c_double),
+                ("gamma_e", C.c_double), ("gamma_r", C.c_double), ("gamma_d", C.c_double),
+                ("alpha", C.c_double), ("mu", C.c_double), ("nu", C.c_double * 4), ("beta_field", _dp)]
+
+
+class Options(C.Structure):
+    _fields_ = [("dt", C.c_double), ("newton_rtol", C.c_double), ("newton_atol", C.c_double),
+                ("newton_maxit", C.c_int32), ("ls_maxit", C.c_int32), ("gmres_restart", C.c_int32),
+                ("gmres_maxit", C.c_int32), ("gmres_rtol", C.c_double), ("gmres_atol", C.c_double),
+                ("gmres_dtol", C.c_double), ("n_subdomains", C.c_int32), ("overlap", C.c_int32),
+                ("coarse", C.c_int32), ("precision", C.c_int32), ("quadrature", C.c_int32),
+                ("pc_lag", C.c_int32), ("owner", _ip), ("seed", C.c_uint64), ("stream", C.c_void_p),
+                ("timing", C.c_int32)]
+
+
+KERNEL_CLASSES = ["residual", "jacobian", "ilu_factor", "coarse_setup", "spmv", "ilu_solve", "coarse_apply", "krylov"]
+
+
+class Stats(C.Structure):
+    _fields_ = [("newton_its", C.c_int32), ("gmres_its", C.c_int32), ("ls_halvings", C.c_int32),
+                ("pc_setups", C.c_int32), ("res0", C.c_double), ("res_final", C.c_double),
+                ("eps_update", C.c_double), ("ms_assemble", C.c_double), ("ms_setup", C.c_double),
+                ("ms_solve", C.c_double), ("ms_total", C.c_double), ("kernel_ms", C.c_double * 8),
+                ("kernel_calls", C.c_int32 * 8)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("kernel_ms", "kernel_calls")}
+        d["kernel_ms"] = {KERNEL_CLASSES[i]: self.kernel_ms[i] for i in range(8)}
+        d["kernel_calls"] = {KERNEL_CLASSES[i]: self.kernel_calls[i] for i in range(8)}
+        return d
+
+
+class Info(C.Structure):
+    _fields_ = [("n_nodes", C.c_int64), ("n_tris", C.c_int64), ("nnzb", C.c_int64), ("n_subdomains", C.c_int32),
+                ("subdomain_rows", C.c_int64), ("subdomain_blocks", C.c_int64), ("max_levels", C.c_int32),
+                ("coarse_band", C.c_int32), ("device_bytes", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def _sig(name, res, args):
+    f = getattr(_lib, name)
+    f.restype = res
+    f.argtypes = args
+    return f
+
+
+_vp = C.c_void_p
+_default_options = _sig("seird_default_options", None, [C.POINTER(Options)])
+_create = _sig("seird_create", C.c_int, [C.POINTER(Mesh), C.POINTER(Params), C.POINTER(Options), C.POINTER(_vp)])
+_destroy = _sig("seird_destroy", None, [_vp])
+_last_error = _sig("seird_last_error", C.c_char_p, [_vp])
+_set_state = _sig("seird_set_state", C.c_int, [_vp, _vp, C.c_int, C.c_double])
+_get_state = _sig("seird_get_state", C.c_int, [_vp, _vp, C.c_int, C.POINTER(C.c_double)])
+_step = _sig("seird_step", C.c_int, [_vp, C.POINTER(Stats)])
+_run = _sig("seird_run", C.c_int, [_vp, C.c_int32, C.POINTER(Stats)])
+_get_info = _sig("seird_get_info", C.c_int, [_vp, C.POINTER(Info)])
+_eval_residual = _sig("seird_eval_residual", C.c_int, [_vp, _vp, _vp, _vp, C.c_int])
+_eval_jacobian = _sig("seird_eval_jacobian", C.c_int, [_vp, _vp, C.c_int])
+_get_jacobian = _sig("seird_get_jacobian", C.c_int, [_vp, _vp, _vp, _vp])
+_apply_jacobian = _sig("seird_apply_jacobian", C.c_int, [_vp, _vp, _vp, C.c_int])
+_precond_setup = _sig("seird_precond_setup", C.c_int, [_vp])
+_precond_apply = _sig("seird_precond_apply", C.c_int, [_vp, _vp, _vp, C.c_int])
+_linear_solve = _sig("seird_linear_solve", C.c_int, [_vp, _vp, _vp, C.c_int, C.POINTER(C.c_int32)])
+_bsr_spmv = _sig("seird_bsr_spmv", C.c_int, [C.c_int64, _vp, _vp, _vp, _vp, _vp, _vp])
+_bsr_spmv_f32 = _sig("seird_bsr_spmv_f32val", C.c_int, [C.c_int64, _vp, _vp, _vp, _vp, _vp, _vp])
+_launch_count = _sig("seird_launch_count", C.c_int64, [])
+
+
+class SeirdError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "E?"), code, msg))
+        self.code = code
+
+
+def default_options(**over) -> Options:
+    o = Options()
+    _default_options(C.byref(o))
+    for k, v in over.items():
+        setattr(o, k, v)
+    return o
+
+
+def launch_count() -> int:
+    return int(_launch_count())
+
+
+def _ptr(a):
+    """(address, on_device) of a numpy array or a torch tensor."""
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data, 0
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), int(a.is_cuda)
+    raise TypeError("expected a numpy array or a torch tensor")
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def bsr_spmv(row_ptr, col, val, x, y, stream=None):
+    """y = A x for 5x5-block BSR device tensors (val float64 or float32)."""
+    n_rows = row_ptr.numel() - 1
+    fn = _bsr_spmv if str(val.dtype).endswith("float64") else _bsr_spmv_f32
+    rc = fn(n_rows, row_ptr.data_ptr(), col.data_ptr(), val.data_ptr(), x.data_ptr(), y.data_ptr(),
+            _stream_handle(stream))
+    if rc != OK:
+        raise SeirdError(rc, "bsr_spmv launch failed")
+
+
+class Solver:
+    """One SEIRD context: mesh, parameters and options live on the device."""
+
+    def __init__(self, xy, tri, params, options: Options | None = None, beta_field=None, owner=None, stream=None,
+                 **opt_over):
+        self._xy = np.ascontiguousarray(xy, dtype=np.float64)
+        self._tri = np.ascontiguousarray(tri, dtype=np.int32)
+        self.n = len(self._xy)
+        mesh = Mesh(self.n, len(self._tri), self._xy.ctypes.data_as(_dp), self._tri.ctypes.data_as(_ip))
+        p = Params()
+        pd = params.as_dict() if hasattr(params, "as_dict") else dict(params)
+        for k in ("A", "beta_i", "beta_e", "sigma", "gamma_e", "gamma_r", "gamma_d", "alpha", "mu"):
+            setattr(p, k, float(pd[k]))
+        for c in range(4):
+            p.nu[c] = float(pd["nu"][c])
+        self._bf = None
+        if beta_field is not None:
+            self._bf = np.ascontiguousarray(beta_field, dtype=np.float64)
+            p.beta_field = self._bf.ctypes.data_as(_dp)
+        o = options if options is not None else default_options()
+        for k, v in opt_over.items():
+            setattr(o, k, v)
+        self._owner = None
+        if owner is not None:
+            self._owner = np.ascontiguousarray(owner, dtype=np.int32)
+            o.owner = self._owner.ctypes.data_as(_ip)
+        if stream is not None:
+            o.stream = _stream_handle(stream)
+        self.options = o
+        h = _vp()
+        rc = _create(C.byref(mesh), C.byref(p), C.byref(o), C.byref(h))
+        if rc != OK:
+            raise SeirdError(rc, _last_error(None).decode())
+        self._h = h
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            _destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _check(self, rc):
+        if rc != OK:
+            raise SeirdError(rc, _last_error(self._h).decode())
+
+    # -- state
+    def set_state(self, u, t=0.0):
+        p, dev = _ptr(u)
+        self._check(_set_state(self._h, p, dev, float(t)))
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.empty((self.n, 5))
+        p, dev = _ptr(out)
+        t = C.c_double()
+        self._check(_get_state(self._h, p, dev, C.byref(t)))
+        self.t = t.value
+        return out
+
+    def step(self):
+        st = Stats()
+        self._check(_step(self._h, C.byref(st)))
+        return st.as_dict()
+
+    def run(self, n_steps):
+        arr = (Stats * max(1, n_steps))()
+        self._check(_run(self._h, int(n_steps), arr))
+        return [arr[k].as_dict() for k in range(n_steps)]
+
+    def info(self):
+        inf = Info()
+        self._check(_get_info(self._h, C.byref(inf)))
+        return inf.as_dict()
+
+    # -- components
+    def residual(self, u, u_prev, out=None):
+        if out is None:
+            out = np.empty((self.n, 5)) if isinstance(u, np.ndarray) else u.new_empty(u.shape)
+        a, dev = _ptr(u)
+        b, _ = _ptr(u_prev)
+        c, _ = _ptr(out)
+        self._check(_eval_residual(self._h, a, b, c, dev))
+        return out
+
+    def jacobian(self, u):
+        a, dev = _ptr(u)
+        self._check(_eval_jacobian(self._h, a, dev))
+
+    def get_jacobian(self):
+        nnzb = self.info()["nnzb"]
+        rp = np.empty(self.n + 1, dtype=np.int32)
+        col = np.empty(nnzb, dtype=np.int32)
+        val = np.empty((nnzb, 5, 5))
+        self._check(_get_jacobian(self._h, rp.ctypes.data, col.ctypes.data, val.ctypes.data))
+        return rp, col, val
+
+    def apply_jacobian(self, x, out=None):
+        if out is None:
+            out = np.empty_like(x) if isinstance(x, np.ndarray) else x.new_empty(x.shape)
+        a, dev = _ptr(x)
+        b, _ = _ptr(out)
+        self._check(_apply_jacobian(self._h, a, b, dev))
+        return out
+
+    def precond_setup(self):
+        self._check(_precond_setup(self._h))
+
+    def precond_apply(self, r, out=None):
+        if out is None:
+            out = np.empty_like(r) if isinstance(r, np.ndarray) else r.new_empty(r.shape)
+        a, dev = _ptr(r)
+        b, _ = _ptr(out)
+        self._check(_precond_apply(self._h, a, b, dev))
+        return out
+
+    def linear_solve(self, b, out=None):
+        if out is None:
+            out = np.empty_like(b) if isinstance(b, np.ndarray) else b.new_empty(b.shape)
+        a, dev = _ptr(b)
+        c, _ = _ptr(out)
+        its = C.c_int32()
+        self._check(_linear_solve(self._h, a, c, dev, C.byref(its)))
+        return out, its.value
+
+
+def declared_functions(header_path=None):
+    """Names of the functions declared in include/seird.h."""
+    import re
+    header_path = header_path or os.path.join(_HERE, "..", "include", "seird.h")
+    txt = open(header_path).read()
+    return sorted(set(re.findall(r"\b(seird_[a-z0-9_]+)\s*\(", txt)))

@@ -1,0 +1,277 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Tolerances (FP64 on both sides, different summation orders):
+  * assembly, SpMV: |diff| <= 1e-12 x (magnitude of the summed terms);
+  * preconditioner apply: 1e-10 relative (triangular solves amplify rounding);
+  * Newton roots: <= 1e-9 relative L2 per compartment (the target stated for
+    the FP64 path), both sides solving to ||F|| <= 1e-12 ||F(u^n)||.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from oracle import seird_oracle as O
+from paper_2208_01839_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+from paper_2208_01839_gb300 import build as _b  # noqa: E402
+
+_b.build()
+from paper_2208_01839_gb300 import seird as S  # noqa: E402
+
+DEV = "cuda"
+
+
+def rel_l2_per_comp(a, b):
+    return [float(np.linalg.norm(a[:, c] - b[:, c]) / max(np.linalg.norm(b[:, c]), 1e-300)) for c in range(5)]
+
+
+def newton_floor(wl):
+    """Absolute Newton tolerance at the FP64 rounding floor: 1e-14 ||M |u^0|||.
+    Where ||F(u^n)|| is small next to ||M u|| (slowly changing states), the
+    relative test alone would ask for a residual below what FP64 can resolve."""
+    return 1e-14 * np.linalg.norm(O.residual(wl.xy, wl.tri, wl.params, 0.0, np.abs(wl.U0), np.zeros_like(wl.U0)))
+
+
+def solver(wl, owner=None, **kw):
+    opts = dict(dt=wl.dt, overlap=wl.overlap, newton_rtol=1e-12, newton_atol=newton_floor(wl), gmres_rtol=1e-12,
+                gmres_restart=30, gmres_maxit=2000)
+    opts.update(kw)
+    return S.Solver(wl.xy, wl.tri, wl.params, owner=wl.owner if owner is None else owner,
+                    beta_field=wl.beta_field, **opts)
+
+
+# ---------------------------------------------------------------------------
+# SpMV
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n_rows,n_cols,bmax,seed", [(0, 0, 1, 0), (1, 1, 1, 1), (7, 5, 4, 2), (1000, 900, 9, 3),
+                                                     (20011, 20011, 8, 4)])
+def test_bsr_spmv_matches_oracle(n_rows, n_cols, bmax, seed):
+    rp, col, val = I.random_bsr(n_rows, n_cols, bmax, seed)
+    x = np.random.default_rng(seed + 1).standard_normal(5 * n_cols)
+    ref = O.bsr_spmv(rp, col, val, x) if n_rows else np.zeros(0)
+    t = lambda a: torch.tensor(a, device=DEV)
+    y = torch.full((5 * n_rows,), np.nan, dtype=torch.float64, device=DEV)
+    S.bsr_spmv(t(rp), t(col), t(val), t(x), y)
+    torch.cuda.synchronize()
+    got = y.cpu().numpy()
+    A = sp.bsr_matrix((np.abs(val), col, rp), shape=(5 * n_rows, 5 * n_cols)) if n_rows else None
+    bound = (A @ np.abs(x)) if n_rows else np.zeros(0)
+    assert np.all(np.abs(got - ref) <= 1e-13 * bound + 1e-300)
+
+
+def test_bsr_spmv_float32_values():
+    rp, col, val = I.random_bsr(3001, 2999, 7, 9)
+    val32 = val.astype(np.float32)
+    x = np.random.default_rng(10).standard_normal(5 * 2999)
+    ref = O.bsr_spmv(rp, col, val32.astype(np.float64), x)
+    t = lambda a: torch.tensor(a, device=DEV)
+    y = torch.empty(5 * 3001, dtype=torch.float64, device=DEV)
+    S.bsr_spmv(t(rp), t(col), t(val32), t(x), y)
+    torch.cuda.synchronize()
+    A = sp.bsr_matrix((np.abs(val), col, rp), shape=(5 * 3001, 5 * 2999))
+    assert np.all(np.abs(y.cpu().numpy() - ref) <= 1e-13 * (A @ np.abs(x)))
+
+
+# ---------------------------------------------------------------------------
+# assembly
+# ---------------------------------------------------------------------------
+
+def _mass_scale(wl, U):
+    """max_i (M |U|)_i: the magnitude of the terms each residual entry sums."""
+    Mabs = O.residual(wl.xy, wl.tri, wl.params, 0.0, np.abs(U), np.zeros_like(U))
+    return np.abs(Mabs).max()
+
+
+def _workloads():
+    sq = I.square_workload(33)
+    irr_xy, irr_tri, _ = I.irregular_mesh(3, 3000)
+    dens = I.urban_density(3)
+    U0 = I.urban_ic(irr_xy, dens, 3)
+    p = I.params_ontario(float(U0.sum(axis=1).max()))
+    irr = I.Workload("irregular3k", irr_xy, irr_tri, p, U0, dt=0.5, n_steps=3, n_subdomains=6, overlap=2,
+                     coarse=True, owner=I.box_partition(irr_xy, 3, 2), beta_field=I.smooth_field(irr_xy, 3))
+    return {"square33": sq, "irregular3k": irr}
+
+
+WL = _workloads()
+
+
+@pytest.mark.parametrize("name", list(WL))
+@pytest.mark.parametrize("rule", [0, 1])
+def test_residual_matches_oracle(name, rule):
+    wl = WL[name]
+    rng = np.random.default_rng(5)
+    U = wl.U0 * (1.0 + 0.05 * rng.standard_normal(wl.U0.shape)) + 1.0
+    ref = O.residual(wl.xy, wl.tri, wl.params, wl.dt, U, wl.U0, bfield=wl.beta_field,
+                     rule="deg5" if rule == 0 else "vertex")
+    with solver(wl, quadrature=rule) as sv:
+        got = sv.residual(U, wl.U0)
+        # device pointers give the same result as host pointers
+        gt = sv.residual(torch.tensor(U, device=DEV), torch.tensor(wl.U0, device=DEV)).cpu().numpy()
+    scale = _mass_scale(wl, U) * (1.0 + wl.dt)
+    assert np.abs(got - ref).max() <= 1e-12 * scale
+    assert np.array_equal(got, gt)
+
+
+@pytest.mark.parametrize("name", list(WL))
+def test_jacobian_matches_oracle(name):
+    wl = WL[name]
+    rng = np.random.default_rng(6)
+    U = wl.U0 * (1.0 + 0.05 * rng.standard_normal(wl.U0.shape)) + 1.0
+    J = O.jacobian(wl.xy, wl.tri, wl.params, wl.dt, U, bfield=wl.beta_field)
+    rp, col, val = O.to_bsr(J)
+    with solver(wl) as sv:
+        sv.jacobian(U)
+        grp, gcol, gval = sv.get_jacobian()
+        x = rng.standard_normal(U.shape)
+        y = sv.apply_jacobian(x)
+    assert np.array_equal(grp, rp) and np.array_equal(gcol, col)
+    scale = np.abs(val).max()
+    assert np.abs(gval - val).max() <= 1e-12 * scale
+    ref = (J @ x.ravel()).reshape(U.shape)
+    Jabs = abs(J)
+    assert np.all(np.abs(y - ref).ravel() <= 1e-12 * (Jabs @ np.abs(x).ravel()) + 1e-300)
+
+
+# ---------------------------------------------------------------------------
+# preconditioner and linear solve
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("overlap,coarse", [(0, 0), (1, 0), (2, 1), (1, 1)])
+def test_ras_apply_matches_oracle(overlap, coarse):
+    wl = I.square_workload(17)
+    owner = I.box_partition(wl.xy, 3, 2)
+    J = O.jacobian(wl.xy, wl.tri, wl.params, wl.dt, wl.U0)
+    rp, col, val = O.to_bsr(J)
+    r = np.random.default_rng(7).standard_normal(5 * wl.n)
+    ref = O.ras_apply(rp, col, val, owner, overlap, r, coarse=bool(coarse))
+    with solver(wl, owner=owner, overlap=overlap, coarse=coarse) as sv:
+        sv.jacobian(wl.U0)
+        sv.precond_setup()
+        got = sv.precond_apply(r.reshape(-1, 5)).ravel()
+    assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+def test_ras_apply_irregular_partition_with_coarse():
+    wl = WL["irregular3k"]
+    owner = I.random_partition(wl.n, 5, 3)  # non-geometric parts: many neighbours, wide coarse band
+    J = O.jacobian(wl.xy, wl.tri, wl.params, wl.dt, wl.U0, bfield=wl.beta_field)
+    rp, col, val = O.to_bsr(J)
+    r = np.random.default_rng(8).standard_normal(5 * wl.n)
+    ref = O.ras_apply(rp, col, val, owner, 1, r, coarse=True)
+    with solver(wl, owner=owner, overlap=1, coarse=1) as sv:
+        sv.jacobian(wl.U0)
+        sv.precond_setup()
+        got = sv.precond_apply(r.reshape(-1, 5)).ravel()
+    assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+def test_linear_solve_matches_direct_solve():
+    wl = WL["irregular3k"]
+    J = O.jacobian(wl.xy, wl.tri, wl.params, wl.dt, wl.U0, bfield=wl.beta_field)
+    b = np.random.default_rng(9).standard_normal(5 * wl.n)
+    ref = spla.spsolve(J.tocsc(), b)
+    with solver(wl, coarse=1, gmres_restart=20) as sv:
+        sv.jacobian(wl.U0)
+        sv.precond_setup()
+        x, its = sv.linear_solve(b.reshape(-1, 5))
+    assert its > 0
+    assert np.linalg.norm(x.ravel() - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
+def test_single_subdomain_without_overlap_is_ilu0():
+    """P = 1, overlap 0: the preconditioner is block ILU(0) of J itself."""
+    wl = I.square_workload(9)
+    J = O.jacobian(wl.xy, wl.tri, wl.params, wl.dt, wl.U0)
+    rp, col, val = O.to_bsr(J)
+    r = np.random.default_rng(3).standard_normal(5 * wl.n)
+    Fk = O.block_ilu0(rp, col, val)
+    ref = O.block_ilu0_solve(rp, col, Fk, r)
+    with solver(wl, owner=np.zeros(wl.n, dtype=np.int32), overlap=0) as sv:
+        sv.jacobian(wl.U0)
+        sv.precond_setup()
+        got = sv.precond_apply(r.reshape(-1, 5)).ravel()
+    assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+# ---------------------------------------------------------------------------
+# Newton steps
+# ---------------------------------------------------------------------------
+
+def test_square_steps_match_oracle_step_by_step():
+    """Config-1 workload (33x33, N = 1e4, dt = 1, 4 box subdomains, overlap 1):
+    every step from the same u^n, and the 10-step trajectory."""
+    wl = I.square_workload(33)
+    U = wl.U0.copy()
+    with solver(wl) as sv:
+        for k in range(wl.n_steps):
+            ref, info = O.newton_step(wl.xy, wl.tri, wl.params, wl.dt, U, rtol=1e-12)
+            sv.set_state(U, t=k * wl.dt)
+            st = sv.step()
+            got = sv.get_state()
+            assert max(rel_l2_per_comp(got, ref)) <= 1e-9, (k, rel_l2_per_comp(got, ref), st)
+            U = ref
+        # whole trajectory from u^0 on the device
+        sv.set_state(wl.U0)
+        sv.run(wl.n_steps)
+        traj = sv.get_state()
+    assert max(rel_l2_per_comp(traj, U)) <= 1e-9
+
+
+def test_paper_density_irregular_with_coarse_and_field():
+    wl = WL["irregular3k"]
+    U_ref, _ = O.run(wl.xy, wl.tri, wl.params, wl.dt, wl.U0, 3, rtol=1e-12, atol=newton_floor(wl),
+                     bfield=wl.beta_field)
+    with solver(wl, coarse=1) as sv:
+        sv.set_state(torch.tensor(wl.U0, device=DEV))
+        sv.run(3)
+        got = sv.get_state(torch.empty((wl.n, 5), dtype=torch.float64, device=DEV)).cpu().numpy()
+    assert max(rel_l2_per_comp(got, U_ref)) <= 1e-9
+
+
+def test_default_partitioner_and_vertex_rule():
+    """Built-in seeded bisection (no owner array) and the three-vertex rule."""
+    wl = I.square_workload(33, N0=2000.0)
+    U_ref, _ = O.run(wl.xy, wl.tri, wl.params, wl.dt, wl.U0, 2, rtol=1e-12, rule="vertex")
+    with S.Solver(wl.xy, wl.tri, wl.params, dt=wl.dt, n_subdomains=7, overlap=2, coarse=1, quadrature=1,
+                  newton_rtol=1e-12, newton_atol=newton_floor(wl), gmres_rtol=1e-12, gmres_maxit=2000) as sv:
+        sv.set_state(wl.U0)
+        sv.run(2)
+        got = sv.get_state()
+        inf = sv.info()
+    assert inf["n_subdomains"] == 7 and inf["coarse_band"] >= 1
+    assert max(rel_l2_per_comp(got, U_ref)) <= 1e-9
+
+
+def test_smallest_mesh_one_triangle():
+    xy = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]])
+    tri = np.array([[0, 1, 2]], dtype=np.int32)
+    p = I.params_square()
+    U0 = np.array([[1800.0, 10.0, 100.0, 0.0, 0.0], [1900.0, 0.0, 50.0, 0.0, 0.0], [2000.0, 0.0, 0.0, 0.0, 0.0]])
+    ref, _ = O.newton_step(xy, tri, p, 0.5, U0, rtol=1e-12)
+    with S.Solver(xy, tri, p, dt=0.5, n_subdomains=1, newton_rtol=1e-12, gmres_rtol=1e-13) as sv:
+        sv.set_state(U0)
+        sv.step()
+        got = sv.get_state()
+    assert np.abs(got - ref).max() <= 1e-9 * np.abs(ref).max()
+
+
+def test_nonpositive_density_is_reported_not_trapped():
+    """Host-prepared state with N < 0: the assembly flags it and the call
+    returns ENONFINITE; the context stays usable."""
+    wl = I.square_workload(9)
+    with solver(wl) as sv:
+        bad = -np.ones_like(wl.U0)
+        with pytest.raises(S.SeirdError) as e:
+            sv.residual(bad, bad)
+        assert e.value.code == -7
+        ok = sv.residual(wl.U0, wl.U0)
+        assert np.isfinite(ok).all()
