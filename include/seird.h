@@ -234,6 +234,44 @@ int seird_bsr_spmv_f32val(int64_t n_rows, const int32_t* row_ptr, const int32_t*
 /* Number of kernels the library has launched in this process so far. */
 int64_t seird_launch_count(void);
 
+/* ---- allocation-free residual --------------------------------------------
+ * For callers that cannot call cudaMalloc (the paper has no counterpart): code
+ * running inside a framework that owns all device memory through its own
+ * arena, or inside a loop that must not allocate (allocation can block, fail
+ * or synchronise).  Such a caller cannot create a context, because
+ * seird_create allocates.  This entry point evaluates F(u; u_prev) of Eq.
+ * weakform -- the same two-phase element/gather computation as
+ * seird_eval_residual -- on a mesh held entirely in caller-owned device
+ * memory, and allocates nothing: its element scratch is one fixed file-scope
+ * device array of SEIRD_NOALLOC_MAX_TRIS triangles (15 doubles each, about
+ * 7.9 MB), which every GPU that loads the library keeps until the process
+ * exits.
+ *
+ * Arguments (all pointers are device pointers except params):
+ *   xy [n_nodes][2], tri [n_tris][3] (counter-clockwise), and the node
+ *   incidence in CSR form: inc_ptr [n_nodes+1], inc [3*n_tris] holding
+ *   3*t + a for every triangle t and corner a, grouped by node and ascending
+ *   in t within a node (the summation order of each F entry);
+ *   params: host struct; params->beta_field is ignored, beta_field_dev is the
+ *   optional device [n_nodes] transmission multiplier (NULL means 1);
+ *   u, u_prev, F: [n_nodes][5] in the mesh's numbering; norm2 (nullable):
+ *   receives ||F||_2^2.  quadrature as in seird_options.
+ * Limits: n_tris <= SEIRD_NOALLOC_MAX_TRIS and n_nodes <= SEIRD_NOALLOC_MAX_NODES,
+ * else SEIRD_EINVAL with a message in seird_last_error(NULL).
+ * Behaviour: runs on `stream` and synchronises it before returning, then
+ * returns SEIRD_ENONFINITE if N <= 0 at a quadrature point.  The first call
+ * on a device looks up the scratch array's device address (a one-time set-up
+ * per device, with that device current); make that first call before any
+ * stream capture.  Every call shares the one scratch array, whose contents
+ * are left over from the last call; calls that overlap on the GPU (other
+ * streams, other host threads) race on it and must be serialised by the caller. */
+#define SEIRD_NOALLOC_MAX_TRIS 65536
+#define SEIRD_NOALLOC_MAX_NODES 65536
+int seird_residual_noalloc(int64_t n_nodes, int64_t n_tris, const double* xy, const int32_t* tri,
+                           const int32_t* inc_ptr, const int32_t* inc, const seird_params* params,
+                           const double* beta_field_dev, double dt, int32_t quadrature, const double* u,
+                           const double* u_prev, double* F, double* norm2, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

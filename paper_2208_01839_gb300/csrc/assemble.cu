@@ -6,7 +6,10 @@
 //                  the incident triangles, lists built at setup.
 // All arithmetic is FP64.
 #include <cmath>
+#include <mutex>
+#include <string>
 
+#include "../../include/seird.h"
 #include "kernels.cuh"
 
 namespace seird {
@@ -381,4 +384,87 @@ void launch_jacobian(int64_t nnzb, int64_t m, const int32_t* tri, const double* 
   count_launch();
 }
 
+// ---- allocation-free residual (seird_residual_noalloc) -----------------------
+// Scratch for callers that cannot allocate: element vectors of up to
+// SEIRD_NOALLOC_MAX_TRIS triangles, the per-CTA partial sums of the gather, and
+// the error word.  Host code must not pass the symbol itself to a kernel (on the
+// host it names a stand-in, not device memory); it looks up the device address
+// with cudaGetSymbolAddress once per device.
+// layout: [elements 15*MAX_TRIS][partials][norm slot][error word]
+constexpr int64_t NOALLOC_PARTIALS = (SEIRD_NOALLOC_MAX_NODES + 255) / 256;
+constexpr int64_t NOALLOC_WORDS = 15 * (int64_t)SEIRD_NOALLOC_MAX_TRIS + NOALLOC_PARTIALS + 2;
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_WORDS];
+
+namespace {
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[64] = {};
+}  // namespace
+
 }  // namespace seird
+
+extern "C" int seird_residual_noalloc(int64_t n_nodes, int64_t n_tris, const double* xy, const int32_t* tri,
+                                      const int32_t* inc_ptr, const int32_t* inc, const seird_params* params,
+                                      const double* beta_field_dev, double dt, int32_t quadrature, const double* u,
+                                      const double* u_prev, double* F, double* norm2, void* stream) {
+  using namespace seird;
+  auto fail = [](int code, const std::string& m) {
+    set_global_error(m);
+    return code;
+  };
+  if (n_nodes < 3 || n_tris < 1 || !xy || !tri || !inc_ptr || !inc || !params || !u || !u_prev || !F)
+    return fail(SEIRD_EINVAL, "seird_residual_noalloc: NULL argument or empty mesh");
+  if (n_tris > SEIRD_NOALLOC_MAX_TRIS || n_nodes > SEIRD_NOALLOC_MAX_NODES)
+    return fail(SEIRD_EINVAL, "seird_residual_noalloc: mesh exceeds the fixed scratch (at most " +
+                                  std::to_string(SEIRD_NOALLOC_MAX_TRIS) + " triangles and " +
+                                  std::to_string(SEIRD_NOALLOC_MAX_NODES) + " nodes)");
+  if (!(dt >= 0) || (quadrature != 0 && quadrature != 1))
+    return fail(SEIRD_EINVAL, "seird_residual_noalloc: bad dt or quadrature");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= 64)
+    return fail(SEIRD_ECUDA, std::string("seird_residual_noalloc: cudaGetDevice: ") + cudaGetErrorString(e));
+  double* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {  // one-time set-up on this device (the device is current)
+      void* p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess)
+        return fail(SEIRD_ECUDA, std::string("seird_residual_noalloc: cudaGetSymbolAddress: ") +
+                                     cudaGetErrorString(e));
+      upload_quadrature();
+      g_noalloc_ptr[dev] = static_cast<double*>(p);
+    }
+    base = g_noalloc_ptr[dev];
+  }
+  double* elem = base;
+  double* partial = base + 15 * (int64_t)SEIRD_NOALLOC_MAX_TRIS;
+  double* nrm = norm2 ? norm2 : partial + NOALLOC_PARTIALS;  // own slot when the caller wants no norm
+  int32_t* err = reinterpret_cast<int32_t*>(partial + NOALLOC_PARTIALS + 1);
+  const cudaStream_t s = (cudaStream_t)stream;
+  // the error word must start at zero; elements and partials are overwritten
+  e = cudaMemsetAsync(err, 0, sizeof(int32_t), s);
+  if (e != cudaSuccess) return fail(SEIRD_ECUDA, std::string("seird_residual_noalloc: ") + cudaGetErrorString(e));
+  Rates r;
+  r.A = params->A;
+  r.bi = params->beta_i;
+  r.be = params->beta_e;
+  r.sigma = params->sigma;
+  r.ge = params->gamma_e;
+  r.gr = params->gamma_r;
+  r.gd = params->gamma_d;
+  r.alpha = params->alpha;
+  r.mu = params->mu;
+  for (int c = 0; c < 4; ++c) r.nu[c] = params->nu[c];
+  r.dt = dt;
+  launch_residual(n_nodes, n_tris, tri, xy, u, u_prev, beta_field_dev, r, quadrature, elem, inc_ptr, inc, F, partial,
+                  0, nrm, err, s);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(SEIRD_ECUDA, std::string("seird_residual_noalloc: launch: ") + cudaGetErrorString(e));
+  int32_t flags = 0;
+  e = cudaMemcpyAsync(&flags, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(SEIRD_ECUDA, std::string("seird_residual_noalloc: ") + cudaGetErrorString(e));
+  if (flags) return fail(SEIRD_ENONFINITE, "seird_residual_noalloc: N <= 0 at a quadrature point");
+  return SEIRD_OK;
+}

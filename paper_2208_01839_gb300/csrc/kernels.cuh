@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <string>
 
 namespace seird {
 
@@ -22,6 +23,8 @@ constexpr int REC_K = 1, REC_G = 7, REC_P = 19;
 
 void count_launch();
 int64_t launch_total();
+// message returned by seird_last_error(NULL) (per host thread)
+void set_global_error(const std::string& msg);
 
 // quadrature tables are uploaded once per process (degree-5 and vertex rules)
 void upload_quadrature();

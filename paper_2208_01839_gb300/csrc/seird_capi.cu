@@ -32,6 +32,12 @@ namespace {
 
 thread_local std::string g_create_error;
 
+}  // namespace
+
+void seird::set_global_error(const std::string& msg) { g_create_error = msg; }
+
+namespace {
+
 int fail(seird_ctx* ctx, int code, const std::string& msg) {
   if (ctx) ctx->last_error = msg;
   else g_create_error = msg;

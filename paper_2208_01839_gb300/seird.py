@@ -104,6 +104,11 @@ _linear_solve = _sig("seird_linear_solve", C.c_int, [_vp, _vp, _vp, C.c_int, C.P
 _bsr_spmv = _sig("seird_bsr_spmv", C.c_int, [C.c_int64, _vp, _vp, _vp, _vp, _vp, _vp])
 _bsr_spmv_f32 = _sig("seird_bsr_spmv_f32val", C.c_int, [C.c_int64, _vp, _vp, _vp, _vp, _vp, _vp])
 _launch_count = _sig("seird_launch_count", C.c_int64, [])
+_residual_noalloc = _sig("seird_residual_noalloc", C.c_int,
+                         [C.c_int64, C.c_int64, _vp, _vp, _vp, _vp, C.POINTER(Params), _vp, C.c_double, C.c_int32,
+                          _vp, _vp, _vp, _vp, _vp])
+NOALLOC_MAX_TRIS = 65536
+NOALLOC_MAX_NODES = 65536
 
 
 class SeirdError(RuntimeError):
@@ -155,6 +160,32 @@ def bsr_spmv(row_ptr, col, val, x, y, stream=None):
         raise SeirdError(rc, "bsr_spmv launch failed")
 
 
+def params_struct(params) -> Params:
+    """Params structure from an object with ``as_dict()`` or a mapping (beta_field left NULL)."""
+    p = Params()
+    pd = params.as_dict() if hasattr(params, "as_dict") else dict(params)
+    for k in ("A", "beta_i", "beta_e", "sigma", "gamma_e", "gamma_r", "gamma_d", "alpha", "mu"):
+        setattr(p, k, float(pd[k]))
+    for c in range(4):
+        p.nu[c] = float(pd["nu"][c])
+    return p
+
+
+def residual_noalloc(xy, tri, inc_ptr, inc, params, u, u_prev, F, dt, quadrature=0, beta_field=None, norm2=None,
+                     stream=None):
+    """F(u; u_prev) on a mesh held in caller-owned device tensors, without any
+    device allocation by the library (see seird_residual_noalloc in seird.h).
+    All array arguments are CUDA tensors; ``inc_ptr``/``inc`` give each node's
+    incident (3*t + a) entries, ascending in t."""
+    p = params_struct(params)
+    rc = _residual_noalloc(xy.shape[0], tri.shape[0], xy.data_ptr(), tri.data_ptr(), inc_ptr.data_ptr(),
+                           inc.data_ptr(), C.byref(p), None if beta_field is None else beta_field.data_ptr(),
+                           float(dt), int(quadrature), u.data_ptr(), u_prev.data_ptr(), F.data_ptr(),
+                           None if norm2 is None else norm2.data_ptr(), _stream_handle(stream))
+    if rc != OK:
+        raise SeirdError(rc, _last_error(None).decode())
+
+
 class Solver:
     """One SEIRD context: mesh, parameters and options live on the device."""
 
@@ -164,12 +195,7 @@ class Solver:
         self._tri = np.ascontiguousarray(tri, dtype=np.int32)
         self.n = len(self._xy)
         mesh = Mesh(self.n, len(self._tri), self._xy.ctypes.data_as(_dp), self._tri.ctypes.data_as(_ip))
-        p = Params()
-        pd = params.as_dict() if hasattr(params, "as_dict") else dict(params)
-        for k in ("A", "beta_i", "beta_e", "sigma", "gamma_e", "gamma_r", "gamma_d", "alpha", "mu"):
-            setattr(p, k, float(pd[k]))
-        for c in range(4):
-            p.nu[c] = float(pd["nu"][c])
+        p = params_struct(params)
         self._bf = None
         if beta_field is not None:
             self._bf = np.ascontiguousarray(beta_field, dtype=np.float64)
