@@ -34,7 +34,13 @@ FALLBACK_HBM_GBS = 6800.0
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from the committed ncu
 # capture of each kernel class at this workload (profiles/); None until captured
 # or after the kernel changed.
-NCU_TRAFFIC = {}
+# (kernel class, precision) -> (bytes per launch at the captured small case,
+# units processed there, seird_get_info key of those units); scaled to the
+# full launch by the units it processes (traffic grows in proportion).
+NCU_TRAFFIC = {
+    ("spmv", "fp64"): (307.414e6, 1400635, "nnzb"),  # profiles/k_bsr_spmv_ontario200k.md
+    ("ilu_solve", "fp64"): (385.943e6, 1577927, "subdomain_blocks"),  # profiles/k_ilu_solve_ontario200k.md (v3)
+}
 
 # kernel classes with one kernel launch per timed call, and their algorithmic
 # bytes per launch ("Algorithmic bytes")
@@ -50,6 +56,9 @@ def parse():
     ap.add_argument("--nodes", type=int, default=2_000_000)
     ap.add_argument("--subdomains", type=int, default=512)
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--forcing", choices=["fixed", "ew"], default="ew")
+    ap.add_argument("--pc-lag", type=int, default=20)
+    ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -164,6 +173,22 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(x, world, device="cuda"):
+    """Max of a per-rank scalar (elapsed time) over all ranks; identity at N = 1."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_value(dof, steps, seconds, world):
+    """Whole-job DOF*steps/s: every rank advances its own replica by `steps` steps."""
+    return world * dof * steps / seconds
+
+
 def hbm_peak():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -173,16 +198,18 @@ def hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def algorithmic_bytes(cls, info):
-    """Bytes each launch of a kernel class must move at least."""
+def algorithmic_bytes(cls, info, precision="fp64"):
+    """Bytes each launch of a kernel class must move at least; the
+    mixed path stores matrix values, factors and the preconditioned basis in FP32."""
     n, nnzb = info["n_nodes"], info["nnzb"]
     nl, nlb = info["subdomain_rows"], info["subdomain_blocks"]
-    if cls == "spmv":  # values + column indices + row pointers + x once + y once
-        return nnzb * (25 * 8 + 4) + (n + 1) * 4 + 2 * 5 * n * 8
+    w = 4 if precision == "mixed" else 8
+    if cls == "spmv":  # values + column indices + row pointers + x once + y once (FP64)
+        return nnzb * (25 * w + 4) + (n + 1) * 4 + 5 * n * w + 5 * n * 8
     if cls == "ilu_solve":  # factor blocks + columns + inverse diagonals + r gathered + z written
-        return nlb * (25 * 8 + 4) + nl * (25 * 8 + 8 + 16) + nl * 5 * 8 + 5 * n * 8
-    if cls == "ilu_factor":  # J blocks gathered, factor blocks written, inverse diagonals written
-        return nlb * (25 * 8 * 2 + 4 + 4) + nl * 25 * 8
+        return nlb * (25 * w + 4) + nl * (25 * w + 8 + 16) + nl * 5 * 8 + 5 * n * w
+    if cls == "ilu_factor":  # J blocks gathered (FP64), factor blocks written, inverse diagonals written
+        return nlb * (25 * 8 + 25 * w + 4 + 4) + nl * 25 * w
     return None
 
 
@@ -190,8 +217,94 @@ def algorithmic_bytes(cls, info):
 # our arm
 # ---------------------------------------------------------------------------
 
+def measure(S, wl, args, stream, precision, forcing, pc_lag, world, local, e2e=True):
+    """Warm-up, then K device-timed steps (and K end-to-end steps) of one variant."""
+    import torch
+    import torch.distributed as dist
+    sv = S.Solver(wl.xy, wl.tri, wl.params, stream=stream, dt=wl.dt, n_subdomains=args.subdomains, overlap=2,
+                  coarse=1, newton_rtol=1e-8, gmres_rtol=1e-5, gmres_restart=30, gmres_maxit=200,
+                  precision=1 if precision == "mixed" else 0, seed=args.seed, timing=1,
+                  gmres_forcing=1 if forcing == "ew" else 0, pc_lag=pc_lag)
+    info = sv.info()
+    sv.set_state(torch.tensor(wl.U0, device="cuda"))
+    for _ in range(args.warmup):
+        sv.step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    launches0 = S.launch_count()
+    stats = []
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            stats.append(sv.step())
+        e1.record(stream)
+        torch.cuda.synchronize()
+    launches = S.launch_count() - launches0
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        dist.barrier()
+    ms = max_over_ranks(ms, world)
+    dof = 5 * wl.n
+    out = {"value": aggregate_value(dof, args.steps, ms * 1e-3, world), "ms_per_step": ms / args.steps,
+           "launches": launches,
+           "clocks": clk.summary(), "info": info, "stats": stats}
+    if e2e:
+        hbuf = torch.empty((wl.n, 5), dtype=torch.float64, pin_memory=True)
+        sv.get_state(hbuf.numpy())
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            sv.set_state(hbuf.numpy())
+            sv.step()
+            sv.get_state(hbuf.numpy())
+        torch.cuda.synchronize()
+        wall = max_over_ranks(time.perf_counter() - t0, world)
+        out["e2e"] = {"value": aggregate_value(dof, args.steps, wall, world), "unit": UNIT,
+                      "h2d_bytes_per_step": dof * 8,
+                      "d2h_bytes_per_step": dof * 8}
+    sv.close()
+    return out
+
+
+def kernel_summary(S, res):
+    stats, info = res["stats"], res["info"]
+    kms = {k: sum(s["kernel_ms"][k] for s in stats) for k in S.KERNEL_CLASSES}
+    kcalls = {k: sum(s["kernel_calls"][k] for s in stats) for k in S.KERNEL_CLASSES}
+    return kms, kcalls
+
+
+def roofline(S, res, precision):
+    kms, kcalls = kernel_summary(S, res)
+    info = res["info"]
+    peak, peak_kind = hbm_peak()
+    dom = max(SINGLE_KERNEL, key=lambda k: kms[k])
+    ab = algorithmic_bytes(dom, info, precision)
+    avg_ms = kms[dom] / max(kcalls[dom], 1)
+    achieved = ab / (avg_ms * 1e-3) / 1e9
+    traffic = None
+    tr = NCU_TRAFFIC.get((dom, precision))
+    if tr is not None:
+        bytes_small, units_small, unit_key = tr
+        traffic = bytes_small * info[unit_key] / units_small
+    sp_ab = algorithmic_bytes("spmv", info, precision)
+    sp_ms = kms["spmv"] / max(kcalls["spmv"], 1)
+    sp_gbs = sp_ab / (sp_ms * 1e-3) / 1e9 if kcalls["spmv"] else None
+    return ({"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+             "frac": achieved / peak, "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind ==
+             "measured" else peak_kind, "traffic": traffic, "algorithmic_bytes_per_launch": ab,
+             "avg_launch_ms": avg_ms, "launches": kcalls[dom]},
+            {"gbs": sp_gbs, "frac_of_hbm": (sp_gbs / peak) if sp_gbs else None, "avg_launch_ms": sp_ms,
+             "launches": kcalls["spmv"], "algorithmic_bytes": sp_ab},
+            kms, kcalls)
+
+
 def run_ours(args):
-    import numpy as np
     import torch
     import torch.distributed as dist
 
@@ -211,73 +324,12 @@ def run_ours(args):
     t_setup = time.perf_counter()
     wl = I.ontario_workload(args.nodes, seed=args.seed, n_subdomains=args.subdomains)
     t_gen = time.perf_counter() - t_setup
-    sv = S.Solver(wl.xy, wl.tri, wl.params, stream=stream, dt=wl.dt, n_subdomains=args.subdomains, overlap=2,
-                  coarse=1, newton_rtol=1e-8, gmres_rtol=1e-5, gmres_restart=30, gmres_maxit=200,
-                  precision=1 if args.precision == "mixed" else 0, seed=args.seed, timing=1)
-    t_create = time.perf_counter() - t_setup - t_gen
-    info = sv.info()
-    sv.set_state(torch.tensor(wl.U0, device="cuda"))
-    for _ in range(args.warmup):
-        sv.step()
-    torch.cuda.synchronize()
 
-    # ---- device-timed region: K steps, inputs resident in HBM
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    launches0 = S.launch_count()
-    stats = []
-    with ClockSampler(local) as clk:
-        e0.record(stream)
-        for _ in range(args.steps):
-            stats.append(sv.step())
-        e1.record(stream)
-        torch.cuda.synchronize()
-    launches = S.launch_count() - launches0
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        dist.barrier()
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    dof = 5 * wl.n
-    value = world * dof * args.steps / (ms * 1e-3)
-
-    # kernel classes over the timed region
-    kms = {k: sum(s["kernel_ms"][k] for s in stats) for k in S.KERNEL_CLASSES}
-    kcalls = {k: sum(s["kernel_calls"][k] for s in stats) for k in S.KERNEL_CLASSES}
-    peak, peak_kind = hbm_peak()
-    dom = max(SINGLE_KERNEL, key=lambda k: kms[k])
-    ab = algorithmic_bytes(dom, info)
-    avg_ms = kms[dom] / max(kcalls[dom], 1)
-    achieved = ab / (avg_ms * 1e-3) / 1e9
-    sp_ab = algorithmic_bytes("spmv", info)
-    sp_ms = kms["spmv"] / max(kcalls["spmv"], 1)
-    sp_gbs = sp_ab / (sp_ms * 1e-3) / 1e9 if kcalls["spmv"] else None
-
-    # ---- end to end through the C ABI with pinned host buffers
-    e2e = None
-    if not args.no_e2e:
-        hbuf = torch.empty((wl.n, 5), dtype=torch.float64, pin_memory=True)
-        sv.get_state(hbuf.numpy())
-        torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            sv.set_state(hbuf.numpy())
-            sv.step()
-            sv.get_state(hbuf.numpy())
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([wall], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            wall = float(t.item())
-        e2e = {"value": world * dof * args.steps / wall, "unit": UNIT, "h2d_bytes_per_step": dof * 8,
-               "d2h_bytes_per_step": dof * 8}
+    res = measure(S, wl, args, stream, args.precision, args.forcing, args.pc_lag, world, local,
+                  e2e=not args.no_e2e)
+    other = None
+    if not args.no_mixed and args.precision == "fp64":
+        other = measure(S, wl, args, stream, "mixed", args.forcing, args.pc_lag, world, local, e2e=False)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -287,28 +339,32 @@ def run_ours(args):
             cpu = {"error": str(ex)[:300]}
 
     if rank == 0:
-        nits = [s["newton_its"] for s in stats]
-        gits = [s["gmres_its"] for s in stats]
+        roof, spmv, kms, kcalls = roofline(S, res, args.precision)
+        nits = [s["newton_its"] for s in res["stats"]]
+        gits = [s["gmres_its"] for s in res["stats"]]
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
             "data": "synthetic (seeded Southern-Ontario-like mesh, density and infection seeds)",
-            "config": dict(workload_config(wl, args), parallelism="replicas" if world > 1 else "single GPU"),
-            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "peak_kind": peak_kind,
-                         "traffic": NCU_TRAFFIC.get(dom), "algorithmic_bytes_per_launch": ab,
-                         "avg_launch_ms": avg_ms, "launches": kcalls[dom]},
-            "spmv": {"gbs": sp_gbs, "frac_of_hbm": (sp_gbs / peak) if sp_gbs else None,
-                     "avg_launch_ms": sp_ms, "launches": kcalls["spmv"], "algorithmic_bytes": sp_ab},
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
+            "config": dict(workload_config(wl, args), precision=args.precision,
+                           forcing="Eisenstat-Walker" if args.forcing == "ew" else "fixed rtol 1e-5",
+                           pc_lag=args.pc_lag, parallelism="replicas" if world > 1 else "single GPU"),
+            "roofline": roof, "spmv": spmv, "cpu_baseline": cpu, "e2e": res.get("e2e"),
+            "gpu_launches": res["launches"], "clocks": res["clocks"],
             "kernel_ms": {k: round(v, 3) for k, v in kms.items()}, "kernel_calls": kcalls,
             "newton_its_per_step": sum(nits) / len(nits), "gmres_its_per_step": sum(gits) / len(gits),
-            "setup_s": {"generate": round(t_gen, 2), "create": round(t_create, 2)},
-            "device_bytes": info["device_bytes"],
+            "setup_s": {"generate": round(t_gen, 2)}, "device_bytes": res["info"]["device_bytes"],
         }
+        if other is not None:
+            r2, s2, k2, c2 = roofline(S, other, "mixed")
+            g2 = [s["gmres_its"] for s in other["stats"]]
+            line["mixed"] = {"value": other["value"], "ms_per_step": other["ms_per_step"],
+                             "speedup_vs_fp64": other["value"] / res["value"], "dtype": "f64+f32",
+                             "roofline": r2, "spmv": s2, "kernel_ms": {k: round(v, 3) for k, v in k2.items()},
+                             "gmres_its_per_step": sum(g2) / len(g2), "gpu_launches": other["launches"],
+                             "clocks": other["clocks"]}
         print(json.dumps(line))
-    sv.close()
     if world > 1:
         dist.destroy_process_group()
 

@@ -110,6 +110,10 @@ typedef struct {
   void* stream;           /* cudaStream_t the context runs on; NULL: a private stream */
   int32_t timing;         /* 1: time every kernel class with CUDA events on the stream and
                              report it in seird_stats.kernel_ms (0) */
+  int32_t gmres_forcing;  /* 0: every linear solve to gmres_rtol (Section 3.2); 1: inexact Newton
+                             with Eisenstat-Walker forcing terms (choice 2, gamma 0.9, alpha 2,
+                             first term 0.1, at most 0.5); once the term comes within 10x of what
+                             reaching the Newton target needs, the solve aims at 0.2x that (0) */
 } seird_options;
 
 /* Kernel classes of seird_stats.kernel_ms / kernel_calls. */
@@ -191,6 +195,42 @@ int seird_run(seird_ctx* ctx, int32_t n_steps, seird_stats* per_step);
 
 /* Sizes of the context. */
 int seird_get_info(const seird_ctx* ctx, seird_info* info);
+
+/* Replaces the rates (and, if params->beta_field is not NULL, the transmission
+ * field; a NULL field keeps the current one).  The mesh, partition and state are
+ * kept.  Host pointers, copied. */
+int seird_set_params(seird_ctx* ctx, const seird_params* params);
+
+/* ---- discrete adjoint -------------------------------------------------------
+ * Misfit of observed infected (I) and deceased (D) densities,
+ *   j = sum_{k in obs_steps} sum_{i in obs_nodes} (u^k_{i,I} - I_hat)^2 + (u^k_{i,D} - D_hat)^2,
+ * over a run of n_steps backward-Euler steps from the context's current state
+ * u^0.  Gradient parameters (the rates the paper calibrates, Section 4.2):
+ *   grad[0..9] = dj/d(beta_i, beta_e, sigma, gamma_e, gamma_r, gamma_d,
+ *                     nubar_S, nubar_E, nubar_I, nubar_R)
+ * and grad_field[j] = dj/db_j for the per-node transmission multiplier b
+ * (1 when the context has no field).  Host arrays. */
+typedef struct {
+  int32_t n_steps;            /* steps of the forward run */
+  int32_t checkpoint_every;   /* states kept every k steps; the reverse sweep recomputes
+                                 each segment from its checkpoint (1 keeps every state) */
+  int32_t n_obs_nodes;
+  const int32_t* obs_nodes;   /* [n_obs_nodes] caller numbering */
+  int32_t n_obs_steps;
+  const int32_t* obs_steps;   /* [n_obs_steps] step indices in 1..n_steps, increasing */
+  const double* I_hat;        /* [n_obs_steps][n_obs_nodes] */
+  const double* D_hat;        /* [n_obs_steps][n_obs_nodes] */
+  double lin_rtol;            /* relative tolerance of the transposed linear solves (0: 1e-10) */
+} seird_misfit;
+
+/* Runs the forward steps (Newton to options.newton_rtol), then the reverse
+ * sweep J_k^T lambda_k = -dj/du^k + M lambda_{k+1} (Jacobian of step k, M the
+ * consistent mass), each solved by the same right-preconditioned FGMRES with
+ * RAS and coarse correction built from J_k^T, and accumulates
+ * dj/dp = sum_k lambda_k^T dF^k/dp.  Outputs: *misfit, grad [10], grad_field
+ * [n_nodes] (nullable, caller numbering).  The state and time are restored to
+ * u^0 on return.  FP64 contexts only (options.precision = 0), else SEIRD_EINVAL. */
+int seird_adjoint(seird_ctx* ctx, const seird_misfit* spec, double* misfit, double* grad, double* grad_field);
 
 /* ---- component entry points (kernel-level parity and measurement) ---- */
 

@@ -69,6 +69,12 @@ __device__ __forceinline__ Tri load_tri(const int32_t* __restrict__ tri, const d
   return T;
 }
 
+template <class T>
+struct TriT {
+  T area, gx[3], gy[3];
+  int32_t v[3];
+};
+
 // Element residual: consistent mass, exact diffusion, quadrature of the reaction.
 template <int RULE, bool BF>
 __global__ void __launch_bounds__(128) k_residual_elem(int64_t m, const int32_t* __restrict__ tri,
@@ -202,78 +208,88 @@ __device__ __forceinline__ int sym(int a, int b) {
 }
 
 // Jacobian record of a triangle.
-template <int RULE, bool BF>
+// T is the arithmetic and storage type: FP64, or FP32 when the Jacobian only
+// feeds the FP32 operator and FP32 factors of the mixed-precision path.
+template <int RULE, bool BF, class T>
 __global__ void __launch_bounds__(128) k_jac_record(int64_t m, const int32_t* __restrict__ tri,
                                                     const double* __restrict__ xy, const double* __restrict__ U,
                                                     const double* __restrict__ bfield, Rates r,
-                                                    double* __restrict__ rec, int32_t* err) {
+                                                    T* __restrict__ rec, int32_t* err) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= m) return;
-  const Tri T = load_tri(tri, xy, t);
-  double u[3][5];
-  double Nbar = 0.0;
+  const Tri Tg = load_tri(tri, xy, t);
+  TriT<T> Tt;
+  Tt.area = (T)Tg.area;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    Tt.gx[a] = (T)Tg.gx[a];
+    Tt.gy[a] = (T)Tg.gy[a];
+    Tt.v[a] = Tg.v[a];
+  }
+  T u[3][5];
+  T Nbar = T(0);
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
-      u[a][c] = U[5 * (int64_t)T.v[a] + c];
+      u[a][c] = (T)U[5 * (int64_t)Tt.v[a] + c];
       Nbar += u[a][c];
     }
-  Nbar *= (1.0 / 3.0);
-  double* out = rec + (int64_t)REC * t;
-  out[0] = T.area;
+  Nbar *= T(1.0 / 3.0);
+  T* out = rec + (int64_t)REC * t;
+  out[0] = Tt.area;
   // N-weighted stiffness |T| mean(N) grad phi_a . grad phi_b
-  const double an = T.area * Nbar;
-  out[REC_K + 0] = an * (T.gx[0] * T.gx[0] + T.gy[0] * T.gy[0]);
-  out[REC_K + 1] = an * (T.gx[1] * T.gx[1] + T.gy[1] * T.gy[1]);
-  out[REC_K + 2] = an * (T.gx[2] * T.gx[2] + T.gy[2] * T.gy[2]);
-  out[REC_K + 3] = an * (T.gx[0] * T.gx[1] + T.gy[0] * T.gy[1]);
-  out[REC_K + 4] = an * (T.gx[0] * T.gx[2] + T.gy[0] * T.gy[2]);
-  out[REC_K + 5] = an * (T.gx[1] * T.gx[2] + T.gy[1] * T.gy[2]);
+  const T an = Tt.area * Nbar;
+  out[REC_K + 0] = an * (Tt.gx[0] * Tt.gx[0] + Tt.gy[0] * Tt.gy[0]);
+  out[REC_K + 1] = an * (Tt.gx[1] * Tt.gx[1] + Tt.gy[1] * Tt.gy[1]);
+  out[REC_K + 2] = an * (Tt.gx[2] * Tt.gx[2] + Tt.gy[2] * Tt.gy[2]);
+  out[REC_K + 3] = an * (Tt.gx[0] * Tt.gx[1] + Tt.gy[0] * Tt.gy[1]);
+  out[REC_K + 4] = an * (Tt.gx[0] * Tt.gx[2] + Tt.gy[0] * Tt.gy[2]);
+  out[REC_K + 5] = an * (Tt.gx[1] * Tt.gx[2] + Tt.gy[1] * Tt.gy[2]);
   // G_{c,a} = |T|/3 grad u_c . grad phi_a (derivative of mean_T(N) by any u_{b,c'})
-  const double a3 = T.area * (1.0 / 3.0);
+  const T a3 = Tt.area * T(1.0 / 3.0);
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
-    const double gux = u[0][c] * T.gx[0] + u[1][c] * T.gx[1] + u[2][c] * T.gx[2];
-    const double guy = u[0][c] * T.gy[0] + u[1][c] * T.gy[1] + u[2][c] * T.gy[2];
+    const T gux = u[0][c] * Tt.gx[0] + u[1][c] * Tt.gx[1] + u[2][c] * Tt.gx[2];
+    const T guy = u[0][c] * Tt.gy[0] + u[1][c] * Tt.gy[1] + u[2][c] * Tt.gy[2];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) out[REC_G + 3 * c + a] = a3 * (gux * T.gx[a] + guy * T.gy[a]);
+    for (int a = 0; a < 3; ++a) out[REC_G + 3 * c + a] = a3 * (gux * Tt.gx[a] + guy * Tt.gy[a]);
   }
   // reaction moments P^k_ab = |T| sum_q w_q phi_a phi_b rho_k(x_q):
   //   rho_0 = A s lam / N^2 (d kappa/du_c' = A/N^2 for every c'), rho_1 = kappa lam,
   //   rho_2 = kappa s beta_E b, rho_3 = kappa s beta_I b.
-  double P[4][6];
+  T P[4][6];
 #pragma unroll
   for (int k = 0; k < 4; ++k)
 #pragma unroll
-    for (int s = 0; s < 6; ++s) P[k][s] = 0.0;
-  double bv[3] = {1.0, 1.0, 1.0};
+    for (int s = 0; s < 6; ++s) P[k][s] = T(0);
+  T bv[3] = {T(1), T(1), T(1)};
   if (BF) {
 #pragma unroll
-    for (int a = 0; a < 3; ++a) bv[a] = bfield[T.v[a]];
+    for (int a = 0; a < 3; ++a) bv[a] = (T)bfield[Tt.v[a]];
   }
   constexpr int NQ = RULE == 0 ? 7 : 3;
   bool bad = false;
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
-    double uq[5];
+    const T L0 = (T)cQL[RULE][q][0], L1 = (T)cQL[RULE][q][1], L2 = (T)cQL[RULE][q][2];
+    T uq[5];
 #pragma unroll
-    for (int c = 0; c < 5; ++c)
-      uq[c] = cQL[RULE][q][0] * u[0][c] + cQL[RULE][q][1] * u[1][c] + cQL[RULE][q][2] * u[2][c];
-    const double bq = BF ? cQL[RULE][q][0] * bv[0] + cQL[RULE][q][1] * bv[1] + cQL[RULE][q][2] * bv[2] : 1.0;
-    const double N = uq[0] + uq[1] + uq[2] + uq[3] + uq[4];
-    bad |= !(N > 0.0);
-    const double invN = 1.0 / N;
-    const double kappa = 1.0 - r.A * invN;
-    const double lam = (r.bi * uq[2] + r.be * uq[1]) * bq;
-    double rho[4];
-    rho[0] = r.A * invN * invN * uq[0] * lam;
+    for (int c = 0; c < 5; ++c) uq[c] = L0 * u[0][c] + L1 * u[1][c] + L2 * u[2][c];
+    const T bq = BF ? L0 * bv[0] + L1 * bv[1] + L2 * bv[2] : T(1);
+    const T N = uq[0] + uq[1] + uq[2] + uq[3] + uq[4];
+    bad |= !(N > T(0));
+    const T invN = T(1) / N;
+    const T A = (T)r.A, bi = (T)r.bi, be = (T)r.be;
+    const T kappa = T(1) - A * invN;
+    const T lam = (bi * uq[2] + be * uq[1]) * bq;
+    T rho[4];
+    rho[0] = A * invN * invN * uq[0] * lam;
     rho[1] = kappa * lam;
-    rho[2] = kappa * uq[0] * r.be * bq;
-    rho[3] = kappa * uq[0] * r.bi * bq;
-    const double wq = T.area * cQW[RULE][q];
-    const double L0 = cQL[RULE][q][0], L1 = cQL[RULE][q][1], L2 = cQL[RULE][q][2];
-    const double w6[6] = {wq * L0 * L0, wq * L1 * L1, wq * L2 * L2, wq * L0 * L1, wq * L0 * L2, wq * L1 * L2};
+    rho[2] = kappa * uq[0] * be * bq;
+    rho[3] = kappa * uq[0] * bi * bq;
+    const T wq = Tt.area * (T)cQW[RULE][q];
+    const T w6[6] = {wq * L0 * L0, wq * L1 * L1, wq * L2 * L2, wq * L0 * L1, wq * L0 * L2, wq * L1 * L2};
 #pragma unroll
     for (int k = 0; k < 4; ++k)
 #pragma unroll
@@ -284,62 +300,209 @@ __global__ void __launch_bounds__(128) k_jac_record(int64_t m, const int32_t* __
   for (int k = 0; k < 4; ++k)
 #pragma unroll
     for (int s = 0; s < 6; ++s) out[REC_P + 6 * k + s] = P[k][s];
-  out[REC - 1] = 0.0;
+  out[REC - 1] = T(0);
 }
 
 // One thread per 5x5 block: fixed-order sums over the triangles sharing the
 // node pair, then the block of dF_i/dU_j:
 //   M delta + dt nubar_c (G_c + K delta) - dt int phi_i phi_j dR_c/du_c'.
+template <class T>
 __global__ void __launch_bounds__(128) k_jac_gather(int64_t nnzb, const int32_t* __restrict__ inc_ptr,
-                                                    const int32_t* __restrict__ inc,
-                                                    const double* __restrict__ rec, Rates r,
-                                                    double* __restrict__ val) {
+                                                    const int32_t* __restrict__ inc, const T* __restrict__ rec,
+                                                    Rates r, T* __restrict__ val) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= nnzb) return;
-  double M = 0, K = 0, G[4] = {0, 0, 0, 0}, P[4] = {0, 0, 0, 0};
+  T M = 0, K = 0, G[4] = {0, 0, 0, 0}, P[4] = {0, 0, 0, 0};
   for (int32_t q = inc_ptr[k]; q < inc_ptr[k + 1]; ++q) {
     const int32_t e = inc[q];
     const int32_t t = e / 9, ab = e - 9 * t;
     const int a = ab / 3, b = ab - 3 * a;
-    const double* R = rec + (int64_t)REC * t;
+    const T* R = rec + (int64_t)REC * t;
     const int s = sym(a, b);
-    M += R[0] * (a == b ? (2.0 / 12.0) : (1.0 / 12.0));
+    M += R[0] * (a == b ? T(2.0 / 12.0) : T(1.0 / 12.0));
     K += R[REC_K + s];
 #pragma unroll
     for (int c = 0; c < 4; ++c) G[c] += R[REC_G + 3 * c + a];
 #pragma unroll
     for (int c = 0; c < 4; ++c) P[c] += R[REC_P + 6 * c + s];
   }
-  const double dt = r.dt;
-  double B[5][5];
+  const T dt = (T)r.dt;
+  const T nu0 = (T)r.nu[0], nu1 = (T)r.nu[1], nu2 = (T)r.nu[2], nu3 = (T)r.nu[3];
+  const T alpha = (T)r.alpha, mu = (T)r.mu, sigma = (T)r.sigma, ge = (T)r.ge, gr = (T)r.gr, gd = (T)r.gd;
+  T B[5][5];
   // rows S, E: transmission derivative row  dT/du_c' = P0 + [S]P1 + [E]P2 + [I]P3
-  const double gS = dt * r.nu[0] * G[0], gE = dt * r.nu[1] * G[1], gI = dt * r.nu[2] * G[2], gR = dt * r.nu[3] * G[3];
+  const T gS = dt * nu0 * G[0], gE = dt * nu1 * G[1], gI = dt * nu2 * G[2], gR = dt * nu3 * G[3];
 #pragma unroll
   for (int c = 0; c < 5; ++c) {
-    B[0][c] = gS - dt * r.alpha * M + dt * P[0];
+    B[0][c] = gS - dt * alpha * M + dt * P[0];
     B[1][c] = gE - dt * P[0];
     B[2][c] = gI;
     B[3][c] = gR;
-    B[4][c] = 0.0;
+    B[4][c] = T(0);
   }
-  B[0][0] += M + dt * r.nu[0] * K + dt * P[1] + dt * r.mu * M;
+  B[0][0] += M + dt * nu0 * K + dt * P[1] + dt * mu * M;
   B[0][1] += dt * P[2];
   B[0][2] += dt * P[3];
   B[1][0] -= dt * P[1];
-  B[1][1] += M + dt * r.nu[1] * K - dt * P[2] + dt * (r.sigma + r.ge + r.mu) * M;
+  B[1][1] += M + dt * nu1 * K - dt * P[2] + dt * (sigma + ge + mu) * M;
   B[1][2] -= dt * P[3];
-  B[2][1] -= dt * r.sigma * M;
-  B[2][2] += M + dt * r.nu[2] * K + dt * (r.gr + r.gd + r.mu) * M;
-  B[3][1] -= dt * r.ge * M;
-  B[3][2] -= dt * r.gr * M;
-  B[3][3] += M + dt * r.nu[3] * K + dt * r.mu * M;
-  B[4][2] -= dt * r.gd * M;
+  B[2][1] -= dt * sigma * M;
+  B[2][2] += M + dt * nu2 * K + dt * (gr + gd + mu) * M;
+  B[3][1] -= dt * ge * M;
+  B[3][2] -= dt * gr * M;
+  B[3][3] += M + dt * nu3 * K + dt * mu * M;
+  B[4][2] -= dt * gd * M;
   B[4][4] += M;
-  double* out = val + 25 * k;
+  T* out = val + 25 * k;
 #pragma unroll
   for (int i = 0; i < 5; ++i)
 #pragma unroll
     for (int c = 0; c < 5; ++c) out[5 * i + c] = B[i][c];
+}
+
+// ---- discrete-adjoint terms ------------------------------------------------
+
+// M V per compartment with the consistent mass: element vectors |T|/12 (V_a + sum_b V_b)
+__global__ void __launch_bounds__(128) k_mass_elem(int64_t m, const int32_t* __restrict__ tri,
+                                                   const double* __restrict__ xy, const double* __restrict__ V,
+                                                   double* __restrict__ elem) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= m) return;
+  const Tri T = load_tri(tri, xy, t);
+  const double m12 = T.area * (1.0 / 12.0);
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    double v[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) v[a] = V[5 * (int64_t)T.v[a] + c];
+    const double s = v[0] + v[1] + v[2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) elem[15 * t + 5 * a + c] = m12 * (v[a] + s);
+  }
+}
+
+// lambda^T dF/dp for the ten rates, summed per CTA (partial[cta*stride + k]),
+// and the transmission-field element terms fe[t][a] = lambda^T dF/db at corner a.
+// F is linear in each rate, so dF/dp_k is read off the weak form:
+//   nubar_c : dt |T| mean(N) grad u_c . grad lambda_c
+//   rates in R: -dt |T| sum_q w_q sum_c lambda_c(x_q) dR_c/dp(x_q), with
+//     beta_I: kappa s i b (lambda_E - lambda_S)   beta_E: kappa s e b (lambda_E - lambda_S)
+//     sigma : e (lambda_I - lambda_E)             gamma_E: e (lambda_R - lambda_E)
+//     gamma_R: i (lambda_R - lambda_I)            gamma_D: i (lambda_D - lambda_I)
+//   field b_j: dt |T| sum_q w_q phi_j kappa s (beta_I i + beta_E e) (lambda_S - lambda_E).
+template <int RULE, bool BF>
+__global__ void __launch_bounds__(256) k_param_contract(int64_t m, const int32_t* __restrict__ tri,
+                                                        const double* __restrict__ xy, const double* __restrict__ U,
+                                                        const double* __restrict__ lam,
+                                                        const double* __restrict__ bfield, Rates r, int stride,
+                                                        double* __restrict__ partial, double* __restrict__ fe) {
+  __shared__ double sh[8];
+  double acc[10];
+#pragma unroll
+  for (int k = 0; k < 10; ++k) acc[k] = 0.0;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x) {
+    const Tri T = load_tri(tri, xy, t);
+    double u[3][5], l[3][5];
+    double Nbar = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        u[a][c] = U[5 * (int64_t)T.v[a] + c];
+        l[a][c] = lam[5 * (int64_t)T.v[a] + c];
+        Nbar += u[a][c];
+      }
+    Nbar *= (1.0 / 3.0);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const double gux = u[0][c] * T.gx[0] + u[1][c] * T.gx[1] + u[2][c] * T.gx[2];
+      const double guy = u[0][c] * T.gy[0] + u[1][c] * T.gy[1] + u[2][c] * T.gy[2];
+      const double glx = l[0][c] * T.gx[0] + l[1][c] * T.gx[1] + l[2][c] * T.gx[2];
+      const double gly = l[0][c] * T.gy[0] + l[1][c] * T.gy[1] + l[2][c] * T.gy[2];
+      acc[6 + c] += r.dt * T.area * Nbar * (gux * glx + guy * gly);
+    }
+    double bv[3] = {1.0, 1.0, 1.0};
+    if (BF) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) bv[a] = bfield[T.v[a]];
+    }
+    double f3[3] = {0.0, 0.0, 0.0};
+    constexpr int NQ = RULE == 0 ? 7 : 3;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      double uq[5], lq[5];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        uq[c] = cQL[RULE][q][0] * u[0][c] + cQL[RULE][q][1] * u[1][c] + cQL[RULE][q][2] * u[2][c];
+        lq[c] = cQL[RULE][q][0] * l[0][c] + cQL[RULE][q][1] * l[1][c] + cQL[RULE][q][2] * l[2][c];
+      }
+      const double bq = BF ? cQL[RULE][q][0] * bv[0] + cQL[RULE][q][1] * bv[1] + cQL[RULE][q][2] * bv[2] : 1.0;
+      const double N = uq[0] + uq[1] + uq[2] + uq[3] + uq[4];
+      const double kappa = 1.0 - r.A / N;
+      const double wq = r.dt * T.area * cQW[RULE][q];
+      const double ks = kappa * uq[0];
+      const double dSE = lq[1] - lq[0];
+      acc[0] -= wq * ks * uq[2] * bq * dSE;
+      acc[1] -= wq * ks * uq[1] * bq * dSE;
+      acc[2] -= wq * uq[1] * (lq[2] - lq[1]);
+      acc[3] -= wq * uq[1] * (lq[3] - lq[1]);
+      acc[4] -= wq * uq[2] * (lq[3] - lq[2]);
+      acc[5] -= wq * uq[2] * (lq[4] - lq[2]);
+      const double fb = -wq * ks * (r.bi * uq[2] + r.be * uq[1]) * dSE;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) f3[a] += fb * cQL[RULE][q][a];
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) fe[3 * t + a] = f3[a];
+  }
+#pragma unroll
+  for (int k = 0; k < 10; ++k) {
+    double v = acc[k];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
+      partial[(int64_t)blockIdx.x * stride + k] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// out[i] += sum over the node's incident (t, a) of fe[3 t + a]  (fixed order)
+__global__ void k_gather_scalar_add(int64_t n, const int32_t* __restrict__ inc_ptr, const int32_t* __restrict__ inc,
+                                    const double* __restrict__ fe, double* __restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int32_t k = inc_ptr[i]; k < inc_ptr[i + 1]; ++k) s += fe[inc[k]];
+  out[i] += s;
+}
+
+// misfit of one observation step (one CTA, fixed-order sum): *jacc += sum (dI^2 + dD^2);
+// with rhs != NULL also rhs -= dj/du = 2 (dI, dD) at the observed entries
+__global__ void k_misfit(int nobs, const int32_t* __restrict__ nodes, const double* __restrict__ Ihat,
+                         const double* __restrict__ Dhat, const double* __restrict__ U, double* rhs, double* jacc) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int k = threadIdx.x; k < nobs; k += blockDim.x) {
+    const int64_t i = nodes[k];
+    const double dI = U[5 * i + 2] - Ihat[k], dD = U[5 * i + 4] - Dhat[k];
+    s += dI * dI + dD * dD;
+    if (rhs) {
+      rhs[5 * i + 2] -= 2.0 * dI;
+      rhs[5 * i + 4] -= 2.0 * dD;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    *jacc += t;
+  }
 }
 
 }  // namespace
@@ -367,20 +530,69 @@ void launch_residual(int64_t n, int64_t m, const int32_t* tri, const double* xy,
 }
 
 void launch_jacobian(int64_t nnzb, int64_t m, const int32_t* tri, const double* xy, const double* U,
-                     const double* bfield, const Rates& r, int rule, double* rec, const int32_t* inc_ptr,
-                     const int32_t* inc, double* val, int32_t* err, cudaStream_t s) {
+                     const double* bfield, const Rates& r, int rule, void* rec, const int32_t* inc_ptr,
+                     const int32_t* inc, void* val, bool fp32, int32_t* err, cudaStream_t s) {
   const int tb = 128;
   const int64_t g = (m + tb - 1) / tb;
-  if (rule == 0) {
-    if (bfield) k_jac_record<0, true><<<g, tb, 0, s>>>(m, tri, xy, U, bfield, r, rec, err);
-    else k_jac_record<0, false><<<g, tb, 0, s>>>(m, tri, xy, U, bfield, r, rec, err);
+  const int64_t g2 = (nnzb + tb - 1) / tb;
+  if (fp32) {
+    float* rc = static_cast<float*>(rec);
+    if (rule == 0) {
+      if (bfield) k_jac_record<0, true, float><<<g, tb, 0, s>>>(m, tri, xy, U, bfield, r, rc, err);
+      else k_jac_record<0, false, float><<<g, tb, 0, s>>>(m, tri, xy, U, bfield, r, rc, err);
+    } else {
+      if (bfield) k_jac_record<1, true, float><<<g, tb, 0, s>>>(m, tri, xy, U, bfield, r, rc, err);
+      else k_jac_record<1, false, float><<<g, tb, 0, s>>>(m, tri, xy, U, bfield, r, rc, err);
+    }
+    k_jac_gather<float><<<g2, tb, 0, s>>>(nnzb, inc_ptr, inc, rc, r, static_cast<float*>(val));
   } else {
-    if (bfield) k_jac_record<1, true><<<g, tb, 0, s>>>(m, tri, xy, U, bfield, r, rec, err);
-    else k_jac_record<1, false><<<g, tb, 0, s>>>(m, tri, xy, U, bfield, r, rec, err);
+    double* rc = static_cast<double*>(rec);
+    if (rule == 0) {
+      if (bfield) k_jac_record<0, true, double><<<g, tb, 0, s>>>(m, tri, xy, U, bfield, r, rc, err);
+      else k_jac_record<0, false, double><<<g, tb, 0, s>>>(m, tri, xy, U, bfield, r, rc, err);
+    } else {
+      if (bfield) k_jac_record<1, true, double><<<g, tb, 0, s>>>(m, tri, xy, U, bfield, r, rc, err);
+      else k_jac_record<1, false, double><<<g, tb, 0, s>>>(m, tri, xy, U, bfield, r, rc, err);
+    }
+    k_jac_gather<double><<<g2, tb, 0, s>>>(nnzb, inc_ptr, inc, rc, r, static_cast<double*>(val));
   }
   count_launch();
-  const int64_t g2 = (nnzb + tb - 1) / tb;
-  k_jac_gather<<<g2, tb, 0, s>>>(nnzb, inc_ptr, inc, rec, r, val);
+  count_launch();
+}
+
+void launch_mass(int64_t n, int64_t m, const int32_t* tri, const double* xy, const double* V, double* elem,
+                 const int32_t* inc_ptr, const int32_t* inc, double* out, double* partial, double* norm2,
+                 cudaStream_t s) {
+  k_mass_elem<<<(m + 127) / 128, 128, 0, s>>>(m, tri, xy, V, elem);
+  const int64_t g2 = (n + 255) / 256;
+  k_residual_gather<<<g2, 256, 0, s>>>(n, inc_ptr, inc, elem, out, partial);
+  k_sum_partials<<<1, 1024, 0, s>>>(g2, partial, norm2);
+  count_launch();
+  count_launch();
+  count_launch();
+}
+
+void launch_param_contract(int64_t n, int64_t m, const int32_t* tri, const double* xy, const double* U,
+                           const double* lam, const double* bfield, const Rates& r, int rule, double* partial,
+                           int grid, int stride, double* fe, const int32_t* inc_ptr, const int32_t* inc,
+                           double* field_out, cudaStream_t s) {
+  if (rule == 0) {
+    if (bfield) k_param_contract<0, true><<<grid, 256, 0, s>>>(m, tri, xy, U, lam, bfield, r, stride, partial, fe);
+    else k_param_contract<0, false><<<grid, 256, 0, s>>>(m, tri, xy, U, lam, bfield, r, stride, partial, fe);
+  } else {
+    if (bfield) k_param_contract<1, true><<<grid, 256, 0, s>>>(m, tri, xy, U, lam, bfield, r, stride, partial, fe);
+    else k_param_contract<1, false><<<grid, 256, 0, s>>>(m, tri, xy, U, lam, bfield, r, stride, partial, fe);
+  }
+  count_launch();
+  if (field_out) {
+    k_gather_scalar_add<<<(n + 255) / 256, 256, 0, s>>>(n, inc_ptr, inc, fe, field_out);
+    count_launch();
+  }
+}
+
+void launch_misfit(int nobs, const int32_t* nodes, const double* Ihat, const double* Dhat, const double* U,
+                   double* rhs, double* jacc, cudaStream_t s) {
+  k_misfit<<<1, 1024, 0, s>>>(nobs, nodes, Ihat, Dhat, U, rhs, jacc);
   count_launch();
 }
 

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/seird.h"
+#include "kernels.cuh"
 
 namespace seird {
 
@@ -21,6 +22,12 @@ enum : int {
 };
 
 constexpr int MAX_RESTART = 64;
+// coarse problems up to this many unknowns (5 x subdomains) keep an explicit
+// inverse (applied as a GEMV); larger ones are solved through the band factors
+constexpr int64_t DENSE_COARSE_MAX = 8192;
+// blocks per ILU-solve level buffer (two buffers of 24 KB in FP64 at 26 doubles per block)
+constexpr int32_t SOLVE_BUF_BLOCKS = SOLVE_BUF_BLOCKS_DEV;
+constexpr int32_t SOLVE_BUF_ROWS = SOLVE_BUF_ROWS_DEV;
 
 // Host-side products of the setup phase (all indices in the internal numbering,
 // where nodes are sorted by (subdomain, caller index)).
@@ -35,6 +42,7 @@ struct HostSetup {
   std::vector<int32_t> tri;      // [m][3] internal node ids (triangles sorted by min node)
   // global 5x5 BSR pattern
   std::vector<int32_t> row_ptr, col;  // [n+1], [nnzb]
+  std::vector<int32_t> tpos;          // [nnzb] index of block (j,i) for block (i,j) (the pattern is symmetric)
   // residual gather: per node, list of (t*3 + a)
   std::vector<int32_t> node_inc_ptr, node_inc;
   // Jacobian gather: per block, list of (t*9 + a*3 + b)
@@ -54,6 +62,23 @@ struct HostSetup {
   std::vector<int32_t> bwd_order, bwd_lev, sd_bwd_lev0;
   int32_t max_levels = 0;
   int32_t max_sd_rows = 0;
+  // ILU(0) solve plans: the solve reads factor blocks from a copy laid out in
+  // level order (forward: each row's strictly lower blocks; backward: each row's
+  // inverted pivot block, then its upper blocks), so that every level is one
+  // contiguous range that is prefetched into shared memory while the previous
+  // level computes.  Levels are split so that a range fits the buffer.
+  struct SolvePlan {
+    std::vector<int32_t> row;     // [NL] local row at each position (per subdomain, level order)
+    std::vector<int64_t> start;   // [NL] first block (absolute, in the solve copy) of each position
+    std::vector<int32_t> cnt;     // [NL] blocks of each position
+    std::vector<int32_t> levpos;  // per subdomain nlev+1 entries: position boundaries (relative)
+    std::vector<int64_t> levblk;  // per subdomain nlev+1 entries: block boundaries (absolute)
+    std::vector<int32_t> sd_lev0; // [P+1] offsets into levpos/levblk
+    std::vector<int64_t> src;     // [nblocks] factor block (>= 0) or -1-R for the inverted pivot of row R
+    std::vector<int32_t> col;     // [nblocks] local column of each block (the row itself for a pivot)
+    std::vector<int32_t> info;    // [NL][4] per position: row, first block relative to its level, blocks, 0
+    int32_t max_lev_blocks = 0;
+  } sp_fwd, sp_bwd;
   // coarse space: subdomain p sits at block row cpos[p] of the banded coarse matrix
   std::vector<int32_t> cpos;        // [P]
   int32_t cband = 0;                // half bandwidth in blocks
@@ -92,6 +117,7 @@ struct seird_ctx {
   int32_t* perm = nullptr;
   int32_t* row_ptr = nullptr;
   int32_t* col = nullptr;
+  int32_t* tpos = nullptr;
   double* val = nullptr;
   float* val32 = nullptr;
   int32_t* node_inc_ptr = nullptr;
@@ -144,6 +170,24 @@ struct seird_ctx {
   float* dinv32 = nullptr;
   double* ywork = nullptr;  // [NL][5]
   double* zwork = nullptr;  // [NL][5]
+  float* ywork32 = nullptr;  // mixed-precision path
+  float* zwork32 = nullptr;
+  struct PlanPtrs {
+    int32_t* row = nullptr;
+    int64_t* start = nullptr;
+    int32_t* cnt = nullptr;
+    int32_t* levpos = nullptr;
+    int64_t* levblk = nullptr;
+    int32_t* sd_lev0 = nullptr;
+    int64_t* src = nullptr;
+    int32_t* col = nullptr;
+    int32_t* info = nullptr;
+  } pf, pb;  // forward / backward solve plans
+  double* fL = nullptr;  // level-ordered factor copies (FP64 path)
+  double* bU = nullptr;
+  float* fL32 = nullptr;  // (mixed path)
+  float* bU32 = nullptr;
+  float* Z32 = nullptr;      // [restart][5n] preconditioned basis in FP32
   // coarse
   int32_t* cpos = nullptr;
   int32_t* cseg_blk = nullptr;
@@ -153,7 +197,8 @@ struct seird_ctx {
   double* cpart = nullptr;  // [nchunk][25]
   double* cband = nullptr;  // [P][2*cband+1][25] banded coarse matrix / factors
   double* cdinv = nullptr;  // [P][25]
-  double* crhs = nullptr;   // [5P]
+  double* crhs = nullptr;   // [2][5P]
+  double* ainvT = nullptr;  // [5P][5P] explicit coarse inverse (transposed)
   bool pc_ready = false;
   bool jac_ready = false;
   // kernel-class timing (options.timing): (class, start event, end event) per launch group

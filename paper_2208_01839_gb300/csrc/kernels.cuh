@@ -35,8 +35,8 @@ void launch_residual(int64_t n, int64_t m, const int32_t* tri, const double* xy,
                      const int32_t* inc, double* F, double* partial, int grid_red, double* out_norm2, int32_t* err,
                      cudaStream_t s);
 void launch_jacobian(int64_t nnzb, int64_t m, const int32_t* tri, const double* xy, const double* U,
-                     const double* bfield, const Rates& r, int rule, double* rec, const int32_t* inc_ptr,
-                     const int32_t* inc, double* val, int32_t* err, cudaStream_t s);
+                     const double* bfield, const Rates& r, int rule, void* rec, const int32_t* inc_ptr,
+                     const int32_t* inc, void* val, bool fp32, int32_t* err, cudaStream_t s);
 template <class VT>
 void launch_spmv(int64_t nrow, const int32_t* rp, const int32_t* col, const VT* val, const double* x, double* y,
                  cudaStream_t s);
@@ -64,7 +64,30 @@ void launch_gather5(int64_t n, const int32_t* idx, const double* src, double* ds
 void launch_scatter5(int64_t n, const int32_t* idx, const double* src, double* dst, cudaStream_t s);
 void launch_check_finite(int64_t len, const double* x, int32_t* err, cudaStream_t s);
 
+// discrete adjoint
+void launch_mass(int64_t n, int64_t m, const int32_t* tri, const double* xy, const double* V, double* elem,
+                 const int32_t* inc_ptr, const int32_t* inc, double* out, double* partial, double* norm2,
+                 cudaStream_t s);
+void launch_param_contract(int64_t n, int64_t m, const int32_t* tri, const double* xy, const double* U,
+                           const double* lam, const double* bfield, const Rates& r, int rule, double* partial,
+                           int grid, int stride, double* fe, const int32_t* inc_ptr, const int32_t* inc,
+                           double* field_out, cudaStream_t s);
+void launch_misfit(int nobs, const int32_t* nodes, const double* Ihat, const double* Dhat, const double* U,
+                   double* rhs, double* jacc, cudaStream_t s);
+void launch_bsr_transpose(int64_t nnzb, const int32_t* tpos, const double* val, double* valT, cudaStream_t s);
+
 // RAS and coarse space
+constexpr int SOLVE_BUF_BLOCKS_DEV = 118;  // factor blocks per ILU-solve stage buffer
+constexpr int SOLVE_BUF_ROWS_DEV = 128;    // rows per ILU-solve stage
+struct SolvePlanDev {
+  const int32_t* row;
+  const int64_t* start;
+  const int32_t* cnt;
+  const int32_t* levpos;
+  const int64_t* levblk;
+  const int32_t* sd_lev0;
+  const int4* info;  // per position: row, first block relative to its stage, block count, 0
+};
 struct RasDev {
   int32_t P;
   const int32_t* sd_row0;
@@ -86,9 +109,27 @@ struct RasDev {
   double* dinv;
   double* ywork;
   double* zwork;
+  float* fval32;  // mixed-precision path
+  float* dinv32;
+  float* ywork32;
+  float* zwork32;
+  SolvePlanDev fwd, bwd;  // level-ordered solve copies of the factors
+  double* fL;
+  double* bU;
+  float* fL32;
+  float* bU32;
 };
-void launch_ilu_factor(const RasDev& d, const double* val, int32_t* err, cudaStream_t s);
-void launch_ilu_solve(const RasDev& d, const double* r, double* z, cudaStream_t s);
+void launch_ilu_factor(const RasDev& d, const double* val, const float* val32, int32_t* err, bool fp32,
+                       cudaStream_t s);
+void launch_ilu_reorg(const RasDev& d, int64_t nfwd, int64_t nbwd, const int64_t* fsrc, const int32_t* fcol,
+                      const int64_t* bsrc, const int32_t* bcol, bool fp32, cudaStream_t s);
+void launch_ilu_solve(const RasDev& d, const double* r, double* z, int32_t* err, cudaStream_t s);
+void launch_ilu_solve32(const RasDev& d, const double* r, float* z, int32_t* err, cudaStream_t s);
+void launch_spmv32(int64_t nrow, const int32_t* rp, const int32_t* col, const float* val, const float* x, double* y,
+                   cudaStream_t s);
+void launch_multi_axpy32(int64_t len, int nv, const float* Zs, int64_t ld, const double* coef, double* x,
+                         cudaStream_t s);
+void launch_f32_to_f64(int64_t n, const float* src, double* dst, cudaStream_t s);
 
 struct CoarseDev {
   int32_t P, band;
@@ -101,13 +142,15 @@ struct CoarseDev {
   const int32_t* cdst_ptr;
   const int64_t* cdst_idx;
   int32_t ndst;
-  double* cpart;
+  double* cpart;   // chunk partial sums (assembly) and GEMV partials (apply)
   double* cband;
   double* cdinv;
-  double* crhs;
+  double* crhs;    // [2 * 5P]: Z^T r, then A_c^{-1} Z^T r
+  double* ainvT;   // [5P][5P] explicit inverse, transposed (NULL: banded solve per apply)
 };
-void launch_coarse_assemble(const CoarseDev& c, const double* val, cudaStream_t s);
+void launch_coarse_assemble(const CoarseDev& c, const double* val, const float* val32, cudaStream_t s);
 void launch_coarse_factor(const CoarseDev& c, int32_t* err, cudaStream_t s);
-void launch_coarse_apply_add(const CoarseDev& c, int64_t n, const double* r, double* z, cudaStream_t s);
+template <class TZ>
+void launch_coarse_apply_add(const CoarseDev& c, int64_t n, const double* r, TZ* z, cudaStream_t s);
 
 }  // namespace seird

@@ -41,6 +41,56 @@ __global__ void __launch_bounds__(256) k_bsr_spmv(int64_t nrow, const int32_t* _
   y[g] = acc;
 }
 
+// Mixed-precision SpMV: FP32 values and FP32 input, FP32 arithmetic, FP64 output.
+__global__ void __launch_bounds__(256) k_bsr_spmv32(int64_t nrow, const int32_t* __restrict__ rp,
+                                                    const int32_t* __restrict__ col, const float* __restrict__ val,
+                                                    const float* __restrict__ x, double* __restrict__ y) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= 5 * nrow) return;
+  const int64_t i = g / 5;
+  const int r = (int)(g - 5 * i);
+  const int32_t k0 = __ldg(rp + i), k1 = __ldg(rp + i + 1);
+  float acc = 0.f;
+  for (int32_t k = k0; k < k1; ++k) {
+    const int64_t j = __ldg(col + k);
+    const float* v = val + 25 * (int64_t)k + 5 * r;
+    const float* xj = x + 5 * j;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) acc = fmaf(__ldg(v + c), __ldg(xj + c), acc);
+  }
+  y[g] = (double)acc;
+}
+
+// x += sum_k coef[k] Z_k with FP32 Z: the sum is formed in FP32, added in FP64
+__global__ void k_multi_axpy32(int64_t len, int nv, const float* __restrict__ Z, int64_t ld,
+                               const double* __restrict__ coef, double* __restrict__ x) {
+  __shared__ float cs[NVMAX];
+  for (int k = threadIdx.x; k < nv; k += blockDim.x) cs[k] = (float)coef[k];
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
+    float v = 0.f;
+    for (int k = 0; k < nv; ++k) v = fmaf(cs[k], Z[k * ld + i], v);
+    x[i] += (double)v;
+  }
+}
+
+// valT = J^T on the same (structurally symmetric) block pattern: block k = (i,j)
+// of J^T is the transpose of block tpos[k] = (j,i) of J
+__global__ void k_bsr_transpose(int64_t nnzb, const int32_t* __restrict__ tpos, const double* __restrict__ val,
+                                double* __restrict__ valT) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < 25 * nnzb;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = g / 25;
+    const int e = (int)(g - 25 * k), rr = e / 5, cc = e % 5;
+    valT[g] = val[25 * (int64_t)tpos[k] + 5 * cc + rr];
+  }
+}
+
+__global__ void k_f32_to_f64(int64_t n, const float* __restrict__ a, double* __restrict__ b) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (double)a[i];
+}
+
 __global__ void k_f64_to_f32(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     b[i] = (float)a[i];
@@ -286,6 +336,29 @@ template void launch_spmv<double>(int64_t, const int32_t*, const int32_t*, const
                                   cudaStream_t);
 template void launch_spmv<float>(int64_t, const int32_t*, const int32_t*, const float*, const double*, double*,
                                  cudaStream_t);
+
+void launch_spmv32(int64_t nrow, const int32_t* rp, const int32_t* col, const float* val, const float* x, double* y,
+                   cudaStream_t s) {
+  if (nrow <= 0) return;
+  k_bsr_spmv32<<<(5 * nrow + 255) / 256, 256, 0, s>>>(nrow, rp, col, val, x, y);
+  count_launch();
+}
+
+void launch_multi_axpy32(int64_t len, int nv, const float* Zs, int64_t ld, const double* coef, double* x,
+                         cudaStream_t s) {
+  k_multi_axpy32<<<grid_for(len), 256, 0, s>>>(len, nv, Zs, ld, coef, x);
+  count_launch();
+}
+
+void launch_bsr_transpose(int64_t nnzb, const int32_t* tpos, const double* val, double* valT, cudaStream_t s) {
+  k_bsr_transpose<<<grid_for(25 * nnzb), 256, 0, s>>>(nnzb, tpos, val, valT);
+  count_launch();
+}
+
+void launch_f32_to_f64(int64_t n, const float* src, double* dst, cudaStream_t s) {
+  k_f32_to_f64<<<grid_for(n), 256, 0, s>>>(n, src, dst);
+  count_launch();
+}
 
 void launch_f64_to_f32(int64_t n, const double* src, float* dst, cudaStream_t s) {
   k_f64_to_f32<<<grid_for(n), 256, 0, s>>>(n, src, dst);

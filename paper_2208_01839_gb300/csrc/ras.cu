@@ -17,36 +17,40 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 
+__device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
+
 // Inverse of a 5x5 block by Gauss-Jordan with partial pivoting, one warp
 // (lanes 0..4 hold the rows).  Sets ERR_SINGULAR (2) on a zero pivot.
-__device__ void warp_inv5(const double* __restrict__ D, double* __restrict__ out, int lane, int32_t* err) {
-  double a[5], b[5];
+template <class T>
+__device__ void warp_inv5(const T* __restrict__ D, T* __restrict__ out, int lane, int32_t* err) {
+  T a[5], b[5];
 #pragma unroll
   for (int c = 0; c < 5; ++c) {
-    a[c] = lane < 5 ? D[5 * lane + c] : 0.0;
-    b[c] = (lane == c) ? 1.0 : 0.0;
+    a[c] = lane < 5 ? D[5 * lane + c] : T(0);
+    b[c] = (lane == c) ? T(1) : T(0);
   }
   bool sing = false;
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
-    double v = (lane >= k && lane < 5) ? fabs(a[k]) : -1.0;
+    T v = (lane >= k && lane < 5) ? (T)fabs(a[k]) : T(-1);
     int idx = lane;
 #pragma unroll
     for (int o = 4; o > 0; o >>= 1) {
-      const double v2 = __shfl_down_sync(FULL, v, o, 8);
+      const T v2 = __shfl_down_sync(FULL, v, o, 8);
       const int i2 = __shfl_down_sync(FULL, idx, o, 8);
       if (v2 > v || (v2 == v && i2 < idx)) {
         v = v2;
         idx = i2;
       }
     }
-    const double vmax = __shfl_sync(FULL, v, 0);
+    const T vmax = __shfl_sync(FULL, v, 0);
     const int piv = __shfl_sync(FULL, idx, 0);
-    if (!(vmax > 0.0)) sing = true;
+    if (!(vmax > T(0))) sing = true;
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
-      const double ak = __shfl_sync(FULL, a[c], k), ap = __shfl_sync(FULL, a[c], piv);
-      const double bk = __shfl_sync(FULL, b[c], k), bp = __shfl_sync(FULL, b[c], piv);
+      const T ak = __shfl_sync(FULL, a[c], k), ap = __shfl_sync(FULL, a[c], piv);
+      const T bk = __shfl_sync(FULL, b[c], k), bp = __shfl_sync(FULL, b[c], piv);
       if (lane == k) {
         a[c] = ap;
         b[c] = bp;
@@ -55,8 +59,8 @@ __device__ void warp_inv5(const double* __restrict__ D, double* __restrict__ out
         b[c] = bk;
       }
     }
-    const double pv = __shfl_sync(FULL, a[k], k);
-    const double pinv = pv != 0.0 ? 1.0 / pv : 0.0;
+    const T pv = __shfl_sync(FULL, a[k], k);
+    const T pinv = pv != T(0) ? T(1) / pv : T(0);
     if (lane == k) {
 #pragma unroll
       for (int c = 0; c < 5; ++c) {
@@ -64,18 +68,18 @@ __device__ void warp_inv5(const double* __restrict__ D, double* __restrict__ out
         b[c] *= pinv;
       }
     }
-    double pr[5], pb[5];
+    T pr[5], pb[5];
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
       pr[c] = __shfl_sync(FULL, a[c], k);
       pb[c] = __shfl_sync(FULL, b[c], k);
     }
     if (lane < 5 && lane != k) {
-      const double f = a[k];
+      const T f = a[k];
 #pragma unroll
       for (int c = 0; c < 5; ++c) {
-        a[c] = fma(-f, pr[c], a[c]);
-        b[c] = fma(-f, pb[c], b[c]);
+        a[c] = fmaT(-f, pr[c], a[c]);
+        b[c] = fmaT(-f, pb[c], b[c]);
       }
     }
   }
@@ -86,8 +90,50 @@ __device__ void warp_inv5(const double* __restrict__ D, double* __restrict__ out
   if (sing && lane == 0) atomicOr(err, 2);
 }
 
-// Block ILU(0) of R_p J R_p^T (IKJ form), rows in forward-level order.
-__global__ void __launch_bounds__(256) k_ilu_factor(RasDev d, const double* __restrict__ val, int32_t* err) {
+template <class T>
+__device__ __forceinline__ T* fvals(const RasDev& d);
+template <>
+__device__ __forceinline__ double* fvals<double>(const RasDev& d) { return d.fval; }
+template <>
+__device__ __forceinline__ float* fvals<float>(const RasDev& d) { return d.fval32; }
+template <class T>
+__device__ __forceinline__ T* dinvs(const RasDev& d);
+template <>
+__device__ __forceinline__ double* dinvs<double>(const RasDev& d) { return d.dinv; }
+template <>
+__device__ __forceinline__ float* dinvs<float>(const RasDev& d) { return d.dinv32; }
+template <class T>
+__device__ __forceinline__ T* ywk(const RasDev& d);
+template <>
+__device__ __forceinline__ double* ywk<double>(const RasDev& d) { return d.ywork; }
+template <>
+__device__ __forceinline__ float* ywk<float>(const RasDev& d) { return d.ywork32; }
+template <class T>
+__device__ __forceinline__ T* zwk(const RasDev& d);
+template <>
+__device__ __forceinline__ double* zwk<double>(const RasDev& d) { return d.zwork; }
+template <>
+__device__ __forceinline__ float* zwk<float>(const RasDev& d) { return d.zwork32; }
+
+template <class T>
+__device__ __forceinline__ const T* solve_fwd(const RasDev& d);
+template <>
+__device__ __forceinline__ const double* solve_fwd<double>(const RasDev& d) { return d.fL; }
+template <>
+__device__ __forceinline__ const float* solve_fwd<float>(const RasDev& d) { return d.fL32; }
+template <class T>
+__device__ __forceinline__ const T* solve_bwd(const RasDev& d);
+template <>
+__device__ __forceinline__ const double* solve_bwd<double>(const RasDev& d) { return d.bU; }
+template <>
+__device__ __forceinline__ const float* solve_bwd<float>(const RasDev& d) { return d.bU32; }
+
+// Block ILU(0) of R_p J R_p^T (IKJ form), rows in forward-level order, in the
+// arithmetic of T (FP64, or FP32 for the mixed-precision path).
+template <class T, class TV>
+__global__ void __launch_bounds__(256) k_ilu_factor(RasDev d, const TV* __restrict__ val, int32_t* err) {
+  T* fval = fvals<T>(d);
+  T* dinv = dinvs<T>(d);
   const int p = blockIdx.x;
   const int32_t r0 = d.sd_row0[p];
   const int32_t r1 = d.sd_row0[p + 1];
@@ -95,7 +141,7 @@ __global__ void __launch_bounds__(256) k_ilu_factor(RasDev d, const double* __re
   for (int64_t idx = threadIdx.x; idx < (b1 - b0) * 25; idx += blockDim.x) {
     const int64_t blk = b0 + idx / 25;
     const int e = (int)(idx % 25);
-    d.fval[25 * blk + e] = val[25 * (int64_t)d.l_gblk[blk] + e];
+    fval[25 * blk + e] = (T)val[25 * (int64_t)d.l_gblk[blk] + e];
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -111,12 +157,12 @@ __global__ void __launch_bounds__(256) k_ilu_factor(RasDev d, const double* __re
       for (int64_t a = a0; a < a1; ++a) {
         const int32_t k = d.l_col[a];
         if (k >= i) break;  // columns are sorted: the strictly lower blocks come first
-        const double* Dk = d.dinv + 25 * ((int64_t)r0 + k);
-        double* A = d.fval + 25 * a;
-        double v = 0.0;
+        const T* Dk = dinv + 25 * ((int64_t)r0 + k);
+        T* A = fval + 25 * a;
+        T v = T(0);
         if (lane < 25) {
 #pragma unroll
-          for (int mm = 0; mm < 5; ++mm) v = fma(A[5 * rr + mm], Dk[5 * mm + cc], v);
+          for (int mm = 0; mm < 5; ++mm) v = fmaT(A[5 * rr + mm], Dk[5 * mm + cc], v);
         }
         __syncwarp();
         if (lane < 25) A[lane] = v;  // L_ik = A_ik U_kk^{-1}
@@ -124,110 +170,239 @@ __global__ void __launch_bounds__(256) k_ilu_factor(RasDev d, const double* __re
         for (int64_t u = d.upd_ptr[a]; u < d.upd_ptr[a + 1]; ++u) {
           const int64_t dst = d.upd[2 * u], src = d.upd[2 * u + 1];
           if (lane < 25) {
-            double t = 0.0;
+            T t = T(0);
 #pragma unroll
-            for (int mm = 0; mm < 5; ++mm) t = fma(A[5 * rr + mm], d.fval[25 * src + 5 * mm + cc], t);
-            d.fval[25 * dst + lane] -= t;  // A_ij -= L_ik U_kj
+            for (int mm = 0; mm < 5; ++mm) t = fmaT(A[5 * rr + mm], fval[25 * src + 5 * mm + cc], t);
+            fval[25 * dst + lane] -= t;  // A_ij -= L_ik U_kj
           }
         }
         __syncwarp();
       }
-      warp_inv5(d.fval + 25 * d.l_diag[R], d.dinv + 25 * R, lane, err);
+      warp_inv5<T>(fval + 25 * d.l_diag[R], dinv + 25 * R, lane, err);
       __syncwarp();
     }
     __syncthreads();
   }
 }
 
-// z_owned += (L_p U_p)^{-1} R_p r restricted to the owned rows (RAS).
-__global__ void __launch_bounds__(256) k_ilu_solve(RasDev d, const double* __restrict__ r, double* __restrict__ z) {
+// ---- subdomain solves ---------------------------------------------------------
+//
+// The solve reads the factors from a copy in level order (SolvePlan): every
+// level of the forward (then backward) sweep is one contiguous range of padded
+// blocks (25 values and the block's local column in slot 25; 26 doubles or 28
+// floats, so a block is a multiple of 16 bytes).  While a level computes, the
+// next level's range is already in flight into the other half of a double
+// buffer in shared memory (cp.async.bulk completing on an mbarrier), so the
+// only global loads on a level's critical path are the solution entries of
+// earlier levels.  Rows are mapped six to a warp (lane = 5 row + component), so
+// the backward sweep's product with the inverted pivot block uses shuffles.
+
+template <class T>
+struct SolveBS;
+template <>
+struct SolveBS<double> {
+  static constexpr int v = 26;
+};
+template <>
+struct SolveBS<float> {
+  static constexpr int v = 28;
+};
+
+__device__ __forceinline__ int col_of(double x) { return (int)__double_as_longlong(x); }
+__device__ __forceinline__ int col_of(float x) { return __float_as_int(x); }
+__device__ __forceinline__ void put_col(double* p, int c) { *p = __longlong_as_double((long long)c); }
+__device__ __forceinline__ void put_col(float* p, int c) { *p = __int_as_float(c); }
+
+template <class T>
+__global__ void k_ilu_reorg(int64_t nblk, const int64_t* __restrict__ src, const int32_t* __restrict__ col,
+                            const T* __restrict__ fval, const T* __restrict__ dinv, T* __restrict__ out) {
+  constexpr int BS = SolveBS<T>::v;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nblk * BS;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = g / BS;
+    const int e = (int)(g - b * BS);
+    if (e < 25) {
+      const int64_t s = src[b];
+      out[g] = s >= 0 ? fval[25 * s + e] : dinv[25 * (-1 - s) + e];
+    } else if (e == 25) {
+      put_col(out + g, col[b]);
+    } else {
+      out[g] = T(0);
+    }
+  }
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait: gives up after a fixed number of polls and reports it
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (int it = 0; it < (1 << 20); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+template <class T, class TZ>
+__global__ void __launch_bounds__(256) k_ilu_solve(RasDev d, const double* __restrict__ r, TZ* __restrict__ z,
+                                                   int32_t* err) {
+  constexpr int BS = SolveBS<T>::v;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ __align__(16) int4 info[2][SOLVE_BUF_ROWS_DEV];
+  __shared__ int sq_rows[2];
+  __shared__ int abort_flag;
+  T* buf[2] = {reinterpret_cast<T*>(smem_raw), reinterpret_cast<T*>(smem_raw) + SOLVE_BUF_BLOCKS_DEV * BS};
   const int p = blockIdx.x;
   const int32_t r0 = d.sd_row0[p];
   const int32_t nl = d.sd_row0[p + 1] - r0;
-  double* y = d.ywork + 5 * (int64_t)r0;
-  double* zz = d.zwork + 5 * (int64_t)r0;
-  const int tid = threadIdx.x, bd = blockDim.x;
-  for (int32_t idx = tid; idx < 5 * nl; idx += bd) {
-    const int32_t l = idx / 5, c = idx - 5 * l;
-    y[idx] = r[5 * (int64_t)d.sd_node[r0 + l] + c];
+  T* y = ywk<T>(d) + 5 * (int64_t)r0;
+  T* zz = zwk<T>(d) + 5 * (int64_t)r0;
+  const T* fL = solve_fwd<T>(d);
+  const T* bU = solve_bwd<T>(d);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int rw = lane / 5, cpt = lane - 5 * rw;
+  const int32_t LF = d.fwd.sd_lev0[p], nF = d.fwd.sd_lev0[p + 1] - LF - 1;
+  const int32_t LB = d.bwd.sd_lev0[p], nB = d.bwd.sd_lev0[p + 1] - LB - 1;
+  const int nstage = nF + nB;
+  if (tid == 0) {
+    mbar_init(&bar[0]);
+    mbar_init(&bar[1]);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int32_t idx = tid; idx < 5 * nl; idx += blockDim.x) {
+    const int32_t l = idx / 5, cc = idx - 5 * l;
+    y[idx] = (T)r[5 * (int64_t)d.sd_node[r0 + l] + cc];
   }
   __syncthreads();
-  // forward: y_i -= sum_{k<i} L_ik y_k
-  {
-    const int32_t L0 = d.sd_fwd_lev0[p];
-    const int32_t nlev = d.sd_fwd_lev0[p + 1] - L0 - 1;
-    for (int32_t lv = 0; lv < nlev; ++lv) {
-      const int32_t s = d.fwd_lev[L0 + lv], e = d.fwd_lev[L0 + lv + 1];
-      for (int32_t idx = tid; idx < 5 * (e - s); idx += bd) {
-        const int32_t ri = s + idx / 5, c = idx % 5;
-        const int32_t i = d.fwd_order[r0 + ri];
-        const int64_t R = (int64_t)r0 + i;
-        double acc = y[5 * i + c];
-        for (int64_t a = d.l_row_ptr[R]; a < d.l_row_ptr[R + 1]; ++a) {
-          const int32_t k = d.l_col[a];
-          if (k >= i) break;
-          const double* L = d.fval + 25 * a + 5 * c;
-          const double* yk = y + 5 * k;
-#pragma unroll
-          for (int mm = 0; mm < 5; ++mm) acc = fma(-L[mm], yk[mm], acc);
-        }
-        y[5 * i + c] = acc;
-      }
-      __syncthreads();
+  // Stage g < nF is forward level g, otherwise backward level g - nF.  One
+  // thread issues the stage's two bulk copies (factor blocks; per-row records)
+  // on the stage buffer's mbarrier and publishes the stage's row count.
+  auto issue = [&](int g) {
+    const bool fw = g < nF;
+    const SolvePlanDev& P = fw ? d.fwd : d.bwd;
+    const int32_t lv = fw ? LF + g : LB + g - nF;
+    const int32_t q0 = P.levpos[lv], q1 = P.levpos[lv + 1];
+    const int64_t b0 = P.levblk[lv], b1 = P.levblk[lv + 1];
+    const uint32_t bytes_b = (uint32_t)((b1 - b0) * BS * sizeof(T));
+    const uint32_t bytes_i = (uint32_t)((q1 - q0) * sizeof(int4));
+    uint64_t* bb = &bar[g & 1];
+    sq_rows[g & 1] = q1 - q0;
+    mbar_arrive_tx(bb, bytes_b + bytes_i);
+    if (bytes_b) bulk_g2s(buf[g & 1], (fw ? fL : bU) + b0 * BS, bytes_b, bb);
+    if (bytes_i) bulk_g2s(info[g & 1], P.info + r0 + q0, bytes_i, bb);
+  };
+  if (tid == 0 && nstage > 0) issue(0);
+  int g = 0;
+  for (; g < nstage; ++g) {
+    if (tid == 0 && g + 1 < nstage) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic reads of that buffer are done
+      issue(g + 1);
     }
+    const bool fw = g < nF;
+    if (!mbar_wait(&bar[g & 1], (uint32_t)((g >> 1) & 1))) abort_flag = 1;
+    __syncthreads();
+    if (abort_flag) break;
+    const T* B = buf[g & 1];
+    const int4* inf = info[g & 1];
+    const int nrows = sq_rows[g & 1];
+    for (int qb = warp * 6; qb < nrows; qb += 6 * (int)(blockDim.x >> 5)) {
+      const int q = qb + rw;
+      const bool act = lane < 30 && q < nrows;
+      int32_t i = 0, st = 0, cn = 0;
+      T acc = T(0), acc2 = T(0);
+      if (act) {
+        const int4 rec = inf[q];
+        i = rec.x;
+        st = rec.y;
+        cn = rec.z;
+        acc = y[5 * i + cpt];
+      }
+      if (fw) {
+        for (int32_t j = 0; j < cn; ++j) {  // y_i -= L_ik y_k  (two accumulators: shorter FMA chains)
+          const T* Lb = B + (st + j) * BS;
+          const T* yk = y + 5 * col_of(Lb[25]);
+          T t = T(0);
+#pragma unroll
+          for (int mm = 0; mm < 5; ++mm) t = fmaT(Lb[5 * cpt + mm], yk[mm], t);
+          if (j & 1) acc2 += t;
+          else acc -= t;
+        }
+        if (act) y[5 * i + cpt] = acc - acc2;
+      } else {
+        for (int32_t j = 1; j < cn; ++j) {  // y_i - sum_j U_ij z_j
+          const T* Ub = B + (st + j) * BS;
+          const T* zj = zz + 5 * col_of(Ub[25]);
+          T t = T(0);
+#pragma unroll
+          for (int mm = 0; mm < 5; ++mm) t = fmaT(Ub[5 * cpt + mm], zj[mm], t);
+          if (j & 1) acc2 += t;
+          else acc -= t;
+        }
+        acc -= acc2;
+        // z_i = U_ii^{-1} (...): the five partial results of row i sit in lanes 5 rw .. 5 rw + 4
+        T v = T(0);
+        const T* Dv = B + st * BS + 5 * cpt;
+#pragma unroll
+        for (int mm = 0; mm < 5; ++mm) {
+          const T am = __shfl_sync(FULL, acc, 5 * rw + mm);
+          if (act) v = fmaT(Dv[mm], am, v);
+        }
+        if (act) zz[5 * i + cpt] = v;
+      }
+    }
+    __syncthreads();
   }
-  // backward: z_i = U_ii^{-1} (y_i - sum_{j>i} U_ij z_j)
-  {
-    const int32_t L0 = d.sd_bwd_lev0[p];
-    const int32_t nlev = d.sd_bwd_lev0[p + 1] - L0 - 1;
-    for (int32_t lv = 0; lv < nlev; ++lv) {
-      const int32_t s = d.bwd_lev[L0 + lv], e = d.bwd_lev[L0 + lv + 1];
-      for (int32_t idx = tid; idx < 5 * (e - s); idx += bd) {
-        const int32_t ri = s + idx / 5, c = idx % 5;
-        const int32_t i = d.bwd_order[r0 + ri];
-        const int64_t R = (int64_t)r0 + i;
-        double acc = y[5 * i + c];
-        for (int64_t a = d.l_diag[R] + 1; a < d.l_row_ptr[R + 1]; ++a) {
-          const int32_t j = d.l_col[a];
-          const double* Ub = d.fval + 25 * a + 5 * c;
-          const double* zj = zz + 5 * j;
-#pragma unroll
-          for (int mm = 0; mm < 5; ++mm) acc = fma(-Ub[mm], zj[mm], acc);
-        }
-        y[5 * i + c] = acc;
-      }
-      __syncthreads();
-      for (int32_t idx = tid; idx < 5 * (e - s); idx += bd) {
-        const int32_t ri = s + idx / 5, c = idx % 5;
-        const int32_t i = d.bwd_order[r0 + ri];
-        const double* Di = d.dinv + 25 * ((int64_t)r0 + i) + 5 * c;
-        const double* yi = y + 5 * i;
-        double v = 0.0;
-#pragma unroll
-        for (int mm = 0; mm < 5; ++mm) v = fma(Di[mm], yi[mm], v);
-        zz[5 * i + c] = v;
-      }
-      __syncthreads();
+  if (abort_flag) {
+    // report, then let every copy still in flight land before the CTA exits
+    if (tid == 0) {
+      atomicOr(err, 8);
+      for (int k = g; k < nstage && k <= g + 1; ++k) mbar_wait(&bar[k & 1], (uint32_t)((k >> 1) & 1));
     }
+    __syncthreads();
+    return;
   }
   const int32_t own0 = d.own_ptr[p], own1 = d.own_ptr[p + 1];
-  for (int32_t idx = tid; idx < 5 * nl; idx += bd) {
-    const int32_t l = idx / 5, c = idx - 5 * l;
+  for (int32_t idx = tid; idx < 5 * nl; idx += blockDim.x) {
+    const int32_t l = idx / 5, cc = idx - 5 * l;
     const int32_t node = d.sd_node[r0 + l];
-    if (node >= own0 && node < own1) z[5 * (int64_t)node + c] = zz[idx];
+    if (node >= own0 && node < own1) z[5 * (int64_t)node + cc] = (TZ)zz[idx];
   }
 }
 
 // ---- coarse space --------------------------------------------------------
 
 // one warp per chunk of J blocks that belong to the same coarse block
+template <class TV>
 __global__ void k_coarse_chunks(int32_t nchunk, const int32_t* __restrict__ cptr, const int32_t* __restrict__ blk,
-                                const double* __restrict__ val, double* __restrict__ cpart) {
+                                const TV* __restrict__ val, double* __restrict__ cpart) {
   const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (gw >= nchunk || lane >= 25) return;
   double s = 0.0;
-  for (int32_t b = cptr[gw]; b < cptr[gw + 1]; ++b) s += val[25 * (int64_t)blk[b] + lane];
+  for (int32_t b = cptr[gw]; b < cptr[gw + 1]; ++b) s += (double)val[25 * (int64_t)blk[b] + lane];
   cpart[25 * gw + lane] = s;
 }
 
@@ -249,7 +424,7 @@ __device__ __forceinline__ double* bblk(double* band, int bw, int ib, int jb) {
 // block step kb: invert the pivot block, form the L column below it
 __global__ void k_band_pivot(int P, int bw, int kb, double* band, double* cdinv, int32_t* err) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  if (warp == 0) warp_inv5(bblk(band, bw, kb, kb), cdinv + 25 * (int64_t)kb, lane, err);
+  if (warp == 0) warp_inv5<double>(bblk(band, bw, kb, kb), cdinv + 25 * (int64_t)kb, lane, err);
   __syncthreads();
   const double* Dk = cdinv + 25 * (int64_t)kb;
   const int rr = lane / 5, cc = lane % 5;
@@ -283,15 +458,22 @@ __global__ void k_band_update(int P, int bw, int kb, double* band) {
   bblk(band, bw, ib, jb)[e] -= v;
 }
 
-// y <- A_c^{-1} y with the banded block LU factors (one CTA, y in shared memory)
+// y <- A_c^{-1} y with the banded block LU factors (one CTA, y in shared memory).
+// With unit != 0, CTA b solves for the unit vector e_b and writes row b of
+// A_c^{-T} (= column b of A_c^{-1}) to yg + b*5P: the explicit inverse.
 __global__ void k_band_solve(int P, int bw, const double* __restrict__ band, const double* __restrict__ cdinv,
-                             double* __restrict__ yg) {
+                             double* __restrict__ yg, int unit) {
   extern __shared__ double ys[];
   const int tid = threadIdx.x, bd = blockDim.x;
   double* bandm = const_cast<double*>(band);
-  for (int k = tid; k < 5 * P; k += bd) ys[k] = yg[k];
+  if (unit) {
+    for (int k = tid; k < 5 * P; k += bd) ys[k] = (k == (int)blockIdx.x) ? 1.0 : 0.0;
+    yg += (int64_t)blockIdx.x * 5 * P;
+  } else {
+    for (int k = tid; k < 5 * P; k += bd) ys[k] = yg[k];
+  }
   __syncthreads();
-  for (int kb = 0; kb < P; ++kb) {
+  for (int kb = unit ? (int)blockIdx.x / 5 : 0; kb < P; ++kb) {  // e_b is zero above block b/5
     const int nb = min(bw, P - 1 - kb);
     for (int t = tid; t < 5 * nb; t += bd) {
       const int ib = kb + 1 + t / 5, r = t % 5;
@@ -327,6 +509,27 @@ __global__ void k_band_solve(int P, int bw, const double* __restrict__ band, con
   for (int k = tid; k < 5 * P; k += bd) yg[k] = ys[k];
 }
 
+// part[chunk][i] = sum_{j in chunk} AinvT[j][i] rc[j]  (AinvT row j = column j of A_c^{-1})
+constexpr int GEMV_CHUNK = 64;
+__global__ void k_coarse_gemv_part(int nc, const double* __restrict__ AinvT, const double* __restrict__ rc,
+                                   double* __restrict__ part) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j0 = blockIdx.y * GEMV_CHUNK;
+  const int j1 = min(nc, j0 + GEMV_CHUNK);
+  if (i >= nc) return;
+  double s = 0.0;
+  for (int j = j0; j < j1; ++j) s = fma(AinvT[(int64_t)j * nc + i], rc[j], s);
+  part[(int64_t)blockIdx.y * nc + i] = s;
+}
+
+__global__ void k_coarse_gemv_sum(int nc, int nchunk, const double* __restrict__ part, double* __restrict__ y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nc) return;
+  double s = 0.0;
+  for (int q = 0; q < nchunk; ++q) s += part[(int64_t)q * nc + i];
+  y[i] = s;
+}
+
 // crhs[cpos[p]] = Z^T r : sums of r over the nodes owned by p, per compartment
 __global__ void __launch_bounds__(256) k_coarse_restrict(const int32_t* __restrict__ own_ptr,
                                                          const int32_t* __restrict__ cpos,
@@ -352,31 +555,59 @@ __global__ void __launch_bounds__(256) k_coarse_restrict(const int32_t* __restri
 }
 
 // z += Z y : every node adds its subdomain's coarse value
+template <class TZ>
 __global__ void k_coarse_prolong_add(int64_t n, const int32_t* __restrict__ owner, const int32_t* __restrict__ cpos,
-                                     const double* __restrict__ y, double* __restrict__ z) {
+                                     const double* __restrict__ y, TZ* __restrict__ z) {
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < 5 * n; g += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = g / 5;
-    z[g] += y[5 * (int64_t)cpos[owner[i]] + (g - 5 * i)];
+    z[g] = (TZ)((double)z[g] + y[5 * (int64_t)cpos[owner[i]] + (g - 5 * i)]);
   }
 }
 
 }  // namespace
 
-void launch_ilu_factor(const RasDev& d, const double* val, int32_t* err, cudaStream_t s) {
-  k_ilu_factor<<<d.P, 256, 0, s>>>(d, val, err);
+void launch_ilu_factor(const RasDev& d, const double* val, const float* val32, int32_t* err, bool fp32,
+                       cudaStream_t s) {
+  if (fp32) k_ilu_factor<float, float><<<d.P, 256, 0, s>>>(d, val32, err);
+  else k_ilu_factor<double, double><<<d.P, 256, 0, s>>>(d, val, err);
   count_launch();
 }
 
-void launch_ilu_solve(const RasDev& d, const double* r, double* z, cudaStream_t s) {
-  k_ilu_solve<<<d.P, 256, 0, s>>>(d, r, z);
+size_t solve_smem(bool fp32) {
+  return fp32 ? 2 * (size_t)SOLVE_BUF_BLOCKS_DEV * SolveBS<float>::v * sizeof(float)
+              : 2 * (size_t)SOLVE_BUF_BLOCKS_DEV * SolveBS<double>::v * sizeof(double);
+}
+
+void launch_ilu_reorg(const RasDev& d, int64_t nfwd, int64_t nbwd, const int64_t* fsrc, const int32_t* fcol,
+                      const int64_t* bsrc, const int32_t* bcol, bool fp32, cudaStream_t s) {
+  const int grid = 152 * 8;
+  if (fp32) {
+    k_ilu_reorg<float><<<grid, 256, 0, s>>>(nfwd, fsrc, fcol, d.fval32, d.dinv32, d.fL32);
+    k_ilu_reorg<float><<<grid, 256, 0, s>>>(nbwd, bsrc, bcol, d.fval32, d.dinv32, d.bU32);
+  } else {
+    k_ilu_reorg<double><<<grid, 256, 0, s>>>(nfwd, fsrc, fcol, d.fval, d.dinv, d.fL);
+    k_ilu_reorg<double><<<grid, 256, 0, s>>>(nbwd, bsrc, bcol, d.fval, d.dinv, d.bU);
+  }
+  count_launch();
   count_launch();
 }
 
-void launch_coarse_assemble(const CoarseDev& c, const double* val, cudaStream_t s) {
+void launch_ilu_solve(const RasDev& d, const double* r, double* z, int32_t* err, cudaStream_t s) {
+  k_ilu_solve<double, double><<<d.P, 256, solve_smem(false), s>>>(d, r, z, err);
+  count_launch();
+}
+
+void launch_ilu_solve32(const RasDev& d, const double* r, float* z, int32_t* err, cudaStream_t s) {
+  k_ilu_solve<float, float><<<d.P, 256, solve_smem(true), s>>>(d, r, z, err);
+  count_launch();
+}
+
+void launch_coarse_assemble(const CoarseDev& c, const double* val, const float* val32, cudaStream_t s) {
   const int64_t W = 2 * (int64_t)c.band + 1;
   cudaMemsetAsync(c.cband, 0, sizeof(double) * 25 * W * c.P, s);
-  k_coarse_chunks<<<(int)((32 * (int64_t)c.nchunk + 255) / 256), 256, 0, s>>>(c.nchunk, c.cchunk_ptr, c.cseg_blk, val,
-                                                                               c.cpart);
+  const int g = (int)((32 * (int64_t)c.nchunk + 255) / 256);
+  if (val) k_coarse_chunks<double><<<g, 256, 0, s>>>(c.nchunk, c.cchunk_ptr, c.cseg_blk, val, c.cpart);
+  else k_coarse_chunks<float><<<g, 256, 0, s>>>(c.nchunk, c.cchunk_ptr, c.cseg_blk, val32, c.cpart);
   k_coarse_dst<<<(int)((25 * (int64_t)c.ndst + 255) / 256), 256, 0, s>>>(c.ndst, c.cdst_ptr, c.cdst_idx, c.cpart,
                                                                           c.cband);
   count_launch();
@@ -394,21 +625,40 @@ void launch_coarse_factor(const CoarseDev& c, int32_t* err, cudaStream_t s) {
       count_launch();
     }
   }
+  if (c.ainvT) {  // explicit inverse: one CTA per unit vector through the banded factors
+    k_band_solve<<<5 * c.P, 256, sizeof(double) * 5 * c.P, s>>>(c.P, c.band, c.cband, c.cdinv, c.ainvT, 1);
+    count_launch();
+  }
 }
 
-void launch_coarse_apply_add(const CoarseDev& c, int64_t n, const double* r, double* z, cudaStream_t s) {
+template <class TZ>
+void launch_coarse_apply_add(const CoarseDev& c, int64_t n, const double* r, TZ* z, cudaStream_t s) {
   k_coarse_restrict<<<c.P, 256, 0, s>>>(c.own_ptr, c.cpos, r, c.crhs);
-  k_band_solve<<<1, 512, sizeof(double) * 5 * c.P, s>>>(c.P, c.band, c.cband, c.cdinv, c.crhs);
+  count_launch();
+  const int nc = 5 * c.P;
+  if (c.ainvT) {
+    const int nchunk = (nc + GEMV_CHUNK - 1) / GEMV_CHUNK;
+    k_coarse_gemv_part<<<dim3((nc + 127) / 128, nchunk), 128, 0, s>>>(nc, c.ainvT, c.crhs, c.cpart);
+    k_coarse_gemv_sum<<<(nc + 127) / 128, 128, 0, s>>>(nc, nchunk, c.cpart, c.crhs + nc);
+    count_launch();
+    count_launch();
+  } else {
+    k_band_solve<<<1, 512, sizeof(double) * nc, s>>>(c.P, c.band, c.cband, c.cdinv, c.crhs, 0);
+    count_launch();
+  }
   int64_t g = (5 * n + 255) / 256;
   if (g > 152 * 8) g = 152 * 8;
-  k_coarse_prolong_add<<<(int)g, 256, 0, s>>>(n, c.owner, c.cpos, c.crhs, z);
-  count_launch();
-  count_launch();
+  k_coarse_prolong_add<TZ><<<(int)g, 256, 0, s>>>(n, c.owner, c.cpos, c.ainvT ? c.crhs + nc : c.crhs, z);
   count_launch();
 }
+template void launch_coarse_apply_add<double>(const CoarseDev&, int64_t, const double*, double*, cudaStream_t);
+template void launch_coarse_apply_add<float>(const CoarseDev&, int64_t, const double*, float*, cudaStream_t);
 
 void coarse_init() {
   cudaFuncSetAttribute(k_band_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  cudaFuncSetAttribute(k_ilu_solve<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)solve_smem(false));
+  cudaFuncSetAttribute(k_ilu_solve<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)solve_smem(true));
 }
 
 }  // namespace seird

@@ -99,6 +99,8 @@ Rates make_rates(const seird_ctx* ctx) {
 
 int64_t vlen(const seird_ctx* ctx) { return 5 * ctx->hs.n; }
 
+bool mixed(const seird_ctx* ctx) { return ctx->opt.precision == 1; }
+
 int check_flags(seird_ctx* ctx, const char* where) {
   CK(cudaMemcpyAsync(ctx->h_err, ctx->err, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
@@ -183,11 +185,13 @@ int residual(seird_ctx* ctx, const double* U, const double* Un, double* F, doubl
 int jacobian(seird_ctx* ctx, const double* U) {
   const HostSetup& hs = ctx->hs;
   KTimer kt_(ctx, SEIRD_K_JACOBIAN);
+  // the mixed path assembles the Jacobian straight into its FP32 copy (FP32
+  // arithmetic); it only feeds the FP32 operator and the FP32 factors
   launch_jacobian((int64_t)hs.col.size(), hs.m, ctx->tri, ctx->xy, U, ctx->bfield, make_rates(ctx),
-                  ctx->opt.quadrature, ctx->rec, ctx->blk_inc_ptr, ctx->blk_inc, ctx->val, ctx->err, ctx->stream);
+                  ctx->opt.quadrature, ctx->rec, ctx->blk_inc_ptr, ctx->blk_inc,
+                  mixed(ctx) ? (void*)ctx->val32 : (void*)ctx->val, mixed(ctx), ctx->err, ctx->stream);
   CK(cudaGetLastError());
-  ctx->jac_ready = true;
-  ctx->pc_ready = false;
+  ctx->jac_ready = true;  // an existing preconditioner stays usable (lagged set-up, options.pc_lag)
   return SEIRD_OK;
 }
 
@@ -213,6 +217,27 @@ RasDev ras_dev(seird_ctx* ctx) {
   d.dinv = ctx->dinv;
   d.ywork = ctx->ywork;
   d.zwork = ctx->zwork;
+  d.fval32 = ctx->fval32;
+  d.dinv32 = ctx->dinv32;
+  d.ywork32 = ctx->ywork32;
+  d.zwork32 = ctx->zwork32;
+  auto plan = [](const seird_ctx::PlanPtrs& q) {
+    SolvePlanDev s;
+    s.row = q.row;
+    s.start = q.start;
+    s.cnt = q.cnt;
+    s.levpos = q.levpos;
+    s.levblk = q.levblk;
+    s.sd_lev0 = q.sd_lev0;
+    s.info = reinterpret_cast<const int4*>(q.info);
+    return s;
+  };
+  d.fwd = plan(ctx->pf);
+  d.bwd = plan(ctx->pb);
+  d.fL = ctx->fL;
+  d.bU = ctx->bU;
+  d.fL32 = ctx->fL32;
+  d.bU32 = ctx->bU32;
   return d;
 }
 
@@ -233,6 +258,7 @@ CoarseDev coarse_dev(seird_ctx* ctx) {
   c.cband = ctx->cband;
   c.cdinv = ctx->cdinv;
   c.crhs = ctx->crhs;
+  c.ainvT = ctx->ainvT;
   return c;
 }
 
@@ -240,13 +266,16 @@ int pc_setup(seird_ctx* ctx) {
   if (!ctx->jac_ready) return fail(ctx, SEIRD_EINVAL, "preconditioner setup needs an assembled Jacobian");
   {
     KTimer kt_(ctx, SEIRD_K_ILU_FACTOR);
-    launch_ilu_factor(ras_dev(ctx), ctx->val, ctx->err, ctx->stream);
+    const RasDev d = ras_dev(ctx);
+    launch_ilu_factor(d, ctx->val, ctx->val32, ctx->err, mixed(ctx), ctx->stream);
+    launch_ilu_reorg(d, (int64_t)ctx->hs.sp_fwd.src.size(), (int64_t)ctx->hs.sp_bwd.src.size(), ctx->pf.src,
+                     ctx->pf.col, ctx->pb.src, ctx->pb.col, mixed(ctx), ctx->stream);
   }
   CK(cudaGetLastError());
   if (ctx->opt.coarse) {
     KTimer kt_(ctx, SEIRD_K_COARSE_SETUP);
     const CoarseDev c = coarse_dev(ctx);
-    launch_coarse_assemble(c, ctx->val, ctx->stream);
+    launch_coarse_assemble(c, ctx->val, ctx->val32, ctx->stream);
     launch_coarse_factor(c, ctx->err, ctx->stream);
     CK(cudaGetLastError());
   }
@@ -255,16 +284,37 @@ int pc_setup(seird_ctx* ctx) {
   return SEIRD_OK;
 }
 
-// z = M^{-1} r  (every node is owned by exactly one subdomain, so the RAS part
-// writes every entry of z; the coarse part adds to it)
-int pc_apply(seird_ctx* ctx, const double* r, double* z) {
+// z = M^{-1} r with FP32 subdomain factors and an FP32 result (mixed path)
+int pc_apply32(seird_ctx* ctx, const double* r, float* z) {
   {
     KTimer kt_(ctx, SEIRD_K_ILU_SOLVE);
-    launch_ilu_solve(ras_dev(ctx), r, z, ctx->stream);
+    launch_ilu_solve32(ras_dev(ctx), r, z, ctx->err, ctx->stream);
   }
   if (ctx->opt.coarse) {
     KTimer kt_(ctx, SEIRD_K_COARSE_APPLY);
-    launch_coarse_apply_add(coarse_dev(ctx), ctx->hs.n, r, z, ctx->stream);
+    launch_coarse_apply_add<float>(coarse_dev(ctx), ctx->hs.n, r, z, ctx->stream);
+  }
+  CK(cudaGetLastError());
+  return SEIRD_OK;
+}
+
+// z = M^{-1} r  (every node is owned by exactly one subdomain, so the RAS part
+// writes every entry of z; the coarse part adds to it).  On the mixed path the
+// FP32 result is widened into z.
+int pc_apply(seird_ctx* ctx, const double* r, double* z) {
+  if (mixed(ctx)) {
+    TRY(pc_apply32(ctx, r, ctx->Z32));
+    launch_f32_to_f64(vlen(ctx), ctx->Z32, z, ctx->stream);
+    CK(cudaGetLastError());
+    return SEIRD_OK;
+  }
+  {
+    KTimer kt_(ctx, SEIRD_K_ILU_SOLVE);
+    launch_ilu_solve(ras_dev(ctx), r, z, ctx->err, ctx->stream);
+  }
+  if (ctx->opt.coarse) {
+    KTimer kt_(ctx, SEIRD_K_COARSE_APPLY);
+    launch_coarse_apply_add<double>(coarse_dev(ctx), ctx->hs.n, r, z, ctx->stream);
   }
   CK(cudaGetLastError());
   return SEIRD_OK;
@@ -272,7 +322,16 @@ int pc_apply(seird_ctx* ctx, const double* r, double* z) {
 
 int spmv(seird_ctx* ctx, const double* x, double* y) {
   KTimer kt_(ctx, SEIRD_K_SPMV);
-  launch_spmv<double>(ctx->hs.n, ctx->row_ptr, ctx->col, ctx->val, x, y, ctx->stream);
+  if (mixed(ctx)) launch_spmv<float>(ctx->hs.n, ctx->row_ptr, ctx->col, ctx->val32, x, y, ctx->stream);
+  else launch_spmv<double>(ctx->hs.n, ctx->row_ptr, ctx->col, ctx->val, x, y, ctx->stream);
+  CK(cudaGetLastError());
+  return SEIRD_OK;
+}
+
+// y = J x with the FP32 matrix copy and FP32 x (mixed path)
+int spmv32(seird_ctx* ctx, const float* x, double* y) {
+  KTimer kt_(ctx, SEIRD_K_SPMV);
+  launch_spmv32(ctx->hs.n, ctx->row_ptr, ctx->col, ctx->val32, x, y, ctx->stream);
   CK(cudaGetLastError());
   return SEIRD_OK;
 }
@@ -296,7 +355,7 @@ int norm2(seird_ctx* ctx, const double* x, double* out) {
 // Stops on ||r|| <= max(rtol ||b||, atol); dtol divergence and non-finite
 // estimates are errors; hitting the iteration limit returns SEIRD_OK with
 // *converged = false (Newton then takes the inexact step).
-int gmres(seird_ctx* ctx, const double* b, double* x, int* its_out, bool* converged) {
+int gmres(seird_ctx* ctx, const double* b, double* x, double rtol, int* its_out, bool* converged) {
   const int64_t len = vlen(ctx);
   const int m = ctx->opt.gmres_restart;
   const int ldh = m + 1;
@@ -313,7 +372,7 @@ int gmres(seird_ctx* ctx, const double* b, double* x, int* its_out, bool* conver
     *converged = true;
     return SEIRD_OK;
   }
-  const double tol = std::max(ctx->opt.gmres_rtol * bnorm, ctx->opt.gmres_atol);
+  const double tol = std::max(rtol * bnorm, ctx->opt.gmres_atol);
   const double* r = b;
   double rnorm = bnorm;
   int its = 0;
@@ -328,9 +387,15 @@ int gmres(seird_ctx* ctx, const double* b, double* x, int* its_out, bool* conver
     bool done = false;
     for (int j = 0; j < m; ++j) {
       double* Vj = ctx->V + (int64_t)j * len;
-      double* Zj = ctx->Z + (int64_t)j * len;
-      TRY(pc_apply(ctx, Vj, Zj));
-      TRY(spmv(ctx, Zj, ctx->w));
+      if (mixed(ctx)) {  // FP32 preconditioner and operator inside the FP64 FGMRES
+        float* Zj = ctx->Z32 + (int64_t)j * len;
+        TRY(pc_apply32(ctx, Vj, Zj));
+        TRY(spmv32(ctx, Zj, ctx->w));
+      } else {
+        double* Zj = ctx->Z + (int64_t)j * len;
+        TRY(pc_apply(ctx, Vj, Zj));
+        TRY(spmv(ctx, Zj, ctx->w));
+      }
       {
         KTimer kt_(ctx, SEIRD_K_KRYLOV);
         launch_mdot(len, j + 1, ctx->V, len, ctx->w, ctx->partial, ctx->red_grid, h1, s);
@@ -354,14 +419,15 @@ int gmres(seird_ctx* ctx, const double* b, double* x, int* its_out, bool* conver
       if (its >= ctx->opt.gmres_maxit) break;
     }
     launch_hsolve(k, ctx->gm, ldh, s);
-    launch_multi_axpy(len, k, ctx->Z, len, gbuf + ldh, x, s);  // y lives right after g
+    if (mixed(ctx)) launch_multi_axpy32(len, k, ctx->Z32, len, gbuf + ldh, x, s);
+    else launch_multi_axpy(len, k, ctx->Z, len, gbuf + ldh, x, s);  // y lives right after g
     CK(cudaGetLastError());
     if (done) {
       *converged = true;
       break;
     }
     if (its >= ctx->opt.gmres_maxit) break;
-    // restart from the true residual r = b - J x
+    // restart from the residual r = b - J x of the operator GMRES works with
     TRY(spmv(ctx, x, ctx->w));
     launch_axpby(len, 1.0, b, -1.0, ctx->w, ctx->w, s);
     TRY(norm2(ctx, ctx->w, &rnorm));
@@ -408,6 +474,7 @@ int newton_step(seird_ctx* ctx, seird_stats* st) {
   double unorm;
   TRY(norm2(ctx, ctx->Un, &unorm));
   int its = 0;
+  double eta = ctx->opt.gmres_rtol, f_prev = f;
   auto restore = [&](int code) {
     cudaMemcpyAsync(ctx->U, ctx->Un, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
     cudaStreamSynchronize(s);
@@ -429,10 +496,24 @@ int newton_step(seird_ctx* ctx, seird_stats* st) {
     }
     // J dU = -F
     launch_axpby(len, -1.0, ctx->F, 0.0, ctx->F, ctx->stage, s);
+    if (ctx->opt.gmres_forcing == 1) {
+      // Eisenstat-Walker choice 2 with the usual safeguard, capped at 0.5, and
+      // no tighter than what brings ||F|| to the Newton target
+      double e = its == 0 ? 0.1 : 0.9 * (f / f_prev) * (f / f_prev);
+      if (its > 0 && 0.9 * eta * eta > 0.1) e = std::max(e, 0.9 * eta * eta);
+      // near the Newton target, solve just far enough to finish in this iteration
+      const double tgt = (ctx->opt.newton_rtol * f0 + ctx->opt.newton_atol) / f;
+      if (e < 10.0 * tgt) e = 0.2 * tgt;
+      e = std::max(e, 0.2 * tgt);
+      eta = std::min(std::max(e, 1e-14), 0.5);
+    } else {
+      eta = ctx->opt.gmres_rtol;
+    }
+    f_prev = f;
     t0 = clk::now();
     int lits = 0;
     bool conv = false;
-    rc = gmres(ctx, ctx->stage, ctx->dU, &lits, &conv);
+    rc = gmres(ctx, ctx->stage, ctx->dU, eta, &lits, &conv);
     S.ms_solve += ms_since(t0);
     S.gmres_its += lits;
     if (rc) return restore(rc);
@@ -456,8 +537,8 @@ int newton_step(seird_ctx* ctx, seird_stats* st) {
     TRY(norm2(ctx, ctx->dU, &dn));
     S.eps_update = unorm > 0 ? lam * dn / unorm : 0.0;
     if (verbose())
-      std::fprintf(stderr, "[seird] t=%g newton %d |F| %.6e -> %.6e (f0 %.6e) gmres %d conv %d lambda %g |dU| %.3e\n",
-                   ctx->t, its, f, ft, f0, lits, (int)conv, lam, dn);
+      std::fprintf(stderr, "[seird] t=%g newton %d |F| %.6e -> %.6e (f0 %.6e) gmres %d (eta %.2e) conv %d lambda %g |dU| %.3e\n",
+                   ctx->t, its, f, ft, f0, lits, eta, (int)conv, lam, dn);
     std::swap(ctx->U, ctx->Ut);
     std::swap(ctx->F, ctx->Ft);
     f = ft;
@@ -498,6 +579,147 @@ int from_internal(seird_ctx* ctx, const double* src, double* dst, int on_device)
   CK(cudaMemcpyAsync(dst, ctx->stage, sizeof(double) * len, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   return SEIRD_OK;
+}
+
+// Device buffers owned by one adjoint call (freed on every return path).
+struct Scratch {
+  std::vector<void*> ptrs;
+  ~Scratch() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+  template <class T>
+  int get(seird_ctx* ctx, T** p, size_t count) {
+    cudaError_t e = cudaMalloc((void**)p, sizeof(T) * std::max<size_t>(count, 1));
+    if (e != cudaSuccess) return fail(ctx, SEIRD_ENOMEM, std::string("adjoint: cudaMalloc: ") + cudaGetErrorString(e));
+    ptrs.push_back(*p);
+    return SEIRD_OK;
+  }
+};
+
+int adjoint_impl(seird_ctx* ctx, const seird_misfit* sp, double* jout, double* grad, double* gfield) {
+  const HostSetup& hs = ctx->hs;
+  const int64_t n = hs.n, len = 5 * n, nnzb = (int64_t)hs.col.size();
+  const int N = sp->n_steps, C = sp->checkpoint_every;
+  if (ctx->opt.precision != 0) return fail(ctx, SEIRD_EINVAL, "adjoint: FP64 contexts only");
+  if (N < 1 || C < 1 || sp->n_obs_nodes < 1 || sp->n_obs_steps < 1 || !sp->obs_nodes || !sp->obs_steps ||
+      !sp->I_hat || !sp->D_hat)
+    return fail(ctx, SEIRD_EINVAL, "adjoint: bad misfit specification");
+  std::vector<int32_t> obs_of_step(N + 1, -1);
+  for (int r = 0; r < sp->n_obs_steps; ++r) {
+    const int k = sp->obs_steps[r];
+    if (k < 1 || k > N || (r > 0 && k <= sp->obs_steps[r - 1]))
+      return fail(ctx, SEIRD_EINVAL, "adjoint: obs_steps must increase within 1..n_steps");
+    obs_of_step[k] = r;
+  }
+  std::vector<int32_t> nodes(sp->n_obs_nodes);
+  std::vector<char> seen(n, 0);
+  for (int q = 0; q < sp->n_obs_nodes; ++q) {
+    const int32_t i = sp->obs_nodes[q];
+    if (i < 0 || i >= n || seen[i]) return fail(ctx, SEIRD_EINVAL, "adjoint: obs_nodes out of range or repeated");
+    seen[i] = 1;
+    nodes[q] = hs.iperm[i];
+  }
+  const double rtol = sp->lin_rtol > 0 ? sp->lin_rtol : 1e-10;
+  const cudaStream_t s = ctx->stream;
+  const int nseg = (N + C - 1) / C;
+  Scratch S;
+  double *ckpt, *seg, *lam, *lam_next, *rhs, *valT, *Ihat, *Dhat, *gacc, *gf, *jacc;
+  int32_t* dnodes;
+  TRY(S.get(ctx, &ckpt, (size_t)(nseg + 1) * len));
+  TRY(S.get(ctx, &seg, (size_t)(C + 1) * len));
+  TRY(S.get(ctx, &lam, len));
+  TRY(S.get(ctx, &lam_next, len));
+  TRY(S.get(ctx, &rhs, len));
+  TRY(S.get(ctx, &valT, 25 * nnzb));
+  TRY(S.get(ctx, &Ihat, (size_t)sp->n_obs_steps * sp->n_obs_nodes));
+  TRY(S.get(ctx, &Dhat, (size_t)sp->n_obs_steps * sp->n_obs_nodes));
+  TRY(S.get(ctx, &gacc, 16));
+  TRY(S.get(ctx, &gf, n));
+  TRY(S.get(ctx, &jacc, 2));
+  TRY(S.get(ctx, &dnodes, sp->n_obs_nodes));
+  const size_t nobs_all = (size_t)sp->n_obs_steps * sp->n_obs_nodes;
+  CK(cudaMemcpyAsync(Ihat, sp->I_hat, sizeof(double) * nobs_all, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(Dhat, sp->D_hat, sizeof(double) * nobs_all, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(dnodes, nodes.data(), sizeof(int32_t) * nodes.size(), cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(gacc, 0, sizeof(double) * 16, s));
+  CK(cudaMemsetAsync(gf, 0, sizeof(double) * n, s));
+  CK(cudaMemsetAsync(jacc, 0, sizeof(double) * 2, s));
+  CK(cudaMemsetAsync(lam_next, 0, sizeof(double) * len, s));
+  const double t0 = ctx->t;
+  CK(cudaMemcpyAsync(ckpt, ctx->U, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
+  auto restore = [&](int code) {
+    cudaMemcpyAsync(ctx->U, ckpt, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
+    cudaStreamSynchronize(s);
+    ctx->t = t0;
+    return code;
+  };
+  const int nobs = sp->n_obs_nodes;
+  // forward run: checkpoints and misfit
+  for (int k = 1; k <= N; ++k) {
+    int rc = newton_step(ctx, nullptr);
+    if (rc) return restore(rc);
+    if (k % C == 0) CK(cudaMemcpyAsync(ckpt + (size_t)(k / C) * len, ctx->U, sizeof(double) * len,
+                                       cudaMemcpyDeviceToDevice, s));
+    if (obs_of_step[k] >= 0) {
+      const int r = obs_of_step[k];
+      launch_misfit(nobs, dnodes, Ihat + (size_t)r * nobs, Dhat + (size_t)r * nobs, ctx->U, nullptr, jacc, s);
+    }
+  }
+  // reverse sweep, segment by segment from the checkpoints
+  const int grid = 152 * 8;
+  for (int sgi = nseg - 1; sgi >= 0; --sgi) {
+    const int k0 = sgi * C, k1 = std::min(N, (sgi + 1) * C);
+    CK(cudaMemcpyAsync(ctx->U, ckpt + (size_t)sgi * len, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(seg, ctx->U, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
+    for (int k = k0 + 1; k <= k1; ++k) {
+      int rc = newton_step(ctx, nullptr);
+      if (rc) return restore(rc);
+      CK(cudaMemcpyAsync(seg + (size_t)(k - k0) * len, ctx->U, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
+    }
+    for (int k = k1; k > k0; --k) {
+      const double* Uk = seg + (size_t)(k - k0) * len;
+      // rhs = M lambda_{k+1} - dj/du^k
+      launch_mass(n, hs.m, ctx->tri, ctx->xy, lam_next, ctx->elem, ctx->node_inc_ptr, ctx->node_inc, rhs,
+                  ctx->partial, ctx->scal + 6, s);
+      if (obs_of_step[k] >= 0) {
+        const int r = obs_of_step[k];
+        launch_misfit(nobs, dnodes, Ihat + (size_t)r * nobs, Dhat + (size_t)r * nobs, Uk, rhs, jacc + 1, s);
+      }
+      // J_k^T lambda_k = rhs with the step's FGMRES and a preconditioner built from J_k^T
+      int rc = jacobian(ctx, Uk);
+      if (rc) return restore(rc);
+      launch_bsr_transpose(nnzb, ctx->tpos, ctx->val, valT, s);
+      std::swap(ctx->val, valT);
+      rc = pc_setup(ctx);
+      int lits = 0;
+      bool conv = false;
+      if (!rc) rc = gmres(ctx, rhs, lam, rtol, &lits, &conv);
+      std::swap(ctx->val, valT);
+      ctx->pc_ready = false;  // the factors belong to J^T
+      if (rc) return restore(rc);
+      if (!conv) return restore(fail(ctx, SEIRD_EGMRES, "adjoint: transposed solve did not converge"));
+      launch_param_contract(n, hs.m, ctx->tri, ctx->xy, Uk, lam, ctx->bfield, make_rates(ctx), ctx->opt.quadrature,
+                            ctx->partial, grid, NV_STRIDE, ctx->elem, ctx->node_inc_ptr, ctx->node_inc, gf, s);
+      launch_reduce_cols(grid, 10, ctx->partial, gacc, 1, s);
+      CK(cudaGetLastError());
+      std::swap(lam, lam_next);
+    }
+  }
+  double jv = 0.0;
+  std::vector<double> g(16);
+  CK(cudaMemcpyAsync(&jv, jacc, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(g.data(), gacc, sizeof(double) * 16, cudaMemcpyDeviceToHost, s));
+  if (gfield) {
+    std::vector<double> gi(n);
+    CK(cudaMemcpyAsync(gi.data(), gf, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int64_t k = 0; k < n; ++k) gfield[hs.perm[k]] = gi[k];
+  }
+  CK(cudaStreamSynchronize(s));
+  if (jout) *jout = jv;
+  if (grad)
+    for (int k = 0; k < 10; ++k) grad[k] = g[k];
+  return restore(SEIRD_OK);
 }
 
 }  // namespace
@@ -553,7 +775,8 @@ static int create_impl(seird_ctx* ctx, const seird_mesh* mesh, const seird_param
   seird_options& o = ctx->opt;
   if (!(o.dt > 0) || o.gmres_restart < 1 || o.gmres_restart > MAX_RESTART || o.gmres_maxit < 1 ||
       o.newton_maxit < 0 || o.ls_maxit < 0 || o.overlap < 0 || (o.coarse != 0 && o.coarse != 1) ||
-      (o.quadrature != 0 && o.quadrature != 1) || (o.precision != 0 && o.precision != 1))
+      (o.quadrature != 0 && o.quadrature != 1) || (o.precision != 0 && o.precision != 1) ||
+      (o.gmres_forcing != 0 && o.gmres_forcing != 1))
     return fail(ctx, SEIRD_EINVAL, "invalid option value");
   std::string err;
   int rc = build_setup(mesh, &o, ctx->hs, err);
@@ -584,6 +807,7 @@ static int create_impl(seird_ctx* ctx, const seird_mesh* mesh, const seird_param
   TRY(upload(ctx, &ctx->perm, hs.perm));
   TRY(upload(ctx, &ctx->row_ptr, hs.row_ptr));
   TRY(upload(ctx, &ctx->col, hs.col));
+  TRY(upload(ctx, &ctx->tpos, hs.tpos));
   TRY(upload(ctx, &ctx->node_inc_ptr, hs.node_inc_ptr));
   TRY(upload(ctx, &ctx->node_inc, hs.node_inc));
   TRY(upload(ctx, &ctx->blk_inc_ptr, hs.blk_inc_ptr));
@@ -593,13 +817,19 @@ static int create_impl(seird_ctx* ctx, const seird_mesh* mesh, const seird_param
     for (int64_t k = 0; k < n; ++k) bf[k] = params->beta_field[hs.perm[k]];
     TRY(upload(ctx, &ctx->bfield, bf));
   }
-  TRY(dalloc(ctx, &ctx->val, 25 * nnzb));
+  if (o.precision == 0) TRY(dalloc(ctx, &ctx->val, 25 * nnzb));
   TRY(dalloc(ctx, &ctx->elem, 15 * m));
   TRY(dalloc(ctx, &ctx->rec, (size_t)REC * m));
   double** vecs[] = {&ctx->U, &ctx->Un, &ctx->F, &ctx->Ft, &ctx->dU, &ctx->Ut, &ctx->stage, &ctx->stage2, &ctx->w};
   for (double** v : vecs) TRY(dalloc(ctx, v, len));
+  const bool mix = o.precision == 1;
   TRY(dalloc(ctx, &ctx->V, (size_t)(R + 1) * len));
-  TRY(dalloc(ctx, &ctx->Z, (size_t)R * len));
+  if (mix) {
+    TRY(dalloc(ctx, &ctx->Z32, (size_t)R * len));
+    TRY(dalloc(ctx, &ctx->val32, 25 * nnzb));
+  } else {
+    TRY(dalloc(ctx, &ctx->Z, (size_t)R * len));
+  }
   const int64_t npart = std::max<int64_t>((int64_t)ctx->red_grid * NV_STRIDE, (n + 255) / 256);
   TRY(dalloc(ctx, &ctx->partial, npart));
   TRY(dalloc(ctx, &ctx->hcol, 2 * NV_STRIDE));
@@ -631,10 +861,32 @@ static int create_impl(seird_ctx* ctx, const seird_mesh* mesh, const seird_param
   TRY(upload(ctx, &ctx->owner, hs.owner));
   const int64_t NL = (int64_t)hs.sd_node.size();
   const int64_t NLB = (int64_t)hs.l_col.size();
-  TRY(dalloc(ctx, &ctx->fval, 25 * NLB));
-  TRY(dalloc(ctx, &ctx->dinv, 25 * NL));
-  TRY(dalloc(ctx, &ctx->ywork, 5 * NL));
-  TRY(dalloc(ctx, &ctx->zwork, 5 * NL));
+  for (int dir = 0; dir < 2; ++dir) {
+    const HostSetup::SolvePlan& sp = dir == 0 ? hs.sp_fwd : hs.sp_bwd;
+    seird_ctx::PlanPtrs& q = dir == 0 ? ctx->pf : ctx->pb;
+    TRY(upload(ctx, &q.row, sp.row));
+    TRY(upload(ctx, &q.start, sp.start));
+    TRY(upload(ctx, &q.cnt, sp.cnt));
+    TRY(upload(ctx, &q.levpos, sp.levpos));
+    TRY(upload(ctx, &q.levblk, sp.levblk));
+    TRY(upload(ctx, &q.sd_lev0, sp.sd_lev0));
+    TRY(upload(ctx, &q.src, sp.src));
+    TRY(upload(ctx, &q.col, sp.col));
+    TRY(upload(ctx, &q.info, sp.info));
+    if (mix) TRY(dalloc(ctx, dir == 0 ? &ctx->fL32 : &ctx->bU32, (size_t)28 * std::max<size_t>(1, sp.src.size())));
+    else TRY(dalloc(ctx, dir == 0 ? &ctx->fL : &ctx->bU, (size_t)26 * std::max<size_t>(1, sp.src.size())));
+  }
+  if (mix) {
+    TRY(dalloc(ctx, &ctx->fval32, 25 * NLB));
+    TRY(dalloc(ctx, &ctx->dinv32, 25 * NL));
+    TRY(dalloc(ctx, &ctx->ywork32, 5 * NL));
+    TRY(dalloc(ctx, &ctx->zwork32, 5 * NL));
+  } else {
+    TRY(dalloc(ctx, &ctx->fval, 25 * NLB));
+    TRY(dalloc(ctx, &ctx->dinv, 25 * NL));
+    TRY(dalloc(ctx, &ctx->ywork, 5 * NL));
+    TRY(dalloc(ctx, &ctx->zwork, 5 * NL));
+  }
   // coarse
   if (o.coarse) {
     TRY(upload(ctx, &ctx->cpos, hs.cpos));
@@ -642,10 +894,14 @@ static int create_impl(seird_ctx* ctx, const seird_mesh* mesh, const seird_param
     TRY(upload(ctx, &ctx->cchunk_ptr, hs.cchunk_ptr));
     TRY(upload(ctx, &ctx->cdst_ptr, hs.cdst_ptr));
     TRY(upload(ctx, &ctx->cdst_idx, hs.cdst_idx));
-    TRY(dalloc(ctx, &ctx->cpart, 25 * (hs.cchunk_ptr.size() - 1)));
+    const int64_t nc = 5 * (int64_t)hs.P;
+    const int64_t nchunk = (int64_t)hs.cchunk_ptr.size() - 1;
+    const bool dense = nc <= DENSE_COARSE_MAX;
+    TRY(dalloc(ctx, &ctx->cpart, std::max<int64_t>(25 * nchunk, dense ? ((nc + 63) / 64) * nc : 0)));
     TRY(dalloc(ctx, &ctx->cband, 25 * (size_t)hs.P * (2 * hs.cband + 1)));
     TRY(dalloc(ctx, &ctx->cdinv, 25 * (size_t)hs.P));
-    TRY(dalloc(ctx, &ctx->crhs, 5 * (size_t)hs.P));
+    TRY(dalloc(ctx, &ctx->crhs, 2 * nc));
+    if (dense) TRY(dalloc(ctx, &ctx->ainvT, (size_t)nc * nc));
   }
   CK(cudaDeviceSynchronize());
   return SEIRD_OK;
@@ -698,6 +954,26 @@ int seird_run(seird_ctx* ctx, int32_t n_steps, seird_stats* per_step) {
   return SEIRD_OK;
 }
 
+int seird_set_params(seird_ctx* ctx, const seird_params* params) {
+  if (!ctx || !params) return fail(ctx, SEIRD_EINVAL, "NULL argument");
+  ctx->params = *params;
+  ctx->params.beta_field = nullptr;
+  if (params->beta_field) {
+    const HostSetup& hs = ctx->hs;
+    std::vector<double> bf(hs.n);
+    for (int64_t k = 0; k < hs.n; ++k) bf[k] = params->beta_field[hs.perm[k]];
+    if (!ctx->bfield) TRY(dalloc(ctx, &ctx->bfield, hs.n));
+    CK(cudaMemcpy(ctx->bfield, bf.data(), sizeof(double) * hs.n, cudaMemcpyHostToDevice));
+  }
+  ctx->pc_ready = false;
+  return SEIRD_OK;
+}
+
+int seird_adjoint(seird_ctx* ctx, const seird_misfit* spec, double* misfit, double* grad, double* grad_field) {
+  if (!ctx || !spec) return fail(ctx, SEIRD_EINVAL, "NULL argument");
+  return adjoint_impl(ctx, spec, misfit, grad, grad_field);
+}
+
 int seird_get_info(const seird_ctx* ctx, seird_info* info) {
   if (!ctx || !info) return SEIRD_EINVAL;
   info->n_nodes = ctx->hs.n;
@@ -736,7 +1012,13 @@ int seird_get_jacobian(const seird_ctx* cctx, int32_t* row_ptr, int32_t* col, do
   const int64_t nnzb = (int64_t)hs.col.size();
   std::vector<double> v(25 * nnzb);
   CK(cudaStreamSynchronize(ctx->stream));
-  CK(cudaMemcpy(v.data(), ctx->val, sizeof(double) * v.size(), cudaMemcpyDeviceToHost));
+  if (mixed(ctx)) {  // the mixed path keeps only the FP32 copy
+    std::vector<float> v32(25 * nnzb);
+    CK(cudaMemcpy(v32.data(), ctx->val32, sizeof(float) * v32.size(), cudaMemcpyDeviceToHost));
+    for (size_t q = 0; q < v.size(); ++q) v[q] = v32[q];
+  } else {
+    CK(cudaMemcpy(v.data(), ctx->val, sizeof(double) * v.size(), cudaMemcpyDeviceToHost));
+  }
   row_ptr[0] = 0;
   std::vector<std::pair<int32_t, int32_t>> ent;
   int64_t pos = 0;
@@ -782,7 +1064,7 @@ int seird_linear_solve(seird_ctx* ctx, const double* b, double* x, int on_device
   TRY(to_internal(ctx, b, on_device, ctx->stage2));
   int k = 0;
   bool conv = false;
-  TRY(gmres(ctx, ctx->stage2, ctx->dU, &k, &conv));
+  TRY(gmres(ctx, ctx->stage2, ctx->dU, ctx->opt.gmres_rtol, &k, &conv));
   if (its) *its = k;
   TRY(from_internal(ctx, ctx->dU, x, on_device));
   return conv ? SEIRD_OK : fail(ctx, SEIRD_EGMRES, "gmres: iteration limit reached");

@@ -215,6 +215,9 @@ int build_setup(const seird_mesh* mesh, const seird_options* opt, HostSetup& hs,
     const int32_t* p = std::lower_bound(b, e, j);
     return (int32_t)(p - hs.col.data());
   };
+  hs.tpos.resize(nnzb);
+  for (int64_t i = 0; i < n; ++i)
+    for (int32_t k = hs.row_ptr[i]; k < hs.row_ptr[i + 1]; ++k) hs.tpos[k] = find_blk(hs.col[k], (int32_t)i);
 
   // ---- element gather lists (deterministic: ordered by triangle) ---------
   hs.node_inc_ptr.assign(n + 1, 0);
@@ -367,6 +370,69 @@ int build_setup(const seird_mesh* mesh, const seird_options* opt, HostSetup& hs,
   if ((int64_t)hs.l_diag.size() != (int64_t)hs.sd_node.size()) {
     err = "internal error: missing diagonal block in a subdomain";
     return SEIRD_EINVAL;
+  }
+
+  // ---- ILU(0) solve plans ---------------------------------------------------
+  for (int dir = 0; dir < 2; ++dir) {
+    HostSetup::SolvePlan& sp = dir == 0 ? hs.sp_fwd : hs.sp_bwd;
+    const std::vector<int32_t>& order = dir == 0 ? hs.fwd_order : hs.bwd_order;
+    const std::vector<int32_t>& levs = dir == 0 ? hs.fwd_lev : hs.bwd_lev;
+    const std::vector<int32_t>& lev0 = dir == 0 ? hs.sd_fwd_lev0 : hs.sd_bwd_lev0;
+    sp.sd_lev0.assign(1, 0);
+    for (int32_t q = 0; q < P; ++q) {
+      const int32_t r0 = hs.sd_row0[q];
+      const int32_t nlev = lev0[q + 1] - lev0[q] - 1;
+      sp.levpos.push_back(0);
+      sp.levblk.push_back((int64_t)sp.src.size());
+      int32_t pos = 0, in_level = 0;
+      for (int32_t v = 0; v < nlev; ++v) {
+        for (int32_t k = levs[lev0[q] + v]; k < levs[lev0[q] + v + 1]; ++k) {
+          const int32_t i = order[r0 + k];
+          const int64_t R = (int64_t)r0 + i;
+          int32_t nb = 0;
+          if (dir == 0) {
+            for (int64_t a = hs.l_row_ptr[R]; a < hs.l_diag[R]; ++a) ++nb;
+          } else {
+            nb = 1 + (int32_t)(hs.l_row_ptr[R + 1] - hs.l_diag[R] - 1);
+          }
+          if ((in_level > 0 && in_level + nb > SOLVE_BUF_BLOCKS) ||
+              pos - sp.levpos.back() >= SOLVE_BUF_ROWS) {  // split: rows of a level are independent
+            sp.levpos.push_back(pos);
+            sp.levblk.push_back((int64_t)sp.src.size());
+            in_level = 0;
+          }
+          sp.row.push_back(i);
+          sp.start.push_back((int64_t)sp.src.size());
+          sp.cnt.push_back(nb);
+          sp.info.push_back(i);
+          sp.info.push_back((int32_t)((int64_t)sp.src.size() - sp.levblk.back()));
+          sp.info.push_back(nb);
+          sp.info.push_back(0);
+          if (dir == 0) {
+            for (int64_t a = hs.l_row_ptr[R]; a < hs.l_diag[R]; ++a) {
+              sp.src.push_back(a);
+              sp.col.push_back(hs.l_col[a]);
+            }
+          } else {
+            sp.src.push_back(-1 - R);
+            sp.col.push_back(i);
+            for (int64_t a = hs.l_diag[R] + 1; a < hs.l_row_ptr[R + 1]; ++a) {
+              sp.src.push_back(a);
+              sp.col.push_back(hs.l_col[a]);
+            }
+          }
+          in_level += nb;
+          ++pos;
+        }
+        sp.levpos.push_back(pos);
+        sp.levblk.push_back((int64_t)sp.src.size());
+        in_level = 0;
+      }
+      sp.sd_lev0.push_back((int32_t)sp.levpos.size());
+    }
+    for (int32_t q = 0; q < P; ++q)
+      for (int32_t v = sp.sd_lev0[q]; v + 1 < sp.sd_lev0[q + 1]; ++v)
+        sp.max_lev_blocks = std::max<int32_t>(sp.max_lev_blocks, (int32_t)(sp.levblk[v + 1] - sp.levblk[v]));
   }
 
   // ---- coarse pattern: subdomain graph, RCM order, band, segment sums -----

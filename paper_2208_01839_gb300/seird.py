@@ -48,7 +48,7 @@ class Options(C.Structure):
                 ("gmres_dtol", C.c_double), ("n_subdomains", C.c_int32), ("overlap", C.c_int32),
                 ("coarse", C.c_int32), ("precision", C.c_int32), ("quadrature", C.c_int32),
                 ("pc_lag", C.c_int32), ("owner", _ip), ("seed", C.c_uint64), ("stream", C.c_void_p),
-                ("timing", C.c_int32)]
+                ("timing", C.c_int32), ("gmres_forcing", C.c_int32)]
 
 
 KERNEL_CLASSES = ["residual", "jacobian", "ilu_factor", "coarse_setup", "spmv", "ilu_solve", "coarse_apply", "krylov"]
@@ -66,6 +66,15 @@ class Stats(C.Structure):
         d["kernel_ms"] = {KERNEL_CLASSES[i]: self.kernel_ms[i] for i in range(8)}
         d["kernel_calls"] = {KERNEL_CLASSES[i]: self.kernel_calls[i] for i in range(8)}
         return d
+
+
+class Misfit(C.Structure):
+    _fields_ = [("n_steps", C.c_int32), ("checkpoint_every", C.c_int32), ("n_obs_nodes", C.c_int32),
+                ("obs_nodes", _ip), ("n_obs_steps", C.c_int32), ("obs_steps", _ip), ("I_hat", _dp),
+                ("D_hat", _dp), ("lin_rtol", C.c_double)]
+
+
+PARAM_NAMES = ("beta_i", "beta_e", "sigma", "gamma_e", "gamma_r", "gamma_d", "nu_S", "nu_E", "nu_I", "nu_R")
 
 
 class Info(C.Structure):
@@ -104,6 +113,8 @@ _linear_solve = _sig("seird_linear_solve", C.c_int, [_vp, _vp, _vp, C.c_int, C.P
 _bsr_spmv = _sig("seird_bsr_spmv", C.c_int, [C.c_int64, _vp, _vp, _vp, _vp, _vp, _vp])
 _bsr_spmv_f32 = _sig("seird_bsr_spmv_f32val", C.c_int, [C.c_int64, _vp, _vp, _vp, _vp, _vp, _vp])
 _launch_count = _sig("seird_launch_count", C.c_int64, [])
+_set_params = _sig("seird_set_params", C.c_int, [_vp, C.POINTER(Params)])
+_adjoint = _sig("seird_adjoint", C.c_int, [_vp, C.POINTER(Misfit), C.POINTER(C.c_double), _vp, _vp])
 _residual_noalloc = _sig("seird_residual_noalloc", C.c_int,
                          [C.c_int64, C.c_int64, _vp, _vp, _vp, _vp, C.POINTER(Params), _vp, C.c_double, C.c_int32,
                           _vp, _vp, _vp, _vp, _vp])
@@ -261,6 +272,31 @@ class Solver:
         arr = (Stats * max(1, n_steps))()
         self._check(_run(self._h, int(n_steps), arr))
         return [arr[k].as_dict() for k in range(n_steps)]
+
+    def set_params(self, params, beta_field=None):
+        p = params_struct(params)
+        if beta_field is not None:
+            self._bf = np.ascontiguousarray(beta_field, dtype=np.float64)
+            p.beta_field = self._bf.ctypes.data_as(_dp)
+        self._check(_set_params(self._h, C.byref(p)))
+
+    def adjoint(self, n_steps, obs_nodes, obs_steps, I_hat, D_hat, checkpoint_every=1, lin_rtol=0.0,
+                field=True):
+        """(misfit, gradient over PARAM_NAMES [10], gradient over the per-node
+        transmission field [n] or None) by the discrete adjoint, from the current
+        state; the state is left unchanged."""
+        nodes = np.ascontiguousarray(obs_nodes, dtype=np.int32)
+        steps = np.ascontiguousarray(obs_steps, dtype=np.int32)
+        Ih = np.ascontiguousarray(I_hat, dtype=np.float64)
+        Dh = np.ascontiguousarray(D_hat, dtype=np.float64)
+        spec = Misfit(int(n_steps), int(checkpoint_every), len(nodes), nodes.ctypes.data_as(_ip), len(steps),
+                      steps.ctypes.data_as(_ip), Ih.ctypes.data_as(_dp), Dh.ctypes.data_as(_dp), float(lin_rtol))
+        j = C.c_double()
+        g = np.zeros(10)
+        gf = np.zeros(self.n) if field else None
+        self._check(_adjoint(self._h, C.byref(spec), C.byref(j), g.ctypes.data,
+                             None if gf is None else gf.ctypes.data))
+        return j.value, g, gf
 
     def info(self):
         inf = Info()

@@ -275,3 +275,49 @@ def test_nonpositive_density_is_reported_not_trapped():
         assert e.value.code == -7
         ok = sv.residual(wl.U0, wl.U0)
         assert np.isfinite(ok).all()
+
+
+# ---------------------------------------------------------------------------
+# mixed precision: FP32 matrix copy and FP32 subdomain factors inside FP64 FGMRES
+# ---------------------------------------------------------------------------
+
+def test_mixed_precision_preconditioner_matches_oracle_to_fp32():
+    wl = I.square_workload(17)
+    owner = I.box_partition(wl.xy, 3, 2)
+    J = O.jacobian(wl.xy, wl.tri, wl.params, wl.dt, wl.U0)
+    rp, col, val = O.to_bsr(J)
+    r = np.random.default_rng(17).standard_normal(5 * wl.n)
+    ref = O.ras_apply(rp, col, val, owner, 1, r, coarse=True)
+    with solver(wl, owner=owner, overlap=1, coarse=1, precision=1) as sv:
+        sv.jacobian(wl.U0)
+        sv.precond_setup()
+        got = sv.precond_apply(r.reshape(-1, 5)).ravel()
+    assert np.linalg.norm(got - ref) <= 1e-4 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("rtol,bar", [(1e-12, 1e-9), (1e-8, 1e-6)])
+def test_mixed_precision_root_matches_fp64_oracle(rtol, bar):
+    """The Newton residual stays FP64, so the FP32 inner solves only change the
+    iteration counts: at a tight tolerance the root matches the FP64 oracle to
+    the FP64 bar; at the metric's 1e-8 it meets the mixed-precision 1e-6 bar."""
+    wl = WL["irregular3k"]
+    atol = newton_floor(wl) if rtol < 1e-9 else 0.0
+    U_ref, _ = O.run(wl.xy, wl.tri, wl.params, wl.dt, wl.U0, 3, rtol=1e-12, atol=newton_floor(wl),
+                     bfield=wl.beta_field)
+    with solver(wl, coarse=1, precision=1, newton_rtol=rtol, newton_atol=atol, gmres_rtol=1e-5) as sv:
+        sv.set_state(wl.U0)
+        stats = sv.run(3)
+        got = sv.get_state()
+    assert max(rel_l2_per_comp(got, U_ref)) <= bar, (rel_l2_per_comp(got, U_ref), stats[-1])
+
+
+def test_mixed_precision_square_step_by_step():
+    wl = I.square_workload(33)
+    U = wl.U0.copy()
+    with solver(wl, precision=1, gmres_rtol=1e-6) as sv:
+        for k in range(3):
+            ref, _ = O.newton_step(wl.xy, wl.tri, wl.params, wl.dt, U, rtol=1e-12)
+            sv.set_state(U)
+            sv.step()
+            assert max(rel_l2_per_comp(sv.get_state(), ref)) <= 1e-9
+            U = ref
