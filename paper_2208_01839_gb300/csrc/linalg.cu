@@ -208,6 +208,32 @@ __global__ void __launch_bounds__(256) k_cgs(int64_t len, int nv, const double* 
 
 inline size_t cgs_smem(int nv) { return sizeof(double) * (TILE + NVMAX + 7 + (size_t)nv * TILE); }
 
+// second CGS pass update and ||w||^2 without staging: every thread needs only its
+// own entries of the basis vectors, so they go straight to registers
+__global__ void __launch_bounds__(256) k_cgs_update_norm(int64_t len, int nv, const double* __restrict__ V,
+                                                         int64_t ld, const double* __restrict__ h,
+                                                         double* __restrict__ w, double* __restrict__ partial) {
+  __shared__ double hs[NVMAX];
+  __shared__ double sh[8];
+  for (int k = threadIdx.x; k < nv; k += blockDim.x) hs[k] = h[k];
+  __syncthreads();
+  double nrm = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
+    double a0 = w[i], a1 = 0.0;
+    int k = 0;
+    for (; k + 1 < nv; k += 2) {
+      a0 = fma(-hs[k], __ldg(V + k * ld + i), a0);
+      a1 = fma(-hs[k + 1], __ldg(V + (k + 1) * ld + i), a1);
+    }
+    if (k < nv) a0 = fma(-hs[k], __ldg(V + k * ld + i), a0);
+    const double wi = a0 + a1;
+    w[i] = wi;
+    nrm = fma(wi, wi, nrm);
+  }
+  nrm = block_sum<256>(nrm, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x * (int64_t)NVMAX] = nrm;
+}
+
 // y = x * a (invert: a := 1/a), a read from device memory; a == 0 gives y = 0
 __global__ void k_scale(int64_t len, const double* __restrict__ x, const double* __restrict__ ap, int invert,
                         double* __restrict__ y) {
@@ -391,7 +417,7 @@ void launch_update_mdot(int64_t len, int nv, const double* V, int64_t ld, const 
 
 void launch_update_norm(int64_t len, int nv, const double* V, int64_t ld, const double* h, double* w,
                         double* partial, int grid, double* out, cudaStream_t s) {
-  k_cgs<2><<<grid, 256, cgs_smem(nv), s>>>(len, nv, V, ld, h, w, partial);
+  k_cgs_update_norm<<<grid, 256, 0, s>>>(len, nv, V, ld, h, w, partial);
   k_reduce_cols<<<1, 256, 0, s>>>(grid, 1, NVMAX, partial, out, 0);
   count_launch();
   count_launch();
@@ -401,7 +427,6 @@ void cgs_init() {
   const int mx = (int)cgs_smem(NVMAX);
   cudaFuncSetAttribute(k_cgs<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_cgs<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_cgs<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
 }
 
 void launch_reduce_cols(int grid, int nv, const double* partial, double* out, int add, cudaStream_t s) {

@@ -288,7 +288,7 @@ int pc_setup(seird_ctx* ctx) {
 int pc_apply32(seird_ctx* ctx, const double* r, float* z) {
   {
     KTimer kt_(ctx, SEIRD_K_ILU_SOLVE);
-    launch_ilu_solve32(ras_dev(ctx), r, z, ctx->err, ctx->stream);
+    launch_ilu_solve32(ras_dev(ctx), r, z, ctx->err, ctx->hs.max_sd_rows, ctx->stream);
   }
   if (ctx->opt.coarse) {
     KTimer kt_(ctx, SEIRD_K_COARSE_APPLY);
@@ -665,8 +665,9 @@ int adjoint_impl(seird_ctx* ctx, const seird_misfit* sp, double* jout, double* g
       launch_misfit(nobs, dnodes, Ihat + (size_t)r * nobs, Dhat + (size_t)r * nobs, ctx->U, nullptr, jacc, s);
     }
   }
-  // reverse sweep, segment by segment from the checkpoints
-  const int grid = 152 * 8;
+  // reverse sweep, segment by segment from the checkpoints; the contraction
+  // kernel's per-CTA partial sums use the red_grid x NV_STRIDE partial buffer
+  const int grid = ctx->red_grid;
   for (int sgi = nseg - 1; sgi >= 0; --sgi) {
     const int k0 = sgi * C, k1 = std::min(N, (sgi + 1) * C);
     CK(cudaMemcpyAsync(ctx->U, ckpt + (size_t)sgi * len, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
