@@ -188,6 +188,9 @@ struct seird_ctx {
   float* fL32 = nullptr;  // (mixed path)
   float* bU32 = nullptr;
   float* Z32 = nullptr;      // [restart][5n] preconditioned basis in FP32
+  double* pct = nullptr;     // [5n] residual between the steps of the multiplicative two-grid
+  double* pcu = nullptr;     // [5n] FP64 post-smoothing correction
+  float* pcu32 = nullptr;    // [5n] FP32 post-smoothing correction
   // coarse
   int32_t* cpos = nullptr;
   int32_t* cseg_blk = nullptr;

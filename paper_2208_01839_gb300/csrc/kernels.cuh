@@ -124,14 +124,13 @@ void launch_ilu_factor(const RasDev& d, const double* val, const float* val32, i
 void launch_ilu_reorg(const RasDev& d, int64_t nfwd, int64_t nbwd, const int64_t* fsrc, const int32_t* fcol,
                       const int64_t* bsrc, const int32_t* bcol, bool fp32, cudaStream_t s);
 void launch_ilu_solve(const RasDev& d, const double* r, double* z, int32_t* err, cudaStream_t s);
-void launch_ilu_solve32(const RasDev& d, const double* r, float* z, int32_t* err, int32_t max_rows, cudaStream_t s);
-// dynamic shared memory of an ILU-solve CTA may not exceed this (static shared memory adds ~4.2 KB)
-constexpr size_t SOLVE_SMEM_LIMIT = 220 * 1024;
+void launch_ilu_solve32(const RasDev& d, const double* r, float* z, int32_t* err, cudaStream_t s);
 void launch_spmv32(int64_t nrow, const int32_t* rp, const int32_t* col, const float* val, const float* x, double* y,
                    cudaStream_t s);
 void launch_multi_axpy32(int64_t len, int nv, const float* Zs, int64_t ld, const double* coef, double* x,
                          cudaStream_t s);
 void launch_f32_to_f64(int64_t n, const float* src, double* dst, cudaStream_t s);
+void launch_add32(int64_t len, const float* u, float* z, cudaStream_t s);
 
 struct CoarseDev {
   int32_t P, band;

@@ -86,6 +86,11 @@ __global__ void k_bsr_transpose(int64_t nnzb, const int32_t* __restrict__ tpos, 
   }
 }
 
+__global__ void k_add32(int64_t len, const float* __restrict__ u, float* __restrict__ z) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
+    z[i] += u[i];
+}
+
 __global__ void k_f32_to_f64(int64_t n, const float* __restrict__ a, double* __restrict__ b) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     b[i] = (double)a[i];
@@ -136,77 +141,94 @@ __global__ void k_reduce_cols(int grid, int nv, int stride, const double* __rest
   }
 }
 
-// CGS2 kernels.  A CTA of 256 threads walks tiles of TILE consecutive entries
-// (grid-stride over tiles); for each tile the nv basis vectors are staged in
-// shared memory once, so every basis vector is read from HBM exactly once per
-// kernel.  Warp wp owns the dot products k = wp, wp+8, ... and keeps their
-// lane partials in registers until the end.
-constexpr int TILE = 256;
 constexpr int KPW = (NVMAX + 7) / 8;  // dot products per warp
 
-// mode 0: partial[cta][k] = sum V_k . w
-// mode 1: w -= V h, then partial[cta][k] = sum V_k . w_new
-// mode 2: w -= V h, then partial[cta][0] = sum w_new^2
-template <int MODE>
-__global__ void __launch_bounds__(256) k_cgs(int64_t len, int nv, const double* __restrict__ V, int64_t ld,
-                                             const double* __restrict__ h, double* __restrict__ w,
-                                             double* __restrict__ partial) {
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, bool valid) {
+  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+  const int n = valid ? 8 : 0;  // src-size 0: nothing is read, the destination is zero-filled
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// CGS passes with double-buffered tiles: while tile t is consumed from shared
+// memory, the basis entries (and w) of tile t+1 stream in through cp.async, so
+// the FP64 pipe does not wait for the loads.  T entries per tile (256, or 128
+// when many basis vectors would not fit twice).
+// mode 0: partial[cta][k] = sum V_k . w ; mode 1: w -= V h, then the dots with w_new
+template <int MODE, int T>
+__global__ void __launch_bounds__(256) k_cgs_db(int64_t len, int nv, const double* __restrict__ V, int64_t ld,
+                                                const double* __restrict__ h, double* __restrict__ w,
+                                                double* __restrict__ partial) {
   extern __shared__ double smem[];
-  double* wt = smem;            // [TILE]
-  double* hs = smem + TILE;     // [NVMAX]
-  double* Vt = hs + NVMAX + 7;  // [nv][TILE]
+  double* hs = smem;                 // [NVMAX + 7]
+  double* wt = hs + NVMAX + 7;       // [T] current w tile (after the update)
+  double* bufs = wt + T;             // [2][nv + 1][T]: basis tiles and the incoming w tile
   const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
-  if (MODE != 0)
+  const int nvb = nv + 1;
+  if (MODE == 1)
     for (int k = tid; k < nv; k += blockDim.x) hs[k] = h[k];
   double acc[KPW];
 #pragma unroll
   for (int q = 0; q < KPW; ++q) acc[q] = 0.0;
-  double nrm = 0.0;
-  const int64_t ntile = (len + TILE - 1) / TILE;
-  for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
-    const int64_t base = tile * TILE;
-    const int64_t i = base + tid;
-    const bool in = i < len;
-    __syncthreads();  // previous tile fully consumed
-    for (int k = 0; k < nv; ++k) Vt[k * TILE + tid] = in ? V[k * ld + i] : 0.0;
-    double wi = in ? w[i] : 0.0;
-    if (MODE != 0) {
-      for (int k = 0; k < nv; ++k) wi = fma(-hs[k], Vt[k * TILE + tid], wi);
-      if (in) w[i] = wi;
+  const int64_t ntile = (len + T - 1) / T;
+  auto load = [&](int64_t tile, int b) {
+    double* dst = bufs + (size_t)b * nvb * T;
+    const int64_t base = tile * T;
+    for (int idx = tid; idx < nvb * T; idx += blockDim.x) {
+      const int k = idx / T, e = idx - k * T;
+      const int64_t i = base + e;
+      const bool ok = i < len;
+      const double* src = (k < nv ? V + k * ld : w) + (ok ? i : 0);
+      cp_async8(dst + idx, src, ok);
     }
-    if (MODE == 2) {
-      nrm = fma(wi, wi, nrm);
-    } else {
-      wt[tid] = wi;
-      __syncthreads();
-#pragma unroll
-      for (int q = 0; q < KPW; ++q) {
-        const int k = wp + 8 * q;
-        if (k < nv) {
-          double s = acc[q];
-#pragma unroll
-          for (int e = lane; e < TILE; e += 32) s = fma(Vt[k * TILE + e], wt[e], s);
-          acc[q] = s;
-        }
+  };
+  int64_t tile = blockIdx.x;
+  if (tile < ntile) load(tile, 0);
+  cp_async_commit();
+  for (int b = 0; tile < ntile; tile += gridDim.x, b ^= 1) {
+    if (tile + gridDim.x < ntile) load(tile + gridDim.x, b ^ 1);
+    cp_async_commit();
+    cp_async_wait1();  // the current tile's group has landed (this thread's copies)
+    __syncthreads();   // ... and everyone else's
+    const double* Vt = bufs + (size_t)b * nvb * T;
+    const double* wsrc = Vt + (size_t)nv * T;
+    for (int e = tid; e < T; e += blockDim.x) {
+      double wi = wsrc[e];
+      if (MODE == 1) {
+        for (int k = 0; k < nv; ++k) wi = fma(-hs[k], Vt[k * T + e], wi);
+        const int64_t i = tile * T + e;
+        if (i < len) w[i] = wi;
       }
+      wt[e] = wi;
     }
-  }
-  if (MODE == 2) {
-    __shared__ double sh[8];
-    const double s = block_sum<256>(nrm, sh);
-    if (tid == 0) partial[blockIdx.x * (int64_t)NVMAX] = s;
-  } else {
+    __syncthreads();
 #pragma unroll
     for (int q = 0; q < KPW; ++q) {
       const int k = wp + 8 * q;
-      double s = acc[q];
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-      if (lane == 0 && k < nv) partial[blockIdx.x * (int64_t)NVMAX + k] = s;
+      if (k < nv) {
+        double s = acc[q];
+#pragma unroll
+        for (int e = lane; e < T; e += 32) s = fma(Vt[k * T + e], wt[e], s);
+        acc[q] = s;
+      }
     }
+    __syncthreads();  // buffer b is refilled two tiles later
+  }
+#pragma unroll
+  for (int q = 0; q < KPW; ++q) {
+    const int k = wp + 8 * q;
+    double s = acc[q];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0 && k < nv) partial[blockIdx.x * (int64_t)NVMAX + k] = s;
   }
 }
 
-inline size_t cgs_smem(int nv) { return sizeof(double) * (TILE + NVMAX + 7 + (size_t)nv * TILE); }
+inline int cgs_tile(int nv) { return nv <= 27 ? 256 : 128; }
+inline size_t cgs_db_smem(int nv) {
+  const int T = cgs_tile(nv);
+  return sizeof(double) * (NVMAX + 7 + T + 2 * (size_t)(nv + 1) * T);
+}
 
 // second CGS pass update and ||w||^2 without staging: every thread needs only its
 // own entries of the basis vectors, so they go straight to registers
@@ -381,6 +403,11 @@ void launch_bsr_transpose(int64_t nnzb, const int32_t* tpos, const double* val, 
   count_launch();
 }
 
+void launch_add32(int64_t len, const float* u, float* z, cudaStream_t s) {
+  k_add32<<<grid_for(len), 256, 0, s>>>(len, u, z);
+  count_launch();
+}
+
 void launch_f32_to_f64(int64_t n, const float* src, double* dst, cudaStream_t s) {
   k_f32_to_f64<<<grid_for(n), 256, 0, s>>>(n, src, dst);
   count_launch();
@@ -400,7 +427,10 @@ void launch_norm2(int64_t len, const double* x, double* partial, int grid, doubl
 
 void launch_mdot(int64_t len, int nv, const double* V, int64_t ld, const double* w, double* partial, int grid,
                  double* out, cudaStream_t s) {
-  k_cgs<0><<<grid, 256, cgs_smem(nv), s>>>(len, nv, V, ld, nullptr, const_cast<double*>(w), partial);
+  if (cgs_tile(nv) == 256)
+    k_cgs_db<0, 256><<<grid, 256, cgs_db_smem(nv), s>>>(len, nv, V, ld, nullptr, const_cast<double*>(w), partial);
+  else
+    k_cgs_db<0, 128><<<grid, 256, cgs_db_smem(nv), s>>>(len, nv, V, ld, nullptr, const_cast<double*>(w), partial);
   k_reduce_cols<<<1, 256, 0, s>>>(grid, nv, NVMAX, partial, out, 0);
   count_launch();
   count_launch();
@@ -410,7 +440,8 @@ void launch_mdot(int64_t len, int nv, const double* V, int64_t ld, const double*
 // are added to out_add (which holds the first-pass coefficients h)
 void launch_update_mdot(int64_t len, int nv, const double* V, int64_t ld, const double* h, double* w,
                         double* partial, int grid, double* out_add, cudaStream_t s) {
-  k_cgs<1><<<grid, 256, cgs_smem(nv), s>>>(len, nv, V, ld, h, w, partial);
+  if (cgs_tile(nv) == 256) k_cgs_db<1, 256><<<grid, 256, cgs_db_smem(nv), s>>>(len, nv, V, ld, h, w, partial);
+  else k_cgs_db<1, 128><<<grid, 256, cgs_db_smem(nv), s>>>(len, nv, V, ld, h, w, partial);
   count_launch();
   (void)out_add;
 }
@@ -424,9 +455,11 @@ void launch_update_norm(int64_t len, int nv, const double* V, int64_t ld, const 
 }
 
 void cgs_init() {
-  const int mx = (int)cgs_smem(NVMAX);
-  cudaFuncSetAttribute(k_cgs<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_cgs<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  const int mx = 227 * 1024;
+  cudaFuncSetAttribute(k_cgs_db<0, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_cgs_db<1, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_cgs_db<0, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_cgs_db<1, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
 }
 
 void launch_reduce_cols(int grid, int nv, const double* partial, double* out, int add, cudaStream_t s) {

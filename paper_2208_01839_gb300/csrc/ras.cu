@@ -264,10 +264,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
-// YS: the subdomain's solution vector lives in shared memory (after the stage
-// buffers) and the backward sweep overwrites y with z in place (row i's y is
-// read into registers before its z is written; rows of a stage are independent).
-template <class T, class TZ, bool YS>
+template <class T, class TZ>
 __global__ void __launch_bounds__(256) k_ilu_solve(RasDev d, const double* __restrict__ r, TZ* __restrict__ z,
                                                    int32_t* err) {
   constexpr int BS = SolveBS<T>::v;
@@ -280,9 +277,8 @@ __global__ void __launch_bounds__(256) k_ilu_solve(RasDev d, const double* __res
   const int p = blockIdx.x;
   const int32_t r0 = d.sd_row0[p];
   const int32_t nl = d.sd_row0[p + 1] - r0;
-  T* ysm = reinterpret_cast<T*>(smem_raw) + 2 * SOLVE_BUF_BLOCKS_DEV * BS;
-  T* y = YS ? ysm : ywk<T>(d) + 5 * (int64_t)r0;
-  T* zz = YS ? ysm : zwk<T>(d) + 5 * (int64_t)r0;
+  T* y = ywk<T>(d) + 5 * (int64_t)r0;
+  T* zz = zwk<T>(d) + 5 * (int64_t)r0;
   const T* fL = solve_fwd<T>(d);
   const T* bU = solve_bwd<T>(d);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -597,15 +593,12 @@ void launch_ilu_reorg(const RasDev& d, int64_t nfwd, int64_t nbwd, const int64_t
 }
 
 void launch_ilu_solve(const RasDev& d, const double* r, double* z, int32_t* err, cudaStream_t s) {
-  k_ilu_solve<double, double, false><<<d.P, 256, solve_smem(false), s>>>(d, r, z, err);
+  k_ilu_solve<double, double><<<d.P, 256, solve_smem(false), s>>>(d, r, z, err);
   count_launch();
 }
 
-// FP32: the solution vector in shared memory when the largest subdomain fits
-void launch_ilu_solve32(const RasDev& d, const double* r, float* z, int32_t* err, int32_t max_rows, cudaStream_t s) {
-  const size_t ys = solve_smem(true) + sizeof(float) * 5 * (size_t)max_rows;
-  if (ys <= SOLVE_SMEM_LIMIT) k_ilu_solve<float, float, true><<<d.P, 256, ys, s>>>(d, r, z, err);
-  else k_ilu_solve<float, float, false><<<d.P, 256, solve_smem(true), s>>>(d, r, z, err);
+void launch_ilu_solve32(const RasDev& d, const double* r, float* z, int32_t* err, cudaStream_t s) {
+  k_ilu_solve<float, float><<<d.P, 256, solve_smem(true), s>>>(d, r, z, err);
   count_launch();
 }
 
@@ -663,12 +656,9 @@ template void launch_coarse_apply_add<float>(const CoarseDev&, int64_t, const do
 
 void coarse_init() {
   cudaFuncSetAttribute(k_band_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-  cudaFuncSetAttribute(k_ilu_solve<double, double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(k_ilu_solve<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)solve_smem(false));
-  cudaFuncSetAttribute(k_ilu_solve<float, float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)solve_smem(true));
-  cudaFuncSetAttribute(k_ilu_solve<float, float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)SOLVE_SMEM_LIMIT);
+  cudaFuncSetAttribute(k_ilu_solve<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)solve_smem(true));
 }
 
 }  // namespace seird

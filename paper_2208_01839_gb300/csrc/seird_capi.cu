@@ -284,15 +284,33 @@ int pc_setup(seird_ctx* ctx) {
   return SEIRD_OK;
 }
 
+int spmv32(seird_ctx* ctx, const float* x, double* y);
+int spmv(seird_ctx* ctx, const double* x, double* y);
+
 // z = M^{-1} r with FP32 subdomain factors and an FP32 result (mixed path)
 int pc_apply32(seird_ctx* ctx, const double* r, float* z) {
+  const int64_t len = vlen(ctx);
   {
     KTimer kt_(ctx, SEIRD_K_ILU_SOLVE);
-    launch_ilu_solve32(ras_dev(ctx), r, z, ctx->err, ctx->hs.max_sd_rows, ctx->stream);
+    launch_ilu_solve32(ras_dev(ctx), r, z, ctx->err, ctx->stream);
   }
-  if (ctx->opt.coarse) {
+  if (ctx->opt.coarse == 1) {
     KTimer kt_(ctx, SEIRD_K_COARSE_APPLY);
     launch_coarse_apply_add<float>(coarse_dev(ctx), ctx->hs.n, r, z, ctx->stream);
+  } else if (ctx->opt.coarse == 2) {  // Eq. RAS_2L: coarse on r - J z, then RAS on the new residual
+    TRY(spmv32(ctx, z, ctx->pct));
+    launch_axpby(len, 1.0, r, -1.0, ctx->pct, ctx->pct, ctx->stream);
+    {
+      KTimer kt_(ctx, SEIRD_K_COARSE_APPLY);
+      launch_coarse_apply_add<float>(coarse_dev(ctx), ctx->hs.n, ctx->pct, z, ctx->stream);
+    }
+    TRY(spmv32(ctx, z, ctx->pct));
+    launch_axpby(len, 1.0, r, -1.0, ctx->pct, ctx->pct, ctx->stream);
+    {
+      KTimer kt_(ctx, SEIRD_K_ILU_SOLVE);
+      launch_ilu_solve32(ras_dev(ctx), ctx->pct, ctx->pcu32, ctx->err, ctx->stream);
+    }
+    launch_add32(len, ctx->pcu32, z, ctx->stream);
   }
   CK(cudaGetLastError());
   return SEIRD_OK;
@@ -312,9 +330,24 @@ int pc_apply(seird_ctx* ctx, const double* r, double* z) {
     KTimer kt_(ctx, SEIRD_K_ILU_SOLVE);
     launch_ilu_solve(ras_dev(ctx), r, z, ctx->err, ctx->stream);
   }
-  if (ctx->opt.coarse) {
+  if (ctx->opt.coarse == 1) {
     KTimer kt_(ctx, SEIRD_K_COARSE_APPLY);
     launch_coarse_apply_add<double>(coarse_dev(ctx), ctx->hs.n, r, z, ctx->stream);
+  } else if (ctx->opt.coarse == 2) {  // Eq. RAS_2L: coarse on r - J z, then RAS on the new residual
+    const int64_t len = vlen(ctx);
+    TRY(spmv(ctx, z, ctx->pct));
+    launch_axpby(len, 1.0, r, -1.0, ctx->pct, ctx->pct, ctx->stream);
+    {
+      KTimer kt_(ctx, SEIRD_K_COARSE_APPLY);
+      launch_coarse_apply_add<double>(coarse_dev(ctx), ctx->hs.n, ctx->pct, z, ctx->stream);
+    }
+    TRY(spmv(ctx, z, ctx->pct));
+    launch_axpby(len, 1.0, r, -1.0, ctx->pct, ctx->pct, ctx->stream);
+    {
+      KTimer kt_(ctx, SEIRD_K_ILU_SOLVE);
+      launch_ilu_solve(ras_dev(ctx), ctx->pct, ctx->pcu, ctx->err, ctx->stream);
+    }
+    launch_axpby(len, 1.0, z, 1.0, ctx->pcu, z, ctx->stream);
   }
   CK(cudaGetLastError());
   return SEIRD_OK;
@@ -775,7 +808,7 @@ void seird_destroy(seird_ctx* ctx) {
 static int create_impl(seird_ctx* ctx, const seird_mesh* mesh, const seird_params* params) {
   seird_options& o = ctx->opt;
   if (!(o.dt > 0) || o.gmres_restart < 1 || o.gmres_restart > MAX_RESTART || o.gmres_maxit < 1 ||
-      o.newton_maxit < 0 || o.ls_maxit < 0 || o.overlap < 0 || (o.coarse != 0 && o.coarse != 1) ||
+      o.newton_maxit < 0 || o.ls_maxit < 0 || o.overlap < 0 || o.coarse < 0 || o.coarse > 2 ||
       (o.quadrature != 0 && o.quadrature != 1) || (o.precision != 0 && o.precision != 1) ||
       (o.gmres_forcing != 0 && o.gmres_forcing != 1))
     return fail(ctx, SEIRD_EINVAL, "invalid option value");
@@ -889,6 +922,11 @@ static int create_impl(seird_ctx* ctx, const seird_mesh* mesh, const seird_param
     TRY(dalloc(ctx, &ctx->zwork, 5 * NL));
   }
   // coarse
+  if (o.coarse == 2) {
+    TRY(dalloc(ctx, &ctx->pct, len));
+    if (o.precision == 1) TRY(dalloc(ctx, &ctx->pcu32, len));
+    else TRY(dalloc(ctx, &ctx->pcu, len));
+  }
   if (o.coarse) {
     TRY(upload(ctx, &ctx->cpos, hs.cpos));
     TRY(upload(ctx, &ctx->cseg_blk, hs.cseg_blk));

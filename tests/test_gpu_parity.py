@@ -321,3 +321,34 @@ def test_mixed_precision_square_step_by_step():
             sv.step()
             assert max(rel_l2_per_comp(sv.get_state(), ref)) <= 1e-9
             U = ref
+
+
+# ---------------------------------------------------------------------------
+# the paper's multiplicative two-grid preconditioner (Eq. RAS_2L), coarse = 2
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("overlap", [1, 2])
+def test_multiplicative_two_grid_apply_matches_oracle(overlap):
+    wl = I.square_workload(17)
+    owner = I.box_partition(wl.xy, 3, 2)
+    J = O.jacobian(wl.xy, wl.tri, wl.params, wl.dt, wl.U0)
+    rp, col, val = O.to_bsr(J)
+    r = np.random.default_rng(21).standard_normal(5 * wl.n)
+    ref = O.ras_apply(rp, col, val, owner, overlap, r, multiplicative=True)
+    with solver(wl, owner=owner, overlap=overlap, coarse=2) as sv:
+        sv.jacobian(wl.U0)
+        sv.precond_setup()
+        got = sv.precond_apply(r.reshape(-1, 5)).ravel()
+    assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_multiplicative_two_grid_steps_match_oracle(precision):
+    wl = WL["irregular3k"]
+    U_ref, _ = O.run(wl.xy, wl.tri, wl.params, wl.dt, wl.U0, 3, rtol=1e-12, atol=newton_floor(wl),
+                     bfield=wl.beta_field)
+    with solver(wl, coarse=2, precision=precision) as sv:
+        sv.set_state(wl.U0)
+        sv.run(3)
+        got = sv.get_state()
+    assert max(rel_l2_per_comp(got, U_ref)) <= 1e-9

@@ -450,3 +450,21 @@ def test_table1_parameters_golden():
     po = I.params_ontario(2.0)
     assert po.A == g["ontario"]["A"] and po.nu[2] == g["ontario"]["nu_I"]
     assert abs(po.gamma_d - g["ontario"]["gamma_d"]) < 1e-17
+
+
+def test_multiplicative_two_grid_matches_the_expanded_operator():
+    """Eq. RAS_2L: the three-step correction equals P5 = P1 + P2 + P3 - P2 A P1
+    - P3 A P1 - P3 A P2 + P3 A P2 A P1 with P1 = P3 = M_RAS^{-1}, P2 = Q."""
+    wl, (rp, col, val) = _assembled(7)
+    n = len(rp) - 1
+    A = sp.bsr_matrix((val, col, rp), shape=(5 * n, 5 * n)).toarray()
+    owner = I.box_partition(wl.xy, 2, 2)
+    r = np.random.default_rng(2).standard_normal(5 * n)
+    Mras = np.column_stack([O.ras_apply(rp, col, val, owner, 1, e, coarse=False) for e in np.eye(5 * n)])
+    Ac, Z = O.coarse_matrix(rp, col, val, owner)
+    Q = Z.toarray() @ np.linalg.solve(Ac, Z.T.toarray())
+    P1 = P3 = Mras
+    P2 = Q
+    P5 = P1 + P2 + P3 - P2 @ A @ P1 - P3 @ A @ P1 - P3 @ A @ P2 + P3 @ A @ P2 @ A @ P1
+    z = O.ras_apply(rp, col, val, owner, 1, r, multiplicative=True)
+    assert np.allclose(z, P5 @ r, rtol=1e-10, atol=1e-12 * np.abs(P5 @ r).max())
