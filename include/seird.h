@@ -11,7 +11,8 @@
  *     Radon's degree-5 seven-point rule (or the three-vertex rule).
  *   - Nonlinear solve: Newton with the exact Jacobian and backtracking on
  *     ||F||_2 (Section 2.2 names Newton as the coupled alternative to its
- *     Picard iteration; both converge to the root of Eq. weakform).
+ *     Picard iteration; both converge to the root of Eq. weakform), or the
+ *     coupled Picard iteration of Eq. weak_vec_implicit (options.nonlinear).
  *   - Linear solve: right-preconditioned restarted (F)GMRES with classical
  *     Gram-Schmidt and one re-orthogonalisation (CGS2); stopping rules of
  *     Section 3.2 (rtol, atol, dtol against ||b||_2).
@@ -116,6 +117,14 @@ typedef struct {
                              with Eisenstat-Walker forcing terms (choice 2, gamma 0.9, alpha 2,
                              first term 0.1, at most 0.5); once the term comes within 10x of what
                              reaching the Newton target needs, the solve aims at 0.2x that (0) */
+  int32_t nonlinear;      /* 0: Newton (exact Jacobian, backtracking line search); 1: the Picard
+                             iteration of Eq. weak_vec_implicit, all five compartments coupled:
+                             the coefficients nu(u) and B(u) of Eq. vec_component1/2 frozen at the
+                             previous iterate, full steps, no line search.  Both iterations have
+                             the root of Eq. weakform as fixed point (0) */
+  double picard_tol;      /* Picard only: stop when eps = ||u^{k+1} - u^k|| / ||u^n|| (Eq. picardtol)
+                             is <= picard_tol; 0 stops on the residual test of newton_rtol and
+                             newton_atol instead.  newton_maxit bounds the iterations (0) */
 } seird_options;
 
 /* Kernel classes of seird_stats.kernel_ms / kernel_calls. */
@@ -173,6 +182,21 @@ void seird_default_options(seird_options* opt);
 int seird_create(const seird_mesh* mesh, const seird_params* params, const seird_options* opt,
                  seird_ctx** out);
 
+/* Ensemble of n_samples independent problems on one mesh (parameter sweeps and
+ * sampling of the rates the paper calibrates, Section 4.2): sample k uses the
+ * rates params[k]; params[0].beta_field, if any, is shared by every sample.
+ * The samples form one block-diagonal system over n_samples x n_nodes nodes:
+ * the mesh is partitioned once (options.owner or the seeded bisection into
+ * options.n_subdomains parts) and every sample gets its own copy of those
+ * subdomains, so every kernel launch of a step covers all samples, and no
+ * subdomain, coarse unknown or matrix block couples two samples.  States are
+ * [n_samples][n_nodes][5]; Newton and GMRES test the norms over all samples,
+ * and each sample's state is the root of its own system.  An ensemble's rates
+ * are fixed (seird_set_params, seird_set_beta_schedule and seird_adjoint
+ * return SEIRD_EINVAL). */
+int seird_create_ensemble(const seird_mesh* mesh, int32_t n_samples, const seird_params* params,
+                          const seird_options* opt, seird_ctx** out);
+
 /* Releases every resource of the context (NULL is ignored). */
 void seird_destroy(seird_ctx* ctx);
 
@@ -202,6 +226,32 @@ int seird_get_info(const seird_ctx* ctx, seird_info* info);
  * field; a NULL field keeps the current one).  The mesh, partition and state are
  * kept.  Host pointers, copied. */
 int seird_set_params(seird_ctx* ctx, const seird_params* params);
+
+/* ---- sigmoid transmission schedule (Section 4.2, Eq. beta_ie and Eq. beta_x) --
+ *   beta_I(x, t) = beta_E(x, t) = beta(t) beta(x),
+ *   beta(t) = b0 - b1 / (1 + exp(t_mid - t)),
+ *   beta(x) = beta_central + (beta_eastern - beta_central) / (1 + exp(-k_eastern (x - x_eastern)))
+ *                          + (beta_western - beta_central) / (1 + exp( k_western (x - x_western))),
+ * with x the first mesh coordinate.  The step from t to t + dt uses beta(t + dt)
+ * (backward Euler takes the rates at the end of the step); beta(x) is evaluated
+ * at the nodes and interpolated linearly on every triangle, like
+ * params.beta_field, which it replaces while the schedule is on.  The paper's
+ * values: b0 = 0.101, b1 = 0.05, t_mid = 130 (days), k_eastern = 5,
+ * k_western = 10 (per unit of x); the regional betas and boundaries are fitted
+ * to case data the paper does not print. */
+typedef struct {
+  double b0, b1, t_mid;
+  double beta_central, beta_eastern, beta_western;
+  double x_eastern, x_western;
+  double k_eastern, k_western;
+} seird_beta_schedule;
+
+/* Turns the schedule on (sched copied) or off (sched == NULL: params.beta_i,
+ * beta_e and the transmission field apply again).  The component entry points
+ * (seird_eval_residual and the rest) use the rates of the step that ends at the
+ * context's time + dt.  seird_adjoint rejects a context whose schedule is on
+ * (SEIRD_EINVAL): its gradients are taken with respect to constant rates. */
+int seird_set_beta_schedule(seird_ctx* ctx, const seird_beta_schedule* sched);
 
 /* ---- discrete adjoint -------------------------------------------------------
  * Misfit of observed infected (I) and deceased (D) densities,
@@ -240,7 +290,10 @@ int seird_adjoint(seird_ctx* ctx, const seird_misfit* spec, double* misfit, doub
  * pointers are device pointers when on_device = 1, host pointers otherwise. */
 int seird_eval_residual(seird_ctx* ctx, const double* u, const double* u_prev, double* F, int on_device);
 
-/* Assembles the exact Jacobian dF/du at u into the context's BSR matrix. */
+/* Assembles, at u, the matrix of the context's nonlinear iteration into its BSR
+ * matrix: the exact Jacobian dF/du (options.nonlinear = 0) or the Picard matrix
+ * of Eq. weak_vec_implicit, M + dt (nu(u) grad, grad) - dt (B(u) ., .)
+ * (options.nonlinear = 1). */
 int seird_eval_jacobian(seird_ctx* ctx, const double* u, int on_device);
 
 /* Copies the context's Jacobian out in caller numbering as host BSR arrays

@@ -80,11 +80,12 @@ template <int RULE, bool BF>
 __global__ void __launch_bounds__(128) k_residual_elem(int64_t m, const int32_t* __restrict__ tri,
                                                        const double* __restrict__ xy, const double* __restrict__ U,
                                                        const double* __restrict__ Un,
-                                                       const double* __restrict__ bfield, Rates r,
+                                                       const double* __restrict__ bfield, Rates rin,
                                                        double* __restrict__ elem, int32_t* err) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= m) return;
   const Tri T = load_tri(tri, xy, t);
+  const Rates r = rates_at(rin, T.v[0]);
   double u[3][5], Fe[3][5];
   double Nbar = 0.0;
 #pragma unroll
@@ -210,14 +211,19 @@ __device__ __forceinline__ int sym(int a, int b) {
 // Jacobian record of a triangle.
 // T is the arithmetic and storage type: FP64, or FP32 when the Jacobian only
 // feeds the FP32 operator and FP32 factors of the mixed-precision path.
-template <int RULE, bool BF, class T>
+// PIC: the record of the Picard matrix of Eq. weak_vec_implicit instead (no
+// derivative of N in the diffusion coefficient, and moment 0 holds the
+// coefficient kappa beta_I i b of B(u)'s (E, S) entry instead of the Allee
+// derivative).
+template <int RULE, bool BF, class T, bool PIC>
 __global__ void __launch_bounds__(128) k_jac_record(int64_t m, const int32_t* __restrict__ tri,
                                                     const double* __restrict__ xy, const double* __restrict__ U,
-                                                    const double* __restrict__ bfield, Rates r,
+                                                    const double* __restrict__ bfield, Rates rin,
                                                     T* __restrict__ rec, int32_t* err) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= m) return;
   const Tri Tg = load_tri(tri, xy, t);
+  const Rates r = rates_at(rin, Tg.v[0]);
   TriT<T> Tt;
   Tt.area = (T)Tg.area;
 #pragma unroll
@@ -248,12 +254,14 @@ __global__ void __launch_bounds__(128) k_jac_record(int64_t m, const int32_t* __
   out[REC_K + 5] = an * (Tt.gx[1] * Tt.gx[2] + Tt.gy[1] * Tt.gy[2]);
   // G_{c,a} = |T|/3 grad u_c . grad phi_a (derivative of mean_T(N) by any u_{b,c'})
   const T a3 = Tt.area * T(1.0 / 3.0);
+  if (!PIC) {
 #pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    const T gux = u[0][c] * Tt.gx[0] + u[1][c] * Tt.gx[1] + u[2][c] * Tt.gx[2];
-    const T guy = u[0][c] * Tt.gy[0] + u[1][c] * Tt.gy[1] + u[2][c] * Tt.gy[2];
+    for (int c = 0; c < 4; ++c) {
+      const T gux = u[0][c] * Tt.gx[0] + u[1][c] * Tt.gx[1] + u[2][c] * Tt.gx[2];
+      const T guy = u[0][c] * Tt.gy[0] + u[1][c] * Tt.gy[1] + u[2][c] * Tt.gy[2];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) out[REC_G + 3 * c + a] = a3 * (gux * Tt.gx[a] + guy * Tt.gy[a]);
+      for (int a = 0; a < 3; ++a) out[REC_G + 3 * c + a] = a3 * (gux * Tt.gx[a] + guy * Tt.gy[a]);
+    }
   }
   // reaction moments P^k_ab = |T| sum_q w_q phi_a phi_b rho_k(x_q):
   //   rho_0 = A s lam / N^2 (d kappa/du_c' = A/N^2 for every c'), rho_1 = kappa lam,
@@ -284,7 +292,7 @@ __global__ void __launch_bounds__(128) k_jac_record(int64_t m, const int32_t* __
     const T kappa = T(1) - A * invN;
     const T lam = (bi * uq[2] + be * uq[1]) * bq;
     T rho[4];
-    rho[0] = A * invN * invN * uq[0] * lam;
+    rho[0] = PIC ? kappa * bi * uq[2] * bq : A * invN * invN * uq[0] * lam;
     rho[1] = kappa * lam;
     rho[2] = kappa * uq[0] * be * bq;
     rho[3] = kappa * uq[0] * bi * bq;
@@ -306,13 +314,22 @@ __global__ void __launch_bounds__(128) k_jac_record(int64_t m, const int32_t* __
 // One thread per 5x5 block: fixed-order sums over the triangles sharing the
 // node pair, then the block of dF_i/dU_j:
 //   M delta + dt nubar_c (G_c + K delta) - dt int phi_i phi_j dR_c/du_c'.
-template <class T>
+// RULE: the reaction quadrature.  The degree-5 rule integrates the linear
+// reaction terms exactly (consistent mass Mr = M); the vertex rule lumps them
+// (Mr = |T|/3 on the diagonal pair only), and the Jacobian follows the residual.
+template <class T, bool PIC, int RULE>
 __global__ void __launch_bounds__(128) k_jac_gather(int64_t nnzb, const int32_t* __restrict__ inc_ptr,
                                                     const int32_t* __restrict__ inc, const T* __restrict__ rec,
-                                                    Rates r, T* __restrict__ val) {
+                                                    const int32_t* __restrict__ tri, Rates rin,
+                                                    T* __restrict__ val) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= nnzb) return;
-  T M = 0, K = 0, G[4] = {0, 0, 0, 0}, P[4] = {0, 0, 0, 0};
+  Rates r = rin;
+  if (rin.tab) {  // the block row's node: row vertex of the first incident triangle
+    const int32_t e = inc[inc_ptr[k]];
+    r = rates_at(rin, tri[3 * (int64_t)(e / 9) + (e % 9) / 3]);
+  }
+  T M = 0, Mr = 0, K = 0, G[4] = {0, 0, 0, 0}, P[4] = {0, 0, 0, 0};
   for (int32_t q = inc_ptr[k]; q < inc_ptr[k + 1]; ++q) {
     const int32_t e = inc[q];
     const int32_t t = e / 9, ab = e - 9 * t;
@@ -320,38 +337,69 @@ __global__ void __launch_bounds__(128) k_jac_gather(int64_t nnzb, const int32_t*
     const T* R = rec + (int64_t)REC * t;
     const int s = sym(a, b);
     M += R[0] * (a == b ? T(2.0 / 12.0) : T(1.0 / 12.0));
+    if (RULE == 1 && a == b) Mr += R[0] * T(1.0 / 3.0);
     K += R[REC_K + s];
+    if (!PIC) {
 #pragma unroll
-    for (int c = 0; c < 4; ++c) G[c] += R[REC_G + 3 * c + a];
+      for (int c = 0; c < 4; ++c) G[c] += R[REC_G + 3 * c + a];
+    }
 #pragma unroll
     for (int c = 0; c < 4; ++c) P[c] += R[REC_P + 6 * c + s];
   }
+  if (RULE == 0) Mr = M;
   const T dt = (T)r.dt;
   const T nu0 = (T)r.nu[0], nu1 = (T)r.nu[1], nu2 = (T)r.nu[2], nu3 = (T)r.nu[3];
   const T alpha = (T)r.alpha, mu = (T)r.mu, sigma = (T)r.sigma, ge = (T)r.ge, gr = (T)r.gr, gd = (T)r.gd;
   T B[5][5];
+  if (PIC) {
+    // Picard matrix: M + dt nubar_c K on the diagonal, minus dt int B_cc'(u^k) phi_i phi_j with
+    // B of Eq. vec_component2 (P1 = kappa(beta_I i + beta_E e) b, P2 = kappa s beta_E b,
+    // P0 = kappa beta_I i b here)
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+#pragma unroll
+      for (int c = 0; c < 5; ++c) B[i][c] = T(0);
+#pragma unroll
+    for (int c = 1; c < 5; ++c) B[0][c] = -dt * alpha * Mr;
+    B[0][0] = M + dt * nu0 * K + dt * (mu - alpha) * Mr + dt * P[1];
+    B[1][0] = -dt * P[0];
+    B[1][1] = M + dt * nu1 * K - dt * P[2] + dt * (sigma + ge + mu) * Mr;
+    B[2][1] = -dt * sigma * Mr;
+    B[2][2] = M + dt * nu2 * K + dt * (gr + gd + mu) * Mr;
+    B[3][1] = -dt * ge * Mr;
+    B[3][2] = -dt * gr * Mr;
+    B[3][3] = M + dt * nu3 * K + dt * mu * Mr;
+    B[4][2] = -dt * gd * Mr;
+    B[4][4] = M;
+    T* out = val + 25 * k;
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+#pragma unroll
+      for (int c = 0; c < 5; ++c) out[5 * i + c] = B[i][c];
+    return;
+  }
   // rows S, E: transmission derivative row  dT/du_c' = P0 + [S]P1 + [E]P2 + [I]P3
   const T gS = dt * nu0 * G[0], gE = dt * nu1 * G[1], gI = dt * nu2 * G[2], gR = dt * nu3 * G[3];
 #pragma unroll
   for (int c = 0; c < 5; ++c) {
-    B[0][c] = gS - dt * alpha * M + dt * P[0];
+    B[0][c] = gS - dt * alpha * Mr + dt * P[0];
     B[1][c] = gE - dt * P[0];
     B[2][c] = gI;
     B[3][c] = gR;
     B[4][c] = T(0);
   }
-  B[0][0] += M + dt * nu0 * K + dt * P[1] + dt * mu * M;
+  B[0][0] += M + dt * nu0 * K + dt * P[1] + dt * mu * Mr;
   B[0][1] += dt * P[2];
   B[0][2] += dt * P[3];
   B[1][0] -= dt * P[1];
-  B[1][1] += M + dt * nu1 * K - dt * P[2] + dt * (sigma + ge + mu) * M;
+  B[1][1] += M + dt * nu1 * K - dt * P[2] + dt * (sigma + ge + mu) * Mr;
   B[1][2] -= dt * P[3];
-  B[2][1] -= dt * sigma * M;
-  B[2][2] += M + dt * nu2 * K + dt * (gr + gd + mu) * M;
-  B[3][1] -= dt * ge * M;
-  B[3][2] -= dt * gr * M;
-  B[3][3] += M + dt * nu3 * K + dt * mu * M;
-  B[4][2] -= dt * gd * M;
+  B[2][1] -= dt * sigma * Mr;
+  B[2][2] += M + dt * nu2 * K + dt * (gr + gd + mu) * Mr;
+  B[3][1] -= dt * ge * Mr;
+  B[3][2] -= dt * gr * Mr;
+  B[3][3] += M + dt * nu3 * K + dt * mu * Mr;
+  B[4][2] -= dt * gd * Mr;
   B[4][4] += M;
   T* out = val + 25 * k;
 #pragma unroll
@@ -529,32 +577,52 @@ void launch_residual(int64_t n, int64_t m, const int32_t* tri, const double* xy,
   count_launch();
 }
 
-void launch_jacobian(int64_t nnzb, int64_t m, const int32_t* tri, const double* xy, const double* U,
-                     const double* bfield, const Rates& r, int rule, void* rec, const int32_t* inc_ptr,
-                     const int32_t* inc, void* val, bool fp32, int32_t* err, cudaStream_t s) {
+// beta(x) of the sigmoid schedule (Eq. beta_x) at every node, x = first coordinate
+__global__ void k_beta_field(int64_t n, const double* __restrict__ xy, seird_beta_schedule s, double* __restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double x = xy[2 * i];
+  const double east = (s.beta_eastern - s.beta_central) / (1.0 + exp(-s.k_eastern * (x - s.x_eastern)));
+  const double west = (s.beta_western - s.beta_central) / (1.0 + exp(s.k_western * (x - s.x_western)));
+  out[i] = s.beta_central + east + west;
+}
+
+void launch_beta_field(int64_t n, const double* xy, const seird_beta_schedule& s, double* out, cudaStream_t st) {
+  k_beta_field<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, xy, s, out);
+  count_launch();
+}
+
+template <class T, bool PIC>
+static void jacobian_kernels(int64_t nnzb, int64_t m, const int32_t* tri, const double* xy, const double* U,
+                             const double* bfield, const Rates& r, int rule, T* rc, const int32_t* inc_ptr,
+                             const int32_t* inc, T* val, int32_t* err, cudaStream_t s) {
   const int tb = 128;
   const int64_t g = (m + tb - 1) / tb;
   const int64_t g2 = (nnzb + tb - 1) / tb;
+  if (rule == 0) {
+    if (bfield) k_jac_record<0, true, T, PIC><<<g, tb, 0, s>>>(m, tri, xy, U, bfield, r, rc, err);
+    else k_jac_record<0, false, T, PIC><<<g, tb, 0, s>>>(m, tri, xy, U, bfield, r, rc, err);
+  } else {
+    if (bfield) k_jac_record<1, true, T, PIC><<<g, tb, 0, s>>>(m, tri, xy, U, bfield, r, rc, err);
+    else k_jac_record<1, false, T, PIC><<<g, tb, 0, s>>>(m, tri, xy, U, bfield, r, rc, err);
+  }
+  if (rule == 0) k_jac_gather<T, PIC, 0><<<g2, tb, 0, s>>>(nnzb, inc_ptr, inc, rc, tri, r, val);
+  else k_jac_gather<T, PIC, 1><<<g2, tb, 0, s>>>(nnzb, inc_ptr, inc, rc, tri, r, val);
+}
+
+void launch_jacobian(int64_t nnzb, int64_t m, const int32_t* tri, const double* xy, const double* U,
+                     const double* bfield, const Rates& r, int rule, void* rec, const int32_t* inc_ptr,
+                     const int32_t* inc, void* val, bool fp32, bool picard, int32_t* err, cudaStream_t s) {
   if (fp32) {
     float* rc = static_cast<float*>(rec);
-    if (rule == 0) {
-      if (bfield) k_jac_record<0, true, float><<<g, tb, 0, s>>>(m, tri, xy, U, bfield, r, rc, err);
-      else k_jac_record<0, false, float><<<g, tb, 0, s>>>(m, tri, xy, U, bfield, r, rc, err);
-    } else {
-      if (bfield) k_jac_record<1, true, float><<<g, tb, 0, s>>>(m, tri, xy, U, bfield, r, rc, err);
-      else k_jac_record<1, false, float><<<g, tb, 0, s>>>(m, tri, xy, U, bfield, r, rc, err);
-    }
-    k_jac_gather<float><<<g2, tb, 0, s>>>(nnzb, inc_ptr, inc, rc, r, static_cast<float*>(val));
+    float* v = static_cast<float*>(val);
+    if (picard) jacobian_kernels<float, true>(nnzb, m, tri, xy, U, bfield, r, rule, rc, inc_ptr, inc, v, err, s);
+    else jacobian_kernels<float, false>(nnzb, m, tri, xy, U, bfield, r, rule, rc, inc_ptr, inc, v, err, s);
   } else {
     double* rc = static_cast<double*>(rec);
-    if (rule == 0) {
-      if (bfield) k_jac_record<0, true, double><<<g, tb, 0, s>>>(m, tri, xy, U, bfield, r, rc, err);
-      else k_jac_record<0, false, double><<<g, tb, 0, s>>>(m, tri, xy, U, bfield, r, rc, err);
-    } else {
-      if (bfield) k_jac_record<1, true, double><<<g, tb, 0, s>>>(m, tri, xy, U, bfield, r, rc, err);
-      else k_jac_record<1, false, double><<<g, tb, 0, s>>>(m, tri, xy, U, bfield, r, rc, err);
-    }
-    k_jac_gather<double><<<g2, tb, 0, s>>>(nnzb, inc_ptr, inc, rc, r, static_cast<double*>(val));
+    double* v = static_cast<double*>(val);
+    if (picard) jacobian_kernels<double, true>(nnzb, m, tri, xy, U, bfield, r, rule, rc, inc_ptr, inc, v, err, s);
+    else jacobian_kernels<double, false>(nnzb, m, tri, xy, U, bfield, r, rule, rc, inc_ptr, inc, v, err, s);
   }
   count_launch();
   count_launch();
@@ -657,7 +725,7 @@ extern "C" int seird_residual_noalloc(int64_t n_nodes, int64_t n_tris, const dou
   // the error word must start at zero; elements and partials are overwritten
   e = cudaMemsetAsync(err, 0, sizeof(int32_t), s);
   if (e != cudaSuccess) return fail(SEIRD_ECUDA, std::string("seird_residual_noalloc: ") + cudaGetErrorString(e));
-  Rates r;
+  Rates r{};
   r.A = params->A;
   r.bi = params->beta_i;
   r.be = params->beta_e;

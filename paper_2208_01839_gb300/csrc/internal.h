@@ -89,6 +89,10 @@ struct HostSetup {
 };
 
 int build_setup(const seird_mesh* mesh, const seird_options* opt, HostSetup& hs, std::string& err);
+// Subdomain of every node: the caller's owner array (validated) or the seeded
+// recursive coordinate bisection into opt->n_subdomains parts.
+int partition_nodes(const seird_mesh* mesh, const seird_options* opt, std::vector<int32_t>& owner, int32_t& P,
+                    std::string& err);
 
 template <class T>
 struct DevArray {
@@ -114,6 +118,14 @@ struct seird_ctx {
   double* xy = nullptr;
   int32_t* tri = nullptr;
   double* bfield = nullptr;
+  // ensembles (seird_create_ensemble): per-sample rate rows, samples of n_per_sample nodes
+  int32_t n_samples = 1;
+  int64_t n_per_sample = 0;
+  double* rtab = nullptr;
+  // sigmoid transmission schedule (seird_set_beta_schedule): beta(x) at the nodes
+  bool sched_on = false;
+  seird_beta_schedule sched{};
+  double* bsched = nullptr;
   int32_t* perm = nullptr;
   int32_t* row_ptr = nullptr;
   int32_t* col = nullptr;

@@ -7,6 +7,8 @@
 #include <cstdint>
 #include <string>
 
+#include "../../include/seird.h"
+
 namespace seird {
 
 // Rates of Eq. seird1-5 plus dt, packed for kernel arguments.
@@ -14,7 +16,35 @@ struct Rates {
   double A, bi, be, sigma, ge, gr, gd, alpha, mu;
   double nu[4];
   double dt;
+  // ensembles: per-sample rows [A, bi, be, sigma, ge, gr, gd, alpha, mu, nu0..3] of a
+  // device table, sample = internal node / nper (NULL: the scalars above for every node)
+  const double* tab;
+  int64_t nper;
 };
+constexpr int RATE_ROW = 13;
+
+#ifdef __CUDACC__
+// The rates that hold at internal node `node` (its sample's row of the table).
+__device__ __forceinline__ Rates rates_at(const Rates& r, int64_t node) {
+  if (!r.tab) return r;
+  Rates q = r;
+  const double* t = r.tab + RATE_ROW * (node / r.nper);
+  q.A = t[0];
+  q.bi = t[1];
+  q.be = t[2];
+  q.sigma = t[3];
+  q.ge = t[4];
+  q.gr = t[5];
+  q.gd = t[6];
+  q.alpha = t[7];
+  q.mu = t[8];
+  q.nu[0] = t[9];
+  q.nu[1] = t[10];
+  q.nu[2] = t[11];
+  q.nu[3] = t[12];
+  return q;
+}
+#endif
 
 // Jacobian record of one triangle (doubles): area, N-weighted stiffness (6),
 // G_{c,a} = |T|/3 grad u_c . grad phi_a (12), reaction moments P^k_ab (24), pad.
@@ -34,9 +64,10 @@ void launch_residual(int64_t n, int64_t m, const int32_t* tri, const double* xy,
                      const double* bfield, const Rates& r, int rule, double* elem, const int32_t* inc_ptr,
                      const int32_t* inc, double* F, double* partial, int grid_red, double* out_norm2, int32_t* err,
                      cudaStream_t s);
+void launch_beta_field(int64_t n, const double* xy, const seird_beta_schedule& s, double* out, cudaStream_t st);
 void launch_jacobian(int64_t nnzb, int64_t m, const int32_t* tri, const double* xy, const double* U,
                      const double* bfield, const Rates& r, int rule, void* rec, const int32_t* inc_ptr,
-                     const int32_t* inc, void* val, bool fp32, int32_t* err, cudaStream_t s);
+                     const int32_t* inc, void* val, bool fp32, bool picard, int32_t* err, cudaStream_t s);
 template <class VT>
 void launch_spmv(int64_t nrow, const int32_t* rp, const int32_t* col, const VT* val, const double* x, double* y,
                  cudaStream_t s);

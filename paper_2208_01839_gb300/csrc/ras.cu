@@ -20,73 +20,56 @@ constexpr unsigned FULL = 0xffffffffu;
 __device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
 
-// Inverse of a 5x5 block by Gauss-Jordan with partial pivoting, one warp
-// (lanes 0..4 hold the rows).  Sets ERR_SINGULAR (2) on a zero pivot.
+// |x| as an ordered integer key: for a value with its sign bit cleared, the
+// bit pattern read as an integer grows with the magnitude (NaN above inf), so
+// the pivot search runs on the integer pipe instead of GB300's narrow FP64 one.
+__device__ __forceinline__ long long mag_key(double x) { return __double_as_longlong(x) & 0x7fffffffffffffffLL; }
+__device__ __forceinline__ long long mag_key(float x) { return (long long)(__float_as_int(x) & 0x7fffffff); }
+__device__ __forceinline__ bool key_ok(double, long long k) { return k != 0 && k <= 0x7ff0000000000000LL; }
+__device__ __forceinline__ bool key_ok(float, long long k) { return k != 0 && k <= 0x7f800000LL; }
+
+// Inverse of a 5x5 block by Gauss-Jordan with partial pivoting (largest |entry|
+// of the column at or below the diagonal, ties to the lower row index), one
+// warp: lane 5 r + c < 25 holds entry (r, c) of the block and of the identity
+// it turns into the inverse, so each elimination step is two FP64 FMAs per
+// lane.  Sets ERR_SINGULAR (2) on a zero (or NaN) pivot.
 template <class T>
 __device__ void warp_inv5(const T* __restrict__ D, T* __restrict__ out, int lane, int32_t* err) {
-  T a[5], b[5];
-#pragma unroll
-  for (int c = 0; c < 5; ++c) {
-    a[c] = lane < 5 ? D[5 * lane + c] : T(0);
-    b[c] = (lane == c) ? T(1) : T(0);
-  }
+  const int r = lane / 5, c = lane - 5 * (lane / 5);
+  const bool act = lane < 25;
+  T a = act ? D[lane] : T(0);
+  T b = (act && r == c) ? T(1) : T(0);
   bool sing = false;
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
-    T v = (lane >= k && lane < 5) ? (T)fabs(a[k]) : T(-1);
-    int idx = lane;
+    int piv = k;
+    long long best = mag_key(__shfl_sync(FULL, a, 5 * k + k));
 #pragma unroll
-    for (int o = 4; o > 0; o >>= 1) {
-      const T v2 = __shfl_down_sync(FULL, v, o, 8);
-      const int i2 = __shfl_down_sync(FULL, idx, o, 8);
-      if (v2 > v || (v2 == v && i2 < idx)) {
-        v = v2;
-        idx = i2;
+    for (int q = k + 1; q < 5; ++q) {
+      const long long kq = mag_key(__shfl_sync(FULL, a, 5 * q + k));
+      if (kq > best) {
+        best = kq;
+        piv = q;
       }
     }
-    const T vmax = __shfl_sync(FULL, v, 0);
-    const int piv = __shfl_sync(FULL, idx, 0);
-    if (!(vmax > T(0))) sing = true;
-#pragma unroll
-    for (int c = 0; c < 5; ++c) {
-      const T ak = __shfl_sync(FULL, a[c], k), ap = __shfl_sync(FULL, a[c], piv);
-      const T bk = __shfl_sync(FULL, b[c], k), bp = __shfl_sync(FULL, b[c], piv);
-      if (lane == k) {
-        a[c] = ap;
-        b[c] = bp;
-      } else if (lane == piv) {
-        a[c] = ak;
-        b[c] = bk;
-      }
+    if (!key_ok(T(0), best)) sing = true;
+    const int src = (r == k) ? 5 * piv + c : (r == piv ? 5 * k + c : lane);
+    a = __shfl_sync(FULL, a, src & 31);
+    b = __shfl_sync(FULL, b, src & 31);
+    const T pinv = T(1) / __shfl_sync(FULL, a, 5 * k + k);
+    if (r == k) {
+      a *= pinv;
+      b *= pinv;
     }
-    const T pv = __shfl_sync(FULL, a[k], k);
-    const T pinv = pv != T(0) ? T(1) / pv : T(0);
-    if (lane == k) {
-#pragma unroll
-      for (int c = 0; c < 5; ++c) {
-        a[c] *= pinv;
-        b[c] *= pinv;
-      }
-    }
-    T pr[5], pb[5];
-#pragma unroll
-    for (int c = 0; c < 5; ++c) {
-      pr[c] = __shfl_sync(FULL, a[c], k);
-      pb[c] = __shfl_sync(FULL, b[c], k);
-    }
-    if (lane < 5 && lane != k) {
-      const T f = a[k];
-#pragma unroll
-      for (int c = 0; c < 5; ++c) {
-        a[c] = fmaT(-f, pr[c], a[c]);
-        b[c] = fmaT(-f, pb[c], b[c]);
-      }
+    const T f = __shfl_sync(FULL, a, (5 * r + k) & 31);
+    const T pa = __shfl_sync(FULL, a, (5 * k + c) & 31);
+    const T pb = __shfl_sync(FULL, b, (5 * k + c) & 31);
+    if (act && r != k) {
+      a = fmaT(-f, pa, a);
+      b = fmaT(-f, pb, b);
     }
   }
-  if (lane < 5) {
-#pragma unroll
-    for (int c = 0; c < 5; ++c) out[5 * lane + c] = b[c];
-  }
+  if (act) out[lane] = b;
   if (sing && lane == 0) atomicOr(err, 2);
 }
 
@@ -169,11 +152,11 @@ __global__ void __launch_bounds__(256) k_ilu_factor(RasDev d, const TV* __restri
         __syncwarp();
         for (int64_t u = d.upd_ptr[a]; u < d.upd_ptr[a + 1]; ++u) {
           const int64_t dst = d.upd[2 * u], src = d.upd[2 * u + 1];
-          if (lane < 25) {
-            T t = T(0);
+          if (lane < 25) {  // A_ij -= L_ik U_kj, folded into the FMA chain
+            T t = fval[25 * dst + lane];
 #pragma unroll
-            for (int mm = 0; mm < 5; ++mm) t = fmaT(A[5 * rr + mm], fval[25 * src + 5 * mm + cc], t);
-            fval[25 * dst + lane] -= t;  // A_ij -= L_ik U_kj
+            for (int mm = 0; mm < 5; ++mm) t = fmaT(-A[5 * rr + mm], fval[25 * src + 5 * mm + cc], t);
+            fval[25 * dst + lane] = t;
           }
         }
         __syncwarp();
@@ -264,71 +247,143 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
+// Stage data of one subdomain stream through two rings in shared memory: the
+// factor blocks (SolveRing<T>::blocks) and the per-row records (SOLVE_RING_ROWS).
+// Warp 7 is the producer: its lane 0 reads the level plan and issues the bulk
+// copies of up to SOLVE_SLOTS stages ahead, as far as both rings have room;
+// a stage's "full" mbarrier completes when its bytes have landed, and its
+// "empty" mbarrier when the consumers are done with it.  Warps 0-6 consume
+// the stages in order and meet at a named barrier after each one (the rows of
+// a level depend on the rows of earlier levels).  A stage never wraps around a
+// ring's end: the producer skips the tail.  Every wait is bounded; on a
+// timeout the kernel sets bit 3 of *err, lets every issued copy land and
+// returns.
+template <class T>
+struct SolveRing;
+template <>
+struct SolveRing<double> {
+  static constexpr int blocks = 2 * SOLVE_BUF_BLOCKS_DEV;  // 236 x 208 B
+};
+template <>
+struct SolveRing<float> {
+  static constexpr int blocks = 432;  // 432 x 112 B: four CTAs per SM still fit
+};
+constexpr int SOLVE_RING_ROWS = 2 * SOLVE_BUF_ROWS_DEV;
+constexpr int SOLVE_SLOTS = 8;
+constexpr int SOLVE_CONSUMERS = 224;  // warps 0-6
+
+__device__ __forceinline__ void mbar_init_count(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void consumers_sync() { asm volatile("bar.sync 1, 224;" ::: "memory"); }
+
 template <class T, class TZ>
-__global__ void __launch_bounds__(256) k_ilu_solve(RasDev d, const double* __restrict__ r, TZ* __restrict__ z,
-                                                   int32_t* err) {
+__global__ void __launch_bounds__(256, 4) k_ilu_solve(RasDev d, const double* __restrict__ r, TZ* __restrict__ z,
+                                                      int32_t* err) {
   constexpr int BS = SolveBS<T>::v;
+  constexpr int RB = SolveRing<T>::blocks;
+  constexpr int RR = SOLVE_RING_ROWS;
+  constexpr int NS = SOLVE_SLOTS;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bar[2];
-  __shared__ __align__(16) int4 info[2][SOLVE_BUF_ROWS_DEV];
-  __shared__ int sq_rows[2];
-  __shared__ int abort_flag;
-  T* buf[2] = {reinterpret_cast<T*>(smem_raw), reinterpret_cast<T*>(smem_raw) + SOLVE_BUF_BLOCKS_DEV * BS};
+  __shared__ __align__(8) uint64_t full[NS];
+  __shared__ __align__(8) uint64_t empty[NS];
+  __shared__ __align__(16) int4 info[RR];
+  __shared__ int slot_vb[NS], slot_vr[NS], slot_n[NS];  // virtual ring starts and row count of a stage
+  __shared__ int abort_at;  // first stage at which a consumer warp's wait gave up (INT_MAX: none)
+  T* ring = reinterpret_cast<T*>(smem_raw);
   const int p = blockIdx.x;
   const int32_t r0 = d.sd_row0[p];
   const int32_t nl = d.sd_row0[p + 1] - r0;
   T* y = ywk<T>(d) + 5 * (int64_t)r0;
   T* zz = zwk<T>(d) + 5 * (int64_t)r0;
-  const T* fL = solve_fwd<T>(d);
-  const T* bU = solve_bwd<T>(d);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int rw = lane / 5, cpt = lane - 5 * rw;
   const int32_t LF = d.fwd.sd_lev0[p], nF = d.fwd.sd_lev0[p + 1] - LF - 1;
   const int32_t LB = d.bwd.sd_lev0[p], nB = d.bwd.sd_lev0[p + 1] - LB - 1;
   const int nstage = nF + nB;
   if (tid == 0) {
-    mbar_init(&bar[0]);
-    mbar_init(&bar[1]);
-    abort_flag = 0;
+    for (int k = 0; k < NS; ++k) {
+      mbar_init_count(&full[k], 1);
+      mbar_init_count(&empty[k], 1);
+    }
+    abort_at = INT_MAX;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int32_t idx = tid; idx < 5 * nl; idx += blockDim.x) {
+  __syncthreads();
+
+  if (warp == 7) {
+    // ---- producer: stage g < nF is forward level g, otherwise backward level
+    // g - nF; it uses slot g % NS, whose barriers complete phase (g / NS) & 1 for it.
+    if (lane != 0) return;
+    const T* fL = solve_fwd<T>(d);
+    const T* bU = solve_bwd<T>(d);
+    int vb = 0, vr = 0, oldest = 0;  // ring heads (virtual, growing); oldest stage not known to be released
+    int gi = 0;
+    bool ok = true;
+    for (; gi < nstage && ok; ++gi) {
+      const bool fw = gi < nF;
+      const SolvePlanDev& P = fw ? d.fwd : d.bwd;
+      const int32_t lv = fw ? LF + gi : LB + gi - nF;
+      const int32_t q0 = P.levpos[lv], q1 = P.levpos[lv + 1];
+      const int64_t b0 = P.levblk[lv];
+      const int nb = (int)(P.levblk[lv + 1] - b0), nr = q1 - q0;
+      int sb = vb, sr = vr;
+      if (sb % RB + nb > RB) sb += RB - sb % RB;
+      if (sr % RR + nr > RR) sr += RR - sr % RR;
+      // release stages (in order) until this one fits and its slot is free
+      while (oldest < gi &&
+             (gi - oldest >= NS || sb + nb - slot_vb[oldest % NS] > RB || sr + nr - slot_vr[oldest % NS] > RR)) {
+        if (!mbar_wait(&empty[oldest % NS], (uint32_t)((oldest / NS) & 1)) ||
+            *(volatile int*)&abort_at != INT_MAX) {
+          ok = false;
+          break;
+        }
+        ++oldest;
+      }
+      if (!ok) break;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      const int sl = gi % NS;
+      slot_vb[sl] = sb;
+      slot_vr[sl] = sr;
+      slot_n[sl] = nr;
+      const uint32_t bytes_b = (uint32_t)nb * BS * (uint32_t)sizeof(T);
+      const uint32_t bytes_i = (uint32_t)nr * (uint32_t)sizeof(int4);
+      mbar_arrive_tx(&full[sl], bytes_b + bytes_i);  // releases the slot fields above to the consumers
+      if (bytes_b) bulk_g2s(ring + (size_t)(sb % RB) * BS, (fw ? fL : bU) + b0 * BS, bytes_b, &full[sl]);
+      if (bytes_i) bulk_g2s(info + sr % RR, P.info + r0 + q0, bytes_i, &full[sl]);
+      vb = sb + nb;
+      vr = sr + nr;
+    }
+    if (!ok) atomicOr(err, 8);
+    // every issued copy lands before the CTA can exit (the last stage issued on
+    // each slot is the only one whose phase is still open)
+    for (int k = gi - 1; k >= 0 && k >= gi - NS; --k) mbar_wait(&full[k % NS], (uint32_t)((k / NS) & 1));
+    return;
+  }
+
+  // ---- consumers (warps 0-6)
+  const int rw = lane / 5, cpt = lane - 5 * rw;
+  for (int32_t idx = tid; idx < 5 * nl; idx += SOLVE_CONSUMERS) {
     const int32_t l = idx / 5, cc = idx - 5 * l;
     y[idx] = (T)r[5 * (int64_t)d.sd_node[r0 + l] + cc];
   }
-  __syncthreads();
-  // Stage g < nF is forward level g, otherwise backward level g - nF.  One
-  // thread issues the stage's two bulk copies (factor blocks; per-row records)
-  // on the stage buffer's mbarrier and publishes the stage's row count.
-  auto issue = [&](int g) {
+  consumers_sync();
+  // A warp whose wait gives up skips the stage and records it; every consumer
+  // reads abort_at after the named barrier that closes the stage, and only
+  // values <= g (written before that barrier) end the loop at stage g, so all
+  // consumer warps leave at the same stage.
+  bool aborted = false;
+  for (int g = 0; g < nstage; ++g) {
     const bool fw = g < nF;
-    const SolvePlanDev& P = fw ? d.fwd : d.bwd;
-    const int32_t lv = fw ? LF + g : LB + g - nF;
-    const int32_t q0 = P.levpos[lv], q1 = P.levpos[lv + 1];
-    const int64_t b0 = P.levblk[lv], b1 = P.levblk[lv + 1];
-    const uint32_t bytes_b = (uint32_t)((b1 - b0) * BS * sizeof(T));
-    const uint32_t bytes_i = (uint32_t)((q1 - q0) * sizeof(int4));
-    uint64_t* bb = &bar[g & 1];
-    sq_rows[g & 1] = q1 - q0;
-    mbar_arrive_tx(bb, bytes_b + bytes_i);
-    if (bytes_b) bulk_g2s(buf[g & 1], (fw ? fL : bU) + b0 * BS, bytes_b, bb);
-    if (bytes_i) bulk_g2s(info[g & 1], P.info + r0 + q0, bytes_i, bb);
-  };
-  if (tid == 0 && nstage > 0) issue(0);
-  int g = 0;
-  for (; g < nstage; ++g) {
-    if (tid == 0 && g + 1 < nstage) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic reads of that buffer are done
-      issue(g + 1);
-    }
-    const bool fw = g < nF;
-    if (!mbar_wait(&bar[g & 1], (uint32_t)((g >> 1) & 1))) abort_flag = 1;
-    __syncthreads();
-    if (abort_flag) break;
-    const T* B = buf[g & 1];
-    const int4* inf = info[g & 1];
-    const int nrows = sq_rows[g & 1];
-    for (int qb = warp * 6; qb < nrows; qb += 6 * (int)(blockDim.x >> 5)) {
+    const int sl = g % NS;
+    const bool landed = __all_sync(FULL, mbar_wait(&full[sl], (uint32_t)((g / NS) & 1)));
+    if (!landed && lane == 0) atomicMin(&abort_at, g);
+    const T* B = ring + (size_t)(slot_vb[sl] % RB) * BS;
+    const int4* inf = info + slot_vr[sl] % RR;
+    const int nrows = landed ? slot_n[sl] : 0;
+    for (int qb = warp * 6; qb < nrows; qb += 6 * (SOLVE_CONSUMERS / 32)) {
       const int q = qb + rw;
       const bool act = lane < 30 && q < nrows;
       int32_t i = 0, st = 0, cn = 0;
@@ -340,28 +395,36 @@ __global__ void __launch_bounds__(256) k_ilu_solve(RasDev d, const double* __res
         cn = rec.z;
         acc = y[5 * i + cpt];
       }
+      // y_i -= sum_k L_ik y_k (forward) or y_i - sum_j U_ij z_j (backward, block 0 is the
+      // inverted pivot).  The solution entries of CH blocks are loaded before any of
+      // their FMAs, so a row waits for one memory latency per CH blocks, not per block.
+      constexpr int CH = sizeof(T) == 8 ? 3 : 4;  // FP64: keeps 4 CTAs per SM without spills
+      const T* vec = fw ? y : zz;
+      for (int32_t j = fw ? 0 : 1; j < cn; j += CH) {
+        const int nb = min(CH, cn - j);
+        T xv[CH][5];
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+          const T* vk = vec + 5 * col_of(B[(st + j + min(u, nb - 1)) * BS + 25]);
+#pragma unroll
+          for (int mm = 0; mm < 5; ++mm) xv[u][mm] = vk[mm];
+        }
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+          if (u < nb) {
+            const T* Lb = B + (st + j + u) * BS + 5 * cpt;
+            T t = T(0);
+#pragma unroll
+            for (int mm = 0; mm < 5; ++mm) t = fmaT(Lb[mm], xv[u][mm], t);
+            if (u & 1) acc2 += t;
+            else acc -= t;
+          }
+        }
+      }
+      acc -= acc2;
       if (fw) {
-        for (int32_t j = 0; j < cn; ++j) {  // y_i -= L_ik y_k  (two accumulators: shorter FMA chains)
-          const T* Lb = B + (st + j) * BS;
-          const T* yk = y + 5 * col_of(Lb[25]);
-          T t = T(0);
-#pragma unroll
-          for (int mm = 0; mm < 5; ++mm) t = fmaT(Lb[5 * cpt + mm], yk[mm], t);
-          if (j & 1) acc2 += t;
-          else acc -= t;
-        }
-        if (act) y[5 * i + cpt] = acc - acc2;
+        if (act) y[5 * i + cpt] = acc;
       } else {
-        for (int32_t j = 1; j < cn; ++j) {  // y_i - sum_j U_ij z_j
-          const T* Ub = B + (st + j) * BS;
-          const T* zj = zz + 5 * col_of(Ub[25]);
-          T t = T(0);
-#pragma unroll
-          for (int mm = 0; mm < 5; ++mm) t = fmaT(Ub[5 * cpt + mm], zj[mm], t);
-          if (j & 1) acc2 += t;
-          else acc -= t;
-        }
-        acc -= acc2;
         // z_i = U_ii^{-1} (...): the five partial results of row i sit in lanes 5 rw .. 5 rw + 4
         T v = T(0);
         const T* Dv = B + st * BS + 5 * cpt;
@@ -373,19 +436,19 @@ __global__ void __launch_bounds__(256) k_ilu_solve(RasDev d, const double* __res
         if (act) zz[5 * i + cpt] = v;
       }
     }
-    __syncthreads();
-  }
-  if (abort_flag) {
-    // report, then let every copy still in flight land before the CTA exits
-    if (tid == 0) {
-      atomicOr(err, 8);
-      for (int k = g; k < nstage && k <= g + 1; ++k) mbar_wait(&bar[k & 1], (uint32_t)((k >> 1) & 1));
+    consumers_sync();  // every row of this level is written; the stage's ring space is free
+    if (*(volatile int*)&abort_at <= g) {
+      aborted = true;
+      break;
     }
-    __syncthreads();
+    if (tid == 0) mbar_arrive(&empty[sl]);
+  }
+  if (aborted) {
+    if (tid == 0) atomicOr(err, 8);
     return;
   }
   const int32_t own0 = d.own_ptr[p], own1 = d.own_ptr[p + 1];
-  for (int32_t idx = tid; idx < 5 * nl; idx += blockDim.x) {
+  for (int32_t idx = tid; idx < 5 * nl; idx += SOLVE_CONSUMERS) {
     const int32_t l = idx / 5, cc = idx - 5 * l;
     const int32_t node = d.sd_node[r0 + l];
     if (node >= own0 && node < own1) z[5 * (int64_t)node + cc] = (TZ)zz[idx];
@@ -574,8 +637,8 @@ void launch_ilu_factor(const RasDev& d, const double* val, const float* val32, i
 }
 
 size_t solve_smem(bool fp32) {
-  return fp32 ? 2 * (size_t)SOLVE_BUF_BLOCKS_DEV * SolveBS<float>::v * sizeof(float)
-              : 2 * (size_t)SOLVE_BUF_BLOCKS_DEV * SolveBS<double>::v * sizeof(double);
+  return fp32 ? (size_t)SolveRing<float>::blocks * SolveBS<float>::v * sizeof(float)
+              : (size_t)SolveRing<double>::blocks * SolveBS<double>::v * sizeof(double);
 }
 
 void launch_ilu_reorg(const RasDev& d, int64_t nfwd, int64_t nbwd, const int64_t* fsrc, const int32_t* fcol,

@@ -80,12 +80,21 @@ int upload(seird_ctx* ctx, T** p, const std::vector<T>& v) {
   return SEIRD_OK;
 }
 
+// beta(t) of the sigmoid schedule (Eq. beta_ie)
+double beta_time(const seird_beta_schedule& s, double t) { return s.b0 - s.b1 / (1.0 + std::exp(s.t_mid - t)); }
+
+// Rates of the step that ends at ctx->t + dt.
 Rates make_rates(const seird_ctx* ctx) {
-  Rates r;
+  Rates r{};
   const seird_params& p = ctx->params;
   r.A = p.A;
   r.bi = p.beta_i;
   r.be = p.beta_e;
+  if (ctx->sched_on) r.bi = r.be = beta_time(ctx->sched, ctx->t + ctx->opt.dt);
+  if (ctx->rtab) {
+    r.tab = ctx->rtab;
+    r.nper = ctx->n_per_sample;
+  }
   r.sigma = p.sigma;
   r.ge = p.gamma_e;
   r.gr = p.gamma_r;
@@ -96,6 +105,9 @@ Rates make_rates(const seird_ctx* ctx) {
   r.dt = ctx->opt.dt;
   return r;
 }
+
+// transmission multiplier field in use (NULL: none)
+const double* bfield_of(const seird_ctx* ctx) { return ctx->sched_on ? ctx->bsched : ctx->bfield; }
 
 int64_t vlen(const seird_ctx* ctx) { return 5 * ctx->hs.n; }
 
@@ -169,7 +181,7 @@ int residual(seird_ctx* ctx, const double* U, const double* Un, double* F, doubl
   const HostSetup& hs = ctx->hs;
   {
     KTimer kt_(ctx, SEIRD_K_RESIDUAL);
-    launch_residual(hs.n, hs.m, ctx->tri, ctx->xy, U, Un, ctx->bfield, make_rates(ctx), ctx->opt.quadrature,
+    launch_residual(hs.n, hs.m, ctx->tri, ctx->xy, U, Un, bfield_of(ctx), make_rates(ctx), ctx->opt.quadrature,
                     ctx->elem, ctx->node_inc_ptr, ctx->node_inc, F, ctx->partial, 0, ctx->scal, ctx->err,
                     ctx->stream);
   }
@@ -182,14 +194,16 @@ int residual(seird_ctx* ctx, const double* U, const double* Un, double* F, doubl
   return SEIRD_OK;
 }
 
-int jacobian(seird_ctx* ctx, const double* U) {
+// Assembles dF/dU at U (picard = false) or the Picard matrix of Eq.
+// weak_vec_implicit with its coefficients frozen at U (picard = true).
+int jacobian(seird_ctx* ctx, const double* U, bool picard = false) {
   const HostSetup& hs = ctx->hs;
   KTimer kt_(ctx, SEIRD_K_JACOBIAN);
   // the mixed path assembles the Jacobian straight into its FP32 copy (FP32
   // arithmetic); it only feeds the FP32 operator and the FP32 factors
-  launch_jacobian((int64_t)hs.col.size(), hs.m, ctx->tri, ctx->xy, U, ctx->bfield, make_rates(ctx),
+  launch_jacobian((int64_t)hs.col.size(), hs.m, ctx->tri, ctx->xy, U, bfield_of(ctx), make_rates(ctx),
                   ctx->opt.quadrature, ctx->rec, ctx->blk_inc_ptr, ctx->blk_inc,
-                  mixed(ctx) ? (void*)ctx->val32 : (void*)ctx->val, mixed(ctx), ctx->err, ctx->stream);
+                  mixed(ctx) ? (void*)ctx->val32 : (void*)ctx->val, mixed(ctx), picard, ctx->err, ctx->stream);
   CK(cudaGetLastError());
   ctx->jac_ready = true;  // an existing preconditioner stays usable (lagged set-up, options.pc_lag)
   return SEIRD_OK;
@@ -488,7 +502,90 @@ double ms_since(std::chrono::steady_clock::time_point t0) {
   return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
 
+// One step by the coupled Picard iteration of Eq. weak_vec_implicit, written in
+// correction form: the Picard matrix P(U^k) satisfies P(U^k) U^k - M U^n =
+// F(U^k), so U^{k+1} = U^k + dU with P(U^k) dU = -F(U^k) solves
+// P(U^k) U^{k+1} = M U^n.  Full steps, no line search; stops on the update
+// measure of Eq. picardtol (picard_tol > 0) or on the residual test.
+int picard_step(seird_ctx* ctx, seird_stats* st) {
+  using clk = std::chrono::steady_clock;
+  const auto t_begin = clk::now();
+  const int64_t len = vlen(ctx);
+  const cudaStream_t s = ctx->stream;
+  seird_stats S;
+  std::memset(&S, 0, sizeof(S));
+  timing_reset(ctx);
+  CK(cudaMemcpyAsync(ctx->Un, ctx->U, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
+  auto t0 = clk::now();
+  double f;
+  int rc = residual(ctx, ctx->U, ctx->Un, ctx->F, &f);
+  S.ms_assemble += ms_since(t0);
+  if (rc) return rc;
+  const double f0 = f;
+  S.res0 = f0;
+  double unorm;
+  TRY(norm2(ctx, ctx->Un, &unorm));
+  auto restore = [&](int code) {
+    cudaMemcpyAsync(ctx->U, ctx->Un, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
+    cudaStreamSynchronize(s);
+    return code;
+  };
+  const double ptol = ctx->opt.picard_tol;
+  int its = 0;
+  double eps = 0.0;
+  for (;;) {
+    const bool done = ptol > 0 ? (its > 0 && eps <= ptol) : (f <= ctx->opt.newton_rtol * f0 + ctx->opt.newton_atol);
+    if (done) break;
+    if (its >= ctx->opt.newton_maxit) return restore(fail(ctx, SEIRD_ENEWTON_MAXIT, "picard: iteration limit"));
+    t0 = clk::now();
+    rc = jacobian(ctx, ctx->U, true);
+    if (rc) return restore(rc);
+    CK(cudaStreamSynchronize(s));
+    S.ms_assemble += ms_since(t0);
+    if (its % std::max(1, ctx->opt.pc_lag) == 0 || !ctx->pc_ready) {
+      t0 = clk::now();
+      rc = pc_setup(ctx);
+      S.ms_setup += ms_since(t0);
+      if (rc) return restore(rc);
+      S.pc_setups++;
+    }
+    launch_axpby(len, -1.0, ctx->F, 0.0, ctx->F, ctx->stage, s);
+    t0 = clk::now();
+    int lits = 0;
+    bool conv = false;
+    rc = gmres(ctx, ctx->stage, ctx->dU, ctx->opt.gmres_rtol, &lits, &conv);
+    S.ms_solve += ms_since(t0);
+    S.gmres_its += lits;
+    if (rc) return restore(rc);
+    t0 = clk::now();
+    launch_axpby(len, 1.0, ctx->U, 1.0, ctx->dU, ctx->Ut, s);
+    double ft;
+    rc = residual(ctx, ctx->Ut, ctx->Un, ctx->Ft, &ft);
+    S.ms_assemble += ms_since(t0);
+    if (rc) return restore(rc);
+    double dn;
+    TRY(norm2(ctx, ctx->dU, &dn));
+    eps = unorm > 0 ? dn / unorm : 0.0;
+    S.eps_update = eps;
+    if (verbose())
+      std::fprintf(stderr, "[seird] t=%g picard %d |F| %.6e -> %.6e (f0 %.6e) gmres %d eps %.3e\n", ctx->t, its, f,
+                   ft, f0, lits, eps);
+    std::swap(ctx->U, ctx->Ut);
+    std::swap(ctx->F, ctx->Ft);
+    f = ft;
+    ++its;
+  }
+  S.newton_its = its;
+  S.res_final = f;
+  ctx->t += ctx->opt.dt;
+  S.ms_total = ms_since(t_begin);
+  timing_collect(ctx, &S);
+  if (st) *st = S;
+  return SEIRD_OK;
+}
+
 int newton_step(seird_ctx* ctx, seird_stats* st) {
+  if (ctx->opt.nonlinear == 1) return picard_step(ctx, st);
   using clk = std::chrono::steady_clock;
   const auto t_begin = clk::now();
   const int64_t len = vlen(ctx);
@@ -810,7 +907,8 @@ static int create_impl(seird_ctx* ctx, const seird_mesh* mesh, const seird_param
   if (!(o.dt > 0) || o.gmres_restart < 1 || o.gmres_restart > MAX_RESTART || o.gmres_maxit < 1 ||
       o.newton_maxit < 0 || o.ls_maxit < 0 || o.overlap < 0 || o.coarse < 0 || o.coarse > 2 ||
       (o.quadrature != 0 && o.quadrature != 1) || (o.precision != 0 && o.precision != 1) ||
-      (o.gmres_forcing != 0 && o.gmres_forcing != 1))
+      (o.gmres_forcing != 0 && o.gmres_forcing != 1) || (o.nonlinear != 0 && o.nonlinear != 1) ||
+      !(o.picard_tol >= 0))
     return fail(ctx, SEIRD_EINVAL, "invalid option value");
   std::string err;
   int rc = build_setup(mesh, &o, ctx->hs, err);
@@ -967,6 +1065,65 @@ int seird_create(const seird_mesh* mesh, const seird_params* params, const seird
   return SEIRD_OK;
 }
 
+int seird_create_ensemble(const seird_mesh* mesh, int32_t n_samples, const seird_params* params,
+                          const seird_options* opt, seird_ctx** out) {
+  if (!out) return fail(nullptr, SEIRD_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!mesh || !params || !mesh->xy || !mesh->tri) return fail(nullptr, SEIRD_EINVAL, "mesh and params must not be NULL");
+  if (n_samples < 1) return fail(nullptr, SEIRD_EINVAL, "n_samples must be >= 1");
+  seird_options o;
+  if (opt) o = *opt;
+  else seird_default_options(&o);
+  const int64_t n = mesh->n_nodes, m = mesh->n_tris, B = n_samples;
+  if (n < 3 || m < 1) return fail(nullptr, SEIRD_EINVAL, "mesh needs at least 3 nodes and 1 triangle");
+  if (B * n > (int64_t)INT32_MAX / 8 || B * m > (int64_t)INT32_MAX / 9)
+    return fail(nullptr, SEIRD_EINVAL, "ensemble too large for 32-bit element maps");
+  // one partition of the mesh, repeated for every sample: sample k owns
+  // subdomains [k P, (k+1) P), so its nodes are one contiguous internal range
+  std::vector<int32_t> own;
+  int32_t P = 0;
+  std::string err;
+  int rc = partition_nodes(mesh, &o, own, P, err);
+  if (rc) return fail(nullptr, rc, err);
+  std::vector<double> xy(2 * B * n);
+  std::vector<int32_t> tri(3 * B * m), owner(B * n);
+  for (int64_t k = 0; k < B; ++k) {
+    std::copy(mesh->xy, mesh->xy + 2 * n, xy.begin() + 2 * k * n);
+    for (int64_t q = 0; q < 3 * m; ++q) tri[3 * k * m + q] = (int32_t)(mesh->tri[q] + k * n);
+    for (int64_t i = 0; i < n; ++i) owner[k * n + i] = (int32_t)(own[i] + k * P);
+  }
+  std::vector<double> bf;
+  seird_params p0 = params[0];
+  if (p0.beta_field) {
+    bf.resize(B * n);
+    for (int64_t k = 0; k < B; ++k) std::copy(p0.beta_field, p0.beta_field + n, bf.begin() + k * n);
+    p0.beta_field = bf.data();
+  }
+  o.owner = owner.data();
+  o.n_subdomains = (int32_t)(B * P);
+  seird_mesh um{B * n, B * m, xy.data(), tri.data()};
+  seird_ctx* ctx = nullptr;
+  rc = seird_create(&um, &p0, &o, &ctx);
+  if (rc) return rc;
+  std::vector<double> rows(RATE_ROW * B);
+  for (int64_t k = 0; k < B; ++k) {
+    const seird_params& q = params[k];
+    const double v[RATE_ROW] = {q.A,     q.beta_i, q.beta_e, q.sigma, q.gamma_e, q.gamma_r, q.gamma_d,
+                                q.alpha, q.mu,     q.nu[0],  q.nu[1], q.nu[2],   q.nu[3]};
+    std::copy(v, v + RATE_ROW, rows.begin() + RATE_ROW * k);
+  }
+  rc = upload(ctx, &ctx->rtab, rows);
+  if (rc) {
+    g_create_error = ctx->last_error;
+    seird_destroy(ctx);
+    return rc;
+  }
+  ctx->n_samples = n_samples;
+  ctx->n_per_sample = n;
+  *out = ctx;
+  return SEIRD_OK;
+}
+
 int seird_set_state(seird_ctx* ctx, const double* u, int on_device, double t) {
   if (!ctx || !u) return fail(ctx, SEIRD_EINVAL, "NULL argument");
   TRY(to_internal(ctx, u, on_device, ctx->U));
@@ -995,6 +1152,7 @@ int seird_run(seird_ctx* ctx, int32_t n_steps, seird_stats* per_step) {
 
 int seird_set_params(seird_ctx* ctx, const seird_params* params) {
   if (!ctx || !params) return fail(ctx, SEIRD_EINVAL, "NULL argument");
+  if (ctx->rtab) return fail(ctx, SEIRD_EINVAL, "set_params: an ensemble's rates are fixed at creation");
   ctx->params = *params;
   ctx->params.beta_field = nullptr;
   if (params->beta_field) {
@@ -1008,8 +1166,32 @@ int seird_set_params(seird_ctx* ctx, const seird_params* params) {
   return SEIRD_OK;
 }
 
+int seird_set_beta_schedule(seird_ctx* ctx, const seird_beta_schedule* sched) {
+  if (!ctx) return fail(ctx, SEIRD_EINVAL, "NULL context");
+  if (ctx->rtab) return fail(ctx, SEIRD_EINVAL, "beta schedule: not available on an ensemble");
+  if (!sched) {
+    ctx->sched_on = false;
+    ctx->pc_ready = false;
+    return SEIRD_OK;
+  }
+  const double v[10] = {sched->b0,        sched->b1,        sched->t_mid,     sched->beta_central, sched->beta_eastern,
+                        sched->beta_western, sched->x_eastern, sched->x_western, sched->k_eastern,   sched->k_western};
+  for (double x : v)
+    if (!std::isfinite(x)) return fail(ctx, SEIRD_EINVAL, "beta schedule: non-finite value");
+  if (!ctx->bsched) TRY(dalloc(ctx, &ctx->bsched, ctx->hs.n));
+  launch_beta_field(ctx->hs.n, ctx->xy, *sched, ctx->bsched, ctx->stream);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->sched = *sched;
+  ctx->sched_on = true;
+  ctx->pc_ready = false;
+  return SEIRD_OK;
+}
+
 int seird_adjoint(seird_ctx* ctx, const seird_misfit* spec, double* misfit, double* grad, double* grad_field) {
   if (!ctx || !spec) return fail(ctx, SEIRD_EINVAL, "NULL argument");
+  if (ctx->sched_on) return fail(ctx, SEIRD_EINVAL, "adjoint: turn the beta schedule off first (constant rates only)");
+  if (ctx->rtab) return fail(ctx, SEIRD_EINVAL, "adjoint: not available on an ensemble");
   return adjoint_impl(ctx, spec, misfit, grad, grad_field);
 }
 
@@ -1039,7 +1221,7 @@ int seird_eval_residual(seird_ctx* ctx, const double* u, const double* u_prev, d
 int seird_eval_jacobian(seird_ctx* ctx, const double* u, int on_device) {
   if (!ctx || !u) return fail(ctx, SEIRD_EINVAL, "NULL argument");
   TRY(to_internal(ctx, u, on_device, ctx->Ut));
-  TRY(jacobian(ctx, ctx->Ut));
+  TRY(jacobian(ctx, ctx->Ut, ctx->opt.nonlinear == 1));
   return check_flags(ctx, "jacobian");
 }
 

@@ -84,38 +84,10 @@ std::vector<int32_t> rcm(const std::vector<std::vector<int32_t>>& adj) {
 
 }  // namespace
 
-int build_setup(const seird_mesh* mesh, const seird_options* opt, HostSetup& hs, std::string& err) {
-  const int64_t n = mesh->n_nodes, m = mesh->n_tris;
-  if (n < 3 || m < 1 || !mesh->xy || !mesh->tri) {
-    err = "mesh needs at least 3 nodes, 1 triangle and non-NULL arrays";
-    return SEIRD_EINVAL;
-  }
-  if (n > (int64_t)INT32_MAX / 8 || m > (int64_t)INT32_MAX / 9) {
-    err = "mesh too large for 32-bit element maps";
-    return SEIRD_EINVAL;
-  }
-  for (int64_t t = 0; t < m; ++t) {
-    const int32_t* v = mesh->tri + 3 * t;
-    for (int a = 0; a < 3; ++a)
-      if (v[a] < 0 || v[a] >= n) {
-        err = "triangle " + std::to_string(t) + " has a node index out of range";
-        return SEIRD_EINVAL;
-      }
-    const double* p0 = mesh->xy + 2 * (int64_t)v[0];
-    const double* p1 = mesh->xy + 2 * (int64_t)v[1];
-    const double* p2 = mesh->xy + 2 * (int64_t)v[2];
-    const double twoA = (p1[0] - p0[0]) * (p2[1] - p0[1]) - (p2[0] - p0[0]) * (p1[1] - p0[1]);
-    if (!(twoA > 0)) {
-      err = "triangle " + std::to_string(t) + " is not counter-clockwise or is degenerate";
-      return SEIRD_EINVAL;
-    }
-  }
-  hs.n = n;
-  hs.m = m;
-
-  // ---- partition ---------------------------------------------------------
-  std::vector<int32_t> owner_c(n);
-  int32_t P;
+int partition_nodes(const seird_mesh* mesh, const seird_options* opt, std::vector<int32_t>& owner_c, int32_t& P,
+                    std::string& err) {
+  const int64_t n = mesh->n_nodes;
+  owner_c.assign(n, 0);
   if (opt->owner) {
     P = 0;
     for (int64_t i = 0; i < n; ++i) {
@@ -147,6 +119,43 @@ int build_setup(const seird_mesh* mesh, const seird_options* opt, HostSetup& hs,
     std::iota(idx.begin(), idx.end(), 0);
     rcb(mesh->xy, idx, 0, n, 0, P, w, owner_c);
   }
+  return SEIRD_OK;
+}
+
+int build_setup(const seird_mesh* mesh, const seird_options* opt, HostSetup& hs, std::string& err) {
+  const int64_t n = mesh->n_nodes, m = mesh->n_tris;
+  if (n < 3 || m < 1 || !mesh->xy || !mesh->tri) {
+    err = "mesh needs at least 3 nodes, 1 triangle and non-NULL arrays";
+    return SEIRD_EINVAL;
+  }
+  if (n > (int64_t)INT32_MAX / 8 || m > (int64_t)INT32_MAX / 9) {
+    err = "mesh too large for 32-bit element maps";
+    return SEIRD_EINVAL;
+  }
+  for (int64_t t = 0; t < m; ++t) {
+    const int32_t* v = mesh->tri + 3 * t;
+    for (int a = 0; a < 3; ++a)
+      if (v[a] < 0 || v[a] >= n) {
+        err = "triangle " + std::to_string(t) + " has a node index out of range";
+        return SEIRD_EINVAL;
+      }
+    const double* p0 = mesh->xy + 2 * (int64_t)v[0];
+    const double* p1 = mesh->xy + 2 * (int64_t)v[1];
+    const double* p2 = mesh->xy + 2 * (int64_t)v[2];
+    const double twoA = (p1[0] - p0[0]) * (p2[1] - p0[1]) - (p2[0] - p0[0]) * (p1[1] - p0[1]);
+    if (!(twoA > 0)) {
+      err = "triangle " + std::to_string(t) + " is not counter-clockwise or is degenerate";
+      return SEIRD_EINVAL;
+    }
+  }
+  hs.n = n;
+  hs.m = m;
+
+  // ---- partition ---------------------------------------------------------
+  std::vector<int32_t> owner_c;
+  int32_t P;
+  const int prc = partition_nodes(mesh, opt, owner_c, P, err);
+  if (prc) return prc;
   hs.P = P;
 
   // ---- internal numbering: nodes sorted by (owner, caller index) ----------

@@ -80,6 +80,26 @@ def params_ontario(max_density: float, **over) -> Params:
 # meshes
 # ---------------------------------------------------------------------------
 
+RATE_NAMES = ("beta_i", "beta_e", "sigma", "gamma_e", "gamma_r", "gamma_d")
+
+
+def rate_samples(base: Params, n_samples: int, seed: int, spread: float = 0.5) -> list:
+    """Ensemble members: each of the ten calibrated rates (beta_I, beta_E, sigma,
+    gamma_E, gamma_R, gamma_D, nubar_S..R) drawn log-uniformly within a factor
+    (1 +- spread) of its base value, independently per sample (seeded)."""
+    rng = np.random.default_rng(seed)
+    lo, hi = np.log(1.0 - spread), np.log(1.0 + spread)
+    out = []
+    for _ in range(n_samples):
+        f = np.exp(rng.uniform(lo, hi, 10))
+        q = Params(**base.as_dict())
+        for k, name in enumerate(RATE_NAMES):
+            setattr(q, name, float(getattr(base, name) * f[k]))
+        q.nu = tuple(float(base.nu[c] * f[6 + c]) for c in range(4))
+        out.append(q)
+    return out
+
+
 def structured_mesh(nx: int, ny: int | None = None, x0=0.0, x1=1.0, y0=0.0, y1=1.0):
     """Structured P1 triangulation of a rectangle with nx*ny vertices.
 

@@ -48,7 +48,14 @@ class Options(C.Structure):
                 ("gmres_dtol", C.c_double), ("n_subdomains", C.c_int32), ("overlap", C.c_int32),
                 ("coarse", C.c_int32), ("precision", C.c_int32), ("quadrature", C.c_int32),
                 ("pc_lag", C.c_int32), ("owner", _ip), ("seed", C.c_uint64), ("stream", C.c_void_p),
-                ("timing", C.c_int32), ("gmres_forcing", C.c_int32)]
+                ("timing", C.c_int32), ("gmres_forcing", C.c_int32), ("nonlinear", C.c_int32),
+                ("picard_tol", C.c_double)]
+
+
+class BetaSchedule(C.Structure):
+    """Sigmoid transmission schedule, Eq. beta_ie and Eq. beta_x."""
+    _fields_ = [(k, C.c_double) for k in ("b0", "b1", "t_mid", "beta_central", "beta_eastern", "beta_western",
+                                          "x_eastern", "x_western", "k_eastern", "k_western")]
 
 
 KERNEL_CLASSES = ["residual", "jacobian", "ilu_factor", "coarse_setup", "spmv", "ilu_solve", "coarse_apply", "krylov"]
@@ -113,7 +120,10 @@ _linear_solve = _sig("seird_linear_solve", C.c_int, [_vp, _vp, _vp, C.c_int, C.P
 _bsr_spmv = _sig("seird_bsr_spmv", C.c_int, [C.c_int64, _vp, _vp, _vp, _vp, _vp, _vp])
 _bsr_spmv_f32 = _sig("seird_bsr_spmv_f32val", C.c_int, [C.c_int64, _vp, _vp, _vp, _vp, _vp, _vp])
 _launch_count = _sig("seird_launch_count", C.c_int64, [])
+_create_ensemble = _sig("seird_create_ensemble", C.c_int,
+                        [C.POINTER(Mesh), C.c_int32, C.POINTER(Params), C.POINTER(Options), C.POINTER(_vp)])
 _set_params = _sig("seird_set_params", C.c_int, [_vp, C.POINTER(Params)])
+_set_beta_schedule = _sig("seird_set_beta_schedule", C.c_int, [_vp, C.POINTER(BetaSchedule)])
 _adjoint = _sig("seird_adjoint", C.c_int, [_vp, C.POINTER(Misfit), C.POINTER(C.c_double), _vp, _vp])
 _residual_noalloc = _sig("seird_residual_noalloc", C.c_int,
                          [C.c_int64, C.c_int64, _vp, _vp, _vp, _vp, C.POINTER(Params), _vp, C.c_double, C.c_int32,
@@ -198,19 +208,29 @@ def residual_noalloc(xy, tri, inc_ptr, inc, params, u, u_prev, F, dt, quadrature
 
 
 class Solver:
-    """One SEIRD context: mesh, parameters and options live on the device."""
+    """One SEIRD context: mesh, parameters and options live on the device.
+
+    ``params`` may be a list of parameter sets: the context is then an ensemble
+    (seird_create_ensemble) with one sample per entry, and states have
+    len(params) * n_nodes rows, sample-major."""
 
     def __init__(self, xy, tri, params, options: Options | None = None, beta_field=None, owner=None, stream=None,
                  **opt_over):
         self._xy = np.ascontiguousarray(xy, dtype=np.float64)
         self._tri = np.ascontiguousarray(tri, dtype=np.int32)
-        self.n = len(self._xy)
-        mesh = Mesh(self.n, len(self._tri), self._xy.ctypes.data_as(_dp), self._tri.ctypes.data_as(_ip))
-        p = params_struct(params)
+        mesh = Mesh(len(self._xy), len(self._tri), self._xy.ctypes.data_as(_dp), self._tri.ctypes.data_as(_ip))
+        samples = list(params) if isinstance(params, (list, tuple)) else None
+        self.n_samples = len(samples) if samples is not None else 1
+        self.n = len(self._xy) * self.n_samples
+        if samples is not None:
+            p = (Params * len(samples))(*[params_struct(q) for q in samples])
+        else:
+            p = params_struct(params)
+        p0 = p[0] if samples is not None else p
         self._bf = None
         if beta_field is not None:
             self._bf = np.ascontiguousarray(beta_field, dtype=np.float64)
-            p.beta_field = self._bf.ctypes.data_as(_dp)
+            p0.beta_field = self._bf.ctypes.data_as(_dp)
         o = options if options is not None else default_options()
         for k, v in opt_over.items():
             setattr(o, k, v)
@@ -222,7 +242,10 @@ class Solver:
             o.stream = _stream_handle(stream)
         self.options = o
         h = _vp()
-        rc = _create(C.byref(mesh), C.byref(p), C.byref(o), C.byref(h))
+        if samples is not None:
+            rc = _create_ensemble(C.byref(mesh), len(samples), p, C.byref(o), C.byref(h))
+        else:
+            rc = _create(C.byref(mesh), C.byref(p), C.byref(o), C.byref(h))
         if rc != OK:
             raise SeirdError(rc, _last_error(None).decode())
         self._h = h
@@ -279,6 +302,14 @@ class Solver:
             self._bf = np.ascontiguousarray(beta_field, dtype=np.float64)
             p.beta_field = self._bf.ctypes.data_as(_dp)
         self._check(_set_params(self._h, C.byref(p)))
+
+    def set_beta_schedule(self, sched):
+        """Turns the sigmoid schedule on (a dict with the BetaSchedule fields) or off (None)."""
+        if sched is None:
+            self._check(_set_beta_schedule(self._h, None))
+        else:
+            s = BetaSchedule(**{k: float(v) for k, v in sched.items()})
+            self._check(_set_beta_schedule(self._h, C.byref(s)))
 
     def adjoint(self, n_steps, obs_nodes, obs_steps, I_hat, D_hat, checkpoint_every=1, lin_rtol=0.0,
                 field=True):

@@ -122,13 +122,14 @@ def test_residual_matches_oracle(name, rule):
 
 
 @pytest.mark.parametrize("name", list(WL))
-def test_jacobian_matches_oracle(name):
+@pytest.mark.parametrize("rule", [0, 1])
+def test_jacobian_matches_oracle(name, rule):
     wl = WL[name]
     rng = np.random.default_rng(6)
     U = wl.U0 * (1.0 + 0.05 * rng.standard_normal(wl.U0.shape)) + 1.0
-    J = O.jacobian(wl.xy, wl.tri, wl.params, wl.dt, U, bfield=wl.beta_field)
+    J = O.jacobian(wl.xy, wl.tri, wl.params, wl.dt, U, bfield=wl.beta_field, rule="deg5" if rule == 0 else "vertex")
     rp, col, val = O.to_bsr(J)
-    with solver(wl) as sv:
+    with solver(wl, quadrature=rule) as sv:
         sv.jacobian(U)
         grp, gcol, gval = sv.get_jacobian()
         x = rng.standard_normal(U.shape)
