@@ -39,11 +39,11 @@ FALLBACK_HBM_GBS = 6800.0
 # full launch by the units it processes (traffic grows in proportion).
 NCU_TRAFFIC = {
     ("spmv", "fp64"): (307.414e6, 1400635, "nnzb"),  # profiles/k_bsr_spmv_ontario200k.md
-    ("ilu_solve", "fp64"): (385.943e6, 1577927, "subdomain_blocks"),  # profiles/k_ilu_solve_ontario200k.md (v3)
+    ("ilu_solve", "fp64"): (385.414e6, 1577927, "subdomain_blocks"),  # profiles/k_ilu_solve_ontario200k.md (v6)
 }
 
 # kernel classes with one kernel launch per timed call, and their algorithmic
-# bytes per launch ("Algorithmic bytes")
+# bytes per launch
 SINGLE_KERNEL = ("spmv", "ilu_solve", "ilu_factor")
 
 
@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--forcing", choices=["fixed", "ew"], default="ew")
     ap.add_argument("--pc-lag", type=int, default=20)
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--cgs2", action="store_true", help="re-orthogonalise (CGS2) instead of PETSc's single pass")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -72,7 +73,9 @@ def workload_config(wl, args):
         "workload": "%s (Southern-Ontario-like 24-gon, %d P1 nodes, %d unknowns)" % (wl.name, wl.n, 5 * wl.n),
         "n_nodes": wl.n, "n_tris": int(len(wl.tri)), "dof": 5 * wl.n, "dt_days": wl.dt,
         "subdomains": args.subdomains, "overlap": 2, "coarse": "additive, constant per subdomain and compartment",
-        "subdomain_solver": "block ILU(0)", "krylov": "FGMRES(30) right-preconditioned, CGS2, rtol 1e-5",
+        "subdomain_solver": "block ILU(0)",
+        "krylov": "FGMRES(30) right-preconditioned, %s, rtol 1e-5" % (
+            "CGS2" if args.cgs2 else "classical Gram-Schmidt single pass (PETSc default)"),
         "newton_rtol": 1e-8, "quadrature": "degree-5 seven-point", "seed": args.seed,
         "l2": "inputs larger than L2 (the FP64 Jacobian alone is > 2.7 GB)",
     }
@@ -200,8 +203,9 @@ def hbm_peak():
 
 
 def algorithmic_bytes(cls, info, precision="fp64"):
-    """Bytes each launch of a kernel class must move at least; the
-    mixed path stores matrix values, factors and the preconditioned basis in FP32."""
+    """Bytes each launch of a kernel class must move at least (each array the
+    kernel needs, read or written once); the mixed path stores matrix values,
+    factors and the preconditioned basis in FP32."""
     n, nnzb = info["n_nodes"], info["nnzb"]
     nl, nlb = info["subdomain_rows"], info["subdomain_blocks"]
     w = 4 if precision == "mixed" else 8
@@ -225,7 +229,7 @@ def measure(S, wl, args, stream, precision, forcing, pc_lag, world, local, e2e=T
     sv = S.Solver(wl.xy, wl.tri, wl.params, stream=stream, dt=wl.dt, n_subdomains=args.subdomains, overlap=2,
                   coarse=1, newton_rtol=1e-8, gmres_rtol=1e-5, gmres_restart=30, gmres_maxit=200,
                   precision=1 if precision == "mixed" else 0, seed=args.seed, timing=1,
-                  gmres_forcing=1 if forcing == "ew" else 0, pc_lag=pc_lag)
+                  gmres_forcing=1 if forcing == "ew" else 0, pc_lag=pc_lag, gmres_one_pass=0 if args.cgs2 else 1)
     info = sv.info()
     sv.set_state(torch.tensor(wl.U0, device="cuda"))
     for _ in range(args.warmup):
@@ -284,7 +288,7 @@ def measure_ensemble(S, I, args, stream, world, local):
     samples = I.rate_samples(wl.params, args.ensemble, args.seed)
     sv = S.Solver(wl.xy, wl.tri, samples, stream=stream, dt=wl.dt, n_subdomains=16, overlap=2, coarse=1,
                   newton_rtol=1e-8, gmres_rtol=1e-5, gmres_restart=30, gmres_maxit=200, seed=args.seed,
-                  gmres_forcing=1, pc_lag=args.pc_lag)
+                  gmres_forcing=1, pc_lag=args.pc_lag, gmres_one_pass=0 if args.cgs2 else 1)
     sv.set_state(torch.tensor(np.concatenate([wl.U0] * len(samples)), device="cuda"))
     for _ in range(args.warmup):
         sv.step()
