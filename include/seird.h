@@ -14,8 +14,9 @@
  *     Picard iteration; both converge to the root of Eq. weakform), or the
  *     coupled Picard iteration of Eq. weak_vec_implicit (options.nonlinear).
  *   - Linear solve: right-preconditioned restarted (F)GMRES with classical
- *     Gram-Schmidt and one re-orthogonalisation (CGS2); stopping rules of
- *     Section 3.2 (rtol, atol, dtol against ||b||_2).
+ *     Gram-Schmidt and one re-orthogonalisation (CGS2), or a single pass
+ *     (options.gmres_one_pass); stopping rules of Section 3.2 (rtol, atol,
+ *     dtol against ||b||_2).
  *   - Preconditioner: restricted additive Schwarz (Eq. RAS) with overlapping
  *     subdomains and block-ILU(0) subdomain solves, plus (optionally) the
  *     additive coarse correction M_2^{-1} = M_RAS^{-1} + Z A_c^{-1} Z^T
@@ -122,6 +123,9 @@ typedef struct {
                              the coefficients nu(u) and B(u) of Eq. vec_component1/2 frozen at the
                              previous iterate, full steps, no line search.  Both iterations have
                              the root of Eq. weakform as fixed point (0) */
+  int32_t gmres_one_pass; /* 0: classical Gram-Schmidt with one re-orthogonalisation (CGS2); 1: one
+                             classical Gram-Schmidt pass, never refined (PETSc's GMRES default, which
+                             Section 3.2's solver configuration leaves in place); half the FMAs (0) */
   double picard_tol;      /* Picard only: stop when eps = ||u^{k+1} - u^k|| / ||u^n|| (Eq. picardtol)
                              is <= picard_tol; 0 stops on the residual test of newton_rtol and
                              newton_atol instead.  newton_maxit bounds the iterations (0) */

@@ -122,6 +122,10 @@ struct seird_ctx {
   int32_t n_samples = 1;
   int64_t n_per_sample = 0;
   double* rtab = nullptr;
+  // the coarse factorisation's fixed launch sequence (two launches per block
+  // column), captured once into a CUDA graph on a private stream and replayed
+  cudaGraphExec_t coarse_graph = nullptr;
+  int64_t coarse_graph_kernels = 0;
   // sigmoid transmission schedule (seird_set_beta_schedule): beta(x) at the nodes
   bool sched_on = false;
   seird_beta_schedule sched{};

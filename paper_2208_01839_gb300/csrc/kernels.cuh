@@ -52,6 +52,7 @@ constexpr int REC = 44;
 constexpr int REC_K = 1, REC_G = 7, REC_P = 19;
 
 void count_launch();
+void count_launches(int64_t k);
 int64_t launch_total();
 // message returned by seird_last_error(NULL) (per host thread)
 void set_global_error(const std::string& msg);

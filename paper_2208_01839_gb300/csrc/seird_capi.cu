@@ -21,6 +21,7 @@ namespace seird {
 
 static std::atomic<int64_t> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 int64_t launch_total() { return g_launches.load(std::memory_order_relaxed); }
 void coarse_init();
 
@@ -290,7 +291,30 @@ int pc_setup(seird_ctx* ctx) {
     KTimer kt_(ctx, SEIRD_K_COARSE_SETUP);
     const CoarseDev c = coarse_dev(ctx);
     launch_coarse_assemble(c, ctx->val, ctx->val32, ctx->stream);
-    launch_coarse_factor(c, ctx->err, ctx->stream);
+    if (!ctx->coarse_graph) {
+      // capture on a private stream (the caller's stream may be the legacy default stream,
+      // which cannot be captured); the replays run on the context's stream
+      cudaStream_t cs;
+      CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+      const int64_t k0 = launch_total();
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        launch_coarse_factor(c, ctx->err, cs);
+        e = cudaStreamEndCapture(cs, &g);
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->coarse_graph, g, 0);
+      if (g) cudaGraphDestroy(g);
+      cudaStreamDestroy(cs);
+      ctx->coarse_graph_kernels = launch_total() - k0;
+      count_launches(-ctx->coarse_graph_kernels);  // captured, not run
+      if (e != cudaSuccess) {
+        ctx->coarse_graph = nullptr;
+        return fail(ctx, SEIRD_ECUDA, std::string("coarse factorisation graph: ") + cudaGetErrorString(e));
+      }
+    }
+    CK(cudaGraphLaunch(ctx->coarse_graph, ctx->stream));
+    count_launches(ctx->coarse_graph_kernels);
     CK(cudaGetLastError());
   }
   TRY(check_flags(ctx, "preconditioner setup"));
@@ -425,6 +449,8 @@ int gmres(seird_ctx* ctx, const double* b, double* x, double rtol, int* its_out,
   int its = 0;
   std::vector<double> g0(ldh, 0.0);
   double* gbuf = ctx->gm + (int64_t)ldh * m + 2 * m;  // g inside the GMRES small state
+  const bool one_pass = ctx->opt.gmres_one_pass == 1;
+  if (one_pass) CK(cudaMemsetAsync(h2, 0, sizeof(double) * NV_STRIDE, s));  // no second-pass coefficients
   while (true) {
     launch_axpby(len, 1.0 / rnorm, r, 0.0, r, ctx->V, s);
     g0.assign(ldh, 0.0);
@@ -446,9 +472,13 @@ int gmres(seird_ctx* ctx, const double* b, double* x, double rtol, int* its_out,
       {
         KTimer kt_(ctx, SEIRD_K_KRYLOV);
         launch_mdot(len, j + 1, ctx->V, len, ctx->w, ctx->partial, ctx->red_grid, h1, s);
-        launch_update_mdot(len, j + 1, ctx->V, len, h1, ctx->w, ctx->partial, ctx->red_grid, nullptr, s);
-        launch_reduce_cols(ctx->red_grid, j + 1, ctx->partial, h2, 0, s);
-        launch_update_norm(len, j + 1, ctx->V, len, h2, ctx->w, ctx->partial, ctx->red_grid, ctx->scal + 5, s);
+        if (one_pass) {
+          launch_update_norm(len, j + 1, ctx->V, len, h1, ctx->w, ctx->partial, ctx->red_grid, ctx->scal + 5, s);
+        } else {
+          launch_update_mdot(len, j + 1, ctx->V, len, h1, ctx->w, ctx->partial, ctx->red_grid, nullptr, s);
+          launch_reduce_cols(ctx->red_grid, j + 1, ctx->partial, h2, 0, s);
+          launch_update_norm(len, j + 1, ctx->V, len, h2, ctx->w, ctx->partial, ctx->red_grid, ctx->scal + 5, s);
+        }
         launch_givens(j, ctx->gm, h1, h2, ctx->scal + 5, ldh, ctx->scal + 2, s);
         launch_scale(len, ctx->w, ctx->scal + 3, 1, ctx->V + (int64_t)(j + 1) * len, s);
       }
@@ -895,6 +925,7 @@ void seird_destroy(seird_ctx* ctx) {
   if (!ctx) return;
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   for (cudaEvent_t e : ctx->evpool) cudaEventDestroy(e);
+  if (ctx->coarse_graph) cudaGraphExecDestroy(ctx->coarse_graph);
   for (void* p : ctx->allocations) cudaFree(p);
   if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
   if (ctx->h_err) cudaFreeHost(ctx->h_err);
@@ -908,6 +939,7 @@ static int create_impl(seird_ctx* ctx, const seird_mesh* mesh, const seird_param
       o.newton_maxit < 0 || o.ls_maxit < 0 || o.overlap < 0 || o.coarse < 0 || o.coarse > 2 ||
       (o.quadrature != 0 && o.quadrature != 1) || (o.precision != 0 && o.precision != 1) ||
       (o.gmres_forcing != 0 && o.gmres_forcing != 1) || (o.nonlinear != 0 && o.nonlinear != 1) ||
+      (o.gmres_one_pass != 0 && o.gmres_one_pass != 1) ||
       !(o.picard_tol >= 0))
     return fail(ctx, SEIRD_EINVAL, "invalid option value");
   std::string err;
