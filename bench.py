@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--forcing", choices=["fixed", "ew"], default="ew")
     ap.add_argument("--pc-lag", type=int, default=20)
+    ap.add_argument("--pc-keep", type=int, default=3, help="steps a preconditioner may be carried over")
+    ap.add_argument("--coarse", type=int, choices=[1, 2], default=2,
+                    help="1 additive coarse correction, 2 the paper's multiplicative two-grid (Eq. RAS_2L)")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--cgs2", action="store_true", help="re-orthogonalise (CGS2) instead of PETSc's single pass")
     ap.add_argument("--seed", type=int, default=0)
@@ -72,7 +75,9 @@ def workload_config(wl, args):
     return {
         "workload": "%s (Southern-Ontario-like 24-gon, %d P1 nodes, %d unknowns)" % (wl.name, wl.n, 5 * wl.n),
         "n_nodes": wl.n, "n_tris": int(len(wl.tri)), "dof": 5 * wl.n, "dt_days": wl.dt,
-        "subdomains": args.subdomains, "overlap": 2, "coarse": "additive, constant per subdomain and compartment",
+        "subdomains": args.subdomains, "overlap": 2,
+        "coarse": ("additive" if args.coarse == 1 else "multiplicative two-grid (Eq. RAS_2L)") +
+                  ", constant per subdomain and compartment",
         "subdomain_solver": "block ILU(0)",
         "krylov": "FGMRES(30) right-preconditioned, %s, rtol 1e-5" % (
             "CGS2" if args.cgs2 else "classical Gram-Schmidt single pass (PETSc default)"),
@@ -227,7 +232,8 @@ def measure(S, wl, args, stream, precision, forcing, pc_lag, world, local, e2e=T
     import torch
     import torch.distributed as dist
     sv = S.Solver(wl.xy, wl.tri, wl.params, stream=stream, dt=wl.dt, n_subdomains=args.subdomains, overlap=2,
-                  coarse=1, newton_rtol=1e-8, gmres_rtol=1e-5, gmres_restart=30, gmres_maxit=200,
+                  coarse=args.coarse, pc_keep_steps=args.pc_keep, newton_rtol=1e-8, gmres_rtol=1e-5,
+                  gmres_restart=30, gmres_maxit=200,
                   precision=1 if precision == "mixed" else 0, seed=args.seed, timing=1,
                   gmres_forcing=1 if forcing == "ew" else 0, pc_lag=pc_lag, gmres_one_pass=0 if args.cgs2 else 1)
     info = sv.info()
@@ -286,9 +292,9 @@ def measure_ensemble(S, I, args, stream, world, local):
     import torch.distributed as dist
     wl = I.ontario_workload(256 * 256, seed=args.seed, structured=True, nside=256)
     samples = I.rate_samples(wl.params, args.ensemble, args.seed)
-    sv = S.Solver(wl.xy, wl.tri, samples, stream=stream, dt=wl.dt, n_subdomains=16, overlap=2, coarse=1,
-                  newton_rtol=1e-8, gmres_rtol=1e-5, gmres_restart=30, gmres_maxit=200, seed=args.seed,
-                  gmres_forcing=1, pc_lag=args.pc_lag, gmres_one_pass=0 if args.cgs2 else 1)
+    sv = S.Solver(wl.xy, wl.tri, samples, stream=stream, dt=wl.dt, n_subdomains=16, overlap=2, coarse=args.coarse,
+                  pc_keep_steps=args.pc_keep, newton_rtol=1e-8, gmres_rtol=1e-5, gmres_restart=30, gmres_maxit=200,
+                  seed=args.seed, gmres_forcing=1, pc_lag=args.pc_lag, gmres_one_pass=0 if args.cgs2 else 1)
     sv.set_state(torch.tensor(np.concatenate([wl.U0] * len(samples)), device="cuda"))
     for _ in range(args.warmup):
         sv.step()
@@ -320,6 +326,19 @@ def kernel_summary(S, res):
     return kms, kcalls
 
 
+# GB300's nominal FP64 rate (no FP64 tensor path beyond the FP64 pipe's 1.25 TFLOP/s)
+FP64_PEAK_TFLOPS = 1.25
+
+
+def algorithmic_fma(cls, info):
+    """FP64 FMAs one launch must perform: 25 per 5x5 block product."""
+    if cls == "spmv":
+        return 25 * info["nnzb"]
+    if cls == "ilu_solve":  # forward L blocks + backward U blocks + the inverted pivots = every local block
+        return 25 * info["subdomain_blocks"]
+    return None
+
+
 def roofline(S, res, precision):
     kms, kcalls = kernel_summary(S, res)
     info = res["info"]
@@ -336,10 +355,16 @@ def roofline(S, res, precision):
     sp_ab = algorithmic_bytes("spmv", info, precision)
     sp_ms = kms["spmv"] / max(kcalls["spmv"], 1)
     sp_gbs = sp_ab / (sp_ms * 1e-3) / 1e9 if kcalls["spmv"] else None
+    fma = algorithmic_fma(dom, info) if precision == "fp64" else None
+    alu = None
+    if fma is not None:
+        tf = 2.0 * fma / (avg_ms * 1e-3) / 1e12
+        alu = {"achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tf / FP64_PEAK_TFLOPS,
+               "peak_kind": "nominal FP64 (profiling recipe)", "fma_per_launch": fma}
     return ({"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
              "frac": achieved / peak, "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind ==
              "measured" else peak_kind, "traffic": traffic, "algorithmic_bytes_per_launch": ab,
-             "avg_launch_ms": avg_ms, "launches": kcalls[dom]},
+             "avg_launch_ms": avg_ms, "launches": kcalls[dom], "fp64_alu": alu},
             {"gbs": sp_gbs, "frac_of_hbm": (sp_gbs / peak) if sp_gbs else None, "avg_launch_ms": sp_ms,
              "launches": kcalls["spmv"], "algorithmic_bytes": sp_ab},
             kms, kcalls)
@@ -394,7 +419,8 @@ def run_ours(args):
             "data": "synthetic (seeded Southern-Ontario-like mesh, density and infection seeds)",
             "config": dict(workload_config(wl, args), precision=args.precision,
                            forcing="Eisenstat-Walker" if args.forcing == "ew" else "fixed rtol 1e-5",
-                           pc_lag=args.pc_lag, parallelism="replicas" if world > 1 else "single GPU"),
+                           pc_lag=args.pc_lag, pc_keep_steps=args.pc_keep,
+                           parallelism="replicas" if world > 1 else "single GPU"),
             "roofline": roof, "spmv": spmv, "cpu_baseline": cpu, "e2e": res.get("e2e"),
             "gpu_launches": res["launches"], "clocks": res["clocks"],
             "kernel_ms": {k: round(v, 3) for k, v in kms.items()}, "kernel_calls": kcalls,

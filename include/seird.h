@@ -129,6 +129,14 @@ typedef struct {
   double picard_tol;      /* Picard only: stop when eps = ||u^{k+1} - u^k|| / ||u^n|| (Eq. picardtol)
                              is <= picard_tol; 0 stops on the residual test of newton_rtol and
                              newton_atol instead.  newton_maxit bounds the iterations (0) */
+  int32_t pc_keep_steps;  /* Newton: a preconditioner may serve the first iterations of up to
+                             pc_keep_steps later time steps before it is rebuilt (0: rebuilt at the
+                             start of every step).  A linear solve that stops unconverged with a
+                             carried-over preconditioner is repeated once with a fresh one (0) */
+  int32_t coarse_group;   /* coarse space: one unit per group of this many consecutive subdomains
+                             (Z's column (g, c) = indicator of the nodes the group owns in compartment c).
+                             0 chooses 1 unless 5 x units would exceed 8192 or units 1160 (the sizes of
+                             the explicit coarse inverse), else the smallest group that fits (0) */
 } seird_options;
 
 /* Kernel classes of seird_stats.kernel_ms / kernel_calls. */

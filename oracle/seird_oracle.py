@@ -459,20 +459,23 @@ def coarse_matrix(row_ptr, col, val, owner):
     return (Z.T @ A @ Z).toarray(), Z
 
 
-def ras_apply(row_ptr, col, val, owner, delta, r, coarse=True, multiplicative=False):
+def ras_apply(row_ptr, col, val, owner, delta, r, coarse=True, multiplicative=False, coarse_owner=None):
     """z = M^{-1} r for the restricted additive Schwarz preconditioner (Eq. RAS)
     with block-ILU(0) subdomain solves on R_p A R_p^T (local unknowns numbered
     by (owner, node index)), plus, if ``coarse``, the additive coarse term
-    Z A_c^{-1} Z^T r (M_2^{-1} = M_RAS^{-1} + Q, Section 3.1).
+    Z A_c^{-1} Z^T r (M_2^{-1} = M_RAS^{-1} + Q, Section 3.1).  ``coarse_owner``
+    (default: ``owner``) assigns the nodes to the coarse space's units when
+    several subdomains share one unit.
 
     With ``multiplicative`` the two-grid preconditioner of Eq. RAS_2L instead:
     the three corrections of Eqs. presmoother, coarsecorrection, postsmoother
     with P1 = P3 = M_RAS^{-1} and P2 = Q, each applied to the residual left by
     the previous one (u^0 = 0, f = r)."""
+    cown = owner if coarse_owner is None else coarse_owner
     if multiplicative:
         n = len(row_ptr) - 1
         A = sp.bsr_matrix((val, col, row_ptr), shape=(5 * n, 5 * n)).tocsr()
-        Ac, Z = coarse_matrix(row_ptr, col, val, owner)
+        Ac, Z = coarse_matrix(row_ptr, col, val, cown)
         u = ras_apply(row_ptr, col, val, owner, delta, r, coarse=False)          # u^{1/3} = P1 f
         u = u + Z @ np.linalg.solve(Ac, Z.T @ (r - A @ u))                       # u^{2/3} = u + P2 (f - A u)
         u = u + ras_apply(row_ptr, col, val, owner, delta, r - A @ u, coarse=False)  # u^1 = u + P3 (f - A u)
@@ -492,7 +495,7 @@ def ras_apply(row_ptr, col, val, owner, delta, r, coarse=True, multiplicative=Fa
         mine = owner[nodes] == q
         zz[nodes[mine]] = zq[mine]
     if coarse:
-        Ac, Z = coarse_matrix(row_ptr, col, val, owner)
+        Ac, Z = coarse_matrix(row_ptr, col, val, cown)
         yc = np.linalg.solve(Ac, Z.T @ r)
         z += Z @ yc
     return z

@@ -25,6 +25,8 @@ constexpr int MAX_RESTART = 64;
 // coarse problems up to this many unknowns (5 x subdomains) keep an explicit
 // inverse (applied as a GEMV); larger ones are solved through the band factors
 constexpr int64_t DENSE_COARSE_MAX = 8192;
+// coarse units whose explicit inverse is built five columns per CTA (25 doubles per unit in shared memory)
+constexpr int32_t COARSE_BLOCKCOL_MAX = 1160;
 // blocks per ILU-solve level buffer (two buffers of 24 KB in FP64 at 26 doubles per block)
 constexpr int32_t SOLVE_BUF_BLOCKS = SOLVE_BUF_BLOCKS_DEV;
 constexpr int32_t SOLVE_BUF_ROWS = SOLVE_BUF_ROWS_DEV;
@@ -80,7 +82,12 @@ struct HostSetup {
     int32_t max_lev_blocks = 0;
   } sp_fwd, sp_bwd;
   // coarse space: subdomain p sits at block row cpos[p] of the banded coarse matrix
-  std::vector<int32_t> cpos;        // [P]
+  // coarse units: groups of cG consecutive subdomains (cG = 1 unless the coarse matrix would be too
+  // large for its explicit inverse); unit u owns the internal nodes [cunit_ptr[u], cunit_ptr[u+1])
+  int32_t cG = 1, Pc = 0;
+  std::vector<int32_t> cunit_ptr;   // [Pc+1]
+  std::vector<int32_t> cunit;       // [n] unit of each internal node
+  std::vector<int32_t> cpos;        // [Pc]
   int32_t cband = 0;                // half bandwidth in blocks
   std::vector<int32_t> cseg_blk;    // [nnzb] J block ids ordered by (cpos p, cpos q) then id
   std::vector<int32_t> cchunk_ptr;  // [nchunk+1] chunks of cseg_blk summed by one warp
@@ -131,6 +138,8 @@ struct seird_ctx {
   seird_beta_schedule sched{};
   double* bsched = nullptr;
   int32_t* perm = nullptr;
+  int32_t* cunit_ptr = nullptr;
+  int32_t* cunit = nullptr;
   int32_t* row_ptr = nullptr;
   int32_t* col = nullptr;
   int32_t* tpos = nullptr;
@@ -219,6 +228,7 @@ struct seird_ctx {
   double* crhs = nullptr;   // [2][5P]
   double* ainvT = nullptr;  // [5P][5P] explicit coarse inverse (transposed)
   bool pc_ready = false;
+  int32_t pc_age_steps = 0;  // time steps completed since the preconditioner was built
   bool jac_ready = false;
   // kernel-class timing (options.timing): (class, start event, end event) per launch group
   std::vector<cudaEvent_t> evpool;

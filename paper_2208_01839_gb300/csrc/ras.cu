@@ -572,6 +572,55 @@ __global__ void k_band_solve(int P, int bw, const double* __restrict__ band, con
   for (int k = tid; k < 5 * P; k += bd) yg[k] = ys[k];
 }
 
+// Explicit inverse, one CTA per block column b of the identity: L U X = E_b for
+// its five columns at once (ys[row][c] in shared memory), so a step over one
+// block row of the band is 25 independent dot products per band block.  X goes
+// to rows 5b..5b+4 of AinvT (row j of AinvT = column j of A_c^{-1}).
+__global__ void __launch_bounds__(256) k_band_inv(int P, int bw, const double* __restrict__ band,
+                                                  const double* __restrict__ cdinv, double* __restrict__ ainvT) {
+  extern __shared__ double ys[];
+  const int tid = threadIdx.x, bd = blockDim.x;
+  const int b = blockIdx.x;
+  double* bandm = const_cast<double*>(band);
+  for (int k = tid; k < 25 * P; k += bd) ys[k] = (k / 5 == 5 * b + k % 5) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int kb = b; kb < P; ++kb) {  // E_b is zero above block row b
+    const int nb = min(bw, P - 1 - kb);
+    for (int t = tid; t < 25 * nb; t += bd) {
+      const int ib = kb + 1 + t / 25, r = (t / 5) % 5, cc = t % 5;
+      const double* L = bblk(bandm, bw, ib, kb) + 5 * r;
+      double v = 0.0;
+#pragma unroll
+      for (int mm = 0; mm < 5; ++mm) v = fma(L[mm], ys[5 * (5 * kb + mm) + cc], v);
+      ys[5 * (5 * ib + r) + cc] -= v;
+    }
+    __syncthreads();
+  }
+  for (int kb = P - 1; kb >= 0; --kb) {
+    double tmp = 0.0;
+    if (tid < 25) {
+      const double* Dk = cdinv + 25 * (int64_t)kb + 5 * (tid / 5);
+#pragma unroll
+      for (int mm = 0; mm < 5; ++mm) tmp = fma(Dk[mm], ys[5 * (5 * kb + mm) + tid % 5], tmp);
+    }
+    __syncthreads();
+    if (tid < 25) ys[5 * (5 * kb + tid / 5) + tid % 5] = tmp;
+    __syncthreads();
+    const int nb = min(bw, kb);
+    for (int t = tid; t < 25 * nb; t += bd) {
+      const int ib = kb - 1 - t / 25, r = (t / 5) % 5, cc = t % 5;
+      const double* Ub = bblk(bandm, bw, ib, kb) + 5 * r;
+      double v = 0.0;
+#pragma unroll
+      for (int mm = 0; mm < 5; ++mm) v = fma(Ub[mm], ys[5 * (5 * kb + mm) + cc], v);
+      ys[5 * (5 * ib + r) + cc] -= v;
+    }
+    __syncthreads();
+  }
+  const int64_t nc = 5 * (int64_t)P;
+  for (int k = tid; k < 25 * P; k += bd) ainvT[(5 * b + k % 5) * nc + k / 5] = ys[k];
+}
+
 // part[chunk][i] = sum_{j in chunk} AinvT[j][i] rc[j]  (AinvT row j = column j of A_c^{-1})
 constexpr int GEMV_CHUNK = 64;
 __global__ void k_coarse_gemv_part(int nc, const double* __restrict__ AinvT, const double* __restrict__ rc,
@@ -688,8 +737,12 @@ void launch_coarse_factor(const CoarseDev& c, int32_t* err, cudaStream_t s) {
       count_launch();
     }
   }
-  if (c.ainvT) {  // explicit inverse: one CTA per unit vector through the banded factors
-    k_band_solve<<<5 * c.P, 256, sizeof(double) * 5 * c.P, s>>>(c.P, c.band, c.cband, c.cdinv, c.ainvT, 1);
+  if (c.ainvT) {  // explicit inverse through the banded factors
+    if (25 * (size_t)c.P * sizeof(double) <= 227 * 1024) {  // a block column of five unit vectors per CTA
+      k_band_inv<<<c.P, 256, 25 * sizeof(double) * c.P, s>>>(c.P, c.band, c.cband, c.cdinv, c.ainvT);
+    } else {  // one unit vector per CTA
+      k_band_solve<<<5 * c.P, 256, sizeof(double) * 5 * c.P, s>>>(c.P, c.band, c.cband, c.cdinv, c.ainvT, 1);
+    }
     count_launch();
   }
 }
@@ -719,6 +772,7 @@ template void launch_coarse_apply_add<float>(const CoarseDev&, int64_t, const do
 
 void coarse_init() {
   cudaFuncSetAttribute(k_band_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  cudaFuncSetAttribute(k_band_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   cudaFuncSetAttribute(k_ilu_solve<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)solve_smem(false));
   cudaFuncSetAttribute(k_ilu_solve<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)solve_smem(true));

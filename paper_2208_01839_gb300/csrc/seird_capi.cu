@@ -258,11 +258,11 @@ RasDev ras_dev(seird_ctx* ctx) {
 
 CoarseDev coarse_dev(seird_ctx* ctx) {
   CoarseDev c;
-  c.P = ctx->hs.P;
+  c.P = ctx->hs.Pc;  // coarse units (groups of cG subdomains)
   c.band = ctx->hs.cband;
   c.cpos = ctx->cpos;
-  c.owner = ctx->owner;
-  c.own_ptr = ctx->own_ptr;
+  c.owner = ctx->cunit;
+  c.own_ptr = ctx->cunit_ptr;
   c.cseg_blk = ctx->cseg_blk;
   c.cchunk_ptr = ctx->cchunk_ptr;
   c.nchunk = (int32_t)ctx->hs.cchunk_ptr.size() - 1;
@@ -319,6 +319,7 @@ int pc_setup(seird_ctx* ctx) {
   }
   TRY(check_flags(ctx, "preconditioner setup"));
   ctx->pc_ready = true;
+  ctx->pc_age_steps = 0;
   return SEIRD_OK;
 }
 
@@ -647,7 +648,9 @@ int newton_step(seird_ctx* ctx, seird_stats* st) {
     if (rc) return restore(rc);
     CK(cudaStreamSynchronize(s));
     S.ms_assemble += ms_since(t0);
-    if (its % std::max(1, ctx->opt.pc_lag) == 0 || !ctx->pc_ready) {
+    const bool rebuild = !ctx->pc_ready || (its == 0 ? ctx->pc_age_steps > ctx->opt.pc_keep_steps
+                                                     : its % std::max(1, ctx->opt.pc_lag) == 0);
+    if (rebuild) {
       t0 = clk::now();
       rc = pc_setup(ctx);
       S.ms_setup += ms_since(t0);
@@ -677,6 +680,18 @@ int newton_step(seird_ctx* ctx, seird_stats* st) {
     S.ms_solve += ms_since(t0);
     S.gmres_its += lits;
     if (rc) return restore(rc);
+    if (!conv && !rebuild) {  // the carried-over preconditioner fell short: rebuild it and solve again
+      t0 = clk::now();
+      rc = pc_setup(ctx);
+      S.ms_setup += ms_since(t0);
+      if (rc) return restore(rc);
+      S.pc_setups++;
+      t0 = clk::now();
+      rc = gmres(ctx, ctx->stage, ctx->dU, eta, &lits, &conv);
+      S.ms_solve += ms_since(t0);
+      S.gmres_its += lits;
+      if (rc) return restore(rc);
+    }
     double lam = 1.0, ft = 0.0;
     t0 = clk::now();
     for (int ls = 0;; ++ls) {
@@ -707,6 +722,7 @@ int newton_step(seird_ctx* ctx, seird_stats* st) {
   S.newton_its = its;
   S.res_final = f;
   ctx->t += ctx->opt.dt;
+  ctx->pc_age_steps++;
   S.ms_total = ms_since(t_begin);
   timing_collect(ctx, &S);
   if (st) *st = S;
@@ -939,15 +955,15 @@ static int create_impl(seird_ctx* ctx, const seird_mesh* mesh, const seird_param
       o.newton_maxit < 0 || o.ls_maxit < 0 || o.overlap < 0 || o.coarse < 0 || o.coarse > 2 ||
       (o.quadrature != 0 && o.quadrature != 1) || (o.precision != 0 && o.precision != 1) ||
       (o.gmres_forcing != 0 && o.gmres_forcing != 1) || (o.nonlinear != 0 && o.nonlinear != 1) ||
-      (o.gmres_one_pass != 0 && o.gmres_one_pass != 1) ||
+      (o.gmres_one_pass != 0 && o.gmres_one_pass != 1) || o.pc_keep_steps < 0 ||
       !(o.picard_tol >= 0))
     return fail(ctx, SEIRD_EINVAL, "invalid option value");
   std::string err;
   int rc = build_setup(mesh, &o, ctx->hs, err);
   if (rc) return fail(ctx, rc, err);
   HostSetup& hs = ctx->hs;
-  if (o.coarse && 5 * (int64_t)hs.P * 8 > 200 * 1024)
-    return fail(ctx, SEIRD_EINVAL, "coarse space supports at most 5120 subdomains");
+  if (o.coarse && 5 * (int64_t)hs.Pc * 8 > 200 * 1024)
+    return fail(ctx, SEIRD_EINVAL, "coarse space supports at most 5120 coarse units (options.coarse_group)");
   if (o.stream) {
     ctx->stream = (cudaStream_t)o.stream;
   } else {
@@ -1058,17 +1074,19 @@ static int create_impl(seird_ctx* ctx, const seird_mesh* mesh, const seird_param
     else TRY(dalloc(ctx, &ctx->pcu, len));
   }
   if (o.coarse) {
+    TRY(upload(ctx, &ctx->cunit_ptr, hs.cunit_ptr));
+    TRY(upload(ctx, &ctx->cunit, hs.cunit));
     TRY(upload(ctx, &ctx->cpos, hs.cpos));
     TRY(upload(ctx, &ctx->cseg_blk, hs.cseg_blk));
     TRY(upload(ctx, &ctx->cchunk_ptr, hs.cchunk_ptr));
     TRY(upload(ctx, &ctx->cdst_ptr, hs.cdst_ptr));
     TRY(upload(ctx, &ctx->cdst_idx, hs.cdst_idx));
-    const int64_t nc = 5 * (int64_t)hs.P;
+    const int64_t nc = 5 * (int64_t)hs.Pc;
     const int64_t nchunk = (int64_t)hs.cchunk_ptr.size() - 1;
     const bool dense = nc <= DENSE_COARSE_MAX;
     TRY(dalloc(ctx, &ctx->cpart, std::max<int64_t>(25 * nchunk, dense ? ((nc + 63) / 64) * nc : 0)));
-    TRY(dalloc(ctx, &ctx->cband, 25 * (size_t)hs.P * (2 * hs.cband + 1)));
-    TRY(dalloc(ctx, &ctx->cdinv, 25 * (size_t)hs.P));
+    TRY(dalloc(ctx, &ctx->cband, 25 * (size_t)hs.Pc * (2 * hs.cband + 1)));
+    TRY(dalloc(ctx, &ctx->cdinv, 25 * (size_t)hs.Pc));
     TRY(dalloc(ctx, &ctx->crhs, 2 * nc));
     if (dense) TRY(dalloc(ctx, &ctx->ainvT, (size_t)nc * nc));
   }
@@ -1133,6 +1151,16 @@ int seird_create_ensemble(const seird_mesh* mesh, int32_t n_samples, const seird
   }
   o.owner = owner.data();
   o.n_subdomains = (int32_t)(B * P);
+  if (o.coarse_group == 0) {
+    // coarse units must not span two samples: the group size divides the per-sample partition
+    int32_t G = 1;
+    auto fits = [&](int32_t g) {
+      const int64_t units = B * (P / g);
+      return 5 * units <= DENSE_COARSE_MAX && units <= COARSE_BLOCKCOL_MAX;
+    };
+    while (G < P && !(P % G == 0 && fits(G))) ++G;
+    o.coarse_group = G;
+  }
   seird_mesh um{B * n, B * m, xy.data(), tri.data()};
   seird_ctx* ctx = nullptr;
   rc = seird_create(&um, &p0, &o, &ctx);

@@ -444,14 +444,38 @@ int build_setup(const seird_mesh* mesh, const seird_options* opt, HostSetup& hs,
         sp.max_lev_blocks = std::max<int32_t>(sp.max_lev_blocks, (int32_t)(sp.levblk[v + 1] - sp.levblk[v]));
   }
 
-  // ---- coarse pattern: subdomain graph, RCM order, band, segment sums -----
+  // ---- coarse units: groups of consecutive subdomains -----------------------
+  // The bisection numbers spatial neighbours consecutively, so a group of G
+  // consecutive subdomains is a compact region.  G = options.coarse_group, or
+  // with 0 the smallest G that keeps the explicit inverse of A_c affordable.
   {
+    int32_t G = opt->coarse_group;
+    if (G < 0) {
+      err = "coarse_group must be >= 0";
+      return SEIRD_EINVAL;
+    }
+    if (G == 0) {
+      G = 1;
+      while (5 * (int64_t)((P + G - 1) / G) > DENSE_COARSE_MAX || (P + G - 1) / G > COARSE_BLOCKCOL_MAX) ++G;
+    }
+    G = std::min(G, P);
+    hs.cG = G;
+    hs.Pc = (P + G - 1) / G;
+    hs.cunit_ptr.resize(hs.Pc + 1);
+    for (int32_t u = 0; u <= hs.Pc; ++u) hs.cunit_ptr[u] = hs.own_ptr[std::min<int64_t>((int64_t)u * G, P)];
+    hs.cunit.resize(n);
+    for (int64_t i = 0; i < n; ++i) hs.cunit[i] = hs.owner[i] / G;
+  }
+
+  // ---- coarse pattern: unit graph, RCM order, band, segment sums ----------
+  {
+    const int32_t P = hs.Pc;  // the coarse matrix has one 5x5 block row per unit
     std::vector<std::vector<int32_t>> adj(P);
     std::vector<int64_t> pq;
     pq.reserve(nnzb);
     for (int64_t i = 0; i < n; ++i)
       for (int32_t k = hs.row_ptr[i]; k < hs.row_ptr[i + 1]; ++k) {
-        int32_t a = hs.owner[i], b = hs.owner[hs.col[k]];
+        int32_t a = hs.cunit[i], b = hs.cunit[hs.col[k]];
         if (a != b) pq.push_back((int64_t)a * P + b);
       }
     std::sort(pq.begin(), pq.end());
@@ -472,7 +496,7 @@ int build_setup(const seird_mesh* mesh, const seird_options* opt, HostSetup& hs,
     hs.cseg_blk.resize(nnzb);
     std::iota(hs.cseg_blk.begin(), hs.cseg_blk.end(), 0);
     for (int64_t k = 0; k < nnzb; ++k)
-      key[k] = (int64_t)hs.cpos[hs.owner[rowof[k]]] * P + hs.cpos[hs.owner[hs.col[k]]];
+      key[k] = (int64_t)hs.cpos[hs.cunit[rowof[k]]] * P + hs.cpos[hs.cunit[hs.col[k]]];
     std::stable_sort(hs.cseg_blk.begin(), hs.cseg_blk.end(), [&](int32_t a, int32_t b) { return key[a] < key[b]; });
     const int32_t CH = 256;  // blocks per chunk
     hs.cchunk_ptr.assign(1, 0);

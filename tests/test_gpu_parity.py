@@ -356,3 +356,36 @@ def test_multiplicative_two_grid_steps_match_oracle(precision):
         sv.run(3)
         got = sv.get_state()
     assert max(rel_l2_per_comp(got, U_ref)) <= 1e-9
+
+
+def test_preconditioner_carried_over_steps():
+    """options.pc_keep_steps: a preconditioner built in one step serves the next
+    ones (iteration counts change, the roots do not); an unconverged solve with a
+    carried-over preconditioner is retried with a fresh one."""
+    wl = WL["irregular3k"]
+    U_ref, _ = O.run(wl.xy, wl.tri, wl.params, wl.dt, wl.U0, 3, rtol=1e-12, atol=newton_floor(wl),
+                     bfield=wl.beta_field)
+    with solver(wl, coarse=1, pc_keep_steps=2, pc_lag=20) as sv:
+        sv.set_state(wl.U0)
+        stats = sv.run(3)
+        got = sv.get_state()
+    assert max(rel_l2_per_comp(got, U_ref)) <= 1e-9
+    assert stats[0]["pc_setups"] >= 1 and stats[1]["pc_setups"] == 0 and stats[2]["pc_setups"] == 0, stats
+
+
+@pytest.mark.parametrize("group,multiplicative", [(2, False), (3, False), (2, True)])
+def test_grouped_coarse_units_match_oracle(group, multiplicative):
+    """options.coarse_group: one coarse unit per group of consecutive subdomains
+    (here 6 box subdomains in groups of 2 or 3); the oracle's coarse space takes
+    the unit of each node as owner // group."""
+    wl = WL["irregular3k"]
+    J = O.jacobian(wl.xy, wl.tri, wl.params, wl.dt, wl.U0, bfield=wl.beta_field)
+    rp, col, val = O.to_bsr(J)
+    r = np.random.default_rng(9).standard_normal(5 * wl.n)
+    ref = O.ras_apply(rp, col, val, wl.owner, 2, r, coarse=True, multiplicative=multiplicative,
+                      coarse_owner=wl.owner // group)
+    with solver(wl, overlap=2, coarse=2 if multiplicative else 1, coarse_group=group) as sv:
+        sv.jacobian(wl.U0)
+        sv.precond_setup()
+        got = sv.precond_apply(r.reshape(-1, 5)).ravel()
+    assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
