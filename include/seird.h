@@ -204,8 +204,8 @@ int seird_create(const seird_mesh* mesh, const seird_params* params, const seird
  * subdomain, coarse unknown or matrix block couples two samples.  States are
  * [n_samples][n_nodes][5]; Newton and GMRES test the norms over all samples,
  * and each sample's state is the root of its own system.  An ensemble's rates
- * are fixed (seird_set_params, seird_set_beta_schedule and seird_adjoint
- * return SEIRD_EINVAL). */
+ * are fixed (seird_set_params and seird_set_beta_schedule return
+ * SEIRD_EINVAL); seird_adjoint gives every sample's gradient. */
 int seird_create_ensemble(const seird_mesh* mesh, int32_t n_samples, const seird_params* params,
                           const seird_options* opt, seird_ctx** out);
 
@@ -292,8 +292,13 @@ typedef struct {
  * consistent mass), each solved by the same right-preconditioned FGMRES with
  * RAS and coarse correction built from J_k^T, and accumulates
  * dj/dp = sum_k lambda_k^T dF^k/dp.  Outputs: *misfit, grad [10], grad_field
- * [n_nodes] (nullable, caller numbering).  The state and time are restored to
- * u^0 on return.  FP64 contexts only (options.precision = 0), else SEIRD_EINVAL. */
+ * [n_nodes] (nullable, caller numbering).  On an ensemble the observation
+ * nodes are ensemble nodes (sample k's node i is k * n_nodes + i), the misfit
+ * sums over the samples and grad is [n_samples][10], each sample's gradient
+ * with respect to its own rates.  The state and time are restored to u^0 on
+ * return; every step builds its own preconditioner during the call
+ * (pc_keep_steps is ignored), so recomputed segments repeat the forward states
+ * exactly.  FP64 contexts only (options.precision = 0), else SEIRD_EINVAL. */
 int seird_adjoint(seird_ctx* ctx, const seird_misfit* spec, double* misfit, double* grad, double* grad_field);
 
 /* ---- component entry points (kernel-level parity and measurement) ---- */

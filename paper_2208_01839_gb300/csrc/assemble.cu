@@ -442,7 +442,7 @@ template <int RULE, bool BF>
 __global__ void __launch_bounds__(256) k_param_contract(int64_t m, const int32_t* __restrict__ tri,
                                                         const double* __restrict__ xy, const double* __restrict__ U,
                                                         const double* __restrict__ lam,
-                                                        const double* __restrict__ bfield, Rates r, int stride,
+                                                        const double* __restrict__ bfield, Rates rin, int stride,
                                                         double* __restrict__ partial, double* __restrict__ fe) {
   __shared__ double sh[8];
   double acc[10];
@@ -450,6 +450,7 @@ __global__ void __launch_bounds__(256) k_param_contract(int64_t m, const int32_t
   for (int k = 0; k < 10; ++k) acc[k] = 0.0;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x) {
     const Tri T = load_tri(tri, xy, t);
+    const Rates r = rates_at(rin, T.v[0]);
     double u[3][5], l[3][5];
     double Nbar = 0.0;
 #pragma unroll
@@ -656,6 +657,12 @@ void launch_param_contract(int64_t n, int64_t m, const int32_t* tri, const doubl
     k_gather_scalar_add<<<(n + 255) / 256, 256, 0, s>>>(n, inc_ptr, inc, fe, field_out);
     count_launch();
   }
+}
+
+void launch_field_gather(int64_t n, const int32_t* inc_ptr, const int32_t* inc, const double* fe, double* out,
+                         cudaStream_t s) {
+  k_gather_scalar_add<<<(n + 255) / 256, 256, 0, s>>>(n, inc_ptr, inc, fe, out);
+  count_launch();
 }
 
 void launch_misfit(int nobs, const int32_t* nodes, const double* Ihat, const double* Dhat, const double* U,

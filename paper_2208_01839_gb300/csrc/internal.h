@@ -129,6 +129,7 @@ struct seird_ctx {
   int32_t n_samples = 1;
   int64_t n_per_sample = 0;
   double* rtab = nullptr;
+  std::vector<int64_t> sample_tri_ptr;  // [n_samples+1] internal triangle range of each sample
   // the coarse factorisation's fixed launch sequence (two launches per block
   // column), captured once into a CUDA graph on a private stream and replayed
   cudaGraphExec_t coarse_graph = nullptr;

@@ -100,6 +100,8 @@ void launch_check_finite(int64_t len, const double* x, int32_t* err, cudaStream_
 void launch_mass(int64_t n, int64_t m, const int32_t* tri, const double* xy, const double* V, double* elem,
                  const int32_t* inc_ptr, const int32_t* inc, double* out, double* partial, double* norm2,
                  cudaStream_t s);
+void launch_field_gather(int64_t n, const int32_t* inc_ptr, const int32_t* inc, const double* fe, double* out,
+                         cudaStream_t s);
 void launch_param_contract(int64_t n, int64_t m, const int32_t* tri, const double* xy, const double* U,
                            const double* lam, const double* bfield, const Rates& r, int rule, double* partial,
                            int grid, int stride, double* fe, const int32_t* inc_ptr, const int32_t* inc,

@@ -809,7 +809,8 @@ int adjoint_impl(seird_ctx* ctx, const seird_misfit* sp, double* jout, double* g
   TRY(S.get(ctx, &valT, 25 * nnzb));
   TRY(S.get(ctx, &Ihat, (size_t)sp->n_obs_steps * sp->n_obs_nodes));
   TRY(S.get(ctx, &Dhat, (size_t)sp->n_obs_steps * sp->n_obs_nodes));
-  TRY(S.get(ctx, &gacc, 16));
+  const int B = ctx->n_samples;
+  TRY(S.get(ctx, &gacc, 16 * (size_t)B));
   TRY(S.get(ctx, &gf, n));
   TRY(S.get(ctx, &jacc, 2));
   TRY(S.get(ctx, &dnodes, sp->n_obs_nodes));
@@ -817,16 +818,21 @@ int adjoint_impl(seird_ctx* ctx, const seird_misfit* sp, double* jout, double* g
   CK(cudaMemcpyAsync(Ihat, sp->I_hat, sizeof(double) * nobs_all, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(Dhat, sp->D_hat, sizeof(double) * nobs_all, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(dnodes, nodes.data(), sizeof(int32_t) * nodes.size(), cudaMemcpyHostToDevice, s));
-  CK(cudaMemsetAsync(gacc, 0, sizeof(double) * 16, s));
+  CK(cudaMemsetAsync(gacc, 0, sizeof(double) * 16 * B, s));
   CK(cudaMemsetAsync(gf, 0, sizeof(double) * n, s));
   CK(cudaMemsetAsync(jacc, 0, sizeof(double) * 2, s));
   CK(cudaMemsetAsync(lam_next, 0, sizeof(double) * len, s));
   const double t0 = ctx->t;
   CK(cudaMemcpyAsync(ckpt, ctx->U, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
+  // every step of the run and of its recomputation builds its own preconditioner, so the
+  // recomputed states are the forward ones bit for bit
+  const int32_t keep = ctx->opt.pc_keep_steps;
+  ctx->opt.pc_keep_steps = 0;
   auto restore = [&](int code) {
     cudaMemcpyAsync(ctx->U, ckpt, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
     cudaStreamSynchronize(s);
     ctx->t = t0;
+    ctx->opt.pc_keep_steps = keep;
     return code;
   };
   const int nobs = sp->n_obs_nodes;
@@ -875,17 +881,29 @@ int adjoint_impl(seird_ctx* ctx, const seird_misfit* sp, double* jout, double* g
       ctx->pc_ready = false;  // the factors belong to J^T
       if (rc) return restore(rc);
       if (!conv) return restore(fail(ctx, SEIRD_EGMRES, "adjoint: transposed solve did not converge"));
-      launch_param_contract(n, hs.m, ctx->tri, ctx->xy, Uk, lam, ctx->bfield, make_rates(ctx), ctx->opt.quadrature,
-                            ctx->partial, grid, NV_STRIDE, ctx->elem, ctx->node_inc_ptr, ctx->node_inc, gf, s);
-      launch_reduce_cols(grid, 10, ctx->partial, gacc, 1, s);
+      if (B == 1) {
+        launch_param_contract(n, hs.m, ctx->tri, ctx->xy, Uk, lam, ctx->bfield, make_rates(ctx),
+                              ctx->opt.quadrature, ctx->partial, grid, NV_STRIDE, ctx->elem, ctx->node_inc_ptr,
+                              ctx->node_inc, gf, s);
+        launch_reduce_cols(grid, 10, ctx->partial, gacc, 1, s);
+      } else {  // an ensemble: each sample's rates get the contraction over its own triangles
+        for (int b = 0; b < B; ++b) {
+          const int64_t t0 = ctx->sample_tri_ptr[b], t1 = ctx->sample_tri_ptr[b + 1];
+          launch_param_contract(n, t1 - t0, ctx->tri + 3 * t0, ctx->xy, Uk, lam, ctx->bfield, make_rates(ctx),
+                                ctx->opt.quadrature, ctx->partial, grid, NV_STRIDE, ctx->elem + 3 * t0, nullptr,
+                                nullptr, nullptr, s);
+          launch_reduce_cols(grid, 10, ctx->partial, gacc + 16 * b, 1, s);
+        }
+        launch_field_gather(n, ctx->node_inc_ptr, ctx->node_inc, ctx->elem, gf, s);
+      }
       CK(cudaGetLastError());
       std::swap(lam, lam_next);
     }
   }
   double jv = 0.0;
-  std::vector<double> g(16);
+  std::vector<double> g(16 * (size_t)B);
   CK(cudaMemcpyAsync(&jv, jacc, sizeof(double), cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(g.data(), gacc, sizeof(double) * 16, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(g.data(), gacc, sizeof(double) * 16 * B, cudaMemcpyDeviceToHost, s));
   if (gfield) {
     std::vector<double> gi(n);
     CK(cudaMemcpyAsync(gi.data(), gf, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
@@ -895,7 +913,8 @@ int adjoint_impl(seird_ctx* ctx, const seird_misfit* sp, double* jout, double* g
   CK(cudaStreamSynchronize(s));
   if (jout) *jout = jv;
   if (grad)
-    for (int k = 0; k < 10; ++k) grad[k] = g[k];
+    for (int b = 0; b < B; ++b)
+      for (int k = 0; k < 10; ++k) grad[10 * b + k] = g[16 * b + k];
   return restore(SEIRD_OK);
 }
 
@@ -1180,6 +1199,13 @@ int seird_create_ensemble(const seird_mesh* mesh, int32_t n_samples, const seird
   }
   ctx->n_samples = n_samples;
   ctx->n_per_sample = n;
+  // internal triangles are ordered by their smallest node, so each sample's are one range
+  ctx->sample_tri_ptr.assign(B + 1, 0);
+  for (int64_t t = 0; t < B * m; ++t) {
+    const int32_t* v = ctx->hs.tri.data() + 3 * t;
+    ctx->sample_tri_ptr[std::min({v[0], v[1], v[2]}) / n + 1]++;
+  }
+  for (int64_t k = 0; k < B; ++k) ctx->sample_tri_ptr[k + 1] += ctx->sample_tri_ptr[k];
   *out = ctx;
   return SEIRD_OK;
 }
@@ -1251,7 +1277,7 @@ int seird_set_beta_schedule(seird_ctx* ctx, const seird_beta_schedule* sched) {
 int seird_adjoint(seird_ctx* ctx, const seird_misfit* spec, double* misfit, double* grad, double* grad_field) {
   if (!ctx || !spec) return fail(ctx, SEIRD_EINVAL, "NULL argument");
   if (ctx->sched_on) return fail(ctx, SEIRD_EINVAL, "adjoint: turn the beta schedule off first (constant rates only)");
-  if (ctx->rtab) return fail(ctx, SEIRD_EINVAL, "adjoint: not available on an ensemble");
+
   return adjoint_impl(ctx, spec, misfit, grad, grad_field);
 }
 

@@ -314,9 +314,9 @@ class Solver:
 
     def adjoint(self, n_steps, obs_nodes, obs_steps, I_hat, D_hat, checkpoint_every=1, lin_rtol=0.0,
                 field=True):
-        """(misfit, gradient over PARAM_NAMES [10], gradient over the per-node
-        transmission field [n] or None) by the discrete adjoint, from the current
-        state; the state is left unchanged."""
+        """(misfit, gradient over PARAM_NAMES [10] (ensembles: [n_samples, 10]),
+        gradient over the per-node transmission field [n] or None) by the discrete
+        adjoint, from the current state; the state is left unchanged."""
         nodes = np.ascontiguousarray(obs_nodes, dtype=np.int32)
         steps = np.ascontiguousarray(obs_steps, dtype=np.int32)
         Ih = np.ascontiguousarray(I_hat, dtype=np.float64)
@@ -324,11 +324,11 @@ class Solver:
         spec = Misfit(int(n_steps), int(checkpoint_every), len(nodes), nodes.ctypes.data_as(_ip), len(steps),
                       steps.ctypes.data_as(_ip), Ih.ctypes.data_as(_dp), Dh.ctypes.data_as(_dp), float(lin_rtol))
         j = C.c_double()
-        g = np.zeros(10)
+        g = np.zeros(10 * self.n_samples)
         gf = np.zeros(self.n) if field else None
         self._check(_adjoint(self._h, C.byref(spec), C.byref(j), g.ctypes.data,
                              None if gf is None else gf.ctypes.data))
-        return j.value, g, gf
+        return j.value, (g if self.n_samples == 1 else g.reshape(self.n_samples, 10)), gf
 
     def info(self):
         inf = Info()

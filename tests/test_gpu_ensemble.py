@@ -7,8 +7,10 @@ their own rates, solved as one block-diagonal system.
 * Steps: every sample's state is the oracle root at its rates (<= 1e-9
   relative L2 per compartment, FP64 and mixed).
 * An ensemble of one sample reproduces the single-problem context bit for bit.
-* Rates of an ensemble are fixed: set_params, the beta schedule and the adjoint
-  are refused.
+* Rates of an ensemble are fixed: set_params and the beta schedule are refused.
+* The ensemble adjoint gives every sample's gradient: sample by sample it is the
+  oracle's adjoint at that sample's rates and observations (1e-7 of the largest
+  scaled component, as the single-context adjoint test).
 """
 import numpy as np
 import pytest
@@ -103,6 +105,38 @@ def test_ensemble_rates_are_fixed():
         with pytest.raises(S.SeirdError):
             sv.set_beta_schedule(dict(b0=0.1, b1=0.05, t_mid=1.0, beta_central=1.0, beta_eastern=1.0,
                                       beta_western=1.0, x_eastern=0.6, x_western=0.4, k_eastern=5.0, k_western=10.0))
-        sv.set_state(np.concatenate([U0] * 2))
-        with pytest.raises(S.SeirdError):
-            sv.adjoint(1, [0], [1], np.zeros((1, 1)), np.zeros((1, 1)))
+
+
+def test_ensemble_adjoint_is_per_sample_oracle_adjoint():
+    from oracle import seird_adjoint as A
+    xy, tri, samples, U0, bf = _problem(n_samples=2, seed=4, n_target=220)
+    n, N, dt = len(xy), 6, 0.5
+    rng = np.random.default_rng(4)
+    obs = [np.sort(rng.choice(n, 12, replace=False)) for _ in samples]
+    steps = [2, 4, 6]
+    atol = 1e-15 * np.linalg.norm(O.residual(xy, tri, samples[0], 0.0, np.abs(U0), np.zeros_like(U0)))
+    refs, I_hat, D_hat = [], [], []
+    for k, p in enumerate(samples):
+        # observations from a run at perturbed rates, as in the single-context tests
+        p_obs = A.with_params(p, A.params_vector(p) * (1.0 + 0.2 * rng.uniform(-1, 1, 10)))
+        S_obs = A.forward_states(xy, tri, p_obs, dt, U0, N, bfield=bf)
+        Ih = np.array([S_obs[s][obs[k], 2] for s in steps])
+        Dh = np.array([S_obs[s][obs[k], 4] for s in steps])
+        Sx = A.forward_states(xy, tri, p, dt, U0, N, bfield=bf, rtol=1e-13, atol=atol)
+        refs.append(A.adjoint_gradient(xy, tri, p, dt, Sx, obs[k], steps, Ih, Dh, bfield=bf))
+        I_hat.append(Ih)
+        D_hat.append(Dh)
+    nodes = np.concatenate([obs[k] + k * n for k in range(len(samples))])
+    with S.Solver(xy, tri, samples, beta_field=bf, owner=I.box_partition(xy, 3, 2),
+                  **_opts(newton_rtol=1e-13, newton_atol=atol, gmres_restart=40, gmres_maxit=3000, overlap=1)) as sv:
+        sv.set_state(np.concatenate([U0] * len(samples)))
+        j, g, gb = sv.adjoint(N, nodes, steps, np.concatenate(I_hat, axis=1), np.concatenate(D_hat, axis=1),
+                              lin_rtol=1e-12)
+    assert g.shape == (len(samples), 10)
+    assert abs(j - sum(r[0] for r in refs)) <= 1e-9 * sum(r[0] for r in refs)
+    for k, p in enumerate(samples):
+        _, g_ref, gb_ref = refs[k]
+        scale = np.abs(g_ref * A.params_vector(p)).max()
+        assert np.all(np.abs(g[k] - g_ref) * np.abs(A.params_vector(p)) <= 1e-7 * scale), (k, g[k], g_ref)
+        gbk = gb[k * n:(k + 1) * n]
+        assert np.linalg.norm(gbk - gb_ref) <= 1e-7 * np.linalg.norm(gb_ref), k
