@@ -116,38 +116,55 @@ __global__ void __launch_bounds__(128) k_residual_elem(int64_t m, const int32_t*
 #pragma unroll
     for (int a = 0; a < 3; ++a) Fe[a][c] += coef * (gux * T.gx[a] + guy * T.gy[a]);
   }
+  // linear reaction terms: (phi_a, u_c) exactly (consistent mass) with the degree-5
+  // rule, which integrates them exactly, or lumped (|T|/3 u_a) with the vertex rule
+  {
+    double Mu[3][5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      const double sc = u[0][c] + u[1][c] + u[2][c];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) Mu[a][c] = RULE == 0 ? m12 * (u[a][c] + sc) : (T.area / 3.0) * u[a][c];
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double MN = Mu[a][0] + Mu[a][1] + Mu[a][2] + Mu[a][3] + Mu[a][4];
+      Fe[a][0] -= r.dt * (r.alpha * MN - r.mu * Mu[a][0]);
+      Fe[a][1] += r.dt * (r.sigma + r.ge + r.mu) * Mu[a][1];
+      Fe[a][2] -= r.dt * (r.sigma * Mu[a][1] - (r.gr + r.gd + r.mu) * Mu[a][2]);
+      Fe[a][3] -= r.dt * (r.ge * Mu[a][1] + r.gr * Mu[a][2] - r.mu * Mu[a][3]);
+      Fe[a][4] -= r.dt * r.gd * Mu[a][2];
+    }
+  }
+  // transmission s -> e, kappa s (beta_I i + beta_E e) b, by the quadrature rule
   double bv[3] = {1.0, 1.0, 1.0};
   if (BF) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) bv[a] = bfield[T.v[a]];
   }
+  double Nv[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) Nv[a] = u[a][0] + u[a][1] + u[a][2] + u[a][3] + u[a][4];
   constexpr int NQ = RULE == 0 ? 7 : 3;
   bool bad = false;
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
-    double uq[5];
-#pragma unroll
-    for (int c = 0; c < 5; ++c)
-      uq[c] = cQL[RULE][q][0] * u[0][c] + cQL[RULE][q][1] * u[1][c] + cQL[RULE][q][2] * u[2][c];
-    const double bq = BF ? cQL[RULE][q][0] * bv[0] + cQL[RULE][q][1] * bv[1] + cQL[RULE][q][2] * bv[2] : 1.0;
-    const double N = uq[0] + uq[1] + uq[2] + uq[3] + uq[4];
+    const double L0 = cQL[RULE][q][0], L1 = cQL[RULE][q][1], L2 = cQL[RULE][q][2];
+    const double sq = L0 * u[0][0] + L1 * u[1][0] + L2 * u[2][0];
+    const double eq = L0 * u[0][1] + L1 * u[1][1] + L2 * u[2][1];
+    const double iq = L0 * u[0][2] + L1 * u[1][2] + L2 * u[2][2];
+    const double N = L0 * Nv[0] + L1 * Nv[1] + L2 * Nv[2];
+    const double bq = BF ? L0 * bv[0] + L1 * bv[1] + L2 * bv[2] : 1.0;
     bad |= !(N > 0.0);
     const double kappa = 1.0 - r.A / N;
-    const double lam = (r.bi * uq[2] + r.be * uq[1]) * bq;
-    const double Tr = kappa * uq[0] * lam;  // transmission s -> e
-    double R[5];
-    R[0] = r.alpha * N - Tr - r.mu * uq[0];
-    R[1] = Tr - (r.sigma + r.ge + r.mu) * uq[1];
-    R[2] = r.sigma * uq[1] - (r.gr + r.gd + r.mu) * uq[2];
-    R[3] = r.ge * uq[1] + r.gr * uq[2] - r.mu * uq[3];
-    R[4] = r.gd * uq[2];
-    const double wq = r.dt * T.area * cQW[RULE][q];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const double wa = wq * cQL[RULE][q][a];
-#pragma unroll
-      for (int c = 0; c < 5; ++c) Fe[a][c] -= wa * R[c];
-    }
+    const double Tr = kappa * sq * (r.bi * iq + r.be * eq) * bq;
+    const double wq = r.dt * T.area * cQW[RULE][q] * Tr;
+    Fe[0][0] += wq * L0;
+    Fe[1][0] += wq * L1;
+    Fe[2][0] += wq * L2;
+    Fe[0][1] -= wq * L0;
+    Fe[1][1] -= wq * L1;
+    Fe[2][1] -= wq * L2;
   }
   if (bad) atomicOr(err, 1);
   double* out = elem + 15 * t;
