@@ -177,8 +177,9 @@ typedef struct {
   int64_t subdomain_rows;      /* sum over subdomains of overlapped node counts */
   int64_t subdomain_blocks;    /* sum over subdomains of local BSR blocks */
   int32_t max_levels;          /* deepest ILU(0) level schedule */
-  int32_t coarse_band;         /* half bandwidth (in subdomains) of the coarse matrix */
+  int32_t coarse_band;         /* half bandwidth (in coarse units) of the coarse matrix */
   int64_t device_bytes;        /* device memory held by the context */
+  int32_t coarse_units;        /* units of the coarse space (groups of options.coarse_group subdomains) */
 } seird_info;
 
 typedef struct seird_ctx seird_ctx;

@@ -88,6 +88,11 @@ struct HostSetup {
   std::vector<int32_t> cunit_ptr;   // [Pc+1]
   std::vector<int32_t> cunit;       // [n] unit of each internal node
   std::vector<int32_t> cpos;        // [Pc]
+  // A Z (J seen through the coarse prolongation): in each BSR row the blocks of one coarse
+  // unit are consecutive, one segment per (row, unit)
+  std::vector<int64_t> az_ptr;      // [n+1] segments of each row
+  std::vector<int32_t> az_unit;     // [nseg] coarse unit of each segment
+  std::vector<int32_t> az_blk;      // [nseg+1] first block of each segment (the last entry is nnzb)
   int32_t cband = 0;                // half bandwidth in blocks
   std::vector<int32_t> cseg_blk;    // [nnzb] J block ids ordered by (cpos p, cpos q) then id
   std::vector<int32_t> cchunk_ptr;  // [nchunk+1] chunks of cseg_blk summed by one warp
@@ -141,6 +146,11 @@ struct seird_ctx {
   int32_t* perm = nullptr;
   int32_t* cunit_ptr = nullptr;
   int32_t* cunit = nullptr;
+  int64_t* az_ptr = nullptr;   // multiplicative two-grid: A Z segments and their 5x5 sums
+  int32_t* az_unit = nullptr;
+  int32_t* az_blk = nullptr;
+  double* azval = nullptr;
+  float* azval32 = nullptr;
   int32_t* row_ptr = nullptr;
   int32_t* col = nullptr;
   int32_t* tpos = nullptr;

@@ -184,6 +184,10 @@ struct CoarseDev {
   double* ainvT;   // [5P][5P] explicit inverse, transposed (NULL: banded solve per apply)
 };
 void launch_coarse_assemble(const CoarseDev& c, const double* val, const float* val32, cudaStream_t s);
+void launch_az_build(int64_t nseg, const int32_t* az_blk, const double* val, const float* val32, double* azval,
+                     float* azval32, bool fp32, cudaStream_t s);
+void launch_az_sub(const CoarseDev& c, int64_t n, const int64_t* az_ptr, const int32_t* az_unit,
+                   const double* azval, const float* azval32, bool fp32, double* t, cudaStream_t s);
 void launch_coarse_factor(const CoarseDev& c, int32_t* err, cudaStream_t s);
 template <class TZ>
 void launch_coarse_apply_add(const CoarseDev& c, int64_t n, const double* r, TZ* z, cudaStream_t s);

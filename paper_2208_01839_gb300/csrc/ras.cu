@@ -770,6 +770,55 @@ void launch_coarse_apply_add(const CoarseDev& c, int64_t n, const double* r, TZ*
 template void launch_coarse_apply_add<double>(const CoarseDev&, int64_t, const double*, double*, cudaStream_t);
 template void launch_coarse_apply_add<float>(const CoarseDev&, int64_t, const double*, float*, cudaStream_t);
 
+// A Z segments: azval[s] = sum of the J blocks of segment s (one thread per entry)
+template <class TV, class TA>
+__global__ void k_az_build(int64_t nseg, const int32_t* __restrict__ az_blk, const TV* __restrict__ val,
+                           TA* __restrict__ azval) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= 25 * nseg) return;
+  const int64_t s = g / 25;
+  const int e = (int)(g - 25 * s);
+  double acc = 0.0;
+  for (int32_t b = az_blk[s]; b < az_blk[s + 1]; ++b) acc += (double)val[25 * (int64_t)b + e];
+  azval[g] = (TA)acc;
+}
+
+// t -= (A Z) y for the coarse solution y (cpos order): one thread per scalar row
+template <class TA>
+__global__ void k_az_sub(int64_t n, const int64_t* __restrict__ az_ptr, const int32_t* __restrict__ az_unit,
+                         const int32_t* __restrict__ cpos, const TA* __restrict__ azval,
+                         const double* __restrict__ y, double* __restrict__ t) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= 5 * n) return;
+  const int64_t i = g / 5;
+  const int rr = (int)(g - 5 * i);
+  double acc = 0.0;
+  for (int64_t s = az_ptr[i]; s < az_ptr[i + 1]; ++s) {
+    const TA* A = azval + 25 * s + 5 * rr;
+    const double* ys = y + 5 * (int64_t)cpos[az_unit[s]];
+#pragma unroll
+    for (int mm = 0; mm < 5; ++mm) acc = fma((double)A[mm], ys[mm], acc);
+  }
+  t[g] -= acc;
+}
+
+void launch_az_build(int64_t nseg, const int32_t* az_blk, const double* val, const float* val32, double* azval,
+                     float* azval32, bool fp32, cudaStream_t s) {
+  const unsigned g = (unsigned)((25 * nseg + 255) / 256);
+  if (fp32) k_az_build<float, float><<<g, 256, 0, s>>>(nseg, az_blk, val32, azval32);
+  else k_az_build<double, double><<<g, 256, 0, s>>>(nseg, az_blk, val, azval);
+  count_launch();
+}
+
+void launch_az_sub(const CoarseDev& c, int64_t n, const int64_t* az_ptr, const int32_t* az_unit,
+                   const double* azval, const float* azval32, bool fp32, double* t, cudaStream_t s) {
+  const double* y = c.ainvT ? c.crhs + 5 * (int64_t)c.P : c.crhs;
+  const unsigned g = (unsigned)((5 * n + 255) / 256);
+  if (fp32) k_az_sub<float><<<g, 256, 0, s>>>(n, az_ptr, az_unit, c.cpos, azval32, y, t);
+  else k_az_sub<double><<<g, 256, 0, s>>>(n, az_ptr, az_unit, c.cpos, azval, y, t);
+  count_launch();
+}
+
 void coarse_init() {
   cudaFuncSetAttribute(k_band_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   cudaFuncSetAttribute(k_band_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);

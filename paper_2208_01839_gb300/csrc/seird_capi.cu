@@ -315,6 +315,9 @@ int pc_setup(seird_ctx* ctx) {
     }
     CK(cudaGraphLaunch(ctx->coarse_graph, ctx->stream));
     count_launches(ctx->coarse_graph_kernels);
+    if (ctx->opt.coarse == 2)  // (A Z) of this set-up: the multiplicative step's residual update
+      launch_az_build((int64_t)ctx->hs.az_unit.size(), ctx->az_blk, ctx->val, ctx->val32, ctx->azval, ctx->azval32,
+                      mixed(ctx), ctx->stream);
     CK(cudaGetLastError());
   }
   TRY(check_flags(ctx, "preconditioner setup"));
@@ -341,10 +344,11 @@ int pc_apply32(seird_ctx* ctx, const double* r, float* z) {
     launch_axpby(len, 1.0, r, -1.0, ctx->pct, ctx->pct, ctx->stream);
     {
       KTimer kt_(ctx, SEIRD_K_COARSE_APPLY);
-      launch_coarse_apply_add<float>(coarse_dev(ctx), ctx->hs.n, ctx->pct, z, ctx->stream);
+      const CoarseDev cd = coarse_dev(ctx);
+      launch_coarse_apply_add<float>(cd, ctx->hs.n, ctx->pct, z, ctx->stream);
+      // r - J (z + Z y) = (r - J z) - (J Z) y, with J Z summed at set-up
+      launch_az_sub(cd, ctx->hs.n, ctx->az_ptr, ctx->az_unit, ctx->azval, ctx->azval32, true, ctx->pct, ctx->stream);
     }
-    TRY(spmv32(ctx, z, ctx->pct));
-    launch_axpby(len, 1.0, r, -1.0, ctx->pct, ctx->pct, ctx->stream);
     {
       KTimer kt_(ctx, SEIRD_K_ILU_SOLVE);
       launch_ilu_solve32(ras_dev(ctx), ctx->pct, ctx->pcu32, ctx->err, ctx->stream);
@@ -378,10 +382,11 @@ int pc_apply(seird_ctx* ctx, const double* r, double* z) {
     launch_axpby(len, 1.0, r, -1.0, ctx->pct, ctx->pct, ctx->stream);
     {
       KTimer kt_(ctx, SEIRD_K_COARSE_APPLY);
-      launch_coarse_apply_add<double>(coarse_dev(ctx), ctx->hs.n, ctx->pct, z, ctx->stream);
+      const CoarseDev cd = coarse_dev(ctx);
+      launch_coarse_apply_add<double>(cd, ctx->hs.n, ctx->pct, z, ctx->stream);
+      // r - J (z + Z y) = (r - J z) - (J Z) y, with J Z summed at set-up
+      launch_az_sub(cd, ctx->hs.n, ctx->az_ptr, ctx->az_unit, ctx->azval, ctx->azval32, false, ctx->pct, ctx->stream);
     }
-    TRY(spmv(ctx, z, ctx->pct));
-    launch_axpby(len, 1.0, r, -1.0, ctx->pct, ctx->pct, ctx->stream);
     {
       KTimer kt_(ctx, SEIRD_K_ILU_SOLVE);
       launch_ilu_solve(ras_dev(ctx), ctx->pct, ctx->pcu, ctx->err, ctx->stream);
@@ -1091,6 +1096,11 @@ static int create_impl(seird_ctx* ctx, const seird_mesh* mesh, const seird_param
     TRY(dalloc(ctx, &ctx->pct, len));
     if (o.precision == 1) TRY(dalloc(ctx, &ctx->pcu32, len));
     else TRY(dalloc(ctx, &ctx->pcu, len));
+    TRY(upload(ctx, &ctx->az_ptr, hs.az_ptr));
+    TRY(upload(ctx, &ctx->az_unit, hs.az_unit));
+    TRY(upload(ctx, &ctx->az_blk, hs.az_blk));
+    if (o.precision == 1) TRY(dalloc(ctx, &ctx->azval32, 25 * hs.az_unit.size()));
+    else TRY(dalloc(ctx, &ctx->azval, 25 * hs.az_unit.size()));
   }
   if (o.coarse) {
     TRY(upload(ctx, &ctx->cunit_ptr, hs.cunit_ptr));
@@ -1292,6 +1302,7 @@ int seird_get_info(const seird_ctx* ctx, seird_info* info) {
   info->max_levels = ctx->hs.max_levels;
   info->coarse_band = ctx->hs.cband;
   info->device_bytes = ctx->device_bytes;
+  info->coarse_units = ctx->hs.Pc;
   return SEIRD_OK;
 }
 

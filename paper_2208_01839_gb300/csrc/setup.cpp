@@ -467,6 +467,24 @@ int build_setup(const seird_mesh* mesh, const seird_options* opt, HostSetup& hs,
     for (int64_t i = 0; i < n; ++i) hs.cunit[i] = hs.owner[i] / G;
   }
 
+  // ---- A Z segments: per row, the blocks of each coarse unit --------------
+  {
+    hs.az_ptr.assign(n + 1, 0);
+    hs.az_unit.clear();
+    hs.az_blk.clear();
+    for (int64_t i = 0; i < n; ++i) {
+      for (int32_t k = hs.row_ptr[i]; k < hs.row_ptr[i + 1]; ++k) {
+        const int32_t u = hs.cunit[hs.col[k]];
+        if (k == hs.row_ptr[i] || u != hs.cunit[hs.col[k - 1]]) {
+          hs.az_unit.push_back(u);
+          hs.az_blk.push_back(k);
+        }
+      }
+      hs.az_ptr[i + 1] = (int64_t)hs.az_unit.size();
+    }
+    hs.az_blk.push_back((int32_t)hs.col.size());
+  }
+
   // ---- coarse pattern: unit graph, RCM order, band, segment sums ----------
   {
     const int32_t P = hs.Pc;  // the coarse matrix has one 5x5 block row per unit

@@ -88,7 +88,7 @@ PARAM_NAMES = ("beta_i", "beta_e", "sigma", "gamma_e", "gamma_r", "gamma_d", "nu
 class Info(C.Structure):
     _fields_ = [("n_nodes", C.c_int64), ("n_tris", C.c_int64), ("nnzb", C.c_int64), ("n_subdomains", C.c_int32),
                 ("subdomain_rows", C.c_int64), ("subdomain_blocks", C.c_int64), ("max_levels", C.c_int32),
-                ("coarse_band", C.c_int32), ("device_bytes", C.c_int64)]
+                ("coarse_band", C.c_int32), ("device_bytes", C.c_int64), ("coarse_units", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -389,3 +389,25 @@ def test_grouped_coarse_units_match_oracle(group, multiplicative):
         sv.precond_setup()
         got = sv.precond_apply(r.reshape(-1, 5)).ravel()
     assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+def test_automatic_coarse_groups_beyond_the_explicit_inverse_limit():
+    """1200 subdomains exceed the 1160 units whose explicit inverse is built five
+    columns per CTA: the context groups them in pairs (600 units), and the
+    preconditioner is the oracle's with the unit of each node = owner // 2."""
+    xy, tri = I.structured_mesh(120)
+    dens = I.urban_density(11)
+    U0 = I.urban_ic(xy, dens, 11)
+    p = I.params_ontario(float(U0.sum(axis=1).max()))
+    owner = I.box_partition(xy, 40, 30)
+    assert owner.max() + 1 == 1200
+    J = O.jacobian(xy, tri, p, 0.5, U0)
+    rp, col, val = O.to_bsr(J)
+    r = np.random.default_rng(12).standard_normal(5 * len(xy))
+    ref = O.ras_apply(rp, col, val, owner, 1, r, coarse=True, coarse_owner=owner // 2)
+    with S.Solver(xy, tri, p, owner=owner, dt=0.5, overlap=1, coarse=1) as sv:
+        assert sv.info()["coarse_units"] == 600
+        sv.jacobian(U0)
+        sv.precond_setup()
+        got = sv.precond_apply(r.reshape(-1, 5)).ravel()
+    assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
