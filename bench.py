@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--forcing", choices=["fixed", "ew"], default="ew")
     ap.add_argument("--pc-lag", type=int, default=20)
     ap.add_argument("--pc-keep", type=int, default=3, help="steps a preconditioner may be carried over")
+    ap.add_argument("--predictor", type=int, choices=[0, 1], default=1,
+                    help="Newton's first iterate: 0 u^n, 1 the extrapolation 2 u^n - u^{n-1}")
     ap.add_argument("--coarse", type=int, choices=[1, 2], default=2,
                     help="1 additive coarse correction, 2 the paper's multiplicative two-grid (Eq. RAS_2L)")
     ap.add_argument("--no-mixed", action="store_true")
@@ -232,7 +234,8 @@ def measure(S, wl, args, stream, precision, forcing, pc_lag, world, local, e2e=T
     import torch
     import torch.distributed as dist
     sv = S.Solver(wl.xy, wl.tri, wl.params, stream=stream, dt=wl.dt, n_subdomains=args.subdomains, overlap=2,
-                  coarse=args.coarse, pc_keep_steps=args.pc_keep, newton_rtol=1e-8, gmres_rtol=1e-5,
+                  coarse=args.coarse, pc_keep_steps=args.pc_keep, predictor=args.predictor, newton_rtol=1e-8,
+                  gmres_rtol=1e-5,
                   gmres_restart=30, gmres_maxit=200,
                   precision=1 if precision == "mixed" else 0, seed=args.seed, timing=1,
                   gmres_forcing=1 if forcing == "ew" else 0, pc_lag=pc_lag, gmres_one_pass=0 if args.cgs2 else 1)
@@ -293,7 +296,8 @@ def measure_ensemble(S, I, args, stream, world, local):
     wl = I.ontario_workload(256 * 256, seed=args.seed, structured=True, nside=256)
     samples = I.rate_samples(wl.params, args.ensemble, args.seed)
     sv = S.Solver(wl.xy, wl.tri, samples, stream=stream, dt=wl.dt, n_subdomains=16, overlap=2, coarse=args.coarse,
-                  pc_keep_steps=args.pc_keep, newton_rtol=1e-8, gmres_rtol=1e-5, gmres_restart=30, gmres_maxit=200,
+                  pc_keep_steps=args.pc_keep, predictor=args.predictor, newton_rtol=1e-8, gmres_rtol=1e-5,
+                  gmres_restart=30, gmres_maxit=200,
                   seed=args.seed, gmres_forcing=1, pc_lag=args.pc_lag, gmres_one_pass=0 if args.cgs2 else 1)
     sv.set_state(torch.tensor(np.concatenate([wl.U0] * len(samples)), device="cuda"))
     for _ in range(args.warmup):
@@ -419,7 +423,7 @@ def run_ours(args):
             "data": "synthetic (seeded Southern-Ontario-like mesh, density and infection seeds)",
             "config": dict(workload_config(wl, args), precision=args.precision,
                            forcing="Eisenstat-Walker" if args.forcing == "ew" else "fixed rtol 1e-5",
-                           pc_lag=args.pc_lag, pc_keep_steps=args.pc_keep,
+                           pc_lag=args.pc_lag, pc_keep_steps=args.pc_keep, predictor=args.predictor,
                            parallelism="replicas" if world > 1 else "single GPU"),
             "roofline": roof, "spmv": spmv, "cpu_baseline": cpu, "e2e": res.get("e2e"),
             "gpu_launches": res["launches"], "clocks": res["clocks"],

@@ -137,6 +137,9 @@ typedef struct {
                              (Z's column (g, c) = indicator of the nodes the group owns in compartment c).
                              0 chooses 1 unless 5 x units would exceed 8192 or units 1160 (the sizes of
                              the explicit coarse inverse), else the smallest group that fits (0) */
+  int32_t predictor;      /* Newton's first iterate: 0 u^n (Section 2.2); 1 the linear extrapolation
+                             2 u^n - u^{n-1} when the previous step is known and it lowers ||F||.
+                             The stopping test stays relative to ||F(u^n)|| either way (0) */
 } seird_options;
 
 /* Kernel classes of seird_stats.kernel_ms / kernel_calls. */
@@ -297,9 +300,9 @@ typedef struct {
  * nodes are ensemble nodes (sample k's node i is k * n_nodes + i), the misfit
  * sums over the samples and grad is [n_samples][10], each sample's gradient
  * with respect to its own rates.  The state and time are restored to u^0 on
- * return; every step builds its own preconditioner during the call
- * (pc_keep_steps is ignored), so recomputed segments repeat the forward states
- * exactly.  FP64 contexts only (options.precision = 0), else SEIRD_EINVAL. */
+ * return; during the call every step builds its own preconditioner and
+ * starts Newton from u^n (pc_keep_steps and predictor are ignored), so
+ * recomputed segments repeat the forward states exactly.  FP64 contexts only (options.precision = 0), else SEIRD_EINVAL. */
 int seird_adjoint(seird_ctx* ctx, const seird_misfit* spec, double* misfit, double* grad, double* grad_field);
 
 /* ---- component entry points (kernel-level parity and measurement) ---- */

@@ -19,6 +19,8 @@ namespace seird {
 // weights 9/40 and (155 -+ sqrt 15)/1200); rule 1 = three vertices, 1/3 each.
 __constant__ double cQL[2][7][3];
 __constant__ double cQW[2][7];
+// w_q phi_a phi_b at point q for the pairs (0,0) (1,1) (2,2) (0,1) (0,2) (1,2)
+__constant__ double cQC[2][7][6];
 
 void upload_quadrature() {
   double L[2][7][3] = {};
@@ -38,8 +40,14 @@ void upload_quadrature() {
     L[1][q][q] = 1.0;
     W[1][q] = 1.0 / 3.0;
   }
+  double Cw[2][7][6] = {};
+  const int pa[6] = {0, 1, 2, 0, 0, 1}, pb[6] = {0, 1, 2, 1, 2, 2};
+  for (int rule = 0; rule < 2; ++rule)
+    for (int q = 0; q < 7; ++q)
+      for (int s = 0; s < 6; ++s) Cw[rule][q][s] = W[rule][q] * L[rule][q][pa[s]] * L[rule][q][pb[s]];
   cudaMemcpyToSymbol(cQL, L, sizeof(L));
   cudaMemcpyToSymbol(cQW, W, sizeof(W));
+  cudaMemcpyToSymbol(cQC, Cw, sizeof(Cw));
 }
 
 namespace {
@@ -277,7 +285,7 @@ __global__ void __launch_bounds__(128) k_jac_record(int64_t m, const int32_t* __
       const T gux = u[0][c] * Tt.gx[0] + u[1][c] * Tt.gx[1] + u[2][c] * Tt.gx[2];
       const T guy = u[0][c] * Tt.gy[0] + u[1][c] * Tt.gy[1] + u[2][c] * Tt.gy[2];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) out[REC_G + 3 * c + a] = a3 * (gux * Tt.gx[a] + guy * Tt.gy[a]);
+      for (int a = 0; a < 3; ++a) out[REC_G + 4 * a + c] = a3 * (gux * Tt.gx[a] + guy * Tt.gy[a]);
     }
   }
   // reaction moments P^k_ab = |T| sum_q w_q phi_a phi_b rho_k(x_q):
@@ -293,39 +301,47 @@ __global__ void __launch_bounds__(128) k_jac_record(int64_t m, const int32_t* __
 #pragma unroll
     for (int a = 0; a < 3; ++a) bv[a] = (T)bfield[Tt.v[a]];
   }
+  T Nv[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) Nv[a] = u[a][0] + u[a][1] + u[a][2] + u[a][3] + u[a][4];
+  const T A = (T)r.A, bi = (T)r.bi, be = (T)r.be;
   constexpr int NQ = RULE == 0 ? 7 : 3;
   bool bad = false;
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
     const T L0 = (T)cQL[RULE][q][0], L1 = (T)cQL[RULE][q][1], L2 = (T)cQL[RULE][q][2];
-    T uq[5];
-#pragma unroll
-    for (int c = 0; c < 5; ++c) uq[c] = L0 * u[0][c] + L1 * u[1][c] + L2 * u[2][c];
+    const T sq = L0 * u[0][0] + L1 * u[1][0] + L2 * u[2][0];
+    const T eq = L0 * u[0][1] + L1 * u[1][1] + L2 * u[2][1];
+    const T iq = L0 * u[0][2] + L1 * u[1][2] + L2 * u[2][2];
+    const T N = L0 * Nv[0] + L1 * Nv[1] + L2 * Nv[2];
     const T bq = BF ? L0 * bv[0] + L1 * bv[1] + L2 * bv[2] : T(1);
-    const T N = uq[0] + uq[1] + uq[2] + uq[3] + uq[4];
     bad |= !(N > T(0));
     const T invN = T(1) / N;
-    const T A = (T)r.A, bi = (T)r.bi, be = (T)r.be;
     const T kappa = T(1) - A * invN;
-    const T lam = (bi * uq[2] + be * uq[1]) * bq;
+    const T lam = (bi * iq + be * eq) * bq;
+    const T ksb = kappa * sq * bq;
     T rho[4];
-    rho[0] = PIC ? kappa * bi * uq[2] * bq : A * invN * invN * uq[0] * lam;
+    rho[0] = PIC ? kappa * bi * iq * bq : A * invN * invN * sq * lam;
     rho[1] = kappa * lam;
-    rho[2] = kappa * uq[0] * be * bq;
-    rho[3] = kappa * uq[0] * bi * bq;
-    const T wq = Tt.area * (T)cQW[RULE][q];
-    const T w6[6] = {wq * L0 * L0, wq * L1 * L1, wq * L2 * L2, wq * L0 * L1, wq * L0 * L2, wq * L1 * L2};
+    rho[2] = ksb * be;
+    rho[3] = ksb * bi;
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
+    for (int s = 0; s < 6; ++s) {
+      const T cw = (T)cQC[RULE][q][s];  // w_q phi_a phi_b; the area multiplies once at the end
 #pragma unroll
-      for (int s = 0; s < 6; ++s) P[k][s] += w6[s] * rho[k];
+      for (int k = 0; k < 4; ++k) P[k][s] += cw * rho[k];
+    }
   }
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int s = 0; s < 6; ++s) P[k][s] *= Tt.area;
   if (bad) atomicOr(err, 1);
 #pragma unroll
   for (int k = 0; k < 4; ++k)
 #pragma unroll
-    for (int s = 0; s < 6; ++s) out[REC_P + 6 * k + s] = P[k][s];
-  out[REC - 1] = T(0);
+    for (int s = 0; s < 6; ++s) out[REC_P + 4 * s + k] = P[k][s];
+  out[REC_K + 6] = T(0);
 }
 
 // One thread per 5x5 block: fixed-order sums over the triangles sharing the
@@ -358,10 +374,10 @@ __global__ void __launch_bounds__(128) k_jac_gather(int64_t nnzb, const int32_t*
     K += R[REC_K + s];
     if (!PIC) {
 #pragma unroll
-      for (int c = 0; c < 4; ++c) G[c] += R[REC_G + 3 * c + a];
+      for (int c = 0; c < 4; ++c) G[c] += R[REC_G + 4 * a + c];
     }
 #pragma unroll
-    for (int c = 0; c < 4; ++c) P[c] += R[REC_P + 6 * c + s];
+    for (int c = 0; c < 4; ++c) P[c] += R[REC_P + 4 * s + c];
   }
   if (RULE == 0) Mr = M;
   const T dt = (T)r.dt;

@@ -165,6 +165,8 @@ struct seird_ctx {
   // state and Newton vectors [n][5]
   double* U = nullptr;
   double* Un = nullptr;
+  double* Uprev = nullptr;  // u^{n-1} for the predictor (options.predictor)
+  bool have_prev = false;
   double* F = nullptr;
   double* Ft = nullptr;
   double* dU = nullptr;

@@ -46,10 +46,12 @@ __device__ __forceinline__ Rates rates_at(const Rates& r, int64_t node) {
 }
 #endif
 
-// Jacobian record of one triangle (doubles): area, N-weighted stiffness (6),
-// G_{c,a} = |T|/3 grad u_c . grad phi_a (12), reaction moments P^k_ab (24), pad.
+// Jacobian record of one triangle: area, N-weighted stiffness K_ab (6 pairs), pad,
+// G_{c,a} = |T|/3 grad u_c . grad phi_a stored [a][c] (12), reaction moments P^k_ab
+// stored [pair][k] (24).  The gather of block (a, b) reads G[a][0..3] and
+// P[pair][0..3]: 32 consecutive bytes each, starting on 32-byte boundaries (FP64).
 constexpr int REC = 44;
-constexpr int REC_K = 1, REC_G = 7, REC_P = 19;
+constexpr int REC_K = 1, REC_G = 8, REC_P = 20;
 
 void count_launch();
 void count_launches(int64_t k);

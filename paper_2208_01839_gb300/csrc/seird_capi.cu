@@ -635,8 +635,23 @@ int newton_step(seird_ctx* ctx, seird_stats* st) {
   int rc = residual(ctx, ctx->U, ctx->Un, ctx->F, &f);
   S.ms_assemble += ms_since(t0);
   if (rc) return rc;
-  const double f0 = f;
+  const double f0 = f;  // the stopping test is relative to ||F(u^n)||
   S.res0 = f0;
+  if (ctx->opt.predictor == 1 && ctx->have_prev && ctx->Uprev) {
+    // first iterate 2 u^n - u^{n-1}, kept only if it is admissible and lowers ||F||
+    t0 = clk::now();
+    launch_axpby(len, 2.0, ctx->Un, -1.0, ctx->Uprev, ctx->Ut, s);
+    double fp = 0.0;
+    rc = residual(ctx, ctx->Ut, ctx->Un, ctx->Ft, &fp);
+    S.ms_assemble += ms_since(t0);
+    if (rc == SEIRD_OK && fp < f) {
+      std::swap(ctx->U, ctx->Ut);
+      std::swap(ctx->F, ctx->Ft);
+      f = fp;
+    } else if (rc != SEIRD_OK && rc != SEIRD_ENONFINITE) {
+      return rc;
+    }
+  }
   double unorm;
   TRY(norm2(ctx, ctx->Un, &unorm));
   int its = 0;
@@ -728,6 +743,10 @@ int newton_step(seird_ctx* ctx, seird_stats* st) {
   S.res_final = f;
   ctx->t += ctx->opt.dt;
   ctx->pc_age_steps++;
+  if (ctx->Uprev) {
+    CK(cudaMemcpyAsync(ctx->Uprev, ctx->Un, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
+    ctx->have_prev = true;
+  }
   S.ms_total = ms_since(t_begin);
   timing_collect(ctx, &S);
   if (st) *st = S;
@@ -831,13 +850,16 @@ int adjoint_impl(seird_ctx* ctx, const seird_misfit* sp, double* jout, double* g
   CK(cudaMemcpyAsync(ckpt, ctx->U, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
   // every step of the run and of its recomputation builds its own preconditioner, so the
   // recomputed states are the forward ones bit for bit
-  const int32_t keep = ctx->opt.pc_keep_steps;
+  const int32_t keep = ctx->opt.pc_keep_steps, pred = ctx->opt.predictor;
   ctx->opt.pc_keep_steps = 0;
+  ctx->opt.predictor = 0;
   auto restore = [&](int code) {
     cudaMemcpyAsync(ctx->U, ckpt, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
     cudaStreamSynchronize(s);
     ctx->t = t0;
     ctx->opt.pc_keep_steps = keep;
+    ctx->opt.predictor = pred;
+    ctx->have_prev = false;
     return code;
   };
   const int nobs = sp->n_obs_nodes;
@@ -980,6 +1002,7 @@ static int create_impl(seird_ctx* ctx, const seird_mesh* mesh, const seird_param
       (o.quadrature != 0 && o.quadrature != 1) || (o.precision != 0 && o.precision != 1) ||
       (o.gmres_forcing != 0 && o.gmres_forcing != 1) || (o.nonlinear != 0 && o.nonlinear != 1) ||
       (o.gmres_one_pass != 0 && o.gmres_one_pass != 1) || o.pc_keep_steps < 0 ||
+      (o.predictor != 0 && o.predictor != 1) ||
       !(o.picard_tol >= 0))
     return fail(ctx, SEIRD_EINVAL, "invalid option value");
   std::string err;
@@ -1026,6 +1049,7 @@ static int create_impl(seird_ctx* ctx, const seird_mesh* mesh, const seird_param
   TRY(dalloc(ctx, &ctx->rec, (size_t)REC * m));
   double** vecs[] = {&ctx->U, &ctx->Un, &ctx->F, &ctx->Ft, &ctx->dU, &ctx->Ut, &ctx->stage, &ctx->stage2, &ctx->w};
   for (double** v : vecs) TRY(dalloc(ctx, v, len));
+  if (o.predictor == 1) TRY(dalloc(ctx, &ctx->Uprev, len));
   const bool mix = o.precision == 1;
   TRY(dalloc(ctx, &ctx->V, (size_t)(R + 1) * len));
   if (mix) {
@@ -1224,6 +1248,7 @@ int seird_set_state(seird_ctx* ctx, const double* u, int on_device, double t) {
   if (!ctx || !u) return fail(ctx, SEIRD_EINVAL, "NULL argument");
   TRY(to_internal(ctx, u, on_device, ctx->U));
   ctx->t = t;
+  ctx->have_prev = false;
   return SEIRD_OK;
 }
 

@@ -411,3 +411,18 @@ def test_automatic_coarse_groups_beyond_the_explicit_inverse_limit():
         sv.precond_setup()
         got = sv.precond_apply(r.reshape(-1, 5)).ravel()
     assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+def test_extrapolation_predictor_reaches_the_same_roots():
+    """options.predictor = 1 starts Newton from 2 u^n - u^{n-1}: the iterates
+    change, the roots (and the stopping test, relative to ||F(u^n)||) do not."""
+    wl = WL["irregular3k"]
+    U_ref, _ = O.run(wl.xy, wl.tri, wl.params, wl.dt, wl.U0, 4, rtol=1e-12, atol=newton_floor(wl),
+                     bfield=wl.beta_field)
+    with solver(wl, coarse=1, predictor=1) as sv:
+        sv.set_state(wl.U0)
+        stats = sv.run(4)
+        got = sv.get_state()
+    assert max(rel_l2_per_comp(got, U_ref)) <= 1e-9
+    # from the second step on the first iterate is the extrapolation, closer to the root
+    assert sum(s["newton_its"] for s in stats[1:]) <= 3 * max(s["newton_its"] for s in stats[:1]), stats
