@@ -61,8 +61,9 @@ def parse():
     ap.add_argument("--pc-keep", type=int, default=3, help="steps a preconditioner may be carried over")
     ap.add_argument("--predictor", type=int, choices=[0, 1], default=1,
                     help="Newton's first iterate: 0 u^n, 1 the extrapolation 2 u^n - u^{n-1}")
-    ap.add_argument("--coarse", type=int, choices=[1, 2], default=2,
-                    help="1 additive coarse correction, 2 the paper's multiplicative two-grid (Eq. RAS_2L)")
+    ap.add_argument("--coarse", type=int, choices=[1, 2, 3], default=2,
+                    help="1 additive coarse correction, 2 the paper's multiplicative two-grid (Eq. RAS_2L), "
+                         "3 coarse correction then RAS")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--cgs2", action="store_true", help="re-orthogonalise (CGS2) instead of PETSc's single pass")
     ap.add_argument("--seed", type=int, default=0)
@@ -78,8 +79,8 @@ def workload_config(wl, args):
         "workload": "%s (Southern-Ontario-like 24-gon, %d P1 nodes, %d unknowns)" % (wl.name, wl.n, 5 * wl.n),
         "n_nodes": wl.n, "n_tris": int(len(wl.tri)), "dof": 5 * wl.n, "dt_days": wl.dt,
         "subdomains": args.subdomains, "overlap": 2,
-        "coarse": ("additive" if args.coarse == 1 else "multiplicative two-grid (Eq. RAS_2L)") +
-                  ", constant per subdomain and compartment",
+        "coarse": {1: "additive", 2: "multiplicative two-grid (Eq. RAS_2L)",
+                   3: "coarse correction, then RAS"}[args.coarse] + ", constant per subdomain and compartment",
         "subdomain_solver": "block ILU(0)",
         "krylov": "FGMRES(30) right-preconditioned, %s, rtol 1e-5" % (
             "CGS2" if args.cgs2 else "classical Gram-Schmidt single pass (PETSc default)"),

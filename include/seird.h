@@ -101,7 +101,9 @@ typedef struct {
   int32_t overlap;        /* graph layers of overlap (1; Section 3.2 uses a minimal one) */
   int32_t coarse;         /* 0: one-level RAS; 1: additive constant coarse space (M_RAS^{-1} + Q);
                              2: multiplicative two-grid of Eq. RAS_2L (RAS, coarse correction,
-                             RAS, each on the residual left by the previous step) (0) */
+                             RAS, each on the residual left by the previous step); 3: coarse
+                             correction, then RAS on the residual it leaves (Q + M_RAS^{-1}(I - J Q),
+                             the two-grid without the pre-smoother) (0) */
   int32_t precision;      /* 0: FP64 throughout; 1: FP32 matrix copy and FP32 subdomain
                              factors inside the FP64 outer FGMRES (0) */
   int32_t quadrature;     /* 0: degree-5 seven-point rule; 1: three-vertex rule (0) */

@@ -470,8 +470,16 @@ def ras_apply(row_ptr, col, val, owner, delta, r, coarse=True, multiplicative=Fa
     With ``multiplicative`` the two-grid preconditioner of Eq. RAS_2L instead:
     the three corrections of Eqs. presmoother, coarsecorrection, postsmoother
     with P1 = P3 = M_RAS^{-1} and P2 = Q, each applied to the residual left by
-    the previous one (u^0 = 0, f = r)."""
+    the previous one (u^0 = 0, f = r).  ``multiplicative="hybrid"`` drops the
+    pre-smoother: Q r, then M_RAS^{-1} on the residual it leaves."""
     cown = owner if coarse_owner is None else coarse_owner
+    if multiplicative == "hybrid":
+        # coarse correction first, then RAS on the residual it leaves: Q r + M_RAS^{-1} (r - A Q r)
+        n = len(row_ptr) - 1
+        A = sp.bsr_matrix((val, col, row_ptr), shape=(5 * n, 5 * n)).tocsr()
+        Ac, Z = coarse_matrix(row_ptr, col, val, cown)
+        u = Z @ np.linalg.solve(Ac, Z.T @ r)
+        return u + ras_apply(row_ptr, col, val, owner, delta, r - A @ u, coarse=False)
     if multiplicative:
         n = len(row_ptr) - 1
         A = sp.bsr_matrix((val, col, row_ptr), shape=(5 * n, 5 * n)).tocsr()

@@ -193,5 +193,8 @@ void launch_az_sub(const CoarseDev& c, int64_t n, const int64_t* az_ptr, const i
 void launch_coarse_factor(const CoarseDev& c, int32_t* err, cudaStream_t s);
 template <class TZ>
 void launch_coarse_apply_add(const CoarseDev& c, int64_t n, const double* r, TZ* z, cudaStream_t s);
+void launch_coarse_solve(const CoarseDev& c, const double* r, cudaStream_t s);
+template <class TZ>
+void launch_coarse_prolong(const CoarseDev& c, int64_t n, TZ* z, cudaStream_t s);
 
 }  // namespace seird

@@ -747,8 +747,8 @@ void launch_coarse_factor(const CoarseDev& c, int32_t* err, cudaStream_t s) {
   }
 }
 
-template <class TZ>
-void launch_coarse_apply_add(const CoarseDev& c, int64_t n, const double* r, TZ* z, cudaStream_t s) {
+// y = A_c^{-1} Z^T r (left in crhs + 5P with the explicit inverse, in crhs otherwise)
+void launch_coarse_solve(const CoarseDev& c, const double* r, cudaStream_t s) {
   k_coarse_restrict<<<c.P, 256, 0, s>>>(c.own_ptr, c.cpos, r, c.crhs);
   count_launch();
   const int nc = 5 * c.P;
@@ -762,10 +762,24 @@ void launch_coarse_apply_add(const CoarseDev& c, int64_t n, const double* r, TZ*
     k_band_solve<<<1, 512, sizeof(double) * nc, s>>>(c.P, c.band, c.cband, c.cdinv, c.crhs, 0);
     count_launch();
   }
+}
+
+// z += Z y for the y of the last launch_coarse_solve
+template <class TZ>
+void launch_coarse_prolong(const CoarseDev& c, int64_t n, TZ* z, cudaStream_t s) {
+  const int nc = 5 * c.P;
   int64_t g = (5 * n + 255) / 256;
   if (g > 152 * 8) g = 152 * 8;
   k_coarse_prolong_add<TZ><<<(int)g, 256, 0, s>>>(n, c.owner, c.cpos, c.ainvT ? c.crhs + nc : c.crhs, z);
   count_launch();
+}
+template void launch_coarse_prolong<double>(const CoarseDev&, int64_t, double*, cudaStream_t);
+template void launch_coarse_prolong<float>(const CoarseDev&, int64_t, float*, cudaStream_t);
+
+template <class TZ>
+void launch_coarse_apply_add(const CoarseDev& c, int64_t n, const double* r, TZ* z, cudaStream_t s) {
+  launch_coarse_solve(c, r, s);
+  launch_coarse_prolong<TZ>(c, n, z, s);
 }
 template void launch_coarse_apply_add<double>(const CoarseDev&, int64_t, const double*, double*, cudaStream_t);
 template void launch_coarse_apply_add<float>(const CoarseDev&, int64_t, const double*, float*, cudaStream_t);

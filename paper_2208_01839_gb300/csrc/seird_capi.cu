@@ -315,7 +315,7 @@ int pc_setup(seird_ctx* ctx) {
     }
     CK(cudaGraphLaunch(ctx->coarse_graph, ctx->stream));
     count_launches(ctx->coarse_graph_kernels);
-    if (ctx->opt.coarse == 2)  // (A Z) of this set-up: the multiplicative step's residual update
+    if (ctx->opt.coarse >= 2)  // (J Z) of this set-up: the residual update after the coarse correction
       launch_az_build((int64_t)ctx->hs.az_unit.size(), ctx->az_blk, ctx->val, ctx->val32, ctx->azval, ctx->azval32,
                       mixed(ctx), ctx->stream);
     CK(cudaGetLastError());
@@ -332,6 +332,25 @@ int spmv(seird_ctx* ctx, const double* x, double* y);
 // z = M^{-1} r with FP32 subdomain factors and an FP32 result (mixed path)
 int pc_apply32(seird_ctx* ctx, const double* r, float* z) {
   const int64_t len = vlen(ctx);
+  if (ctx->opt.coarse == 3) {  // coarse correction, then RAS on the residual it leaves
+    const CoarseDev cd = coarse_dev(ctx);
+    {
+      KTimer kt_(ctx, SEIRD_K_COARSE_APPLY);
+      launch_coarse_solve(cd, r, ctx->stream);
+      CK(cudaMemcpyAsync(ctx->pct, r, sizeof(double) * len, cudaMemcpyDeviceToDevice, ctx->stream));
+      launch_az_sub(cd, ctx->hs.n, ctx->az_ptr, ctx->az_unit, ctx->azval, ctx->azval32, true, ctx->pct, ctx->stream);
+    }
+    {
+      KTimer kt_(ctx, SEIRD_K_ILU_SOLVE);
+      launch_ilu_solve32(ras_dev(ctx), ctx->pct, z, ctx->err, ctx->stream);
+    }
+    {
+      KTimer kt_(ctx, SEIRD_K_COARSE_APPLY);
+      launch_coarse_prolong<float>(cd, ctx->hs.n, z, ctx->stream);
+    }
+    CK(cudaGetLastError());
+    return SEIRD_OK;
+  }
   {
     KTimer kt_(ctx, SEIRD_K_ILU_SOLVE);
     launch_ilu_solve32(ras_dev(ctx), r, z, ctx->err, ctx->stream);
@@ -366,6 +385,26 @@ int pc_apply(seird_ctx* ctx, const double* r, double* z) {
   if (mixed(ctx)) {
     TRY(pc_apply32(ctx, r, ctx->Z32));
     launch_f32_to_f64(vlen(ctx), ctx->Z32, z, ctx->stream);
+    CK(cudaGetLastError());
+    return SEIRD_OK;
+  }
+  if (ctx->opt.coarse == 3) {  // coarse correction, then RAS on the residual it leaves
+    const int64_t len = vlen(ctx);
+    const CoarseDev cd = coarse_dev(ctx);
+    {
+      KTimer kt_(ctx, SEIRD_K_COARSE_APPLY);
+      launch_coarse_solve(cd, r, ctx->stream);
+      CK(cudaMemcpyAsync(ctx->pct, r, sizeof(double) * len, cudaMemcpyDeviceToDevice, ctx->stream));
+      launch_az_sub(cd, ctx->hs.n, ctx->az_ptr, ctx->az_unit, ctx->azval, ctx->azval32, false, ctx->pct, ctx->stream);
+    }
+    {
+      KTimer kt_(ctx, SEIRD_K_ILU_SOLVE);
+      launch_ilu_solve(ras_dev(ctx), ctx->pct, z, ctx->err, ctx->stream);
+    }
+    {
+      KTimer kt_(ctx, SEIRD_K_COARSE_APPLY);
+      launch_coarse_prolong<double>(cd, ctx->hs.n, z, ctx->stream);
+    }
     CK(cudaGetLastError());
     return SEIRD_OK;
   }
@@ -998,7 +1037,7 @@ void seird_destroy(seird_ctx* ctx) {
 static int create_impl(seird_ctx* ctx, const seird_mesh* mesh, const seird_params* params) {
   seird_options& o = ctx->opt;
   if (!(o.dt > 0) || o.gmres_restart < 1 || o.gmres_restart > MAX_RESTART || o.gmres_maxit < 1 ||
-      o.newton_maxit < 0 || o.ls_maxit < 0 || o.overlap < 0 || o.coarse < 0 || o.coarse > 2 ||
+      o.newton_maxit < 0 || o.ls_maxit < 0 || o.overlap < 0 || o.coarse < 0 || o.coarse > 3 ||
       (o.quadrature != 0 && o.quadrature != 1) || (o.precision != 0 && o.precision != 1) ||
       (o.gmres_forcing != 0 && o.gmres_forcing != 1) || (o.nonlinear != 0 && o.nonlinear != 1) ||
       (o.gmres_one_pass != 0 && o.gmres_one_pass != 1) || o.pc_keep_steps < 0 ||
@@ -1116,7 +1155,7 @@ static int create_impl(seird_ctx* ctx, const seird_mesh* mesh, const seird_param
     TRY(dalloc(ctx, &ctx->zwork, 5 * NL));
   }
   // coarse
-  if (o.coarse == 2) {
+  if (o.coarse >= 2) {
     TRY(dalloc(ctx, &ctx->pct, len));
     if (o.precision == 1) TRY(dalloc(ctx, &ctx->pcu32, len));
     else TRY(dalloc(ctx, &ctx->pcu, len));

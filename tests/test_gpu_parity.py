@@ -332,14 +332,15 @@ def test_mixed_precision_square_step_by_step():
 # ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("overlap", [1, 2])
-def test_multiplicative_two_grid_apply_matches_oracle(overlap):
+@pytest.mark.parametrize("mode", [True, "hybrid"])
+def test_multiplicative_two_grid_apply_matches_oracle(overlap, mode):
     wl = I.square_workload(17)
     owner = I.box_partition(wl.xy, 3, 2)
     J = O.jacobian(wl.xy, wl.tri, wl.params, wl.dt, wl.U0)
     rp, col, val = O.to_bsr(J)
     r = np.random.default_rng(21).standard_normal(5 * wl.n)
-    ref = O.ras_apply(rp, col, val, owner, overlap, r, multiplicative=True)
-    with solver(wl, owner=owner, overlap=overlap, coarse=2) as sv:
+    ref = O.ras_apply(rp, col, val, owner, overlap, r, multiplicative=mode)
+    with solver(wl, owner=owner, overlap=overlap, coarse=2 if mode is True else 3) as sv:
         sv.jacobian(wl.U0)
         sv.precond_setup()
         got = sv.precond_apply(r.reshape(-1, 5)).ravel()
@@ -347,11 +348,12 @@ def test_multiplicative_two_grid_apply_matches_oracle(overlap):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-def test_multiplicative_two_grid_steps_match_oracle(precision):
+@pytest.mark.parametrize("coarse", [2, 3])
+def test_multiplicative_two_grid_steps_match_oracle(precision, coarse):
     wl = WL["irregular3k"]
     U_ref, _ = O.run(wl.xy, wl.tri, wl.params, wl.dt, wl.U0, 3, rtol=1e-12, atol=newton_floor(wl),
                      bfield=wl.beta_field)
-    with solver(wl, coarse=2, precision=precision) as sv:
+    with solver(wl, coarse=coarse, precision=precision) as sv:
         sv.set_state(wl.U0)
         sv.run(3)
         got = sv.get_state()

@@ -384,6 +384,12 @@ def test_ilu0_exact_on_block_tridiagonal_and_single_subdomain_ras_is_inverse():
     owner = np.zeros(12, dtype=np.int32)
     z = O.ras_apply(rp, col, val, owner, 1, r, coarse=False)
     assert np.allclose(z, np.linalg.solve(A, r), rtol=1e-10, atol=1e-12)
+    # with an exact subdomain solve both two-level forms are the inverse too: the smoother
+    # after the coarse correction removes whatever residual the correction leaves
+    owner2 = np.repeat(np.arange(2, dtype=np.int32), 6)
+    for mode in (True, "hybrid"):
+        zz = O.ras_apply(rp, col, val, owner, 1, r, multiplicative=mode, coarse_owner=owner2)
+        assert np.allclose(zz, np.linalg.solve(A, r), rtol=1e-10, atol=1e-12), mode
 
 
 def test_overlap_layers_and_partition_of_unity():
