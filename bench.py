@@ -39,7 +39,7 @@ FALLBACK_HBM_GBS = 6800.0
 # full launch by the units it processes (traffic grows in proportion).
 NCU_TRAFFIC = {
     ("spmv", "fp64"): (307.414e6, 1400635, "nnzb"),  # profiles/k_bsr_spmv_ontario200k.md
-    ("ilu_solve", "fp64"): (385.414e6, 1577927, "subdomain_blocks"),  # profiles/k_ilu_solve_ontario200k.md (v6)
+    ("ilu_solve", "fp64"): (384.383e6, 1577927, "subdomain_blocks"),  # profiles/k_ilu_solve_ontario200k.md (v7)
 }
 
 # kernel classes with one kernel launch per timed call, and their algorithmic
@@ -70,6 +70,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ensemble", type=int, default=64, help="samples of the ensemble line (0: skip it)")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint timing line")
     ap.add_argument("--oracle-sample", type=str, default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -234,6 +235,7 @@ def measure(S, wl, args, stream, precision, forcing, pc_lag, world, local, e2e=T
     """Warm-up, then K device-timed steps (and K end-to-end steps) of one variant."""
     import torch
     import torch.distributed as dist
+    t_create = time.perf_counter()
     sv = S.Solver(wl.xy, wl.tri, wl.params, stream=stream, dt=wl.dt, n_subdomains=args.subdomains, overlap=2,
                   coarse=args.coarse, pc_keep_steps=args.pc_keep, predictor=args.predictor, newton_rtol=1e-8,
                   gmres_rtol=1e-5,
@@ -241,6 +243,7 @@ def measure(S, wl, args, stream, precision, forcing, pc_lag, world, local, e2e=T
                   precision=1 if precision == "mixed" else 0, seed=args.seed, timing=1,
                   gmres_forcing=1 if forcing == "ew" else 0, pc_lag=pc_lag, gmres_one_pass=0 if args.cgs2 else 1)
     info = sv.info()
+    t_create = time.perf_counter() - t_create  # partition, patterns, level schedules, upload
     sv.set_state(torch.tensor(wl.U0, device="cuda"))
     for _ in range(args.warmup):
         sv.step()
@@ -265,7 +268,7 @@ def measure(S, wl, args, stream, precision, forcing, pc_lag, world, local, e2e=T
     ms = max_over_ranks(ms, world)
     dof = 5 * wl.n
     out = {"value": aggregate_value(dof, args.steps, ms * 1e-3, world), "ms_per_step": ms / args.steps,
-           "launches": launches,
+           "launches": launches, "create_s": t_create,
            "clocks": clk.summary(), "info": info, "stats": stats}
     if e2e:
         hbuf = torch.empty((wl.n, 5), dtype=torch.float64, pin_memory=True)
@@ -322,6 +325,46 @@ def measure_ensemble(S, I, args, stream, world, local):
             "ms_per_step": ms / args.steps, "n_samples": len(samples), "dtype": "f64", "gpu_launches": launches,
             "newton_its_per_step": sum(s["newton_its"] for s in stats) / len(stats),
             "gmres_its_per_step": sum(s["gmres_its"] for s in stats) / len(stats)}
+
+
+def measure_adjoint(S, I, args, stream):
+    """Discrete adjoint of a 30-day run (60 steps of half a day) on the 256x256 urban square, checkpoints every 5
+    steps, misfit of I and D at 50 seeded nodes observed daily, gradient w.r.t. the 10 rates and the per-node
+    transmission field; timed against the same 60 forward steps."""
+    import numpy as np
+    import torch
+    wl = I.ontario_workload(256 * 256, seed=args.seed, structured=True, nside=256)
+    rng = np.random.default_rng(args.seed)
+    nodes = np.sort(rng.choice(wl.n, 50, replace=False)).astype(np.int32)
+    steps = np.arange(2, 61, 2, dtype=np.int32)
+    field = np.ones(wl.n)
+    sv = S.Solver(wl.xy, wl.tri, wl.params, beta_field=field, stream=stream, dt=wl.dt, n_subdomains=16, overlap=2,
+                  coarse=args.coarse, newton_rtol=1e-8, gmres_rtol=1e-5, gmres_restart=30, gmres_maxit=200,
+                  seed=args.seed, gmres_forcing=1, pc_lag=args.pc_lag, gmres_one_pass=0 if args.cgs2 else 1)
+    u0 = torch.tensor(wl.U0, device="cuda")
+    sv.set_state(u0)
+    obs = []
+    for k in range(1, 61):
+        sv.step()
+        if k % 2 == 0:
+            obs.append(sv.get_state()[nodes])
+    obs = np.array(obs)
+    I_hat, D_hat = 1.1 * obs[:, :, 2], 0.9 * obs[:, :, 4]  # misfit of a perturbed observation
+    sv.set_state(u0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sv.run(60)
+    torch.cuda.synchronize()
+    fwd = time.perf_counter() - t0
+    sv.set_state(u0)
+    t0 = time.perf_counter()
+    j, g, gb = sv.adjoint(60, nodes, steps, I_hat, D_hat, checkpoint_every=5)
+    torch.cuda.synchronize()
+    adj = time.perf_counter() - t0
+    sv.close()
+    return {"workload": "30-day discrete adjoint on the 256x256 urban square (327680 unknowns), checkpoints every 5 "
+                        "steps, 50 observed nodes", "seconds": adj, "forward_seconds": fwd, "ratio_to_forward": adj / fwd,
+            "misfit": j, "gradient_entries": int(g.size + gb.size)}
 
 
 def kernel_summary(S, res):
@@ -405,6 +448,9 @@ def run_ours(args):
     ens = None
     if args.ensemble > 0:
         ens = measure_ensemble(S, I, args, stream, world, local)
+    adj = None
+    if not args.no_adjoint and rank == 0:
+        adj = measure_adjoint(S, I, args, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -430,7 +476,8 @@ def run_ours(args):
             "gpu_launches": res["launches"], "clocks": res["clocks"],
             "kernel_ms": {k: round(v, 3) for k, v in kms.items()}, "kernel_calls": kcalls,
             "newton_its_per_step": sum(nits) / len(nits), "gmres_its_per_step": sum(gits) / len(gits),
-            "setup_s": {"generate": round(t_gen, 2)}, "device_bytes": res["info"]["device_bytes"],
+            "setup_s": {"generate": round(t_gen, 2), "create": round(res["create_s"], 2)},
+            "device_bytes": res["info"]["device_bytes"],
         }
         if other is not None:
             r2, s2, k2, c2 = roofline(S, other, "mixed")
@@ -442,6 +489,8 @@ def run_ours(args):
                              "clocks": other["clocks"]}
         if ens is not None:
             line["ensemble"] = ens
+        if adj is not None:
+            line["adjoint"] = adj
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
