@@ -71,6 +71,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ensemble", type=int, default=64, help="samples of the ensemble line (0: skip it)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint timing line")
+    ap.add_argument("--no-autotune", action="store_true", help="fixed launch shapes instead of the autotuner's")
     ap.add_argument("--oracle-sample", type=str, default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -241,7 +242,8 @@ def measure(S, wl, args, stream, precision, forcing, pc_lag, world, local, e2e=T
                   gmres_rtol=1e-5,
                   gmres_restart=30, gmres_maxit=200,
                   precision=1 if precision == "mixed" else 0, seed=args.seed, timing=1,
-                  gmres_forcing=1 if forcing == "ew" else 0, pc_lag=pc_lag, gmres_one_pass=0 if args.cgs2 else 1)
+                  gmres_forcing=1 if forcing == "ew" else 0, pc_lag=pc_lag, gmres_one_pass=0 if args.cgs2 else 1,
+                  autotune=0 if args.no_autotune else 1)
     info = sv.info()
     t_create = time.perf_counter() - t_create  # partition, patterns, level schedules, upload
     sv.set_state(torch.tensor(wl.U0, device="cuda"))
@@ -263,6 +265,7 @@ def measure(S, wl, args, stream, precision, forcing, pc_lag, world, local, e2e=T
         torch.cuda.synchronize()
     launches = S.launch_count() - launches0
     ms = e0.elapsed_time(e1)
+    info = sv.info()  # after the first solve: the autotuner's launch shapes
     if world > 1:
         dist.barrier()
     ms = max_over_ranks(ms, world)
@@ -477,6 +480,7 @@ def run_ours(args):
             "kernel_ms": {k: round(v, 3) for k, v in kms.items()}, "kernel_calls": kcalls,
             "newton_its_per_step": sum(nits) / len(nits), "gmres_its_per_step": sum(gits) / len(gits),
             "setup_s": {"generate": round(t_gen, 2), "create": round(res["create_s"], 2)},
+            "launch_shapes": {k: res["info"][k] for k in ("spmv_threads", "cgs_ctas", "cgs_tile")},
             "device_bytes": res["info"]["device_bytes"],
         }
         if other is not None:

@@ -142,6 +142,12 @@ typedef struct {
   int32_t predictor;      /* Newton's first iterate: 0 u^n (Section 2.2); 1 the linear extrapolation
                              2 u^n - u^{n-1} when the previous step is known and it lowers ||F||.
                              The stopping test stays relative to ||F(u^n)|| either way (0) */
+  int32_t autotune;       /* 1: at the first linear solve, time the candidate launch shapes of the SpMV
+                             (128/256/512 threads per CTA) and of the Gram-Schmidt kernels (2/3/4/6 CTAs
+                             per SM, 128- or 256-entry tiles) on the context's own vectors and keep the
+                             fastest; the choice is reported by seird_get_info.  The Gram-Schmidt shape
+                             sets the order of its sums, so results are reproducible for a given choice,
+                             not across choices.  0: fixed shapes (256 threads, 3 CTAs per SM, 256) (0) */
 } seird_options;
 
 /* Kernel classes of seird_stats.kernel_ms / kernel_calls. */
@@ -185,6 +191,9 @@ typedef struct {
   int32_t coarse_band;         /* half bandwidth (in coarse units) of the coarse matrix */
   int64_t device_bytes;        /* device memory held by the context */
   int32_t coarse_units;        /* units of the coarse space (groups of options.coarse_group subdomains) */
+  int32_t spmv_threads;        /* launch shapes in use (options.autotune): SpMV threads per CTA, */
+  int32_t cgs_ctas;            /* Gram-Schmidt CTAs, */
+  int32_t cgs_tile;            /* Gram-Schmidt tile entries (0: 256 up to depth 27, then 128) */
 } seird_info;
 
 typedef struct seird_ctx seird_ctx;

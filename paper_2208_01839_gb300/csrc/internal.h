@@ -166,6 +166,7 @@ struct seird_ctx {
   double* U = nullptr;
   double* Un = nullptr;
   double* Uprev = nullptr;  // u^{n-1} for the predictor (options.predictor)
+  double* Flast = nullptr;  // F(u^n; u^{n-1}), the previous step's last residual
   bool have_prev = false;
   double* F = nullptr;
   double* Ft = nullptr;
@@ -241,6 +242,10 @@ struct seird_ctx {
   double* crhs = nullptr;   // [2][5P]
   double* ainvT = nullptr;  // [5P][5P] explicit coarse inverse (transposed)
   bool pc_ready = false;
+  // launch shapes (options.autotune)
+  int spmv_tb = 256, cgs_tile = 0, sms = 1;
+  bool tuned = false;
+  double* tune_buf = nullptr;
   int32_t pc_age_steps = 0;  // time steps completed since the preconditioner was built
   bool jac_ready = false;
   // kernel-class timing (options.timing): (class, start event, end event) per launch group

@@ -73,15 +73,15 @@ void launch_jacobian(int64_t nnzb, int64_t m, const int32_t* tri, const double* 
                      const int32_t* inc, void* val, bool fp32, bool picard, int32_t* err, cudaStream_t s);
 template <class VT>
 void launch_spmv(int64_t nrow, const int32_t* rp, const int32_t* col, const VT* val, const double* x, double* y,
-                 cudaStream_t s);
+                 cudaStream_t s, int tb = 256);
 void launch_f64_to_f32(int64_t n, const double* src, float* dst, cudaStream_t s);
 
 // vectors (length len, grid-stride)
 void launch_norm2(int64_t len, const double* x, double* partial, int grid, double* out, cudaStream_t s);
 void launch_mdot(int64_t len, int nv, const double* V, int64_t ld, const double* w, double* partial, int grid,
-                 double* out, cudaStream_t s);
+                 double* out, cudaStream_t s, int tile = 0);
 void launch_update_mdot(int64_t len, int nv, const double* V, int64_t ld, const double* h, double* w,
-                        double* partial, int grid, double* out_add, cudaStream_t s);
+                        double* partial, int grid, double* out_add, cudaStream_t s, int tile = 0);
 void launch_update_norm(int64_t len, int nv, const double* V, int64_t ld, const double* h, double* w,
                         double* partial, int grid, double* out, cudaStream_t s);
 void launch_scale(int64_t len, const double* x, const double* alpha_ptr, int invert, double* y, cudaStream_t s);
@@ -162,7 +162,7 @@ void launch_ilu_reorg(const RasDev& d, int64_t nfwd, int64_t nbwd, const int64_t
 void launch_ilu_solve(const RasDev& d, const double* r, double* z, int32_t* err, cudaStream_t s);
 void launch_ilu_solve32(const RasDev& d, const double* r, float* z, int32_t* err, cudaStream_t s);
 void launch_spmv32(int64_t nrow, const int32_t* rp, const int32_t* col, const float* val, const float* x, double* y,
-                   cudaStream_t s);
+                   cudaStream_t s, int tb = 256);
 void launch_multi_axpy32(int64_t len, int nv, const float* Zs, int64_t ld, const double* coef, double* x,
                          cudaStream_t s);
 void launch_f32_to_f64(int64_t n, const float* src, double* dst, cudaStream_t s);

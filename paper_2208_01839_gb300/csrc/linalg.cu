@@ -19,7 +19,7 @@ __device__ __forceinline__ double ld_val(const float* p) { return (double)__ldg(
 // y = A x, 5x5 blocks.  One thread per scalar output row (block row i, row r):
 // all 32 lanes of every warp do useful FP64 work, 25 FMA per block per 5 threads.
 template <class VT>
-__global__ void __launch_bounds__(256) k_bsr_spmv(int64_t nrow, const int32_t* __restrict__ rp,
+__global__ void __launch_bounds__(512) k_bsr_spmv(int64_t nrow, const int32_t* __restrict__ rp,
                                                   const int32_t* __restrict__ col, const VT* __restrict__ val,
                                                   const double* __restrict__ x, double* __restrict__ y) {
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(256) k_bsr_spmv(int64_t nrow, const int32_t* _
 }
 
 // Mixed-precision SpMV: FP32 values and FP32 input, FP32 arithmetic, FP64 output.
-__global__ void __launch_bounds__(256) k_bsr_spmv32(int64_t nrow, const int32_t* __restrict__ rp,
+__global__ void __launch_bounds__(512) k_bsr_spmv32(int64_t nrow, const int32_t* __restrict__ rp,
                                                     const int32_t* __restrict__ col, const float* __restrict__ val,
                                                     const float* __restrict__ x, double* __restrict__ y) {
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -224,11 +224,13 @@ __global__ void __launch_bounds__(256) k_cgs_db(int64_t len, int nv, const doubl
   }
 }
 
-inline int cgs_tile(int nv) { return nv <= 27 ? 256 : 128; }
-inline size_t cgs_db_smem(int nv) {
-  const int T = cgs_tile(nv);
-  return sizeof(double) * (NVMAX + 7 + T + 2 * (size_t)(nv + 1) * T);
+// tile entries per CTA step: the caller's choice (128 or 256; 0 = by depth), 128 whenever
+// 256 would not fit twice in shared memory
+inline int cgs_tile(int nv, int want = 0) {
+  if (nv > 27) return 128;
+  return want == 128 ? 128 : 256;
 }
+inline size_t cgs_db_smem(int nv, int T) { return sizeof(double) * (NVMAX + 7 + T + 2 * (size_t)(nv + 1) * T); }
 
 // second CGS pass update and ||w||^2 without staging: every thread needs only its
 // own entries of the basis vectors, so they go straight to registers
@@ -373,22 +375,21 @@ inline int grid_for(int64_t len, int tb = 256, int cap = 152 * 8) {
 
 template <class VT>
 void launch_spmv(int64_t nrow, const int32_t* rp, const int32_t* col, const VT* val, const double* x, double* y,
-                 cudaStream_t s) {
+                 cudaStream_t s, int tb) {
   if (nrow <= 0) return;
-  const int tb = 256;
   const int64_t g = (5 * nrow + tb - 1) / tb;
   k_bsr_spmv<VT><<<g, tb, 0, s>>>(nrow, rp, col, val, x, y);
   count_launch();
 }
 template void launch_spmv<double>(int64_t, const int32_t*, const int32_t*, const double*, const double*, double*,
-                                  cudaStream_t);
+                                  cudaStream_t, int);
 template void launch_spmv<float>(int64_t, const int32_t*, const int32_t*, const float*, const double*, double*,
-                                 cudaStream_t);
+                                 cudaStream_t, int);
 
 void launch_spmv32(int64_t nrow, const int32_t* rp, const int32_t* col, const float* val, const float* x, double* y,
-                   cudaStream_t s) {
+                   cudaStream_t s, int tb) {
   if (nrow <= 0) return;
-  k_bsr_spmv32<<<(5 * nrow + 255) / 256, 256, 0, s>>>(nrow, rp, col, val, x, y);
+  k_bsr_spmv32<<<(5 * nrow + tb - 1) / tb, tb, 0, s>>>(nrow, rp, col, val, x, y);
   count_launch();
 }
 
@@ -426,11 +427,13 @@ void launch_norm2(int64_t len, const double* x, double* partial, int grid, doubl
 }
 
 void launch_mdot(int64_t len, int nv, const double* V, int64_t ld, const double* w, double* partial, int grid,
-                 double* out, cudaStream_t s) {
-  if (cgs_tile(nv) == 256)
-    k_cgs_db<0, 256><<<grid, 256, cgs_db_smem(nv), s>>>(len, nv, V, ld, nullptr, const_cast<double*>(w), partial);
+                 double* out, cudaStream_t s, int tile) {
+  if (cgs_tile(nv, tile) == 256)
+    k_cgs_db<0, 256><<<grid, 256, cgs_db_smem(nv, 256), s>>>(len, nv, V, ld, nullptr, const_cast<double*>(w),
+                                                            partial);
   else
-    k_cgs_db<0, 128><<<grid, 256, cgs_db_smem(nv), s>>>(len, nv, V, ld, nullptr, const_cast<double*>(w), partial);
+    k_cgs_db<0, 128><<<grid, 256, cgs_db_smem(nv, 128), s>>>(len, nv, V, ld, nullptr, const_cast<double*>(w),
+                                                            partial);
   k_reduce_cols<<<1, 256, 0, s>>>(grid, nv, NVMAX, partial, out, 0);
   count_launch();
   count_launch();
@@ -439,9 +442,11 @@ void launch_mdot(int64_t len, int nv, const double* V, int64_t ld, const double*
 // first CGS pass update fused with the second pass's dot products; the dots
 // are added to out_add (which holds the first-pass coefficients h)
 void launch_update_mdot(int64_t len, int nv, const double* V, int64_t ld, const double* h, double* w,
-                        double* partial, int grid, double* out_add, cudaStream_t s) {
-  if (cgs_tile(nv) == 256) k_cgs_db<1, 256><<<grid, 256, cgs_db_smem(nv), s>>>(len, nv, V, ld, h, w, partial);
-  else k_cgs_db<1, 128><<<grid, 256, cgs_db_smem(nv), s>>>(len, nv, V, ld, h, w, partial);
+                        double* partial, int grid, double* out_add, cudaStream_t s, int tile) {
+  if (cgs_tile(nv, tile) == 256)
+    k_cgs_db<1, 256><<<grid, 256, cgs_db_smem(nv, 256), s>>>(len, nv, V, ld, h, w, partial);
+  else
+    k_cgs_db<1, 128><<<grid, 256, cgs_db_smem(nv, 128), s>>>(len, nv, V, ld, h, w, partial);
   count_launch();
   (void)out_add;
 }

@@ -438,8 +438,8 @@ int pc_apply(seird_ctx* ctx, const double* r, double* z) {
 
 int spmv(seird_ctx* ctx, const double* x, double* y) {
   KTimer kt_(ctx, SEIRD_K_SPMV);
-  if (mixed(ctx)) launch_spmv<float>(ctx->hs.n, ctx->row_ptr, ctx->col, ctx->val32, x, y, ctx->stream);
-  else launch_spmv<double>(ctx->hs.n, ctx->row_ptr, ctx->col, ctx->val, x, y, ctx->stream);
+  if (mixed(ctx)) launch_spmv<float>(ctx->hs.n, ctx->row_ptr, ctx->col, ctx->val32, x, y, ctx->stream, ctx->spmv_tb);
+  else launch_spmv<double>(ctx->hs.n, ctx->row_ptr, ctx->col, ctx->val, x, y, ctx->stream, ctx->spmv_tb);
   CK(cudaGetLastError());
   return SEIRD_OK;
 }
@@ -447,7 +447,7 @@ int spmv(seird_ctx* ctx, const double* x, double* y) {
 // y = J x with the FP32 matrix copy and FP32 x (mixed path)
 int spmv32(seird_ctx* ctx, const float* x, double* y) {
   KTimer kt_(ctx, SEIRD_K_SPMV);
-  launch_spmv32(ctx->hs.n, ctx->row_ptr, ctx->col, ctx->val32, x, y, ctx->stream);
+  launch_spmv32(ctx->hs.n, ctx->row_ptr, ctx->col, ctx->val32, x, y, ctx->stream, ctx->spmv_tb);
   CK(cudaGetLastError());
   return SEIRD_OK;
 }
@@ -471,6 +471,70 @@ int norm2(seird_ctx* ctx, const double* x, double* out) {
 // Stops on ||r|| <= max(rtol ||b||, atol); dtol divergence and non-finite
 // estimates are errors; hitting the iteration limit returns SEIRD_OK with
 // *converged = false (Newton then takes the inexact step).
+bool verbose();
+
+// Launch-shape autotuner (options.autotune): times the candidates on the context's own
+// vectors (V[0] holds the first Krylov vector; the Gram-Schmidt candidates run at depth 8
+// with V[1..7] set to copies of it, which GMRES overwrites later) and keeps the fastest.
+int autotune(seird_ctx* ctx) {
+  ctx->tuned = true;
+  const int64_t len = vlen(ctx);
+  const cudaStream_t s = ctx->stream;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  auto best_of = [&](auto&& launch) {
+    float best = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(e0, s);
+      launch();
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      best = std::min(best, ms);
+    }
+    return best;
+  };
+  float tbest = 1e30f;
+  for (int tb : {128, 256, 512}) {
+    const float t = best_of([&] {
+      if (mixed(ctx)) launch_spmv32(ctx->hs.n, ctx->row_ptr, ctx->col, ctx->val32, ctx->Z32, ctx->tune_buf, s, tb);
+      else launch_spmv<double>(ctx->hs.n, ctx->row_ptr, ctx->col, ctx->val, ctx->V, ctx->tune_buf, s, tb);
+    });
+    if (t < tbest) {
+      tbest = t;
+      ctx->spmv_tb = tb;
+    }
+  }
+  const int nv = 8;
+  for (int k = 1; k < nv; ++k)
+    CK(cudaMemcpyAsync(ctx->V + (int64_t)k * len, ctx->V, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(ctx->tune_buf, ctx->V, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
+  tbest = 1e30f;
+  for (int per_sm : {2, 3, 4, 6}) {
+    const int grid = per_sm * ctx->sms;
+    for (int tile : {128, 256}) {
+      const float t = best_of([&] {
+        launch_mdot(len, nv, ctx->V, len, ctx->tune_buf, ctx->partial, grid, ctx->hcol, s, tile);
+        launch_update_norm(len, nv, ctx->V, len, ctx->hcol, ctx->tune_buf, ctx->partial, grid, ctx->scal + 7, s);
+      });
+      if (t < tbest) {
+        tbest = t;
+        ctx->red_grid = grid;
+        ctx->cgs_tile = tile;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CK(cudaGetLastError());
+  if (verbose())
+    std::fprintf(stderr, "[seird] autotune: spmv %d threads, gram-schmidt %d CTAs, tile %d\n", ctx->spmv_tb,
+                 ctx->red_grid, ctx->cgs_tile);
+  return SEIRD_OK;
+}
+
 int gmres(seird_ctx* ctx, const double* b, double* x, double rtol, int* its_out, bool* converged) {
   const int64_t len = vlen(ctx);
   const int m = ctx->opt.gmres_restart;
@@ -498,6 +562,7 @@ int gmres(seird_ctx* ctx, const double* b, double* x, double rtol, int* its_out,
   if (one_pass) CK(cudaMemsetAsync(h2, 0, sizeof(double) * NV_STRIDE, s));  // no second-pass coefficients
   while (true) {
     launch_axpby(len, 1.0 / rnorm, r, 0.0, r, ctx->V, s);
+    if (ctx->opt.autotune && !ctx->tuned) TRY(autotune(ctx));
     g0.assign(ldh, 0.0);
     g0[0] = rnorm;
     CK(cudaMemcpyAsync(gbuf, g0.data(), sizeof(double) * ldh, cudaMemcpyHostToDevice, s));
@@ -516,11 +581,12 @@ int gmres(seird_ctx* ctx, const double* b, double* x, double rtol, int* its_out,
       }
       {
         KTimer kt_(ctx, SEIRD_K_KRYLOV);
-        launch_mdot(len, j + 1, ctx->V, len, ctx->w, ctx->partial, ctx->red_grid, h1, s);
+        launch_mdot(len, j + 1, ctx->V, len, ctx->w, ctx->partial, ctx->red_grid, h1, s, ctx->cgs_tile);
         if (one_pass) {
           launch_update_norm(len, j + 1, ctx->V, len, h1, ctx->w, ctx->partial, ctx->red_grid, ctx->scal + 5, s);
         } else {
-          launch_update_mdot(len, j + 1, ctx->V, len, h1, ctx->w, ctx->partial, ctx->red_grid, nullptr, s);
+          launch_update_mdot(len, j + 1, ctx->V, len, h1, ctx->w, ctx->partial, ctx->red_grid, nullptr, s,
+                             ctx->cgs_tile);
           launch_reduce_cols(ctx->red_grid, j + 1, ctx->partial, h2, 0, s);
           launch_update_norm(len, j + 1, ctx->V, len, h2, ctx->w, ctx->partial, ctx->red_grid, ctx->scal + 5, s);
         }
@@ -671,7 +737,19 @@ int newton_step(seird_ctx* ctx, seird_stats* st) {
   CK(cudaMemcpyAsync(ctx->Un, ctx->U, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
   auto t0 = clk::now();
   double f;
-  int rc = residual(ctx, ctx->U, ctx->Un, ctx->F, &f);
+  int rc = SEIRD_OK;
+  if (ctx->have_prev && ctx->Flast && !ctx->sched_on) {
+    // F(u^n; u^n) = F(u^n; u^{n-1}) - M (u^n - u^{n-1}): the previous step's last residual
+    // minus a mass product (same rates, same dt), instead of a full assembly
+    launch_axpby(len, 1.0, ctx->Un, -1.0, ctx->Uprev, ctx->Ut, s);
+    launch_mass(ctx->hs.n, ctx->hs.m, ctx->tri, ctx->xy, ctx->Ut, ctx->elem, ctx->node_inc_ptr, ctx->node_inc,
+                ctx->F, ctx->partial, ctx->scal + 6, s);
+    launch_axpby(len, 1.0, ctx->Flast, -1.0, ctx->F, ctx->F, s);
+    CK(cudaGetLastError());
+    TRY(norm2(ctx, ctx->F, &f));
+  } else {
+    rc = residual(ctx, ctx->U, ctx->Un, ctx->F, &f);
+  }
   S.ms_assemble += ms_since(t0);
   if (rc) return rc;
   const double f0 = f;  // the stopping test is relative to ||F(u^n)||
@@ -784,6 +862,7 @@ int newton_step(seird_ctx* ctx, seird_stats* st) {
   ctx->pc_age_steps++;
   if (ctx->Uprev) {
     CK(cudaMemcpyAsync(ctx->Uprev, ctx->Un, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(ctx->Flast, ctx->F, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
     ctx->have_prev = true;
   }
   S.ms_total = ms_since(t_begin);
@@ -904,6 +983,7 @@ int adjoint_impl(seird_ctx* ctx, const seird_misfit* sp, double* jout, double* g
   const int nobs = sp->n_obs_nodes;
   // forward run: checkpoints and misfit
   for (int k = 1; k <= N; ++k) {
+    ctx->have_prev = false;  // no step history: every step starts from its own u^n
     int rc = newton_step(ctx, nullptr);
     if (rc) return restore(rc);
     if (k % C == 0) CK(cudaMemcpyAsync(ckpt + (size_t)(k / C) * len, ctx->U, sizeof(double) * len,
@@ -921,6 +1001,7 @@ int adjoint_impl(seird_ctx* ctx, const seird_misfit* sp, double* jout, double* g
     CK(cudaMemcpyAsync(ctx->U, ckpt + (size_t)sgi * len, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(seg, ctx->U, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
     for (int k = k0 + 1; k <= k1; ++k) {
+      ctx->have_prev = false;
       int rc = newton_step(ctx, nullptr);
       if (rc) return restore(rc);
       CK(cudaMemcpyAsync(seg + (size_t)(k - k0) * len, ctx->U, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
@@ -1041,7 +1122,7 @@ static int create_impl(seird_ctx* ctx, const seird_mesh* mesh, const seird_param
       (o.quadrature != 0 && o.quadrature != 1) || (o.precision != 0 && o.precision != 1) ||
       (o.gmres_forcing != 0 && o.gmres_forcing != 1) || (o.nonlinear != 0 && o.nonlinear != 1) ||
       (o.gmres_one_pass != 0 && o.gmres_one_pass != 1) || o.pc_keep_steps < 0 ||
-      (o.predictor != 0 && o.predictor != 1) ||
+      (o.predictor != 0 && o.predictor != 1) || (o.autotune != 0 && o.autotune != 1) ||
       !(o.picard_tol >= 0))
     return fail(ctx, SEIRD_EINVAL, "invalid option value");
   std::string err;
@@ -1063,7 +1144,8 @@ static int create_impl(seird_ctx* ctx, const seird_mesh* mesh, const seird_param
   int dev = 0, sms = 0;
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  ctx->red_grid = std::max(1, sms) * 3;
+  ctx->sms = std::max(1, sms);
+  ctx->red_grid = ctx->sms * 3;
   const int64_t n = hs.n, m = hs.m, len = 5 * n;
   const int64_t nnzb = (int64_t)hs.col.size();
   const int R = o.gmres_restart;
@@ -1088,7 +1170,10 @@ static int create_impl(seird_ctx* ctx, const seird_mesh* mesh, const seird_param
   TRY(dalloc(ctx, &ctx->rec, (size_t)REC * m));
   double** vecs[] = {&ctx->U, &ctx->Un, &ctx->F, &ctx->Ft, &ctx->dU, &ctx->Ut, &ctx->stage, &ctx->stage2, &ctx->w};
   for (double** v : vecs) TRY(dalloc(ctx, v, len));
-  if (o.predictor == 1) TRY(dalloc(ctx, &ctx->Uprev, len));
+  if (o.predictor == 1) {
+    TRY(dalloc(ctx, &ctx->Uprev, len));
+    TRY(dalloc(ctx, &ctx->Flast, len));
+  }
   const bool mix = o.precision == 1;
   TRY(dalloc(ctx, &ctx->V, (size_t)(R + 1) * len));
   if (mix) {
@@ -1097,7 +1182,8 @@ static int create_impl(seird_ctx* ctx, const seird_mesh* mesh, const seird_param
   } else {
     TRY(dalloc(ctx, &ctx->Z, (size_t)R * len));
   }
-  const int64_t npart = std::max<int64_t>((int64_t)ctx->red_grid * NV_STRIDE, (n + 255) / 256);
+  const int64_t npart = std::max<int64_t>((int64_t)ctx->sms * 6 * NV_STRIDE, (n + 255) / 256);  // up to 6 CTAs/SM
+  if (o.autotune) TRY(dalloc(ctx, &ctx->tune_buf, len));
   TRY(dalloc(ctx, &ctx->partial, npart));
   TRY(dalloc(ctx, &ctx->hcol, 2 * NV_STRIDE));
   TRY(dalloc(ctx, &ctx->gm, (size_t)(R + 1) * R + 2 * R + (R + 1) + R));
@@ -1313,6 +1399,7 @@ int seird_run(seird_ctx* ctx, int32_t n_steps, seird_stats* per_step) {
 int seird_set_params(seird_ctx* ctx, const seird_params* params) {
   if (!ctx || !params) return fail(ctx, SEIRD_EINVAL, "NULL argument");
   if (ctx->rtab) return fail(ctx, SEIRD_EINVAL, "set_params: an ensemble's rates are fixed at creation");
+  ctx->have_prev = false;  // the previous step's residual belongs to the old rates
   ctx->params = *params;
   ctx->params.beta_field = nullptr;
   if (params->beta_field) {
@@ -1329,6 +1416,7 @@ int seird_set_params(seird_ctx* ctx, const seird_params* params) {
 int seird_set_beta_schedule(seird_ctx* ctx, const seird_beta_schedule* sched) {
   if (!ctx) return fail(ctx, SEIRD_EINVAL, "NULL context");
   if (ctx->rtab) return fail(ctx, SEIRD_EINVAL, "beta schedule: not available on an ensemble");
+  ctx->have_prev = false;
   if (!sched) {
     ctx->sched_on = false;
     ctx->pc_ready = false;
@@ -1367,6 +1455,9 @@ int seird_get_info(const seird_ctx* ctx, seird_info* info) {
   info->coarse_band = ctx->hs.cband;
   info->device_bytes = ctx->device_bytes;
   info->coarse_units = ctx->hs.Pc;
+  info->spmv_threads = ctx->spmv_tb;
+  info->cgs_ctas = ctx->red_grid;
+  info->cgs_tile = ctx->cgs_tile;
   return SEIRD_OK;
 }
 

@@ -50,7 +50,7 @@ class Options(C.Structure):
                 ("pc_lag", C.c_int32), ("owner", _ip), ("seed", C.c_uint64), ("stream", C.c_void_p),
                 ("timing", C.c_int32), ("gmres_forcing", C.c_int32), ("nonlinear", C.c_int32),
                 ("gmres_one_pass", C.c_int32), ("picard_tol", C.c_double), ("pc_keep_steps", C.c_int32),
-                ("coarse_group", C.c_int32), ("predictor", C.c_int32)]
+                ("coarse_group", C.c_int32), ("predictor", C.c_int32), ("autotune", C.c_int32)]
 
 
 class BetaSchedule(C.Structure):
@@ -88,7 +88,8 @@ PARAM_NAMES = ("beta_i", "beta_e", "sigma", "gamma_e", "gamma_r", "gamma_d", "nu
 class Info(C.Structure):
     _fields_ = [("n_nodes", C.c_int64), ("n_tris", C.c_int64), ("nnzb", C.c_int64), ("n_subdomains", C.c_int32),
                 ("subdomain_rows", C.c_int64), ("subdomain_blocks", C.c_int64), ("max_levels", C.c_int32),
-                ("coarse_band", C.c_int32), ("device_bytes", C.c_int64), ("coarse_units", C.c_int32)]
+                ("coarse_band", C.c_int32), ("device_bytes", C.c_int64), ("coarse_units", C.c_int32),
+                ("spmv_threads", C.c_int32), ("cgs_ctas", C.c_int32), ("cgs_tile", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

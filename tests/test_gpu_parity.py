@@ -428,3 +428,20 @@ def test_extrapolation_predictor_reaches_the_same_roots():
     assert max(rel_l2_per_comp(got, U_ref)) <= 1e-9
     # from the second step on the first iterate is the extrapolation, closer to the root
     assert sum(s["newton_its"] for s in stats[1:]) <= 3 * max(s["newton_its"] for s in stats[:1]), stats
+
+
+def test_autotuned_launch_shapes():
+    """options.autotune picks the SpMV and Gram-Schmidt launch shapes by timing them on
+    the context's vectors; the roots are those of the fixed shapes."""
+    wl = WL["irregular3k"]
+    U_ref, _ = O.run(wl.xy, wl.tri, wl.params, wl.dt, wl.U0, 3, rtol=1e-12, atol=newton_floor(wl),
+                     bfield=wl.beta_field)
+    for precision in (0, 1):
+        with solver(wl, coarse=1, autotune=1, precision=precision) as sv:
+            sv.set_state(wl.U0)
+            sv.run(3)
+            got = sv.get_state()
+            inf = sv.info()
+        assert inf["spmv_threads"] in (128, 256, 512) and inf["cgs_tile"] in (128, 256), inf
+        assert inf["cgs_ctas"] > 0
+        assert max(rel_l2_per_comp(got, U_ref)) <= (1e-9 if precision == 0 else 1e-6), precision
