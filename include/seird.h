@@ -148,6 +148,13 @@ typedef struct {
                              fastest; the choice is reported by seird_get_info.  The Gram-Schmidt shape
                              sets the order of its sums, so results are reproducible for a given choice,
                              not across choices.  0: fixed shapes (256 threads, 3 CTAs per SM, 256) (0) */
+  int32_t graph;          /* 1: each GMRES restart cycle runs as one replay of a CUDA graph captured at
+                             the first solve: iteration j is a conditional node that the Givens kernel
+                             of iteration j - 1 arms while the residual estimate is above the
+                             tolerance, so the host reads the outcome once per cycle instead of once
+                             per iteration.  Same kernels and arithmetic as 0 (results identical).
+                             Needs a driver with conditional graph nodes (CUDA 12.4+); ignored while
+                             timing = 1 and in the adjoint's transposed solves (0) */
 } seird_options;
 
 /* Kernel classes of seird_stats.kernel_ms / kernel_calls. */

@@ -246,6 +246,13 @@ struct seird_ctx {
   int spmv_tb = 256, cgs_tile = 0, sms = 1;
   bool tuned = false;
   double* tune_buf = nullptr;
+  // GMRES restart cycle captured into a CUDA graph (options.graph)
+  cudaGraphExec_t cycle_exec = nullptr;
+  int cycle_m = 0;
+  std::vector<int64_t> cycle_launches;  // kernels of the first j captured iterations, j <= m
+  int* cyc_ctl = nullptr;              // device [4]: iterations run, limit, outcome
+  int* h_cyc = nullptr;                // pinned [8]: [0, 4) uploaded, [4, 8) read back
+  bool eager_cycles = false;           // while the adjoint has J^T swapped in
   int32_t pc_age_steps = 0;  // time steps completed since the preconditioner was built
   bool jac_ready = false;
   // kernel-class timing (options.timing): (class, start event, end event) per launch group

@@ -88,8 +88,16 @@ void launch_scale(int64_t len, const double* x, const double* alpha_ptr, int inv
 void launch_axpby(int64_t len, double a, const double* x, double b, const double* y, double* out, cudaStream_t s);
 void launch_multi_axpy(int64_t len, int nv, const double* Zs, int64_t ld, const double* coef, double* x,
                        cudaStream_t s);
+// Convergence control of a GMRES restart cycle captured into a CUDA graph (see k_givens);
+// all zero outside captures.
+struct CycleCtl {
+  int* ctl = nullptr;
+  const double* tol = nullptr;
+  cudaGraphConditionalHandle next = 0;
+  int has_next = 0;
+};
 void launch_givens(int j, double* gm, const double* h1, const double* h2, const double* hnext, int ldh,
-                   double* out_res, cudaStream_t s);
+                   double* out_res, cudaStream_t s, const CycleCtl& cc = CycleCtl());
 void launch_reduce_cols(int grid, int nv, const double* partial, double* out, int add, cudaStream_t s);
 void cgs_init();
 constexpr int NV_STRIDE = 65;  // row stride of the CGS partial-sum buffer

@@ -290,8 +290,13 @@ __global__ void k_multi_axpy(int64_t len, int nv, const double* __restrict__ Z, 
 //   H[ldh*restart] column-major (H[row + ldh*col]), cs[restart], sn[restart], g[ldh], y[restart]
 // Column j of H gets hcol[0..j] and hnext; previous rotations are applied, a new
 // rotation annihilates H[j+1, j]; |g[j+1]| (the residual norm) goes to *out_res.
+// In a captured restart cycle (cc.ctl != NULL) the kernel also takes the convergence
+// decision of the iteration: cc.ctl[0] = iterations run, cc.ctl[2] = outcome (0 go on,
+// 1 converged or breakdown, 2 past dtol or not finite), cc.ctl[1] = iteration limit of
+// the cycle; cc.tol = {tolerance, dtol * ||b||}.  It arms the conditional node of the
+// next iteration (cc.next) only while the outcome is 0 and the limit is not reached.
 __global__ void k_givens(int j, double* gm, const double* __restrict__ h1, const double* __restrict__ h2,
-                         const double* __restrict__ hnext_sq, int ldh, double* out_res) {
+                         const double* __restrict__ hnext_sq, int ldh, double* out_res, CycleCtl cc) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const int restart = ldh - 1;
   double* H = gm;
@@ -324,6 +329,15 @@ __global__ void k_givens(int j, double* gm, const double* __restrict__ h1, const
   g[j + 1] = -s * gj;
   out_res[0] = fabs(g[j + 1]);
   out_res[1] = hn;
+  if (cc.ctl) {
+    const double res = fabs(g[j + 1]);
+    int outcome = 0;
+    if (!(res <= cc.tol[1]) || !isfinite(res)) outcome = 2;
+    else if (res <= cc.tol[0] || hn == 0.0) outcome = 1;
+    cc.ctl[0] = j + 1;
+    cc.ctl[2] = outcome;
+    if (cc.has_next) cudaGraphSetConditional(cc.next, (outcome == 0 && j + 1 < cc.ctl[1]) ? 1u : 0u);
+  }
 }
 
 // y = H(0:k,0:k)^{-1} g(0:k) by back substitution (one thread)
@@ -489,8 +503,8 @@ void launch_multi_axpy(int64_t len, int nv, const double* Zs, int64_t ld, const 
 }
 
 void launch_givens(int j, double* gm, const double* h1, const double* h2, const double* hnext, int ldh,
-                   double* out_res, cudaStream_t s) {
-  k_givens<<<1, 32, 0, s>>>(j, gm, h1, h2, hnext, ldh, out_res);
+                   double* out_res, cudaStream_t s, const CycleCtl& cc) {
+  k_givens<<<1, 32, 0, s>>>(j, gm, h1, h2, hnext, ldh, out_res, cc);
   count_launch();
 }
 

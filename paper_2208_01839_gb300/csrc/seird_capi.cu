@@ -535,12 +535,108 @@ int autotune(seird_ctx* ctx) {
   return SEIRD_OK;
 }
 
+// Arnoldi iteration j of the FGMRES cycle: z_j = M^{-1} v_j, w = J z_j, Gram-Schmidt of w
+// against v_0..v_j, Givens update of H and g, v_{j+1} = w / ||w||.  Device work only, so
+// that a restart cycle can be captured into a CUDA graph.
+static int arnoldi_iteration(seird_ctx* ctx, int j, const CycleCtl& cc) {
+  const int64_t len = vlen(ctx);
+  const int ldh = ctx->opt.gmres_restart + 1;
+  const cudaStream_t s = ctx->stream;
+  double* h1 = ctx->hcol;
+  double* h2 = ctx->hcol + NV_STRIDE;
+  double* Vj = ctx->V + (int64_t)j * len;
+  if (mixed(ctx)) {  // FP32 preconditioner and operator inside the FP64 FGMRES
+    float* Zj = ctx->Z32 + (int64_t)j * len;
+    TRY(pc_apply32(ctx, Vj, Zj));
+    TRY(spmv32(ctx, Zj, ctx->w));
+  } else {
+    double* Zj = ctx->Z + (int64_t)j * len;
+    TRY(pc_apply(ctx, Vj, Zj));
+    TRY(spmv(ctx, Zj, ctx->w));
+  }
+  KTimer kt_(ctx, SEIRD_K_KRYLOV);
+  launch_mdot(len, j + 1, ctx->V, len, ctx->w, ctx->partial, ctx->red_grid, h1, s, ctx->cgs_tile);
+  if (ctx->opt.gmres_one_pass == 1) {
+    launch_update_norm(len, j + 1, ctx->V, len, h1, ctx->w, ctx->partial, ctx->red_grid, ctx->scal + 5, s);
+  } else {
+    launch_update_mdot(len, j + 1, ctx->V, len, h1, ctx->w, ctx->partial, ctx->red_grid, nullptr, s,
+                       ctx->cgs_tile);
+    launch_reduce_cols(ctx->red_grid, j + 1, ctx->partial, h2, 0, s);
+    launch_update_norm(len, j + 1, ctx->V, len, h2, ctx->w, ctx->partial, ctx->red_grid, ctx->scal + 5, s);
+  }
+  launch_givens(j, ctx->gm, h1, h2, ctx->scal + 5, ldh, ctx->scal + 2, s, cc);
+  launch_scale(len, ctx->w, ctx->scal + 3, 1, ctx->V + (int64_t)(j + 1) * len, s);
+  CK(cudaGetLastError());
+  return SEIRD_OK;
+}
+
+// Captures one restart cycle (options.graph): Arnoldi iteration j is the body of a
+// conditional IF node, the nodes in sequence; iteration 0's condition defaults to 1 at
+// every launch, the others to 0, and the Givens kernel of iteration j sets that of j + 1
+// (k_givens).  A replay thus runs iterations until convergence, dtol or the cycle's limit
+// (ctl[1]) with no host round trip, and skipped iterations launch nothing.  The graph
+// bakes in the Krylov, preconditioner and matrix buffers and the launch shapes, which are
+// fixed once the autotuner has run.
+static int build_cycle_graph(seird_ctx* ctx) {
+  const int m = ctx->opt.gmres_restart;
+  cudaStream_t cs = nullptr;
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  std::vector<cudaGraphConditionalHandle> hnd(m);
+  for (int j = 0; j < m && e == cudaSuccess; ++j)
+    e = cudaGraphConditionalHandleCreate(&hnd[j], g, j == 0 ? 1u : 0u, cudaGraphCondAssignDefault);
+  const cudaStream_t saved = ctx->stream;
+  ctx->stream = cs;  // the launchers capture on the context's stream
+  int rc = SEIRD_OK;
+  std::vector<int64_t> launches(1, 0);
+  cudaGraphNode_t prev = nullptr;
+  for (int j = 0; j < m && e == cudaSuccess && rc == SEIRD_OK; ++j) {
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = hnd[j];
+    np.conditional.type = cudaGraphCondTypeIf;
+    np.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    e = cudaGraphAddNode(&node, g, prev ? &prev : nullptr, nullptr, prev ? 1 : 0, &np);
+    if (e != cudaSuccess) break;
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) break;
+    CycleCtl cc;
+    cc.ctl = ctx->cyc_ctl;
+    cc.tol = ctx->scal + 10;
+    cc.has_next = j + 1 < m;
+    cc.next = cc.has_next ? hnd[j + 1] : 0;
+    const int64_t k0 = launch_total();
+    rc = arnoldi_iteration(ctx, j, cc);
+    launches.push_back(launches.back() + launch_total() - k0);
+    count_launches(k0 - launch_total());  // captured, not run
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &body);
+    if (e == cudaSuccess) e = e2;
+    prev = node;
+  }
+  ctx->stream = saved;
+  if (e == cudaSuccess && rc == SEIRD_OK) e = cudaGraphInstantiate(&ctx->cycle_exec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(cs);
+  if (rc) return rc;
+  if (e != cudaSuccess) {
+    ctx->cycle_exec = nullptr;
+    cudaGetLastError();
+    return fail(ctx, SEIRD_ECUDA, std::string("gmres: capture of the restart cycle failed: ") +
+                                       cudaGetErrorString(e));
+  }
+  ctx->cycle_m = m;
+  ctx->cycle_launches = launches;
+  return SEIRD_OK;
+}
+
 int gmres(seird_ctx* ctx, const double* b, double* x, double rtol, int* its_out, bool* converged) {
   const int64_t len = vlen(ctx);
   const int m = ctx->opt.gmres_restart;
   const int ldh = m + 1;
   const cudaStream_t s = ctx->stream;
-  double* h1 = ctx->hcol;
   double* h2 = ctx->hcol + NV_STRIDE;
   *its_out = 0;
   *converged = false;
@@ -558,8 +654,16 @@ int gmres(seird_ctx* ctx, const double* b, double* x, double rtol, int* its_out,
   int its = 0;
   std::vector<double> g0(ldh, 0.0);
   double* gbuf = ctx->gm + (int64_t)ldh * m + 2 * m;  // g inside the GMRES small state
-  const bool one_pass = ctx->opt.gmres_one_pass == 1;
-  if (one_pass) CK(cudaMemsetAsync(h2, 0, sizeof(double) * NV_STRIDE, s));  // no second-pass coefficients
+  if (ctx->opt.gmres_one_pass == 1)
+    CK(cudaMemsetAsync(h2, 0, sizeof(double) * NV_STRIDE, s));  // no second-pass coefficients
+  // captured cycles: not under per-kernel timing (events cannot sit in conditional bodies)
+  // nor while the adjoint has J^T swapped in
+  const bool graph = ctx->opt.graph == 1 && !ctx->opt.timing && !ctx->eager_cycles;
+  if (graph) {  // the cycle's tolerances, read by k_givens
+    ctx->h_scal[10] = tol;
+    ctx->h_scal[11] = ctx->opt.gmres_dtol * bnorm;
+    CK(cudaMemcpyAsync(ctx->scal + 10, ctx->h_scal + 10, 2 * sizeof(double), cudaMemcpyHostToDevice, s));
+  }
   while (true) {
     launch_axpby(len, 1.0 / rnorm, r, 0.0, r, ctx->V, s);
     if (ctx->opt.autotune && !ctx->tuned) TRY(autotune(ctx));
@@ -568,43 +672,42 @@ int gmres(seird_ctx* ctx, const double* b, double* x, double rtol, int* its_out,
     CK(cudaMemcpyAsync(gbuf, g0.data(), sizeof(double) * ldh, cudaMemcpyHostToDevice, s));
     int k = 0;
     bool done = false;
-    for (int j = 0; j < m; ++j) {
-      double* Vj = ctx->V + (int64_t)j * len;
-      if (mixed(ctx)) {  // FP32 preconditioner and operator inside the FP64 FGMRES
-        float* Zj = ctx->Z32 + (int64_t)j * len;
-        TRY(pc_apply32(ctx, Vj, Zj));
-        TRY(spmv32(ctx, Zj, ctx->w));
-      } else {
-        double* Zj = ctx->Z + (int64_t)j * len;
-        TRY(pc_apply(ctx, Vj, Zj));
-        TRY(spmv(ctx, Zj, ctx->w));
-      }
-      {
-        KTimer kt_(ctx, SEIRD_K_KRYLOV);
-        launch_mdot(len, j + 1, ctx->V, len, ctx->w, ctx->partial, ctx->red_grid, h1, s, ctx->cgs_tile);
-        if (one_pass) {
-          launch_update_norm(len, j + 1, ctx->V, len, h1, ctx->w, ctx->partial, ctx->red_grid, ctx->scal + 5, s);
-        } else {
-          launch_update_mdot(len, j + 1, ctx->V, len, h1, ctx->w, ctx->partial, ctx->red_grid, nullptr, s,
-                             ctx->cgs_tile);
-          launch_reduce_cols(ctx->red_grid, j + 1, ctx->partial, h2, 0, s);
-          launch_update_norm(len, j + 1, ctx->V, len, h2, ctx->w, ctx->partial, ctx->red_grid, ctx->scal + 5, s);
-        }
-        launch_givens(j, ctx->gm, h1, h2, ctx->scal + 5, ldh, ctx->scal + 2, s);
-        launch_scale(len, ctx->w, ctx->scal + 3, 1, ctx->V + (int64_t)(j + 1) * len, s);
-      }
-      CK(cudaGetLastError());
+    if (graph) {
+      if (!ctx->cycle_exec || ctx->cycle_m != m) TRY(build_cycle_graph(ctx));
+      int* hin = ctx->h_cyc;
+      int* hout = ctx->h_cyc + 4;
+      hin[0] = 0;
+      hin[1] = std::min(m, ctx->opt.gmres_maxit - its);
+      hin[2] = 0;
+      hin[3] = 0;
+      CK(cudaMemcpyAsync(ctx->cyc_ctl, hin, 4 * sizeof(int), cudaMemcpyHostToDevice, s));
+      CK(cudaGraphLaunch(ctx->cycle_exec, s));
+      CK(cudaMemcpyAsync(hout, ctx->cyc_ctl, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
       TRY(read_scalars(ctx, 2, 2));
-      ++its;
-      k = j + 1;
-      const double res = ctx->h_scal[2], hn = ctx->h_scal[3];
-      if (!std::isfinite(res)) return fail(ctx, SEIRD_ENONFINITE, "gmres: non-finite residual estimate");
-      if (res > ctx->opt.gmres_dtol * bnorm) return fail(ctx, SEIRD_EGMRES, "gmres: diverged (dtol)");
-      if (res <= tol || hn == 0.0) {
-        done = true;
-        break;
+      k = hout[0];
+      its += k;
+      if (k < 1 || k > m) return fail(ctx, SEIRD_ECUDA, "gmres: captured cycle reported no iterations");
+      count_launches(ctx->cycle_launches[k]);
+      if (hout[2] == 2) {
+        if (!std::isfinite(ctx->h_scal[2])) return fail(ctx, SEIRD_ENONFINITE, "gmres: non-finite residual estimate");
+        return fail(ctx, SEIRD_EGMRES, "gmres: diverged (dtol)");
       }
-      if (its >= ctx->opt.gmres_maxit) break;
+      done = hout[2] == 1;
+    } else {
+      for (int j = 0; j < m; ++j) {
+        TRY(arnoldi_iteration(ctx, j, CycleCtl()));
+        TRY(read_scalars(ctx, 2, 2));
+        ++its;
+        k = j + 1;
+        const double res = ctx->h_scal[2], hn = ctx->h_scal[3];
+        if (!std::isfinite(res)) return fail(ctx, SEIRD_ENONFINITE, "gmres: non-finite residual estimate");
+        if (res > ctx->opt.gmres_dtol * bnorm) return fail(ctx, SEIRD_EGMRES, "gmres: diverged (dtol)");
+        if (res <= tol || hn == 0.0) {
+          done = true;
+          break;
+        }
+        if (its >= ctx->opt.gmres_maxit) break;
+      }
     }
     launch_hsolve(k, ctx->gm, ldh, s);
     if (mixed(ctx)) launch_multi_axpy32(len, k, ctx->Z32, len, gbuf + ldh, x, s);
@@ -1020,10 +1123,12 @@ int adjoint_impl(seird_ctx* ctx, const seird_misfit* sp, double* jout, double* g
       if (rc) return restore(rc);
       launch_bsr_transpose(nnzb, ctx->tpos, ctx->val, valT, s);
       std::swap(ctx->val, valT);
+      ctx->eager_cycles = true;  // a captured cycle holds the pointer of J, not of J^T
       rc = pc_setup(ctx);
       int lits = 0;
       bool conv = false;
       if (!rc) rc = gmres(ctx, rhs, lam, rtol, &lits, &conv);
+      ctx->eager_cycles = false;
       std::swap(ctx->val, valT);
       ctx->pc_ready = false;  // the factors belong to J^T
       if (rc) return restore(rc);
@@ -1108,8 +1213,10 @@ void seird_destroy(seird_ctx* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   for (cudaEvent_t e : ctx->evpool) cudaEventDestroy(e);
   if (ctx->coarse_graph) cudaGraphExecDestroy(ctx->coarse_graph);
+  if (ctx->cycle_exec) cudaGraphExecDestroy(ctx->cycle_exec);
   for (void* p : ctx->allocations) cudaFree(p);
   if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
+  if (ctx->h_cyc) cudaFreeHost(ctx->h_cyc);
   if (ctx->h_err) cudaFreeHost(ctx->h_err);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
@@ -1122,7 +1229,7 @@ static int create_impl(seird_ctx* ctx, const seird_mesh* mesh, const seird_param
       (o.quadrature != 0 && o.quadrature != 1) || (o.precision != 0 && o.precision != 1) ||
       (o.gmres_forcing != 0 && o.gmres_forcing != 1) || (o.nonlinear != 0 && o.nonlinear != 1) ||
       (o.gmres_one_pass != 0 && o.gmres_one_pass != 1) || o.pc_keep_steps < 0 ||
-      (o.predictor != 0 && o.predictor != 1) || (o.autotune != 0 && o.autotune != 1) ||
+      (o.predictor != 0 && o.predictor != 1) || (o.autotune != 0 && o.autotune != 1) || (o.graph != 0 && o.graph != 1) ||
       !(o.picard_tol >= 0))
     return fail(ctx, SEIRD_EINVAL, "invalid option value");
   std::string err;
@@ -1193,6 +1300,10 @@ static int create_impl(seird_ctx* ctx, const seird_mesh* mesh, const seird_param
   CK(cudaMemset(ctx->U, 0, sizeof(double) * len));
   CK(cudaMemset(ctx->gm, 0, sizeof(double) * ((size_t)(R + 1) * R + 2 * R + (R + 1) + R)));
   CK(cudaMallocHost((void**)&ctx->h_scal, sizeof(double) * 16));
+  if (o.graph) {
+    TRY(dalloc(ctx, &ctx->cyc_ctl, 4));
+    CK(cudaMallocHost((void**)&ctx->h_cyc, sizeof(int) * 8));
+  }
   CK(cudaMallocHost((void**)&ctx->h_err, sizeof(int32_t)));
   *ctx->h_err = 0;
   // RAS

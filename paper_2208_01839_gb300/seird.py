@@ -50,7 +50,8 @@ class Options(C.Structure):
                 ("pc_lag", C.c_int32), ("owner", _ip), ("seed", C.c_uint64), ("stream", C.c_void_p),
                 ("timing", C.c_int32), ("gmres_forcing", C.c_int32), ("nonlinear", C.c_int32),
                 ("gmres_one_pass", C.c_int32), ("picard_tol", C.c_double), ("pc_keep_steps", C.c_int32),
-                ("coarse_group", C.c_int32), ("predictor", C.c_int32), ("autotune", C.c_int32)]
+                ("coarse_group", C.c_int32), ("predictor", C.c_int32), ("autotune", C.c_int32),
+                ("graph", C.c_int32)]
 
 
 class BetaSchedule(C.Structure):
