@@ -21,6 +21,18 @@ __constant__ double cQL[2][7][3];
 __constant__ double cQW[2][7];
 // w_q phi_a phi_b at point q for the pairs (0,0) (1,1) (2,2) (0,1) (0,2) (1,2)
 __constant__ double cQC[2][7][6];
+// The degree-5 rule by its symmetry orbits: the centroid (weight W0) and two
+// three-point orbits o = 1, 2 whose point k has barycentric coordinate B_o at
+// vertex k and A_o at the other two (D_o = B_o - A_o, weight W_o).  A point value
+// of a P1 field x is then A_o sum(x) + D_o x_k, and sums over an orbit of
+// w_q phi_a phi_b f(q) reduce to the orbit sum of f and single point values:
+//   sum_k W L_a L_a f_k = W A^2 S + W (B^2 - A^2) f_a
+//   sum_k W L_a L_b f_k = W A B S - W A D f_c      (a != b, c the third vertex)
+//   sum_k W L_a f_k     = W A S + W D f_a.
+// cORB: [0..2] A1 D1 W1, [3..5] A2 D2 W2, [6] W0, [7] W0/3, [8] W1 A1, [9] W2 A2,
+// [10] W1 D1, [11] W2 D2, [12] W0/9, [13] W1 A1^2, [14] W1 (B1^2 - A1^2), [15] W1 A1 B1,
+// [16] -W1 A1 D1, [17..20] the same for orbit 2.
+__constant__ double cORB[21];
 
 void upload_quadrature() {
   double L[2][7][3] = {};
@@ -48,6 +60,16 @@ void upload_quadrature() {
   cudaMemcpyToSymbol(cQL, L, sizeof(L));
   cudaMemcpyToSymbol(cQW, W, sizeof(W));
   cudaMemcpyToSymbol(cQC, Cw, sizeof(Cw));
+  // orbit form of the same table: point 1 + k (4 + k) has its larger (smaller) coordinate at vertex k
+  double O[21];
+  const double A1 = L[0][1][1], B1 = L[0][1][0], A2 = L[0][4][1], B2 = L[0][4][0];
+  const double W0 = W[0][0], W1 = W[0][1], W2 = W[0][4];
+  const double D1 = B1 - A1, D2 = B2 - A2;
+  const double orb[21] = {A1, D1, W1, A2, D2, W2, W0, W0 / 3.0, W1 * A1, W2 * A2, W1 * D1, W2 * D2, W0 / 9.0,
+                          W1 * A1 * A1, W1 * (B1 * B1 - A1 * A1), W1 * A1 * B1, -W1 * A1 * D1,
+                          W2 * A2 * A2, W2 * (B2 * B2 - A2 * A2), W2 * A2 * B2, -W2 * A2 * D2};
+  for (int k = 0; k < 21; ++k) O[k] = orb[k];
+  cudaMemcpyToSymbol(cORB, O, sizeof(O));
 }
 
 namespace {
@@ -83,7 +105,40 @@ struct TriT {
   int32_t v[3];
 };
 
+// x > 0 and not NaN, from the bits (integer pipe): 0 < bits <= bits(+inf)
+__device__ __forceinline__ bool positive(double x) {
+  return (unsigned long long)(__double_as_longlong(x) - 1) < 0x7FF0000000000000ull;
+}
+
+// 1/N at the seven points of the degree-5 rule with one division (Montgomery's
+// simultaneous inversion: prefix products, one reciprocal, back substitution).
+// The point values of a P1 field lie within a factor 1/min(A2, B2) < 17 of each
+// other, so when the full product is in [1e-280, 1e280] no prefix product left
+// the normal range; otherwise the points are divided one by one.
+__device__ __forceinline__ void reciprocals7(const double (&N)[7], double (&r)[7]) {
+  double pre[7];
+  pre[0] = N[0];
+#pragma unroll
+  for (int q = 1; q < 7; ++q) pre[q] = pre[q - 1] * N[q];
+  if (pre[6] >= 1e-280 && pre[6] <= 1e280) {
+    double inv = 1.0 / pre[6];
+#pragma unroll
+    for (int q = 6; q > 0; --q) {
+      r[q] = inv * pre[q - 1];
+      inv *= N[q];
+    }
+    r[0] = inv;
+  } else {
+#pragma unroll
+    for (int q = 0; q < 7; ++q) r[q] = 1.0 / N[q];
+  }
+}
+
 // Element residual: consistent mass, exact diffusion, quadrature of the reaction.
+// Degree-5 rule: the time difference and the linear reaction terms are one mass
+// product M (u - u^n - dt L u), L the linear part of Eq. seird1-5 (exact, the rule
+// integrates them exactly), and the transmission term goes through the rule's
+// orbit form (cORB).  Vertex rule: the linear reaction terms are lumped.
 template <int RULE, bool BF>
 __global__ void __launch_bounds__(128) k_residual_elem(int64_t m, const int32_t* __restrict__ tri,
                                                        const double* __restrict__ xy, const double* __restrict__ U,
@@ -94,26 +149,63 @@ __global__ void __launch_bounds__(128) k_residual_elem(int64_t m, const int32_t*
   if (t >= m) return;
   const Tri T = load_tri(tri, xy, t);
   const Rates r = rates_at(rin, T.v[0]);
-  double u[3][5], Fe[3][5];
-  double Nbar = 0.0;
+  double u[3][5], Fe[3][5], Nv[3];
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) u[a][c] = U[5 * (int64_t)T.v[a] + c];
+    Nv[a] = u[a][0] + u[a][1] + u[a][2] + u[a][3] + u[a][4];
+  }
+  const double SN = Nv[0] + Nv[1] + Nv[2];
+  const double Nbar = SN * (1.0 / 3.0);
+  const double m12 = T.area * (1.0 / 12.0);  // (phi_a, phi_b) = |T| (1 + delta_ab) / 12
+  if (RULE == 0) {
+    // w = u - u^n - dt L u at the vertices, then Fe = M w
+    const double kS = r.dt * r.alpha, mS = r.dt * r.mu, kE = r.dt * (r.sigma + r.ge + r.mu);
+    const double kIe = r.dt * r.sigma, kI = r.dt * (r.gr + r.gd + r.mu), kRe = r.dt * r.ge, kRi = r.dt * r.gr;
+    const double kD = r.dt * r.gd;
+    double w[3][5];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      double du[5];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) du[c] = u[a][c] - Un[5 * (int64_t)T.v[a] + c];
+      w[a][0] = du[0] - kS * Nv[a] + mS * u[a][0];
+      w[a][1] = du[1] + kE * u[a][1];
+      w[a][2] = du[2] - kIe * u[a][1] + kI * u[a][2];
+      w[a][3] = du[3] - kRe * u[a][1] - kRi * u[a][2] + mS * u[a][3];
+      w[a][4] = du[4] - kD * u[a][2];
+    }
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
-      u[a][c] = U[5 * (int64_t)T.v[a] + c];
-      Nbar += u[a][c];
+      const double sw = w[0][c] + w[1][c] + w[2][c];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) Fe[a][c] = m12 * (w[a][c] + sw);
     }
-  Nbar *= (1.0 / 3.0);
-  // consistent mass: (phi_a, phi_b) = |T| (1 + delta_ab) / 12
-  const double m12 = T.area * (1.0 / 12.0);
+  } else {
 #pragma unroll
-  for (int c = 0; c < 5; ++c) {
-    double du[3];
+    for (int c = 0; c < 5; ++c) {
+      double du[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) du[a] = u[a][c] - Un[5 * (int64_t)T.v[a] + c];
-    const double sdu = du[0] + du[1] + du[2];
+      for (int a = 0; a < 3; ++a) du[a] = u[a][c] - Un[5 * (int64_t)T.v[a] + c];
+      const double sdu = du[0] + du[1] + du[2];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) Fe[a][c] = m12 * (du[a] + sdu);
+      for (int a = 0; a < 3; ++a) Fe[a][c] = m12 * (du[a] + sdu);
+    }
+    // linear reaction terms, lumped: |T|/3 u_a
+    const double a3 = T.area / 3.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      double Mu[5];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) Mu[c] = a3 * u[a][c];
+      const double MN = Mu[0] + Mu[1] + Mu[2] + Mu[3] + Mu[4];
+      Fe[a][0] -= r.dt * (r.alpha * MN - r.mu * Mu[0]);
+      Fe[a][1] += r.dt * (r.sigma + r.ge + r.mu) * Mu[1];
+      Fe[a][2] -= r.dt * (r.sigma * Mu[1] - (r.gr + r.gd + r.mu) * Mu[2]);
+      Fe[a][3] -= r.dt * (r.ge * Mu[1] + r.gr * Mu[2] - r.mu * Mu[3]);
+      Fe[a][4] -= r.dt * r.gd * Mu[2];
+    }
   }
   // diffusion: dt nubar_c |T| mean_T(N) grad u_c . grad phi_a  (nubar_D = 0)
 #pragma unroll
@@ -124,55 +216,69 @@ __global__ void __launch_bounds__(128) k_residual_elem(int64_t m, const int32_t*
 #pragma unroll
     for (int a = 0; a < 3; ++a) Fe[a][c] += coef * (gux * T.gx[a] + guy * T.gy[a]);
   }
-  // linear reaction terms: (phi_a, u_c) exactly (consistent mass) with the degree-5
-  // rule, which integrates them exactly, or lumped (|T|/3 u_a) with the vertex rule
-  {
-    double Mu[3][5];
-#pragma unroll
-    for (int c = 0; c < 5; ++c) {
-      const double sc = u[0][c] + u[1][c] + u[2][c];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) Mu[a][c] = RULE == 0 ? m12 * (u[a][c] + sc) : (T.area / 3.0) * u[a][c];
-    }
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const double MN = Mu[a][0] + Mu[a][1] + Mu[a][2] + Mu[a][3] + Mu[a][4];
-      Fe[a][0] -= r.dt * (r.alpha * MN - r.mu * Mu[a][0]);
-      Fe[a][1] += r.dt * (r.sigma + r.ge + r.mu) * Mu[a][1];
-      Fe[a][2] -= r.dt * (r.sigma * Mu[a][1] - (r.gr + r.gd + r.mu) * Mu[a][2]);
-      Fe[a][3] -= r.dt * (r.ge * Mu[a][1] + r.gr * Mu[a][2] - r.mu * Mu[a][3]);
-      Fe[a][4] -= r.dt * r.gd * Mu[a][2];
-    }
-  }
   // transmission s -> e, kappa s (beta_I i + beta_E e) b, by the quadrature rule
   double bv[3] = {1.0, 1.0, 1.0};
   if (BF) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) bv[a] = bfield[T.v[a]];
   }
-  double Nv[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) Nv[a] = u[a][0] + u[a][1] + u[a][2] + u[a][3] + u[a][4];
-  constexpr int NQ = RULE == 0 ? 7 : 3;
   bool bad = false;
+  if (RULE == 0) {
+    const double A1 = cORB[0], D1 = cORB[1], A2 = cORB[3], D2 = cORB[4];
+    double l[3];
 #pragma unroll
-  for (int q = 0; q < NQ; ++q) {
-    const double L0 = cQL[RULE][q][0], L1 = cQL[RULE][q][1], L2 = cQL[RULE][q][2];
-    const double sq = L0 * u[0][0] + L1 * u[1][0] + L2 * u[2][0];
-    const double eq = L0 * u[0][1] + L1 * u[1][1] + L2 * u[2][1];
-    const double iq = L0 * u[0][2] + L1 * u[1][2] + L2 * u[2][2];
-    const double N = L0 * Nv[0] + L1 * Nv[1] + L2 * Nv[2];
-    const double bq = BF ? L0 * bv[0] + L1 * bv[1] + L2 * bv[2] : 1.0;
-    bad |= !(N > 0.0);
-    const double kappa = 1.0 - r.A / N;
-    const double Tr = kappa * sq * (r.bi * iq + r.be * eq) * bq;
-    const double wq = r.dt * T.area * cQW[RULE][q] * Tr;
-    Fe[0][0] += wq * L0;
-    Fe[1][0] += wq * L1;
-    Fe[2][0] += wq * L2;
-    Fe[0][1] -= wq * L0;
-    Fe[1][1] -= wq * L1;
-    Fe[2][1] -= wq * L2;
+    for (int a = 0; a < 3; ++a) l[a] = r.bi * u[a][2] + r.be * u[a][1];
+    const double Ss = u[0][0] + u[1][0] + u[2][0], Sl = l[0] + l[1] + l[2];
+    const double Sb = BF ? bv[0] + bv[1] + bv[2] : 3.0;
+    // N at the points: centroid, orbit 1, orbit 2
+    double Nq[7], rq[7];
+    Nq[0] = Nbar;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      Nq[1 + k] = A1 * SN + D1 * Nv[k];
+      Nq[4 + k] = A2 * SN + D2 * Nv[k];
+    }
+#pragma unroll
+    for (int q = 0; q < 7; ++q) bad |= !positive(Nq[q]);
+    reciprocals7(Nq, rq);
+    const double T0 = (1.0 - r.A * rq[0]) * (Ss * (1.0 / 3.0)) * (Sl * (1.0 / 3.0)) *
+                      (BF ? Sb * (1.0 / 3.0) : 1.0);
+    double T1[3], T2[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const double s1 = A1 * Ss + D1 * u[k][0], l1 = A1 * Sl + D1 * l[k];
+      const double s2 = A2 * Ss + D2 * u[k][0], l2 = A2 * Sl + D2 * l[k];
+      T1[k] = (1.0 - r.A * rq[1 + k]) * s1 * l1 * (BF ? A1 * Sb + D1 * bv[k] : 1.0);
+      T2[k] = (1.0 - r.A * rq[4 + k]) * s2 * l2 * (BF ? A2 * Sb + D2 * bv[k] : 1.0);
+    }
+    const double sh = cORB[7] * T0 + cORB[8] * (T1[0] + T1[1] + T1[2]) + cORB[9] * (T2[0] + T2[1] + T2[2]);
+    const double dA = r.dt * T.area;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double v = dA * (sh + cORB[10] * T1[a] + cORB[11] * T2[a]);
+      Fe[a][0] += v;
+      Fe[a][1] -= v;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const double L0 = cQL[RULE][q][0], L1 = cQL[RULE][q][1], L2 = cQL[RULE][q][2];
+      const double sq = L0 * u[0][0] + L1 * u[1][0] + L2 * u[2][0];
+      const double eq = L0 * u[0][1] + L1 * u[1][1] + L2 * u[2][1];
+      const double iq = L0 * u[0][2] + L1 * u[1][2] + L2 * u[2][2];
+      const double N = L0 * Nv[0] + L1 * Nv[1] + L2 * Nv[2];
+      const double bq = BF ? L0 * bv[0] + L1 * bv[1] + L2 * bv[2] : 1.0;
+      bad |= !(N > 0.0);
+      const double kappa = 1.0 - r.A / N;
+      const double Tr = kappa * sq * (r.bi * iq + r.be * eq) * bq;
+      const double wq = r.dt * T.area * cQW[RULE][q] * Tr;
+      Fe[0][0] += wq * L0;
+      Fe[1][0] += wq * L1;
+      Fe[2][0] += wq * L2;
+      Fe[0][1] -= wq * L0;
+      Fe[1][1] -= wq * L1;
+      Fe[2][1] -= wq * L2;
+    }
   }
   if (bad) atomicOr(err, 1);
   double* out = elem + 15 * t;
@@ -305,37 +411,109 @@ __global__ void __launch_bounds__(128) k_jac_record(int64_t m, const int32_t* __
 #pragma unroll
   for (int a = 0; a < 3; ++a) Nv[a] = u[a][0] + u[a][1] + u[a][2] + u[a][3] + u[a][4];
   const T A = (T)r.A, bi = (T)r.bi, be = (T)r.be;
-  constexpr int NQ = RULE == 0 ? 7 : 3;
   bool bad = false;
+  if (RULE == 0 && !PIC) {
+    // the degree-5 rule by its orbits (cORB): per moment, the centroid value, the two
+    // orbit sums and the six point values give the six pair moments
+    const T A1 = (T)cORB[0], D1 = (T)cORB[1], A2 = (T)cORB[3], D2 = (T)cORB[4];
+    T l[3];
 #pragma unroll
-  for (int q = 0; q < NQ; ++q) {
-    const T L0 = (T)cQL[RULE][q][0], L1 = (T)cQL[RULE][q][1], L2 = (T)cQL[RULE][q][2];
-    const T sq = L0 * u[0][0] + L1 * u[1][0] + L2 * u[2][0];
-    const T eq = L0 * u[0][1] + L1 * u[1][1] + L2 * u[2][1];
-    const T iq = L0 * u[0][2] + L1 * u[1][2] + L2 * u[2][2];
-    const T N = L0 * Nv[0] + L1 * Nv[1] + L2 * Nv[2];
-    const T bq = BF ? L0 * bv[0] + L1 * bv[1] + L2 * bv[2] : T(1);
-    bad |= !(N > T(0));
-    const T invN = T(1) / N;
-    const T kappa = T(1) - A * invN;
-    const T lam = (bi * iq + be * eq) * bq;
-    const T ksb = kappa * sq * bq;
-    T rho[4];
-    rho[0] = PIC ? kappa * bi * iq * bq : A * invN * invN * sq * lam;
-    rho[1] = kappa * lam;
-    rho[2] = ksb * be;
-    rho[3] = ksb * bi;
+    for (int a = 0; a < 3; ++a) l[a] = bi * u[a][2] + be * u[a][1];
+    const T Ss = u[0][0] + u[1][0] + u[2][0], Sl = l[0] + l[1] + l[2], SN = Nv[0] + Nv[1] + Nv[2];
+    const T Sb = BF ? bv[0] + bv[1] + bv[2] : T(3);
+    T Nq[7], rq[7];
+    Nq[0] = Nbar;
 #pragma unroll
-    for (int s = 0; s < 6; ++s) {
-      const T cw = (T)cQC[RULE][q][s];  // w_q phi_a phi_b; the area multiplies once at the end
-#pragma unroll
-      for (int k = 0; k < 4; ++k) P[k][s] += cw * rho[k];
+    for (int k = 0; k < 3; ++k) {
+      Nq[1 + k] = A1 * SN + D1 * Nv[k];
+      Nq[4 + k] = A2 * SN + D2 * Nv[k];
     }
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+      if constexpr (sizeof(T) == 8) bad |= !positive(Nq[q]);
+      else bad |= !(Nq[q] > T(0));
+    }
+    if constexpr (sizeof(T) == 8) {
+      reciprocals7(Nq, rq);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 7; ++q) rq[q] = T(1) / Nq[q];
+    }
+    // rho at point q from s, l, b there
+    auto moments = [&](int q, T s, T lv, T b, T (&rho)[4]) {
+      const T Ar = A * rq[q];
+      const T kappa = T(1) - Ar;
+      const T lam = lv * b;
+      const T ksb = kappa * s * b;
+      rho[0] = Ar * rq[q] * (s * lam);
+      rho[1] = kappa * lam;
+      rho[2] = ksb * be;
+      rho[3] = ksb * bi;
+    };
+    T rc[4], S1[4] = {0, 0, 0, 0}, S2[4] = {0, 0, 0, 0};
+    moments(0, Ss * T(1.0 / 3.0), Sl * T(1.0 / 3.0), BF ? Sb * T(1.0 / 3.0) : T(1), rc);
+    // P[k][a] (a < 3, pair (a, a)) and P[k][3 + (2 - c)] (the pair opposite vertex c) take the
+    // point values; the orbit sums and the centroid value are added to all pairs at the end
+    const T ar = Tt.area;
+    const T cdR1 = ar * (T)cORB[14], coR1 = ar * (T)cORB[16], cdR2 = ar * (T)cORB[18], coR2 = ar * (T)cORB[20];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      T rho1[4], rho2[4];
+      moments(1 + k, A1 * Ss + D1 * u[k][0], A1 * Sl + D1 * l[k], BF ? A1 * Sb + D1 * bv[k] : T(1), rho1);
+      moments(4 + k, A2 * Ss + D2 * u[k][0], A2 * Sl + D2 * l[k], BF ? A2 * Sb + D2 * bv[k] : T(1), rho2);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        S1[j] += rho1[j];
+        S2[j] += rho2[j];
+        P[j][k] = cdR1 * rho1[j] + cdR2 * rho2[j];
+        P[j][5 - k] = coR1 * rho1[j] + coR2 * rho2[j];  // pairs (1,2) (0,2) (0,1) at 5, 4, 3
+      }
+    }
+    const T c0 = ar * (T)cORB[12], cdS1 = ar * (T)cORB[13], coS1 = ar * (T)cORB[15];
+    const T cdS2 = ar * (T)cORB[17], coS2 = ar * (T)cORB[19];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const T base = c0 * rc[j];
+      const T bd = base + cdS1 * S1[j] + cdS2 * S2[j];
+      const T bo = base + coS1 * S1[j] + coS2 * S2[j];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        P[j][a] += bd;
+        P[j][3 + a] += bo;
+      }
+    }
+  } else {
+    constexpr int NQ = RULE == 0 ? 7 : 3;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const T L0 = (T)cQL[RULE][q][0], L1 = (T)cQL[RULE][q][1], L2 = (T)cQL[RULE][q][2];
+      const T sq = L0 * u[0][0] + L1 * u[1][0] + L2 * u[2][0];
+      const T eq = L0 * u[0][1] + L1 * u[1][1] + L2 * u[2][1];
+      const T iq = L0 * u[0][2] + L1 * u[1][2] + L2 * u[2][2];
+      const T N = L0 * Nv[0] + L1 * Nv[1] + L2 * Nv[2];
+      const T bq = BF ? L0 * bv[0] + L1 * bv[1] + L2 * bv[2] : T(1);
+      bad |= !(N > T(0));
+      const T invN = T(1) / N;
+      const T kappa = T(1) - A * invN;
+      const T lam = (bi * iq + be * eq) * bq;
+      const T ksb = kappa * sq * bq;
+      T rho[4];
+      rho[0] = PIC ? kappa * bi * iq * bq : A * invN * invN * sq * lam;
+      rho[1] = kappa * lam;
+      rho[2] = ksb * be;
+      rho[3] = ksb * bi;
+#pragma unroll
+      for (int s = 0; s < 6; ++s) {
+        const T cw = (T)cQC[RULE][q][s];  // w_q phi_a phi_b; the area multiplies once at the end
+#pragma unroll
+        for (int k = 0; k < 4; ++k) P[k][s] += cw * rho[k];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int s = 0; s < 6; ++s) P[k][s] *= Tt.area;
   }
-#pragma unroll
-  for (int k = 0; k < 4; ++k)
-#pragma unroll
-    for (int s = 0; s < 6; ++s) P[k][s] *= Tt.area;
   if (bad) atomicOr(err, 1);
 #pragma unroll
   for (int k = 0; k < 4; ++k)
