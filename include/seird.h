@@ -376,10 +376,10 @@ int64_t seird_launch_count(void);
  * seird_create allocates.  This entry point evaluates F(u; u_prev) of Eq.
  * weakform -- the same two-phase element/gather computation as
  * seird_eval_residual -- on a mesh held entirely in caller-owned device
- * memory, and allocates nothing: its element scratch is one fixed file-scope
- * device array of SEIRD_NOALLOC_MAX_TRIS triangles (15 doubles each, about
- * 7.9 MB), which every GPU that loads the library keeps until the process
- * exits.
+ * memory, and allocates nothing: its scratch is one fixed file-scope device
+ * array of SEIRD_NOALLOC_MAX_TRIS element vectors (15 doubles each) and
+ * SEIRD_NOALLOC_MAX_NODES node terms (8 doubles each), about 12 MB, which
+ * every GPU that loads the library keeps until the process exits.
  *
  * Arguments (all pointers are device pointers except params):
  *   xy [n_nodes][2], tri [n_tris][3] (counter-clockwise), and the node

@@ -134,20 +134,172 @@ __device__ __forceinline__ void reciprocals7(const double (&N)[7], double (&r)[7
   }
 }
 
-// Element residual: consistent mass, exact diffusion, quadrature of the reaction.
-// Degree-5 rule: the time difference and the linear reaction terms are one mass
-// product M (u - u^n - dt L u), L the linear part of Eq. seird1-5 (exact, the rule
-// integrates them exactly), and the transmission term goes through the rule's
-// orbit form (cORB).  Vertex rule: the linear reaction terms are lumped.
-template <int RULE, bool BF>
-__global__ void __launch_bounds__(128) k_residual_elem(int64_t m, const int32_t* __restrict__ tri,
-                                                       const double* __restrict__ xy, const double* __restrict__ U,
-                                                       const double* __restrict__ Un,
-                                                       const double* __restrict__ bfield, Rates rin,
-                                                       double* __restrict__ elem, int32_t* err) {
+// Triangle t from the geometry table written at set-up (k_tri_geometry: |T| and the
+// gradients of the three hat functions, 8 doubles per triangle), or from the
+// coordinates when there is no table.
+__device__ __forceinline__ Tri tri_of(const int32_t* __restrict__ tri, const double* __restrict__ xy,
+                                      const double* __restrict__ geo, int64_t t) {
+  if (!geo) return load_tri(tri, xy, t);
+  Tri T;
+  T.v[0] = tri[3 * t];
+  T.v[1] = tri[3 * t + 1];
+  T.v[2] = tri[3 * t + 2];
+  const double2* g = reinterpret_cast<const double2*>(geo + 8 * t);
+  const double2 g0 = g[0], g1 = g[1], g2 = g[2], g3 = g[3];
+  T.area = g0.x;
+  T.gx[0] = g0.y;
+  T.gx[1] = g1.x;
+  T.gx[2] = g1.y;
+  T.gy[0] = g2.x;
+  T.gy[1] = g2.y;
+  T.gy[2] = g3.x;
+  return T;
+}
+
+__global__ void __launch_bounds__(256) k_tri_geometry(int64_t m, const int32_t* __restrict__ tri,
+                                                      const double* __restrict__ xy, double* __restrict__ geo) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= m) return;
   const Tri T = load_tri(tri, xy, t);
+  double2* g = reinterpret_cast<double2*>(geo + 8 * t);
+  g[0] = make_double2(T.area, T.gx[0]);
+  g[1] = make_double2(T.gx[1], T.gx[2]);
+  g[2] = make_double2(T.gy[0], T.gy[1]);
+  g[3] = make_double2(T.gy[2], 0.0);
+}
+
+// Node terms of the degree-5 residual, 8 doubles per node: w = u - u^n - dt L u (L the
+// linear part of the reaction of Eq. seird1-5), N = s + e + i + r + d and
+// l = beta_I i + beta_E e.  The element phase reads them at its vertices.
+__global__ void __launch_bounds__(256) k_residual_node(int64_t n, const double* __restrict__ U,
+                                                       const double* __restrict__ Un, Rates rin,
+                                                       double* __restrict__ nd) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const Rates r = rates_at(rin, i);
+  double u[5], du[5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    u[c] = U[5 * i + c];
+    du[c] = u[c] - Un[5 * i + c];
+  }
+  const double N = u[0] + u[1] + u[2] + u[3] + u[4];
+  const double dt = r.dt;
+  double2* o = reinterpret_cast<double2*>(nd + 8 * i);
+  o[0] = make_double2(du[0] - dt * (r.alpha * N - r.mu * u[0]), du[1] + dt * (r.sigma + r.ge + r.mu) * u[1]);
+  o[1] = make_double2(du[2] - dt * (r.sigma * u[1] - (r.gr + r.gd + r.mu) * u[2]),
+                      du[3] - dt * (r.ge * u[1] + r.gr * u[2] - r.mu * u[3]));
+  o[2] = make_double2(du[4] - dt * r.gd * u[2], N);
+  o[3] = make_double2(r.bi * u[2] + r.be * u[1], 0.0);
+}
+
+// Element residual with the degree-5 rule: consistent mass, exact diffusion, and the
+// reaction as the mass product M w of the node terms (the rule integrates the linear
+// terms exactly) plus the transmission term through the rule's orbit form (cORB).
+template <bool BF>
+__global__ void __launch_bounds__(128) k_residual_elem5(int64_t m, const int32_t* __restrict__ tri,
+                                                        const double* __restrict__ xy,
+                                                        const double* __restrict__ geo,
+                                                        const double* __restrict__ U, const double* __restrict__ nd,
+                                                        const double* __restrict__ bfield, Rates rin,
+                                                        double* __restrict__ elem, int32_t* err) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= m) return;
+  const Tri T = tri_of(tri, xy, geo, t);
+  const Rates r = rates_at(rin, T.v[0]);
+  double u[3][4], w[3][5], Nv[3], l[3], Fe[3][5];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const double2* q = reinterpret_cast<const double2*>(nd + 8 * (int64_t)T.v[a]);
+    const double2 q0 = q[0], q1 = q[1], q2 = q[2], q3 = q[3];
+    w[a][0] = q0.x;
+    w[a][1] = q0.y;
+    w[a][2] = q1.x;
+    w[a][3] = q1.y;
+    w[a][4] = q2.x;
+    Nv[a] = q2.y;
+    l[a] = q3.x;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) u[a][c] = U[5 * (int64_t)T.v[a] + c];
+  }
+  const double SN = Nv[0] + Nv[1] + Nv[2];
+  const double Nbar = SN * (1.0 / 3.0);
+  const double m12 = T.area * (1.0 / 12.0);  // (phi_a, phi_b) = |T| (1 + delta_ab) / 12
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    const double sw = w[0][c] + w[1][c] + w[2][c];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) Fe[a][c] = m12 * (w[a][c] + sw);
+  }
+  // diffusion: dt nubar_c |T| mean_T(N) grad u_c . grad phi_a  (nubar_D = 0)
+  const double dNA = r.dt * Nbar * T.area;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const double coef = dNA * r.nu[c];
+    const double gux = coef * (u[0][c] * T.gx[0] + u[1][c] * T.gx[1] + u[2][c] * T.gx[2]);
+    const double guy = coef * (u[0][c] * T.gy[0] + u[1][c] * T.gy[1] + u[2][c] * T.gy[2]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) Fe[a][c] += gux * T.gx[a] + guy * T.gy[a];
+  }
+  // transmission s -> e, kappa s (beta_I i + beta_E e) b, at the rule's points
+  double bv[3] = {1.0, 1.0, 1.0};
+  if (BF) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) bv[a] = bfield[T.v[a]];
+  }
+  const double A1 = cORB[0], D1 = cORB[1], A2 = cORB[3], D2 = cORB[4];
+  const double Ss = u[0][0] + u[1][0] + u[2][0], Sl = l[0] + l[1] + l[2];
+  const double Sb = BF ? bv[0] + bv[1] + bv[2] : 3.0;
+  double Nq[7], rq[7];  // centroid, orbit 1, orbit 2
+  Nq[0] = Nbar;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    Nq[1 + k] = A1 * SN + D1 * Nv[k];
+    Nq[4 + k] = A2 * SN + D2 * Nv[k];
+  }
+  bool bad = false;
+#pragma unroll
+  for (int q = 0; q < 7; ++q) bad |= !positive(Nq[q]);
+  reciprocals7(Nq, rq);
+  const double T0 = (1.0 - r.A * rq[0]) * (Ss * (1.0 / 3.0)) * (Sl * (1.0 / 3.0)) * (BF ? Sb * (1.0 / 3.0) : 1.0);
+  double T1[3], T2[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double s1 = A1 * Ss + D1 * u[k][0], l1 = A1 * Sl + D1 * l[k];
+    const double s2 = A2 * Ss + D2 * u[k][0], l2 = A2 * Sl + D2 * l[k];
+    T1[k] = (1.0 - r.A * rq[1 + k]) * s1 * l1 * (BF ? A1 * Sb + D1 * bv[k] : 1.0);
+    T2[k] = (1.0 - r.A * rq[4 + k]) * s2 * l2 * (BF ? A2 * Sb + D2 * bv[k] : 1.0);
+  }
+  const double sh = cORB[7] * T0 + cORB[8] * (T1[0] + T1[1] + T1[2]) + cORB[9] * (T2[0] + T2[1] + T2[2]);
+  const double dA = r.dt * T.area;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const double v = dA * (sh + cORB[10] * T1[a] + cORB[11] * T2[a]);
+    Fe[a][0] += v;
+    Fe[a][1] -= v;
+  }
+  if (bad) atomicOr(err, 1);
+  double* out = elem + 15 * t;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int c = 0; c < 5; ++c) out[5 * a + c] = Fe[a][c];
+}
+
+// Element residual with the three-vertex rule: consistent mass for the time
+// difference, exact diffusion, the linear reaction terms lumped (|T|/3 at each
+// vertex) and the transmission term at the vertices.
+template <bool BF>
+__global__ void __launch_bounds__(128) k_residual_elem_vertex(int64_t m, const int32_t* __restrict__ tri,
+                                                              const double* __restrict__ xy,
+                                                              const double* __restrict__ geo,
+                                                              const double* __restrict__ U,
+                                                              const double* __restrict__ Un,
+                                                              const double* __restrict__ bfield, Rates rin,
+                                                              double* __restrict__ elem, int32_t* err) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= m) return;
+  const Tri T = tri_of(tri, xy, geo, t);
   const Rates r = rates_at(rin, T.v[0]);
   double u[3][5], Fe[3][5], Nv[3];
 #pragma unroll
@@ -156,58 +308,30 @@ __global__ void __launch_bounds__(128) k_residual_elem(int64_t m, const int32_t*
     for (int c = 0; c < 5; ++c) u[a][c] = U[5 * (int64_t)T.v[a] + c];
     Nv[a] = u[a][0] + u[a][1] + u[a][2] + u[a][3] + u[a][4];
   }
-  const double SN = Nv[0] + Nv[1] + Nv[2];
-  const double Nbar = SN * (1.0 / 3.0);
-  const double m12 = T.area * (1.0 / 12.0);  // (phi_a, phi_b) = |T| (1 + delta_ab) / 12
-  if (RULE == 0) {
-    // w = u - u^n - dt L u at the vertices, then Fe = M w
-    const double kS = r.dt * r.alpha, mS = r.dt * r.mu, kE = r.dt * (r.sigma + r.ge + r.mu);
-    const double kIe = r.dt * r.sigma, kI = r.dt * (r.gr + r.gd + r.mu), kRe = r.dt * r.ge, kRi = r.dt * r.gr;
-    const double kD = r.dt * r.gd;
-    double w[3][5];
+  const double Nbar = (Nv[0] + Nv[1] + Nv[2]) * (1.0 / 3.0);
+  const double m12 = T.area * (1.0 / 12.0);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      double du[5];
+  for (int c = 0; c < 5; ++c) {
+    double du[3];
 #pragma unroll
-      for (int c = 0; c < 5; ++c) du[c] = u[a][c] - Un[5 * (int64_t)T.v[a] + c];
-      w[a][0] = du[0] - kS * Nv[a] + mS * u[a][0];
-      w[a][1] = du[1] + kE * u[a][1];
-      w[a][2] = du[2] - kIe * u[a][1] + kI * u[a][2];
-      w[a][3] = du[3] - kRe * u[a][1] - kRi * u[a][2] + mS * u[a][3];
-      w[a][4] = du[4] - kD * u[a][2];
-    }
+    for (int a = 0; a < 3; ++a) du[a] = u[a][c] - Un[5 * (int64_t)T.v[a] + c];
+    const double sdu = du[0] + du[1] + du[2];
 #pragma unroll
-    for (int c = 0; c < 5; ++c) {
-      const double sw = w[0][c] + w[1][c] + w[2][c];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) Fe[a][c] = m12 * (w[a][c] + sw);
-    }
-  } else {
-#pragma unroll
-    for (int c = 0; c < 5; ++c) {
-      double du[3];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) du[a] = u[a][c] - Un[5 * (int64_t)T.v[a] + c];
-      const double sdu = du[0] + du[1] + du[2];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) Fe[a][c] = m12 * (du[a] + sdu);
-    }
-    // linear reaction terms, lumped: |T|/3 u_a
-    const double a3 = T.area / 3.0;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      double Mu[5];
-#pragma unroll
-      for (int c = 0; c < 5; ++c) Mu[c] = a3 * u[a][c];
-      const double MN = Mu[0] + Mu[1] + Mu[2] + Mu[3] + Mu[4];
-      Fe[a][0] -= r.dt * (r.alpha * MN - r.mu * Mu[0]);
-      Fe[a][1] += r.dt * (r.sigma + r.ge + r.mu) * Mu[1];
-      Fe[a][2] -= r.dt * (r.sigma * Mu[1] - (r.gr + r.gd + r.mu) * Mu[2]);
-      Fe[a][3] -= r.dt * (r.ge * Mu[1] + r.gr * Mu[2] - r.mu * Mu[3]);
-      Fe[a][4] -= r.dt * r.gd * Mu[2];
-    }
+    for (int a = 0; a < 3; ++a) Fe[a][c] = m12 * (du[a] + sdu);
   }
-  // diffusion: dt nubar_c |T| mean_T(N) grad u_c . grad phi_a  (nubar_D = 0)
+  const double a3 = T.area / 3.0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    double Mu[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) Mu[c] = a3 * u[a][c];
+    const double MN = Mu[0] + Mu[1] + Mu[2] + Mu[3] + Mu[4];
+    Fe[a][0] -= r.dt * (r.alpha * MN - r.mu * Mu[0]);
+    Fe[a][1] += r.dt * (r.sigma + r.ge + r.mu) * Mu[1];
+    Fe[a][2] -= r.dt * (r.sigma * Mu[1] - (r.gr + r.gd + r.mu) * Mu[2]);
+    Fe[a][3] -= r.dt * (r.ge * Mu[1] + r.gr * Mu[2] - r.mu * Mu[3]);
+    Fe[a][4] -= r.dt * r.gd * Mu[2];
+  }
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     const double gux = u[0][c] * T.gx[0] + u[1][c] * T.gx[1] + u[2][c] * T.gx[2];
@@ -216,69 +340,17 @@ __global__ void __launch_bounds__(128) k_residual_elem(int64_t m, const int32_t*
 #pragma unroll
     for (int a = 0; a < 3; ++a) Fe[a][c] += coef * (gux * T.gx[a] + guy * T.gy[a]);
   }
-  // transmission s -> e, kappa s (beta_I i + beta_E e) b, by the quadrature rule
-  double bv[3] = {1.0, 1.0, 1.0};
-  if (BF) {
-#pragma unroll
-    for (int a = 0; a < 3; ++a) bv[a] = bfield[T.v[a]];
-  }
   bool bad = false;
-  if (RULE == 0) {
-    const double A1 = cORB[0], D1 = cORB[1], A2 = cORB[3], D2 = cORB[4];
-    double l[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) l[a] = r.bi * u[a][2] + r.be * u[a][1];
-    const double Ss = u[0][0] + u[1][0] + u[2][0], Sl = l[0] + l[1] + l[2];
-    const double Sb = BF ? bv[0] + bv[1] + bv[2] : 3.0;
-    // N at the points: centroid, orbit 1, orbit 2
-    double Nq[7], rq[7];
-    Nq[0] = Nbar;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      Nq[1 + k] = A1 * SN + D1 * Nv[k];
-      Nq[4 + k] = A2 * SN + D2 * Nv[k];
-    }
-#pragma unroll
-    for (int q = 0; q < 7; ++q) bad |= !positive(Nq[q]);
-    reciprocals7(Nq, rq);
-    const double T0 = (1.0 - r.A * rq[0]) * (Ss * (1.0 / 3.0)) * (Sl * (1.0 / 3.0)) *
-                      (BF ? Sb * (1.0 / 3.0) : 1.0);
-    double T1[3], T2[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const double s1 = A1 * Ss + D1 * u[k][0], l1 = A1 * Sl + D1 * l[k];
-      const double s2 = A2 * Ss + D2 * u[k][0], l2 = A2 * Sl + D2 * l[k];
-      T1[k] = (1.0 - r.A * rq[1 + k]) * s1 * l1 * (BF ? A1 * Sb + D1 * bv[k] : 1.0);
-      T2[k] = (1.0 - r.A * rq[4 + k]) * s2 * l2 * (BF ? A2 * Sb + D2 * bv[k] : 1.0);
-    }
-    const double sh = cORB[7] * T0 + cORB[8] * (T1[0] + T1[1] + T1[2]) + cORB[9] * (T2[0] + T2[1] + T2[2]);
-    const double dA = r.dt * T.area;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const double v = dA * (sh + cORB[10] * T1[a] + cORB[11] * T2[a]);
-      Fe[a][0] += v;
-      Fe[a][1] -= v;
-    }
-  } else {
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const double L0 = cQL[RULE][q][0], L1 = cQL[RULE][q][1], L2 = cQL[RULE][q][2];
-      const double sq = L0 * u[0][0] + L1 * u[1][0] + L2 * u[2][0];
-      const double eq = L0 * u[0][1] + L1 * u[1][1] + L2 * u[2][1];
-      const double iq = L0 * u[0][2] + L1 * u[1][2] + L2 * u[2][2];
-      const double N = L0 * Nv[0] + L1 * Nv[1] + L2 * Nv[2];
-      const double bq = BF ? L0 * bv[0] + L1 * bv[1] + L2 * bv[2] : 1.0;
-      bad |= !(N > 0.0);
-      const double kappa = 1.0 - r.A / N;
-      const double Tr = kappa * sq * (r.bi * iq + r.be * eq) * bq;
-      const double wq = r.dt * T.area * cQW[RULE][q] * Tr;
-      Fe[0][0] += wq * L0;
-      Fe[1][0] += wq * L1;
-      Fe[2][0] += wq * L2;
-      Fe[0][1] -= wq * L0;
-      Fe[1][1] -= wq * L1;
-      Fe[2][1] -= wq * L2;
-    }
+  for (int a = 0; a < 3; ++a) {  // |T|/3 at vertex a
+    const double N = Nv[a];
+    const double bq = BF ? bfield[T.v[a]] : 1.0;
+    bad |= !(N > 0.0);
+    const double kappa = 1.0 - r.A / N;
+    const double Tr = kappa * u[a][0] * (r.bi * u[a][2] + r.be * u[a][1]) * bq;
+    const double wq = r.dt * a3 * Tr;
+    Fe[a][0] += wq;
+    Fe[a][1] -= wq;
   }
   if (bad) atomicOr(err, 1);
   double* out = elem + 15 * t;
@@ -348,12 +420,13 @@ __device__ __forceinline__ int sym(int a, int b) {
 // derivative).
 template <int RULE, bool BF, class T, bool PIC>
 __global__ void __launch_bounds__(128) k_jac_record(int64_t m, const int32_t* __restrict__ tri,
-                                                    const double* __restrict__ xy, const double* __restrict__ U,
+                                                    const double* __restrict__ xy, const double* __restrict__ geo,
+                                                    const double* __restrict__ U,
                                                     const double* __restrict__ bfield, Rates rin,
                                                     T* __restrict__ rec, int32_t* err) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= m) return;
-  const Tri Tg = load_tri(tri, xy, t);
+  const Tri Tg = tri_of(tri, xy, geo, t);
   const Rates r = rates_at(rin, Tg.v[0]);
   TriT<T> Tt;
   Tt.area = (T)Tg.area;
@@ -375,26 +448,29 @@ __global__ void __launch_bounds__(128) k_jac_record(int64_t m, const int32_t* __
   Nbar *= T(1.0 / 3.0);
   T* out = rec + (int64_t)REC * t;
   out[0] = Tt.area;
-  // N-weighted stiffness |T| mean(N) grad phi_a . grad phi_b
-  const T an = Tt.area * Nbar;
+  // N-weighted stiffness dt |T| mean(N) grad phi_a . grad phi_b
+  // the gather reads the sums below already scaled: K and P by dt, G_c by dt nu_c
+  const T dtT = (T)r.dt;
+  const T an = dtT * Tt.area * Nbar;
   out[REC_K + 0] = an * (Tt.gx[0] * Tt.gx[0] + Tt.gy[0] * Tt.gy[0]);
   out[REC_K + 1] = an * (Tt.gx[1] * Tt.gx[1] + Tt.gy[1] * Tt.gy[1]);
   out[REC_K + 2] = an * (Tt.gx[2] * Tt.gx[2] + Tt.gy[2] * Tt.gy[2]);
   out[REC_K + 3] = an * (Tt.gx[0] * Tt.gx[1] + Tt.gy[0] * Tt.gy[1]);
   out[REC_K + 4] = an * (Tt.gx[0] * Tt.gx[2] + Tt.gy[0] * Tt.gy[2]);
   out[REC_K + 5] = an * (Tt.gx[1] * Tt.gx[2] + Tt.gy[1] * Tt.gy[2]);
-  // G_{c,a} = |T|/3 grad u_c . grad phi_a (derivative of mean_T(N) by any u_{b,c'})
+  // G_{c,a} = dt nubar_c |T|/3 grad u_c . grad phi_a (derivative of mean_T(N) by any u_{b,c'})
   const T a3 = Tt.area * T(1.0 / 3.0);
   if (!PIC) {
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       const T gux = u[0][c] * Tt.gx[0] + u[1][c] * Tt.gx[1] + u[2][c] * Tt.gx[2];
       const T guy = u[0][c] * Tt.gy[0] + u[1][c] * Tt.gy[1] + u[2][c] * Tt.gy[2];
+      const T gsc = a3 * dtT * (T)r.nu[c];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) out[REC_G + 4 * a + c] = a3 * (gux * Tt.gx[a] + guy * Tt.gy[a]);
+      for (int a = 0; a < 3; ++a) out[REC_G + 4 * a + c] = gsc * (gux * Tt.gx[a] + guy * Tt.gy[a]);
     }
   }
-  // reaction moments P^k_ab = |T| sum_q w_q phi_a phi_b rho_k(x_q):
+  // reaction moments P^k_ab = dt |T| sum_q w_q phi_a phi_b rho_k(x_q):
   //   rho_0 = A s lam / N^2 (d kappa/du_c' = A/N^2 for every c'), rho_1 = kappa lam,
   //   rho_2 = kappa s beta_E b, rho_3 = kappa s beta_I b.
   T P[4][6];
@@ -454,7 +530,7 @@ __global__ void __launch_bounds__(128) k_jac_record(int64_t m, const int32_t* __
     moments(0, Ss * T(1.0 / 3.0), Sl * T(1.0 / 3.0), BF ? Sb * T(1.0 / 3.0) : T(1), rc);
     // P[k][a] (a < 3, pair (a, a)) and P[k][3 + (2 - c)] (the pair opposite vertex c) take the
     // point values; the orbit sums and the centroid value are added to all pairs at the end
-    const T ar = Tt.area;
+    const T ar = dtT * Tt.area;
     const T cdR1 = ar * (T)cORB[14], coR1 = ar * (T)cORB[16], cdR2 = ar * (T)cORB[18], coR2 = ar * (T)cORB[20];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -512,7 +588,7 @@ __global__ void __launch_bounds__(128) k_jac_record(int64_t m, const int32_t* __
 #pragma unroll
     for (int k = 0; k < 4; ++k)
 #pragma unroll
-      for (int s = 0; s < 6; ++s) P[k][s] *= Tt.area;
+      for (int s = 0; s < 6; ++s) P[k][s] *= dtT * Tt.area;
   }
   if (bad) atomicOr(err, 1);
 #pragma unroll
@@ -520,6 +596,27 @@ __global__ void __launch_bounds__(128) k_jac_record(int64_t m, const int32_t* __
 #pragma unroll
     for (int s = 0; s < 6; ++s) out[REC_P + 4 * s + k] = P[k][s];
   out[REC_K + 6] = T(0);
+}
+
+// Writes each thread's 5x5 block B to val[25 k ...] through shared memory, so that a
+// warp stores its 32 consecutive blocks as contiguous 800-value runs (one thread per
+// block would store 25 values 200 bytes apart per instruction).  Every thread of
+// the CTA calls it; blocks k >= nnzb are not written.
+template <class T>
+__device__ __forceinline__ void stage_store25(const T (&B)[5][5], int64_t k, int64_t nnzb, T* __restrict__ val) {
+  __shared__ T sm[128 * 25];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T* ws = sm + warp * 32 * 25;
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int c = 0; c < 5; ++c) ws[lane * 25 + 5 * i + c] = B[i][c];
+  __syncwarp();
+  const int64_t k0 = k - lane;  // the warp's first block
+  const int64_t nb = nnzb - k0 < 32 ? nnzb - k0 : 32;
+  if (nb <= 0) return;
+  T* dst = val + 25 * k0;
+  for (int j = lane; j < 25 * nb; j += 32) dst[j] = ws[j];
 }
 
 // One thread per 5x5 block: fixed-order sums over the triangles sharing the
@@ -534,14 +631,15 @@ __global__ void __launch_bounds__(128) k_jac_gather(int64_t nnzb, const int32_t*
                                                     const int32_t* __restrict__ tri, Rates rin,
                                                     T* __restrict__ val) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (k >= nnzb) return;
+  const bool live = k < nnzb;
   Rates r = rin;
-  if (rin.tab) {  // the block row's node: row vertex of the first incident triangle
+  if (live && rin.tab) {  // the block row's node: row vertex of the first incident triangle
     const int32_t e = inc[inc_ptr[k]];
     r = rates_at(rin, tri[3 * (int64_t)(e / 9) + (e % 9) / 3]);
   }
   T M = 0, Mr = 0, K = 0, G[4] = {0, 0, 0, 0}, P[4] = {0, 0, 0, 0};
-  for (int32_t q = inc_ptr[k]; q < inc_ptr[k + 1]; ++q) {
+  const int32_t q0 = live ? inc_ptr[k] : 0, q1 = live ? inc_ptr[k + 1] : 0;
+  for (int32_t q = q0; q < q1; ++q) {
     const int32_t e = inc[q];
     const int32_t t = e / 9, ab = e - 9 * t;
     const int a = ab / 3, b = ab - 3 * a;
@@ -558,65 +656,50 @@ __global__ void __launch_bounds__(128) k_jac_gather(int64_t nnzb, const int32_t*
     for (int c = 0; c < 4; ++c) P[c] += R[REC_P + 4 * s + c];
   }
   if (RULE == 0) Mr = M;
+  // K, G and P arrive scaled by dt (G_c by dt nubar_c), see k_jac_record
   const T dt = (T)r.dt;
   const T nu0 = (T)r.nu[0], nu1 = (T)r.nu[1], nu2 = (T)r.nu[2], nu3 = (T)r.nu[3];
+  const T dMr = dt * Mr;
   const T alpha = (T)r.alpha, mu = (T)r.mu, sigma = (T)r.sigma, ge = (T)r.ge, gr = (T)r.gr, gd = (T)r.gd;
   T B[5][5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int c = 0; c < 5; ++c) B[i][c] = T(0);
   if (PIC) {
     // Picard matrix: M + dt nubar_c K on the diagonal, minus dt int B_cc'(u^k) phi_i phi_j with
     // B of Eq. vec_component2 (P1 = kappa(beta_I i + beta_E e) b, P2 = kappa s beta_E b,
     // P0 = kappa beta_I i b here)
 #pragma unroll
-    for (int i = 0; i < 5; ++i)
+    for (int c = 1; c < 5; ++c) B[0][c] = -alpha * dMr;
+    B[0][0] = M + nu0 * K + (mu - alpha) * dMr + P[1];
+    B[1][0] = -P[0];
+    B[1][1] = M + nu1 * K - P[2] + (sigma + ge + mu) * dMr;
+  } else {
+    // rows S, E: transmission derivative row  dT/du_c' = P0 + [S]P1 + [E]P2 + [I]P3
+    const T rS = G[0] - alpha * dMr + P[0], rE = G[1] - P[0];
 #pragma unroll
-      for (int c = 0; c < 5; ++c) B[i][c] = T(0);
-#pragma unroll
-    for (int c = 1; c < 5; ++c) B[0][c] = -dt * alpha * Mr;
-    B[0][0] = M + dt * nu0 * K + dt * (mu - alpha) * Mr + dt * P[1];
-    B[1][0] = -dt * P[0];
-    B[1][1] = M + dt * nu1 * K - dt * P[2] + dt * (sigma + ge + mu) * Mr;
-    B[2][1] = -dt * sigma * Mr;
-    B[2][2] = M + dt * nu2 * K + dt * (gr + gd + mu) * Mr;
-    B[3][1] = -dt * ge * Mr;
-    B[3][2] = -dt * gr * Mr;
-    B[3][3] = M + dt * nu3 * K + dt * mu * Mr;
-    B[4][2] = -dt * gd * Mr;
-    B[4][4] = M;
-    T* out = val + 25 * k;
-#pragma unroll
-    for (int i = 0; i < 5; ++i)
-#pragma unroll
-      for (int c = 0; c < 5; ++c) out[5 * i + c] = B[i][c];
-    return;
+    for (int c = 0; c < 5; ++c) {
+      B[0][c] = rS;
+      B[1][c] = rE;
+      B[2][c] = G[2];
+      B[3][c] = G[3];
+    }
+    B[0][0] += M + nu0 * K + P[1] + mu * dMr;
+    B[0][1] += P[2];
+    B[0][2] += P[3];
+    B[1][0] -= P[1];
+    B[1][1] += M + nu1 * K - P[2] + (sigma + ge + mu) * dMr;
+    B[1][2] -= P[3];
   }
-  // rows S, E: transmission derivative row  dT/du_c' = P0 + [S]P1 + [E]P2 + [I]P3
-  const T gS = dt * nu0 * G[0], gE = dt * nu1 * G[1], gI = dt * nu2 * G[2], gR = dt * nu3 * G[3];
-#pragma unroll
-  for (int c = 0; c < 5; ++c) {
-    B[0][c] = gS - dt * alpha * Mr + dt * P[0];
-    B[1][c] = gE - dt * P[0];
-    B[2][c] = gI;
-    B[3][c] = gR;
-    B[4][c] = T(0);
-  }
-  B[0][0] += M + dt * nu0 * K + dt * P[1] + dt * mu * Mr;
-  B[0][1] += dt * P[2];
-  B[0][2] += dt * P[3];
-  B[1][0] -= dt * P[1];
-  B[1][1] += M + dt * nu1 * K - dt * P[2] + dt * (sigma + ge + mu) * Mr;
-  B[1][2] -= dt * P[3];
-  B[2][1] -= dt * sigma * Mr;
-  B[2][2] += M + dt * nu2 * K + dt * (gr + gd + mu) * Mr;
-  B[3][1] -= dt * ge * Mr;
-  B[3][2] -= dt * gr * Mr;
-  B[3][3] += M + dt * nu3 * K + dt * mu * Mr;
-  B[4][2] -= dt * gd * Mr;
+  B[2][1] -= sigma * dMr;
+  B[2][2] += M + nu2 * K + (gr + gd + mu) * dMr;
+  B[3][1] -= ge * dMr;
+  B[3][2] -= gr * dMr;
+  B[3][3] += M + nu3 * K + mu * dMr;
+  B[4][2] -= gd * dMr;
   B[4][4] += M;
-  T* out = val + 25 * k;
-#pragma unroll
-  for (int i = 0; i < 5; ++i)
-#pragma unroll
-    for (int c = 0; c < 5; ++c) out[5 * i + c] = B[i][c];
+  stage_store25<T>(B, k, nnzb, val);
 }
 
 // ---- discrete-adjoint terms ------------------------------------------------
@@ -767,19 +850,26 @@ __global__ void k_misfit(int nobs, const int32_t* __restrict__ nodes, const doub
 
 }  // namespace
 
-void launch_residual(int64_t n, int64_t m, const int32_t* tri, const double* xy, const double* U, const double* Un,
-                     const double* bfield, const Rates& r, int rule, double* elem, const int32_t* inc_ptr,
-                     const int32_t* inc, double* F, double* partial, int grid_red, double* out_norm2, int32_t* err,
-                     cudaStream_t s) {
-  (void)grid_red;
+void launch_tri_geometry(int64_t m, const int32_t* tri, const double* xy, double* geo, cudaStream_t s) {
+  if (m <= 0) return;
+  k_tri_geometry<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(m, tri, xy, geo);
+  count_launch();
+}
+
+void launch_residual(int64_t n, int64_t m, const int32_t* tri, const double* xy, const double* geo, const double* U,
+                     const double* Un, const double* bfield, const Rates& r, int rule, double* nd, double* elem,
+                     const int32_t* inc_ptr, const int32_t* inc, double* F, double* partial, double* out_norm2,
+                     int32_t* err, cudaStream_t s) {
   const int tb = 128;
   const int64_t g = (m + tb - 1) / tb;
   if (rule == 0) {
-    if (bfield) k_residual_elem<0, true><<<g, tb, 0, s>>>(m, tri, xy, U, Un, bfield, r, elem, err);
-    else k_residual_elem<0, false><<<g, tb, 0, s>>>(m, tri, xy, U, Un, bfield, r, elem, err);
+    k_residual_node<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, U, Un, r, nd);
+    count_launch();
+    if (bfield) k_residual_elem5<true><<<g, tb, 0, s>>>(m, tri, xy, geo, U, nd, bfield, r, elem, err);
+    else k_residual_elem5<false><<<g, tb, 0, s>>>(m, tri, xy, geo, U, nd, bfield, r, elem, err);
   } else {
-    if (bfield) k_residual_elem<1, true><<<g, tb, 0, s>>>(m, tri, xy, U, Un, bfield, r, elem, err);
-    else k_residual_elem<1, false><<<g, tb, 0, s>>>(m, tri, xy, U, Un, bfield, r, elem, err);
+    if (bfield) k_residual_elem_vertex<true><<<g, tb, 0, s>>>(m, tri, xy, geo, U, Un, bfield, r, elem, err);
+    else k_residual_elem_vertex<false><<<g, tb, 0, s>>>(m, tri, xy, geo, U, Un, bfield, r, elem, err);
   }
   count_launch();
   const int64_t g2 = (n + 255) / 256;
@@ -805,36 +895,37 @@ void launch_beta_field(int64_t n, const double* xy, const seird_beta_schedule& s
 }
 
 template <class T, bool PIC>
-static void jacobian_kernels(int64_t nnzb, int64_t m, const int32_t* tri, const double* xy, const double* U,
+static void jacobian_kernels(int64_t nnzb, int64_t m, const int32_t* tri, const double* xy, const double* geo,
+                             const double* U,
                              const double* bfield, const Rates& r, int rule, T* rc, const int32_t* inc_ptr,
                              const int32_t* inc, T* val, int32_t* err, cudaStream_t s) {
-  const int tb = 128;
+  const int tb = 128;  // k_jac_gather stages 128 blocks per CTA in shared memory
   const int64_t g = (m + tb - 1) / tb;
   const int64_t g2 = (nnzb + tb - 1) / tb;
   if (rule == 0) {
-    if (bfield) k_jac_record<0, true, T, PIC><<<g, tb, 0, s>>>(m, tri, xy, U, bfield, r, rc, err);
-    else k_jac_record<0, false, T, PIC><<<g, tb, 0, s>>>(m, tri, xy, U, bfield, r, rc, err);
+    if (bfield) k_jac_record<0, true, T, PIC><<<g, tb, 0, s>>>(m, tri, xy, geo, U, bfield, r, rc, err);
+    else k_jac_record<0, false, T, PIC><<<g, tb, 0, s>>>(m, tri, xy, geo, U, bfield, r, rc, err);
   } else {
-    if (bfield) k_jac_record<1, true, T, PIC><<<g, tb, 0, s>>>(m, tri, xy, U, bfield, r, rc, err);
-    else k_jac_record<1, false, T, PIC><<<g, tb, 0, s>>>(m, tri, xy, U, bfield, r, rc, err);
+    if (bfield) k_jac_record<1, true, T, PIC><<<g, tb, 0, s>>>(m, tri, xy, geo, U, bfield, r, rc, err);
+    else k_jac_record<1, false, T, PIC><<<g, tb, 0, s>>>(m, tri, xy, geo, U, bfield, r, rc, err);
   }
   if (rule == 0) k_jac_gather<T, PIC, 0><<<g2, tb, 0, s>>>(nnzb, inc_ptr, inc, rc, tri, r, val);
   else k_jac_gather<T, PIC, 1><<<g2, tb, 0, s>>>(nnzb, inc_ptr, inc, rc, tri, r, val);
 }
 
-void launch_jacobian(int64_t nnzb, int64_t m, const int32_t* tri, const double* xy, const double* U,
+void launch_jacobian(int64_t nnzb, int64_t m, const int32_t* tri, const double* xy, const double* geo, const double* U,
                      const double* bfield, const Rates& r, int rule, void* rec, const int32_t* inc_ptr,
                      const int32_t* inc, void* val, bool fp32, bool picard, int32_t* err, cudaStream_t s) {
   if (fp32) {
     float* rc = static_cast<float*>(rec);
     float* v = static_cast<float*>(val);
-    if (picard) jacobian_kernels<float, true>(nnzb, m, tri, xy, U, bfield, r, rule, rc, inc_ptr, inc, v, err, s);
-    else jacobian_kernels<float, false>(nnzb, m, tri, xy, U, bfield, r, rule, rc, inc_ptr, inc, v, err, s);
+    if (picard) jacobian_kernels<float, true>(nnzb, m, tri, xy, geo, U, bfield, r, rule, rc, inc_ptr, inc, v, err, s);
+    else jacobian_kernels<float, false>(nnzb, m, tri, xy, geo, U, bfield, r, rule, rc, inc_ptr, inc, v, err, s);
   } else {
     double* rc = static_cast<double*>(rec);
     double* v = static_cast<double*>(val);
-    if (picard) jacobian_kernels<double, true>(nnzb, m, tri, xy, U, bfield, r, rule, rc, inc_ptr, inc, v, err, s);
-    else jacobian_kernels<double, false>(nnzb, m, tri, xy, U, bfield, r, rule, rc, inc_ptr, inc, v, err, s);
+    if (picard) jacobian_kernels<double, true>(nnzb, m, tri, xy, geo, U, bfield, r, rule, rc, inc_ptr, inc, v, err, s);
+    else jacobian_kernels<double, false>(nnzb, m, tri, xy, geo, U, bfield, r, rule, rc, inc_ptr, inc, v, err, s);
   }
   count_launch();
   count_launch();
@@ -888,9 +979,10 @@ void launch_misfit(int nobs, const int32_t* nodes, const double* Ihat, const dou
 // the error word.  Host code must not pass the symbol itself to a kernel (on the
 // host it names a stand-in, not device memory); it looks up the device address
 // with cudaGetSymbolAddress once per device.
-// layout: [elements 15*MAX_TRIS][partials][norm slot][error word]
+// layout: [elements 15*MAX_TRIS][node terms 8*MAX_NODES][partials][norm slot][error word]
 constexpr int64_t NOALLOC_PARTIALS = (SEIRD_NOALLOC_MAX_NODES + 255) / 256;
-constexpr int64_t NOALLOC_WORDS = 15 * (int64_t)SEIRD_NOALLOC_MAX_TRIS + NOALLOC_PARTIALS + 2;
+constexpr int64_t NOALLOC_WORDS =
+    15 * (int64_t)SEIRD_NOALLOC_MAX_TRIS + 8 * (int64_t)SEIRD_NOALLOC_MAX_NODES + NOALLOC_PARTIALS + 2;
 static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_WORDS];
 
 namespace {
@@ -936,7 +1028,8 @@ extern "C" int seird_residual_noalloc(int64_t n_nodes, int64_t n_tris, const dou
     base = g_noalloc_ptr[dev];
   }
   double* elem = base;
-  double* partial = base + 15 * (int64_t)SEIRD_NOALLOC_MAX_TRIS;
+  double* nd = base + 15 * (int64_t)SEIRD_NOALLOC_MAX_TRIS;
+  double* partial = nd + 8 * (int64_t)SEIRD_NOALLOC_MAX_NODES;
   double* nrm = norm2 ? norm2 : partial + NOALLOC_PARTIALS;  // own slot when the caller wants no norm
   int32_t* err = reinterpret_cast<int32_t*>(partial + NOALLOC_PARTIALS + 1);
   const cudaStream_t s = (cudaStream_t)stream;
@@ -955,8 +1048,8 @@ extern "C" int seird_residual_noalloc(int64_t n_nodes, int64_t n_tris, const dou
   r.mu = params->mu;
   for (int c = 0; c < 4; ++c) r.nu[c] = params->nu[c];
   r.dt = dt;
-  launch_residual(n_nodes, n_tris, tri, xy, u, u_prev, beta_field_dev, r, quadrature, elem, inc_ptr, inc, F, partial,
-                  0, nrm, err, s);
+  launch_residual(n_nodes, n_tris, tri, xy, nullptr, u, u_prev, beta_field_dev, r, quadrature, nd, elem, inc_ptr, inc,
+                  F, partial, nrm, err, s);
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(SEIRD_ECUDA, std::string("seird_residual_noalloc: launch: ") + cudaGetErrorString(e));
   int32_t flags = 0;

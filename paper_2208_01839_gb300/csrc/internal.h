@@ -181,6 +181,8 @@ struct seird_ctx {
   double* partial = nullptr;  // [grid][MAX_RESTART+1]
   double* hcol = nullptr;   // [MAX_RESTART+1] reduced dot products
   double* gm = nullptr;     // GMRES small state: H, cs, sn, g, y
+  double* geo = nullptr;      // [m][8] |T| and hat-function gradients (set-up)
+  double* nodebuf = nullptr;  // [n][8] node terms of the residual
   double* scal = nullptr;   // scalar outputs (norms)
   double* h_scal = nullptr; // pinned host mirror
   int32_t* err = nullptr;   // device error flags

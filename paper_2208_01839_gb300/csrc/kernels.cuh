@@ -63,12 +63,15 @@ void set_global_error(const std::string& msg);
 void upload_quadrature();
 
 // ---- launchers (defined in the .cu files) ----
-void launch_residual(int64_t n, int64_t m, const int32_t* tri, const double* xy, const double* U, const double* Un,
-                     const double* bfield, const Rates& r, int rule, double* elem, const int32_t* inc_ptr,
-                     const int32_t* inc, double* F, double* partial, int grid_red, double* out_norm2, int32_t* err,
-                     cudaStream_t s);
+// geo: per-triangle |T| and hat-function gradients (8 doubles each) from launch_tri_geometry,
+// or NULL to compute them from xy; nd: 8 doubles per node of scratch (degree-5 rule)
+void launch_tri_geometry(int64_t m, const int32_t* tri, const double* xy, double* geo, cudaStream_t s);
+void launch_residual(int64_t n, int64_t m, const int32_t* tri, const double* xy, const double* geo, const double* U,
+                     const double* Un, const double* bfield, const Rates& r, int rule, double* nd, double* elem,
+                     const int32_t* inc_ptr, const int32_t* inc, double* F, double* partial, double* out_norm2,
+                     int32_t* err, cudaStream_t s);
 void launch_beta_field(int64_t n, const double* xy, const seird_beta_schedule& s, double* out, cudaStream_t st);
-void launch_jacobian(int64_t nnzb, int64_t m, const int32_t* tri, const double* xy, const double* U,
+void launch_jacobian(int64_t nnzb, int64_t m, const int32_t* tri, const double* xy, const double* geo, const double* U,
                      const double* bfield, const Rates& r, int rule, void* rec, const int32_t* inc_ptr,
                      const int32_t* inc, void* val, bool fp32, bool picard, int32_t* err, cudaStream_t s);
 template <class VT>

@@ -182,9 +182,9 @@ int residual(seird_ctx* ctx, const double* U, const double* Un, double* F, doubl
   const HostSetup& hs = ctx->hs;
   {
     KTimer kt_(ctx, SEIRD_K_RESIDUAL);
-    launch_residual(hs.n, hs.m, ctx->tri, ctx->xy, U, Un, bfield_of(ctx), make_rates(ctx), ctx->opt.quadrature,
-                    ctx->elem, ctx->node_inc_ptr, ctx->node_inc, F, ctx->partial, 0, ctx->scal, ctx->err,
-                    ctx->stream);
+    launch_residual(hs.n, hs.m, ctx->tri, ctx->xy, ctx->geo, U, Un, bfield_of(ctx), make_rates(ctx),
+                    ctx->opt.quadrature, ctx->nodebuf, ctx->elem, ctx->node_inc_ptr, ctx->node_inc, F, ctx->partial,
+                    ctx->scal, ctx->err, ctx->stream);
   }
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(ctx->h_scal, ctx->scal, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
@@ -202,7 +202,7 @@ int jacobian(seird_ctx* ctx, const double* U, bool picard = false) {
   KTimer kt_(ctx, SEIRD_K_JACOBIAN);
   // the mixed path assembles the Jacobian straight into its FP32 copy (FP32
   // arithmetic); it only feeds the FP32 operator and the FP32 factors
-  launch_jacobian((int64_t)hs.col.size(), hs.m, ctx->tri, ctx->xy, U, bfield_of(ctx), make_rates(ctx),
+  launch_jacobian((int64_t)hs.col.size(), hs.m, ctx->tri, ctx->xy, ctx->geo, U, bfield_of(ctx), make_rates(ctx),
                   ctx->opt.quadrature, ctx->rec, ctx->blk_inc_ptr, ctx->blk_inc,
                   mixed(ctx) ? (void*)ctx->val32 : (void*)ctx->val, mixed(ctx), picard, ctx->err, ctx->stream);
   CK(cudaGetLastError());
@@ -1274,6 +1274,10 @@ static int create_impl(seird_ctx* ctx, const seird_mesh* mesh, const seird_param
   }
   if (o.precision == 0) TRY(dalloc(ctx, &ctx->val, 25 * nnzb));
   TRY(dalloc(ctx, &ctx->elem, 15 * m));
+  TRY(dalloc(ctx, &ctx->geo, 8 * m));
+  launch_tri_geometry(m, ctx->tri, ctx->xy, ctx->geo, ctx->stream);
+  CK(cudaGetLastError());
+  TRY(dalloc(ctx, &ctx->nodebuf, 8 * (size_t)hs.n));
   TRY(dalloc(ctx, &ctx->rec, (size_t)REC * m));
   double** vecs[] = {&ctx->U, &ctx->Un, &ctx->F, &ctx->Ft, &ctx->dU, &ctx->Ut, &ctx->stage, &ctx->stage2, &ctx->w};
   for (double** v : vecs) TRY(dalloc(ctx, v, len));
