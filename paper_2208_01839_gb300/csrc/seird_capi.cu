@@ -570,51 +570,61 @@ static int arnoldi_iteration(seird_ctx* ctx, int j, const CycleCtl& cc) {
   return SEIRD_OK;
 }
 
-// Captures one restart cycle (options.graph): Arnoldi iteration j is the body of a
-// conditional IF node, the nodes in sequence; iteration 0's condition defaults to 1 at
-// every launch, the others to 0, and the Givens kernel of iteration j sets that of j + 1
-// (k_givens).  A replay thus runs iterations until convergence, dtol or the cycle's limit
-// (ctl[1]) with no host round trip, and skipped iterations launch nothing.  The graph
-// bakes in the Krylov, preconditioner and matrix buffers and the launch shapes, which are
-// fixed once the autotuner has run.
+// Captures one restart cycle (options.graph) as nested conditional IF nodes: the body
+// of node j holds Arnoldi iteration j followed by node j + 1, whose condition the Givens
+// kernel of iteration j sets (k_givens).  Node 0's condition defaults to 1 at every
+// launch.  A replay thus runs iterations until convergence, dtol or the cycle's limit
+// (ctl[1]) with no host round trip, and once a condition is 0 the rest of the cycle is
+// skipped as a whole.  The graph bakes in the Krylov, preconditioner and matrix buffers
+// and the launch shapes, which are fixed once the autotuner has run.
 static int build_cycle_graph(seird_ctx* ctx) {
   const int m = ctx->opt.gmres_restart;
   cudaStream_t cs = nullptr;
   cudaGraph_t g = nullptr;
   CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   cudaError_t e = cudaGraphCreate(&g, 0);
-  std::vector<cudaGraphConditionalHandle> hnd(m);
-  for (int j = 0; j < m && e == cudaSuccess; ++j)
-    e = cudaGraphConditionalHandleCreate(&hnd[j], g, j == 0 ? 1u : 0u, cudaGraphCondAssignDefault);
+  cudaGraphConditionalHandle hnd = 0;
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hnd, g, 1u, cudaGraphCondAssignDefault);
   const cudaStream_t saved = ctx->stream;
   ctx->stream = cs;  // the launchers capture on the context's stream
   int rc = SEIRD_OK;
   std::vector<int64_t> launches(1, 0);
-  cudaGraphNode_t prev = nullptr;
+  cudaGraph_t parent = g;
+  cudaGraphNode_t dep = nullptr;  // node j's predecessor inside its parent
   for (int j = 0; j < m && e == cudaSuccess && rc == SEIRD_OK; ++j) {
     cudaGraphNodeParams np{};
     np.type = cudaGraphNodeTypeConditional;
-    np.conditional.handle = hnd[j];
+    np.conditional.handle = hnd;
     np.conditional.type = cudaGraphCondTypeIf;
     np.conditional.size = 1;
     cudaGraphNode_t node = nullptr;
-    e = cudaGraphAddNode(&node, g, prev ? &prev : nullptr, nullptr, prev ? 1 : 0, &np);
+    e = cudaGraphAddNode(&node, parent, dep ? &dep : nullptr, nullptr, dep ? 1 : 0, &np);
     if (e != cudaSuccess) break;
     cudaGraph_t body = np.conditional.phGraph_out[0];
-    e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
-    if (e != cudaSuccess) break;
     CycleCtl cc;
     cc.ctl = ctx->cyc_ctl;
     cc.tol = ctx->scal + 10;
     cc.has_next = j + 1 < m;
-    cc.next = cc.has_next ? hnd[j + 1] : 0;
+    if (cc.has_next) {  // the next node's condition, set by this iteration's Givens kernel
+      e = cudaGraphConditionalHandleCreate(&cc.next, body, 0u, 0);
+      if (e != cudaSuccess) break;
+    }
+    e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) break;
     const int64_t k0 = launch_total();
     rc = arnoldi_iteration(ctx, j, cc);
     launches.push_back(launches.back() + launch_total() - k0);
     count_launches(k0 - launch_total());  // captured, not run
+    cudaStreamCaptureStatus st;
+    const cudaGraphNode_t* last = nullptr;
+    size_t nlast = 0;
+    e = cudaStreamGetCaptureInfo(cs, &st, nullptr, nullptr, &last, nullptr, &nlast);
+    dep = (e == cudaSuccess && nlast == 1) ? last[0] : nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(cs, &body);
     if (e == cudaSuccess) e = e2;
-    prev = node;
+    if (e == cudaSuccess && !dep) e = cudaErrorStreamCaptureUnjoined;  // the capture must end in one node
+    parent = body;
+    hnd = cc.next;
   }
   ctx->stream = saved;
   if (e == cudaSuccess && rc == SEIRD_OK) e = cudaGraphInstantiate(&ctx->cycle_exec, g, 0);
