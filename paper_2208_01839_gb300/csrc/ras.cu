@@ -292,11 +292,11 @@ __global__ void __launch_bounds__(256, 4) k_ilu_solve(RasDev d, const double* __
   __shared__ __align__(8) uint64_t empty[NS];
   __shared__ __align__(16) int4 info[RR];
   __shared__ int slot_vb[NS], slot_vr[NS], slot_n[NS];  // virtual ring starts and row count of a stage
+  __shared__ int slot_k0[NS];                            // sweep position of a stage's first row
   __shared__ int abort_at;  // first stage at which a consumer warp's wait gave up (INT_MAX: none)
   T* ring = reinterpret_cast<T*>(smem_raw);
   const int p = blockIdx.x;
   const int32_t r0 = d.sd_row0[p];
-  const int32_t nl = d.sd_row0[p + 1] - r0;
   T* y = ywk<T>(d) + 5 * (int64_t)r0;
   T* zz = zwk<T>(d) + 5 * (int64_t)r0;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -348,6 +348,7 @@ __global__ void __launch_bounds__(256, 4) k_ilu_solve(RasDev d, const double* __
       slot_vb[sl] = sb;
       slot_vr[sl] = sr;
       slot_n[sl] = nr;
+      slot_k0[sl] = q0;
       const uint32_t bytes_b = (uint32_t)nb * BS * (uint32_t)sizeof(T);
       const uint32_t bytes_i = (uint32_t)nr * (uint32_t)sizeof(int4);
       mbar_arrive_tx(&full[sl], bytes_b + bytes_i);  // releases the slot fields above to the consumers
@@ -364,12 +365,12 @@ __global__ void __launch_bounds__(256, 4) k_ilu_solve(RasDev d, const double* __
   }
 
   // ---- consumers (warps 0-6)
+  // Solution entries are numbered by their position in the sweep: y (forward) and
+  // z (backward) of position k live at 5 k in the subdomain's work arrays, so a
+  // stage writes one contiguous run and reads the runs of earlier stages.  (A
+  // shared-memory window of recent entries measured slower: the dependency loads
+  // hit L1, and the window's shared memory comes out of L1.)
   const int rw = lane / 5, cpt = lane - 5 * rw;
-  for (int32_t idx = tid; idx < 5 * nl; idx += SOLVE_CONSUMERS) {
-    const int32_t l = idx / 5, cc = idx - 5 * l;
-    y[idx] = (T)r[5 * (int64_t)d.sd_node[r0 + l] + cc];
-  }
-  consumers_sync();
   // A warp whose wait gives up skips the stage and records it; every consumer
   // reads abort_at after the named barrier that closes the stage, and only
   // values <= g (written before that barrier) end the loop at stage g, so all
@@ -383,29 +384,31 @@ __global__ void __launch_bounds__(256, 4) k_ilu_solve(RasDev d, const double* __
     const T* B = ring + (size_t)(slot_vb[sl] % RB) * BS;
     const int4* inf = info + slot_vr[sl] % RR;
     const int nrows = landed ? slot_n[sl] : 0;
+    const int k0 = slot_k0[sl];
+    T* vec = fw ? y : zz;
     for (int qb = warp * 6; qb < nrows; qb += 6 * (SOLVE_CONSUMERS / 32)) {
       const int q = qb + rw;
       const bool act = lane < 30 && q < nrows;
-      int32_t i = 0, st = 0, cn = 0;
+      int32_t st = 0, cn = 0, onode = -1;
       T acc = T(0), acc2 = T(0);
       if (act) {
         const int4 rec = inf[q];
-        i = rec.x;
         st = rec.y;
         cn = rec.z;
-        acc = y[5 * i + cpt];
+        onode = rec.w;
+        // forward: r of the row's node; backward: the row's forward result
+        acc = fw ? (T)r[5 * (int64_t)rec.x + cpt] : y[5 * rec.x + cpt];
       }
-      // y_i -= sum_k L_ik y_k (forward) or y_i - sum_j U_ij z_j (backward, block 0 is the
-      // inverted pivot).  The solution entries of CH blocks are loaded before any of
-      // their FMAs, so a row waits for one memory latency per CH blocks, not per block.
+      // y_k -= sum L y_j (forward) or y_k - sum U z_j (backward, block 0 is the
+      // inverted pivot).  The entries of CH blocks are loaded before any of their
+      // FMAs, so a row waits for one memory latency per CH blocks, not per block.
       constexpr int CH = sizeof(T) == 8 ? 3 : 4;  // FP64: keeps 4 CTAs per SM without spills
-      const T* vec = fw ? y : zz;
       for (int32_t j = fw ? 0 : 1; j < cn; j += CH) {
         const int nb = min(CH, cn - j);
         T xv[CH][5];
 #pragma unroll
         for (int u = 0; u < CH; ++u) {
-          const T* vk = vec + 5 * col_of(B[(st + j + min(u, nb - 1)) * BS + 25]);
+          const T* vk = vec + 5 * (int64_t)col_of(B[(st + j + min(u, nb - 1)) * BS + 25]);
 #pragma unroll
           for (int mm = 0; mm < 5; ++mm) xv[u][mm] = vk[mm];
         }
@@ -422,37 +425,31 @@ __global__ void __launch_bounds__(256, 4) k_ilu_solve(RasDev d, const double* __
         }
       }
       acc -= acc2;
-      if (fw) {
-        if (act) y[5 * i + cpt] = acc;
-      } else {
-        // z_i = U_ii^{-1} (...): the five partial results of row i sit in lanes 5 rw .. 5 rw + 4
-        T v = T(0);
+      const int kq = k0 + q;  // this row's position
+      T v = acc;
+      if (!fw) {
+        // z = U_kk^{-1} (...): the five partial results of the row sit in lanes 5 rw .. 5 rw + 4
+        v = T(0);
         const T* Dv = B + st * BS + 5 * cpt;
 #pragma unroll
         for (int mm = 0; mm < 5; ++mm) {
           const T am = __shfl_sync(FULL, acc, 5 * rw + mm);
           if (act) v = fmaT(Dv[mm], am, v);
         }
-        if (act) zz[5 * i + cpt] = v;
+      }
+      if (act) {
+        vec[5 * (int64_t)kq + cpt] = v;
+        if (!fw && onode >= 0) z[5 * (int64_t)onode + cpt] = (TZ)v;
       }
     }
-    consumers_sync();  // every row of this level is written; the stage's ring space is free
+    consumers_sync();  // every row of this stage is written; the stage's ring space is free
     if (*(volatile int*)&abort_at <= g) {
       aborted = true;
       break;
     }
     if (tid == 0) mbar_arrive(&empty[sl]);
   }
-  if (aborted) {
-    if (tid == 0) atomicOr(err, 8);
-    return;
-  }
-  const int32_t own0 = d.own_ptr[p], own1 = d.own_ptr[p + 1];
-  for (int32_t idx = tid; idx < 5 * nl; idx += SOLVE_CONSUMERS) {
-    const int32_t l = idx / 5, cc = idx - 5 * l;
-    const int32_t node = d.sd_node[r0 + l];
-    if (node >= own0 && node < own1) z[5 * (int64_t)node + cc] = (TZ)zz[idx];
-  }
+  if (aborted && tid == 0) atomicOr(err, 8);
 }
 
 // ---- coarse space --------------------------------------------------------

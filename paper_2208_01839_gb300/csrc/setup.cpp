@@ -382,6 +382,13 @@ int build_setup(const seird_mesh* mesh, const seird_options* opt, HostSetup& hs,
   }
 
   // ---- ILU(0) solve plans ---------------------------------------------------
+  // The solve numbers a subdomain's solution entries by their position in the
+  // sweep (forward y and backward z each in their own order), so the column of
+  // every factor block is the position of the entry it multiplies, and a row
+  // record holds: forward (node, first block, block count, 0); backward (forward
+  // position of the row, first block, block count, node if the subdomain owns it
+  // else -1).
+  std::vector<int32_t> posf, posd;
   for (int dir = 0; dir < 2; ++dir) {
     HostSetup::SolvePlan& sp = dir == 0 ? hs.sp_fwd : hs.sp_bwd;
     const std::vector<int32_t>& order = dir == 0 ? hs.fwd_order : hs.bwd_order;
@@ -390,6 +397,13 @@ int build_setup(const seird_mesh* mesh, const seird_options* opt, HostSetup& hs,
     sp.sd_lev0.assign(1, 0);
     for (int32_t q = 0; q < P; ++q) {
       const int32_t r0 = hs.sd_row0[q];
+      const int32_t nlq = hs.sd_row0[q + 1] - r0;
+      posf.assign(nlq, 0);
+      posd.assign(nlq, 0);
+      for (int32_t k = 0; k < nlq; ++k) {
+        posf[hs.fwd_order[r0 + k]] = k;
+        posd[order[r0 + k]] = k;
+      }
       const int32_t nlev = lev0[q + 1] - lev0[q] - 1;
       sp.levpos.push_back(0);
       sp.levblk.push_back((int64_t)sp.src.size());
@@ -413,21 +427,23 @@ int build_setup(const seird_mesh* mesh, const seird_options* opt, HostSetup& hs,
           sp.row.push_back(i);
           sp.start.push_back((int64_t)sp.src.size());
           sp.cnt.push_back(nb);
-          sp.info.push_back(i);
+          const int32_t node = hs.sd_node[R];
+          const bool owned = node >= hs.own_ptr[q] && node < hs.own_ptr[q + 1];
+          sp.info.push_back(dir == 0 ? node : posf[i]);
           sp.info.push_back((int32_t)((int64_t)sp.src.size() - sp.levblk.back()));
           sp.info.push_back(nb);
-          sp.info.push_back(0);
+          sp.info.push_back(dir == 0 ? 0 : (owned ? node : -1));
           if (dir == 0) {
             for (int64_t a = hs.l_row_ptr[R]; a < hs.l_diag[R]; ++a) {
               sp.src.push_back(a);
-              sp.col.push_back(hs.l_col[a]);
+              sp.col.push_back(posf[hs.l_col[a]]);
             }
           } else {
             sp.src.push_back(-1 - R);
-            sp.col.push_back(i);
+            sp.col.push_back(posd[i]);
             for (int64_t a = hs.l_diag[R] + 1; a < hs.l_row_ptr[R + 1]; ++a) {
               sp.src.push_back(a);
-              sp.col.push_back(hs.l_col[a]);
+              sp.col.push_back(posd[hs.l_col[a]]);
             }
           }
           in_level += nb;
