@@ -39,7 +39,7 @@ FALLBACK_HBM_GBS = 6800.0
 # full launch by the units it processes (traffic grows in proportion).
 NCU_TRAFFIC = {
     ("spmv", "fp64"): (307.414e6, 1400635, "nnzb"),  # profiles/k_bsr_spmv_ontario200k.md
-    ("ilu_solve", "fp64"): (384.383e6, 1577927, "subdomain_blocks"),  # profiles/k_ilu_solve_ontario200k.md (v7)
+    ("ilu_solve", "fp64"): (374.700e6, 1577927, "subdomain_blocks"),  # profiles/k_ilu_solve_ontario200k.md (v8)
 }
 
 # kernel classes with one kernel launch per timed call, and their algorithmic
