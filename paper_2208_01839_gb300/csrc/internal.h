@@ -242,6 +242,7 @@ struct seird_ctx {
   double* cband = nullptr;  // [P][2*cband+1][25] banded coarse matrix / factors
   double* cdinv = nullptr;  // [P][25]
   double* crhs = nullptr;   // [2][5P]
+  float* cy32 = nullptr;    // [5P] FP32 copy of the coarse solution (mixed path)
   double* ainvT = nullptr;  // [5P][5P] explicit coarse inverse (transposed)
   bool pc_ready = false;
   // launch shapes (options.autotune)

@@ -195,6 +195,7 @@ struct CoarseDev {
   double* cdinv;
   double* crhs;    // [2 * 5P]: Z^T r, then A_c^{-1} Z^T r
   double* ainvT;   // [5P][5P] explicit inverse, transposed (NULL: banded solve per apply)
+  float* y32;      // [5P] FP32 copy of A_c^{-1} Z^T r for the mixed-precision path
 };
 void launch_coarse_assemble(const CoarseDev& c, const double* val, const float* val32, cudaStream_t s);
 void launch_az_build(int64_t nseg, const int32_t* az_blk, const double* val, const float* val32, double* azval,
@@ -205,6 +206,10 @@ void launch_coarse_factor(const CoarseDev& c, int32_t* err, cudaStream_t s);
 template <class TZ>
 void launch_coarse_apply_add(const CoarseDev& c, int64_t n, const double* r, TZ* z, cudaStream_t s);
 void launch_coarse_solve(const CoarseDev& c, const double* r, cudaStream_t s);
+// mixed-precision path, after launch_coarse_solve: y32 = (float) y, then z += Z y32 in FP32,
+// and t -= (J Z) y32 with FP32 products (accumulated in FP32, subtracted in FP64)
+void launch_coarse_y32(const CoarseDev& c, cudaStream_t s);
+void launch_coarse_prolong32(const CoarseDev& c, int64_t n, float* z, cudaStream_t s);
 template <class TZ>
 void launch_coarse_prolong(const CoarseDev& c, int64_t n, TZ* z, cudaStream_t s);
 

@@ -673,6 +673,20 @@ __global__ void k_coarse_prolong_add(int64_t n, const int32_t* __restrict__ owne
   }
 }
 
+// z += Z y in FP32 (mixed path): every node adds its unit's coarse value
+__global__ void k_coarse_prolong_add32(int64_t n, const int32_t* __restrict__ owner, const int32_t* __restrict__ cpos,
+                                       const float* __restrict__ y, float* __restrict__ z) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < 5 * n; g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = g / 5;
+    z[g] += y[5 * (int64_t)cpos[owner[i]] + (g - 5 * i)];
+  }
+}
+
+__global__ void k_coarse_to_f32(int n, const double* __restrict__ y, float* __restrict__ y32) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < n) y32[g] = (float)y[g];
+}
+
 }  // namespace
 
 void launch_ilu_factor(const RasDev& d, const double* val, const float* val32, int32_t* err, bool fp32,
@@ -771,7 +785,19 @@ void launch_coarse_prolong(const CoarseDev& c, int64_t n, TZ* z, cudaStream_t s)
   count_launch();
 }
 template void launch_coarse_prolong<double>(const CoarseDev&, int64_t, double*, cudaStream_t);
-template void launch_coarse_prolong<float>(const CoarseDev&, int64_t, float*, cudaStream_t);
+
+void launch_coarse_y32(const CoarseDev& c, cudaStream_t s) {
+  const int nc = 5 * c.P;
+  k_coarse_to_f32<<<(nc + 255) / 256, 256, 0, s>>>(nc, c.ainvT ? c.crhs + nc : c.crhs, c.y32);
+  count_launch();
+}
+
+void launch_coarse_prolong32(const CoarseDev& c, int64_t n, float* z, cudaStream_t s) {
+  int64_t g = (5 * n + 255) / 256;
+  if (g > 152 * 8) g = 152 * 8;
+  k_coarse_prolong_add32<<<(int)g, 256, 0, s>>>(n, c.owner, c.cpos, c.y32, z);
+  count_launch();
+}
 
 template <class TZ>
 void launch_coarse_apply_add(const CoarseDev& c, int64_t n, const double* r, TZ* z, cudaStream_t s) {
@@ -779,7 +805,6 @@ void launch_coarse_apply_add(const CoarseDev& c, int64_t n, const double* r, TZ*
   launch_coarse_prolong<TZ>(c, n, z, s);
 }
 template void launch_coarse_apply_add<double>(const CoarseDev&, int64_t, const double*, double*, cudaStream_t);
-template void launch_coarse_apply_add<float>(const CoarseDev&, int64_t, const double*, float*, cudaStream_t);
 
 // A Z segments: azval[s] = sum of the J blocks of segment s (one thread per entry)
 template <class TV, class TA>
@@ -813,6 +838,24 @@ __global__ void k_az_sub(int64_t n, const int64_t* __restrict__ az_ptr, const in
   t[g] -= acc;
 }
 
+// the same with FP32 products for the mixed path (its result feeds an FP32 subdomain solve)
+__global__ void k_az_sub32(int64_t n, const int64_t* __restrict__ az_ptr, const int32_t* __restrict__ az_unit,
+                           const int32_t* __restrict__ cpos, const float* __restrict__ azval,
+                           const float* __restrict__ y, double* __restrict__ t) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= 5 * n) return;
+  const int64_t i = g / 5;
+  const int rr = (int)(g - 5 * i);
+  float acc = 0.0f;
+  for (int64_t s = az_ptr[i]; s < az_ptr[i + 1]; ++s) {
+    const float* A = azval + 25 * s + 5 * rr;
+    const float* ys = y + 5 * (int64_t)cpos[az_unit[s]];
+#pragma unroll
+    for (int mm = 0; mm < 5; ++mm) acc = fmaf(A[mm], ys[mm], acc);
+  }
+  t[g] -= (double)acc;
+}
+
 void launch_az_build(int64_t nseg, const int32_t* az_blk, const double* val, const float* val32, double* azval,
                      float* azval32, bool fp32, cudaStream_t s) {
   const unsigned g = (unsigned)((25 * nseg + 255) / 256);
@@ -825,7 +868,7 @@ void launch_az_sub(const CoarseDev& c, int64_t n, const int64_t* az_ptr, const i
                    const double* azval, const float* azval32, bool fp32, double* t, cudaStream_t s) {
   const double* y = c.ainvT ? c.crhs + 5 * (int64_t)c.P : c.crhs;
   const unsigned g = (unsigned)((5 * n + 255) / 256);
-  if (fp32) k_az_sub<float><<<g, 256, 0, s>>>(n, az_ptr, az_unit, c.cpos, azval32, y, t);
+  if (fp32) k_az_sub32<<<g, 256, 0, s>>>(n, az_ptr, az_unit, c.cpos, azval32, c.y32, t);
   else k_az_sub<double><<<g, 256, 0, s>>>(n, az_ptr, az_unit, c.cpos, azval, y, t);
   count_launch();
 }

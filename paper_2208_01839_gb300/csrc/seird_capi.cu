@@ -274,6 +274,7 @@ CoarseDev coarse_dev(seird_ctx* ctx) {
   c.cdinv = ctx->cdinv;
   c.crhs = ctx->crhs;
   c.ainvT = ctx->ainvT;
+  c.y32 = ctx->cy32;
   return c;
 }
 
@@ -337,6 +338,7 @@ int pc_apply32(seird_ctx* ctx, const double* r, float* z) {
     {
       KTimer kt_(ctx, SEIRD_K_COARSE_APPLY);
       launch_coarse_solve(cd, r, ctx->stream);
+      launch_coarse_y32(cd, ctx->stream);
       CK(cudaMemcpyAsync(ctx->pct, r, sizeof(double) * len, cudaMemcpyDeviceToDevice, ctx->stream));
       launch_az_sub(cd, ctx->hs.n, ctx->az_ptr, ctx->az_unit, ctx->azval, ctx->azval32, true, ctx->pct, ctx->stream);
     }
@@ -346,7 +348,7 @@ int pc_apply32(seird_ctx* ctx, const double* r, float* z) {
     }
     {
       KTimer kt_(ctx, SEIRD_K_COARSE_APPLY);
-      launch_coarse_prolong<float>(cd, ctx->hs.n, z, ctx->stream);
+      launch_coarse_prolong32(cd, ctx->hs.n, z, ctx->stream);
     }
     CK(cudaGetLastError());
     return SEIRD_OK;
@@ -357,14 +359,19 @@ int pc_apply32(seird_ctx* ctx, const double* r, float* z) {
   }
   if (ctx->opt.coarse == 1) {
     KTimer kt_(ctx, SEIRD_K_COARSE_APPLY);
-    launch_coarse_apply_add<float>(coarse_dev(ctx), ctx->hs.n, r, z, ctx->stream);
+    const CoarseDev cd = coarse_dev(ctx);
+    launch_coarse_solve(cd, r, ctx->stream);
+    launch_coarse_y32(cd, ctx->stream);
+    launch_coarse_prolong32(cd, ctx->hs.n, z, ctx->stream);
   } else if (ctx->opt.coarse == 2) {  // Eq. RAS_2L: coarse on r - J z, then RAS on the new residual
     TRY(spmv32(ctx, z, ctx->pct));
     launch_axpby(len, 1.0, r, -1.0, ctx->pct, ctx->pct, ctx->stream);
     {
       KTimer kt_(ctx, SEIRD_K_COARSE_APPLY);
       const CoarseDev cd = coarse_dev(ctx);
-      launch_coarse_apply_add<float>(cd, ctx->hs.n, ctx->pct, z, ctx->stream);
+      launch_coarse_solve(cd, ctx->pct, ctx->stream);
+      launch_coarse_y32(cd, ctx->stream);
+      launch_coarse_prolong32(cd, ctx->hs.n, z, ctx->stream);
       // r - J (z + Z y) = (r - J z) - (J Z) y, with J Z summed at set-up
       launch_az_sub(cd, ctx->hs.n, ctx->az_ptr, ctx->az_unit, ctx->azval, ctx->azval32, true, ctx->pct, ctx->stream);
     }
@@ -1391,6 +1398,7 @@ static int create_impl(seird_ctx* ctx, const seird_mesh* mesh, const seird_param
     TRY(dalloc(ctx, &ctx->cband, 25 * (size_t)hs.Pc * (2 * hs.cband + 1)));
     TRY(dalloc(ctx, &ctx->cdinv, 25 * (size_t)hs.Pc));
     TRY(dalloc(ctx, &ctx->crhs, 2 * nc));
+    TRY(dalloc(ctx, &ctx->cy32, nc));
     if (dense) TRY(dalloc(ctx, &ctx->ainvT, (size_t)nc * nc));
   }
   CK(cudaDeviceSynchronize());
