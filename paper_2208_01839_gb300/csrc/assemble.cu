@@ -33,6 +33,7 @@ __constant__ double cQC[2][7][6];
 // [10] W1 D1, [11] W2 D2, [12] W0/9, [13] W1 A1^2, [14] W1 (B1^2 - A1^2), [15] W1 A1 B1,
 // [16] -W1 A1 D1, [17..20] the same for orbit 2.
 __constant__ double cORB[21];
+__constant__ float cORBf[21];  // the same in FP32 (FP32 Jacobian record)
 
 void upload_quadrature() {
   double L[2][7][3] = {};
@@ -68,8 +69,13 @@ void upload_quadrature() {
   const double orb[21] = {A1, D1, W1, A2, D2, W2, W0, W0 / 3.0, W1 * A1, W2 * A2, W1 * D1, W2 * D2, W0 / 9.0,
                           W1 * A1 * A1, W1 * (B1 * B1 - A1 * A1), W1 * A1 * B1, -W1 * A1 * D1,
                           W2 * A2 * A2, W2 * (B2 * B2 - A2 * A2), W2 * A2 * B2, -W2 * A2 * D2};
-  for (int k = 0; k < 21; ++k) O[k] = orb[k];
+  float Of[21];
+  for (int k = 0; k < 21; ++k) {
+    O[k] = orb[k];
+    Of[k] = (float)orb[k];
+  }
   cudaMemcpyToSymbol(cORB, O, sizeof(O));
+  cudaMemcpyToSymbol(cORBf, Of, sizeof(Of));
 }
 
 namespace {
@@ -104,6 +110,12 @@ struct TriT {
   T area, gx[3], gy[3];
   int32_t v[3];
 };
+
+template <class T>
+__device__ __forceinline__ T orb(int i) {
+  if constexpr (sizeof(T) == 4) return cORBf[i];
+  else return cORB[i];
+}
 
 // x > 0 and not NaN, from the bits (integer pipe): 0 < bits <= bits(+inf)
 __device__ __forceinline__ bool positive(double x) {
@@ -227,9 +239,9 @@ __global__ void __launch_bounds__(128) k_residual_elem5(int64_t m, const int32_t
   const double m12 = T.area * (1.0 / 12.0);  // (phi_a, phi_b) = |T| (1 + delta_ab) / 12
 #pragma unroll
   for (int c = 0; c < 5; ++c) {
-    const double sw = w[0][c] + w[1][c] + w[2][c];
+    const double msw = m12 * (w[0][c] + w[1][c] + w[2][c]);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) Fe[a][c] = m12 * (w[a][c] + sw);
+    for (int a = 0; a < 3; ++a) Fe[a][c] = fma(m12, w[a][c], msw);
   }
   // diffusion: dt nubar_c |T| mean_T(N) grad u_c . grad phi_a  (nubar_D = 0)
   const double dNA = r.dt * Nbar * T.area;
@@ -239,7 +251,7 @@ __global__ void __launch_bounds__(128) k_residual_elem5(int64_t m, const int32_t
     const double gux = coef * (u[0][c] * T.gx[0] + u[1][c] * T.gx[1] + u[2][c] * T.gx[2]);
     const double guy = coef * (u[0][c] * T.gy[0] + u[1][c] * T.gy[1] + u[2][c] * T.gy[2]);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) Fe[a][c] += gux * T.gx[a] + guy * T.gy[a];
+    for (int a = 0; a < 3; ++a) Fe[a][c] = fma(gux, T.gx[a], fma(guy, T.gy[a], Fe[a][c]));
   }
   // transmission s -> e, kappa s (beta_I i + beta_E e) b, at the rule's points
   double bv[3] = {1.0, 1.0, 1.0};
@@ -270,11 +282,12 @@ __global__ void __launch_bounds__(128) k_residual_elem5(int64_t m, const int32_t
     T1[k] = (1.0 - r.A * rq[1 + k]) * s1 * l1 * (BF ? A1 * Sb + D1 * bv[k] : 1.0);
     T2[k] = (1.0 - r.A * rq[4 + k]) * s2 * l2 * (BF ? A2 * Sb + D2 * bv[k] : 1.0);
   }
-  const double sh = cORB[7] * T0 + cORB[8] * (T1[0] + T1[1] + T1[2]) + cORB[9] * (T2[0] + T2[1] + T2[2]);
   const double dA = r.dt * T.area;
+  const double sh = dA * (cORB[7] * T0 + cORB[8] * (T1[0] + T1[1] + T1[2]) + cORB[9] * (T2[0] + T2[1] + T2[2]));
+  const double e1 = dA * cORB[10], e2 = dA * cORB[11];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const double v = dA * (sh + cORB[10] * T1[a] + cORB[11] * T2[a]);
+    const double v = fma(e1, T1[a], fma(e2, T2[a], sh));
     Fe[a][0] += v;
     Fe[a][1] -= v;
   }
@@ -425,9 +438,23 @@ __global__ void __launch_bounds__(128) k_jac_record(int64_t m, const int32_t* __
                                                     const double* __restrict__ bfield, Rates rin,
                                                     T* __restrict__ rec, int32_t* err) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  // A, beta_I, beta_E, dt, nubar_S..R in type T (see rate_consts)
+  constexpr bool kCTA = sizeof(T) == 4;
+  __shared__ T srk[8];
+  if (kCTA && !rin.tab) {
+    if (threadIdx.x == 0) {
+      srk[0] = (T)rin.A;
+      srk[1] = (T)rin.bi;
+      srk[2] = (T)rin.be;
+      srk[3] = (T)rin.dt;
+      for (int c = 0; c < 4; ++c) srk[4 + c] = (T)rin.nu[c];
+    }
+    __syncthreads();
+  }
   if (t >= m) return;
   const Tri Tg = tri_of(tri, xy, geo, t);
   const Rates r = rates_at(rin, Tg.v[0]);
+  const bool shr = kCTA && !rin.tab;
   TriT<T> Tt;
   Tt.area = (T)Tg.area;
 #pragma unroll
@@ -450,7 +477,7 @@ __global__ void __launch_bounds__(128) k_jac_record(int64_t m, const int32_t* __
   out[0] = Tt.area;
   // N-weighted stiffness dt |T| mean(N) grad phi_a . grad phi_b
   // the gather reads the sums below already scaled: K and P by dt, G_c by dt nu_c
-  const T dtT = (T)r.dt;
+  const T dtT = shr ? srk[3] : (T)r.dt;
   const T an = dtT * Tt.area * Nbar;
   out[REC_K + 0] = an * (Tt.gx[0] * Tt.gx[0] + Tt.gy[0] * Tt.gy[0]);
   out[REC_K + 1] = an * (Tt.gx[1] * Tt.gx[1] + Tt.gy[1] * Tt.gy[1]);
@@ -465,7 +492,7 @@ __global__ void __launch_bounds__(128) k_jac_record(int64_t m, const int32_t* __
     for (int c = 0; c < 4; ++c) {
       const T gux = u[0][c] * Tt.gx[0] + u[1][c] * Tt.gx[1] + u[2][c] * Tt.gx[2];
       const T guy = u[0][c] * Tt.gy[0] + u[1][c] * Tt.gy[1] + u[2][c] * Tt.gy[2];
-      const T gsc = a3 * dtT * (T)r.nu[c];
+      const T gsc = a3 * dtT * (shr ? srk[4 + c] : (T)r.nu[c]);
 #pragma unroll
       for (int a = 0; a < 3; ++a) out[REC_G + 4 * a + c] = gsc * (gux * Tt.gx[a] + guy * Tt.gy[a]);
     }
@@ -486,12 +513,12 @@ __global__ void __launch_bounds__(128) k_jac_record(int64_t m, const int32_t* __
   T Nv[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) Nv[a] = u[a][0] + u[a][1] + u[a][2] + u[a][3] + u[a][4];
-  const T A = (T)r.A, bi = (T)r.bi, be = (T)r.be;
+  const T A = shr ? srk[0] : (T)r.A, bi = shr ? srk[1] : (T)r.bi, be = shr ? srk[2] : (T)r.be;
   bool bad = false;
   if (RULE == 0 && !PIC) {
     // the degree-5 rule by its orbits (cORB): per moment, the centroid value, the two
     // orbit sums and the six point values give the six pair moments
-    const T A1 = (T)cORB[0], D1 = (T)cORB[1], A2 = (T)cORB[3], D2 = (T)cORB[4];
+    const T A1 = orb<T>(0), D1 = orb<T>(1), A2 = orb<T>(3), D2 = orb<T>(4);
     T l[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) l[a] = bi * u[a][2] + be * u[a][1];
@@ -531,7 +558,7 @@ __global__ void __launch_bounds__(128) k_jac_record(int64_t m, const int32_t* __
     // P[k][a] (a < 3, pair (a, a)) and P[k][3 + (2 - c)] (the pair opposite vertex c) take the
     // point values; the orbit sums and the centroid value are added to all pairs at the end
     const T ar = dtT * Tt.area;
-    const T cdR1 = ar * (T)cORB[14], coR1 = ar * (T)cORB[16], cdR2 = ar * (T)cORB[18], coR2 = ar * (T)cORB[20];
+    const T cdR1 = ar * orb<T>(14), coR1 = ar * orb<T>(16), cdR2 = ar * orb<T>(18), coR2 = ar * orb<T>(20);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       T rho1[4], rho2[4];
@@ -545,8 +572,8 @@ __global__ void __launch_bounds__(128) k_jac_record(int64_t m, const int32_t* __
         P[j][5 - k] = coR1 * rho1[j] + coR2 * rho2[j];  // pairs (1,2) (0,2) (0,1) at 5, 4, 3
       }
     }
-    const T c0 = ar * (T)cORB[12], cdS1 = ar * (T)cORB[13], coS1 = ar * (T)cORB[15];
-    const T cdS2 = ar * (T)cORB[17], coS2 = ar * (T)cORB[19];
+    const T c0 = ar * orb<T>(12), cdS1 = ar * orb<T>(13), coS1 = ar * orb<T>(15);
+    const T cdS2 = ar * orb<T>(17), coS2 = ar * orb<T>(19);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const T base = c0 * rc[j];
@@ -596,6 +623,33 @@ __global__ void __launch_bounds__(128) k_jac_record(int64_t m, const int32_t* __
 #pragma unroll
     for (int s = 0; s < 6; ++s) out[REC_P + 4 * s + k] = P[k][s];
   out[REC_K + 6] = T(0);
+}
+
+// dt, nubar_S..R, alpha, mu, sigma, gamma_E, gamma_R, gamma_D in type T.  FP32 kernels with one
+// set of rates (no per-sample table) convert them once per CTA: GB300 converts FP64 to FP32
+// at its FP64 rate, which per thread would cost as much as the block's arithmetic.  Every
+// thread of the CTA calls it.
+template <class T>
+__device__ __forceinline__ void rate_consts(const Rates& rin, const Rates& r, T (&k)[11]) {
+  auto fill = [](const Rates& q, T* o) {
+    o[0] = (T)q.dt;
+    for (int c = 0; c < 4; ++c) o[1 + c] = (T)q.nu[c];
+    o[5] = (T)q.alpha;
+    o[6] = (T)q.mu;
+    o[7] = (T)q.sigma;
+    o[8] = (T)q.ge;
+    o[9] = (T)q.gr;
+    o[10] = (T)q.gd;
+  };
+  if (sizeof(T) == 4 && !rin.tab) {
+    __shared__ T sk[11];
+    if (threadIdx.x == 0) fill(rin, sk);
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 11; ++i) k[i] = sk[i];
+  } else {
+    fill(r, k);
+  }
 }
 
 // Writes each thread's 5x5 block B to val[25 k ...] through shared memory, so that a
@@ -657,10 +711,12 @@ __global__ void __launch_bounds__(128) k_jac_gather(int64_t nnzb, const int32_t*
   }
   if (RULE == 0) Mr = M;
   // K, G and P arrive scaled by dt (G_c by dt nubar_c), see k_jac_record
-  const T dt = (T)r.dt;
-  const T nu0 = (T)r.nu[0], nu1 = (T)r.nu[1], nu2 = (T)r.nu[2], nu3 = (T)r.nu[3];
+  T rk[11];
+  rate_consts<T>(rin, r, rk);
+  const T dt = rk[0];
+  const T nu0 = rk[1], nu1 = rk[2], nu2 = rk[3], nu3 = rk[4];
   const T dMr = dt * Mr;
-  const T alpha = (T)r.alpha, mu = (T)r.mu, sigma = (T)r.sigma, ge = (T)r.ge, gr = (T)r.gr, gd = (T)r.gd;
+  const T alpha = rk[5], mu = rk[6], sigma = rk[7], ge = rk[8], gr = rk[9], gd = rk[10];
   T B[5][5];
 #pragma unroll
   for (int i = 0; i < 5; ++i)
