@@ -74,9 +74,10 @@ void launch_beta_field(int64_t n, const double* xy, const seird_beta_schedule& s
 void launch_jacobian(int64_t nnzb, int64_t m, const int32_t* tri, const double* xy, const double* geo, const double* U,
                      const double* bfield, const Rates& r, int rule, void* rec, const int32_t* inc_ptr,
                      const int32_t* inc, void* val, bool fp32, bool picard, int32_t* err, cudaStream_t s);
+// y = A x, or y = b - A x when b != NULL
 template <class VT>
 void launch_spmv(int64_t nrow, const int32_t* rp, const int32_t* col, const VT* val, const double* x, double* y,
-                 cudaStream_t s, int tb = 256);
+                 cudaStream_t s, int tb = 256, const double* b = nullptr);
 void launch_f64_to_f32(int64_t n, const double* src, float* dst, cudaStream_t s);
 
 // vectors (length len, grid-stride)
@@ -173,7 +174,7 @@ void launch_ilu_reorg(const RasDev& d, int64_t nfwd, int64_t nbwd, const int64_t
 void launch_ilu_solve(const RasDev& d, const double* r, double* z, int32_t* err, cudaStream_t s);
 void launch_ilu_solve32(const RasDev& d, const double* r, float* z, int32_t* err, cudaStream_t s);
 void launch_spmv32(int64_t nrow, const int32_t* rp, const int32_t* col, const float* val, const float* x, double* y,
-                   cudaStream_t s, int tb = 256);
+                   cudaStream_t s, int tb = 256, const double* b = nullptr);
 void launch_multi_axpy32(int64_t len, int nv, const float* Zs, int64_t ld, const double* coef, double* x,
                          cudaStream_t s);
 void launch_f32_to_f64(int64_t n, const float* src, double* dst, cudaStream_t s);

@@ -16,12 +16,13 @@ constexpr int NVMAX = 65;  // restart <= 64 -> at most 65 basis vectors
 __device__ __forceinline__ double ld_val(const double* p) { return __ldg(p); }
 __device__ __forceinline__ double ld_val(const float* p) { return (double)__ldg(p); }
 
-// y = A x, 5x5 blocks.  One thread per scalar output row (block row i, row r):
-// all 32 lanes of every warp do useful FP64 work, 25 FMA per block per 5 threads.
+// y = A x (b == NULL) or y = b - A x, 5x5 blocks.  One thread per scalar output row (block
+// row i, row r): all 32 lanes of every warp do useful FP64 work, 25 FMA per block per 5 threads.
 template <class VT>
 __global__ void __launch_bounds__(512) k_bsr_spmv(int64_t nrow, const int32_t* __restrict__ rp,
                                                   const int32_t* __restrict__ col, const VT* __restrict__ val,
-                                                  const double* __restrict__ x, double* __restrict__ y) {
+                                                  const double* __restrict__ x, const double* __restrict__ b,
+                                                  double* __restrict__ y) {
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= 5 * nrow) return;
   const int64_t i = g / 5;
@@ -38,13 +39,15 @@ __global__ void __launch_bounds__(512) k_bsr_spmv(int64_t nrow, const int32_t* _
     acc = fma(ld_val(v + 3), __ldg(xj + 3), acc);
     acc = fma(ld_val(v + 4), __ldg(xj + 4), acc);
   }
-  y[g] = acc;
+  y[g] = b ? b[g] - acc : acc;
 }
 
-// Mixed-precision SpMV: FP32 values and FP32 input, FP32 arithmetic, FP64 output.
+// Mixed-precision SpMV: FP32 values and FP32 input, FP32 arithmetic, FP64 output (y = A x,
+// or y = b - A x when b != NULL).
 __global__ void __launch_bounds__(512) k_bsr_spmv32(int64_t nrow, const int32_t* __restrict__ rp,
                                                     const int32_t* __restrict__ col, const float* __restrict__ val,
-                                                    const float* __restrict__ x, double* __restrict__ y) {
+                                                    const float* __restrict__ x, const double* __restrict__ b,
+                                                    double* __restrict__ y) {
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= 5 * nrow) return;
   const int64_t i = g / 5;
@@ -58,7 +61,7 @@ __global__ void __launch_bounds__(512) k_bsr_spmv32(int64_t nrow, const int32_t*
 #pragma unroll
     for (int c = 0; c < 5; ++c) acc = fmaf(__ldg(v + c), __ldg(xj + c), acc);
   }
-  y[g] = (double)acc;
+  y[g] = b ? b[g] - (double)acc : (double)acc;
 }
 
 // x += sum_k coef[k] Z_k with FP32 Z: the sum is formed in FP32, added in FP64
@@ -389,21 +392,21 @@ inline int grid_for(int64_t len, int tb = 256, int cap = 152 * 8) {
 
 template <class VT>
 void launch_spmv(int64_t nrow, const int32_t* rp, const int32_t* col, const VT* val, const double* x, double* y,
-                 cudaStream_t s, int tb) {
+                 cudaStream_t s, int tb, const double* b) {
   if (nrow <= 0) return;
   const int64_t g = (5 * nrow + tb - 1) / tb;
-  k_bsr_spmv<VT><<<g, tb, 0, s>>>(nrow, rp, col, val, x, y);
+  k_bsr_spmv<VT><<<g, tb, 0, s>>>(nrow, rp, col, val, x, b, y);
   count_launch();
 }
 template void launch_spmv<double>(int64_t, const int32_t*, const int32_t*, const double*, const double*, double*,
-                                  cudaStream_t, int);
+                                  cudaStream_t, int, const double*);
 template void launch_spmv<float>(int64_t, const int32_t*, const int32_t*, const float*, const double*, double*,
-                                 cudaStream_t, int);
+                                 cudaStream_t, int, const double*);
 
 void launch_spmv32(int64_t nrow, const int32_t* rp, const int32_t* col, const float* val, const float* x, double* y,
-                   cudaStream_t s, int tb) {
+                   cudaStream_t s, int tb, const double* b) {
   if (nrow <= 0) return;
-  k_bsr_spmv32<<<(5 * nrow + tb - 1) / tb, tb, 0, s>>>(nrow, rp, col, val, x, y);
+  k_bsr_spmv32<<<(5 * nrow + tb - 1) / tb, tb, 0, s>>>(nrow, rp, col, val, x, b, y);
   count_launch();
 }
 

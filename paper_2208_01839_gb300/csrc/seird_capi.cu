@@ -327,8 +327,8 @@ int pc_setup(seird_ctx* ctx) {
   return SEIRD_OK;
 }
 
-int spmv32(seird_ctx* ctx, const float* x, double* y);
-int spmv(seird_ctx* ctx, const double* x, double* y);
+int spmv32(seird_ctx* ctx, const float* x, double* y, const double* b = nullptr);
+int spmv(seird_ctx* ctx, const double* x, double* y, const double* b = nullptr);
 
 // z = M^{-1} r with FP32 subdomain factors and an FP32 result (mixed path)
 int pc_apply32(seird_ctx* ctx, const double* r, float* z) {
@@ -364,8 +364,7 @@ int pc_apply32(seird_ctx* ctx, const double* r, float* z) {
     launch_coarse_y32(cd, ctx->stream);
     launch_coarse_prolong32(cd, ctx->hs.n, z, ctx->stream);
   } else if (ctx->opt.coarse == 2) {  // Eq. RAS_2L: coarse on r - J z, then RAS on the new residual
-    TRY(spmv32(ctx, z, ctx->pct));
-    launch_axpby(len, 1.0, r, -1.0, ctx->pct, ctx->pct, ctx->stream);
+    TRY(spmv32(ctx, z, ctx->pct, r));  // r - J z
     {
       KTimer kt_(ctx, SEIRD_K_COARSE_APPLY);
       const CoarseDev cd = coarse_dev(ctx);
@@ -424,8 +423,7 @@ int pc_apply(seird_ctx* ctx, const double* r, double* z) {
     launch_coarse_apply_add<double>(coarse_dev(ctx), ctx->hs.n, r, z, ctx->stream);
   } else if (ctx->opt.coarse == 2) {  // Eq. RAS_2L: coarse on r - J z, then RAS on the new residual
     const int64_t len = vlen(ctx);
-    TRY(spmv(ctx, z, ctx->pct));
-    launch_axpby(len, 1.0, r, -1.0, ctx->pct, ctx->pct, ctx->stream);
+    TRY(spmv(ctx, z, ctx->pct, r));  // r - J z
     {
       KTimer kt_(ctx, SEIRD_K_COARSE_APPLY);
       const CoarseDev cd = coarse_dev(ctx);
@@ -443,18 +441,20 @@ int pc_apply(seird_ctx* ctx, const double* r, double* z) {
   return SEIRD_OK;
 }
 
-int spmv(seird_ctx* ctx, const double* x, double* y) {
+// y = J x, or y = b - J x when b != NULL
+int spmv(seird_ctx* ctx, const double* x, double* y, const double* b) {
   KTimer kt_(ctx, SEIRD_K_SPMV);
-  if (mixed(ctx)) launch_spmv<float>(ctx->hs.n, ctx->row_ptr, ctx->col, ctx->val32, x, y, ctx->stream, ctx->spmv_tb);
-  else launch_spmv<double>(ctx->hs.n, ctx->row_ptr, ctx->col, ctx->val, x, y, ctx->stream, ctx->spmv_tb);
+  if (mixed(ctx))
+    launch_spmv<float>(ctx->hs.n, ctx->row_ptr, ctx->col, ctx->val32, x, y, ctx->stream, ctx->spmv_tb, b);
+  else launch_spmv<double>(ctx->hs.n, ctx->row_ptr, ctx->col, ctx->val, x, y, ctx->stream, ctx->spmv_tb, b);
   CK(cudaGetLastError());
   return SEIRD_OK;
 }
 
-// y = J x with the FP32 matrix copy and FP32 x (mixed path)
-int spmv32(seird_ctx* ctx, const float* x, double* y) {
+// y = J x (or b - J x) with the FP32 matrix copy and FP32 x (mixed path)
+int spmv32(seird_ctx* ctx, const float* x, double* y, const double* b) {
   KTimer kt_(ctx, SEIRD_K_SPMV);
-  launch_spmv32(ctx->hs.n, ctx->row_ptr, ctx->col, ctx->val32, x, y, ctx->stream, ctx->spmv_tb);
+  launch_spmv32(ctx->hs.n, ctx->row_ptr, ctx->col, ctx->val32, x, y, ctx->stream, ctx->spmv_tb, b);
   CK(cudaGetLastError());
   return SEIRD_OK;
 }
@@ -736,8 +736,7 @@ int gmres(seird_ctx* ctx, const double* b, double* x, double rtol, int* its_out,
     }
     if (its >= ctx->opt.gmres_maxit) break;
     // restart from the residual r = b - J x of the operator GMRES works with
-    TRY(spmv(ctx, x, ctx->w));
-    launch_axpby(len, 1.0, b, -1.0, ctx->w, ctx->w, s);
+    TRY(spmv(ctx, x, ctx->w, b));
     TRY(norm2(ctx, ctx->w, &rnorm));
     if (!std::isfinite(rnorm)) return fail(ctx, SEIRD_ENONFINITE, "gmres: non-finite restart residual");
     if (rnorm <= tol) {
