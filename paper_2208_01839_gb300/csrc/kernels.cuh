@@ -78,7 +78,6 @@ void launch_jacobian(int64_t nnzb, int64_t m, const int32_t* tri, const double* 
 template <class VT>
 void launch_spmv(int64_t nrow, const int32_t* rp, const int32_t* col, const VT* val, const double* x, double* y,
                  cudaStream_t s, int tb = 256, const double* b = nullptr);
-void launch_f64_to_f32(int64_t n, const double* src, float* dst, cudaStream_t s);
 
 // vectors (length len, grid-stride)
 void launch_norm2(int64_t len, const double* x, double* partial, int grid, double* out, cudaStream_t s);
@@ -108,7 +107,6 @@ constexpr int NV_STRIDE = 65;  // row stride of the CGS partial-sum buffer
 void launch_hsolve(int k, double* gm, int ldh, cudaStream_t s);
 void launch_gather5(int64_t n, const int32_t* idx, const double* src, double* dst, cudaStream_t s);
 void launch_scatter5(int64_t n, const int32_t* idx, const double* src, double* dst, cudaStream_t s);
-void launch_check_finite(int64_t len, const double* x, int32_t* err, cudaStream_t s);
 
 // discrete adjoint
 void launch_mass(int64_t n, int64_t m, const int32_t* tri, const double* xy, const double* V, double* elem,

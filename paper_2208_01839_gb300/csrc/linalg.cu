@@ -99,11 +99,6 @@ __global__ void k_f32_to_f64(int64_t n, const float* __restrict__ a, double* __r
     b[i] = (double)a[i];
 }
 
-__global__ void k_f64_to_f32(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    b[i] = (float)a[i];
-}
-
 template <int NT>
 __device__ __forceinline__ double block_sum(double v, double* sh) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -374,13 +369,6 @@ __global__ void k_scatter5(int64_t n, const int32_t* __restrict__ idx, const dou
   }
 }
 
-__global__ void k_check_finite(int64_t len, const double* __restrict__ x, int32_t* err) {
-  bool bad = false;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
-    bad |= !isfinite(x[i]);
-  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, 4);
-}
-
 inline int grid_for(int64_t len, int tb = 256, int cap = 152 * 8) {
   int64_t g = (len + tb - 1) / tb;
   if (g > cap) g = cap;
@@ -428,11 +416,6 @@ void launch_add32(int64_t len, const float* u, float* z, cudaStream_t s) {
 
 void launch_f32_to_f64(int64_t n, const float* src, double* dst, cudaStream_t s) {
   k_f32_to_f64<<<grid_for(n), 256, 0, s>>>(n, src, dst);
-  count_launch();
-}
-
-void launch_f64_to_f32(int64_t n, const double* src, float* dst, cudaStream_t s) {
-  k_f64_to_f32<<<grid_for(n), 256, 0, s>>>(n, src, dst);
   count_launch();
 }
 
@@ -523,11 +506,6 @@ void launch_gather5(int64_t n, const int32_t* idx, const double* src, double* ds
 
 void launch_scatter5(int64_t n, const int32_t* idx, const double* src, double* dst, cudaStream_t s) {
   k_scatter5<<<grid_for(5 * n), 256, 0, s>>>(n, idx, src, dst);
-  count_launch();
-}
-
-void launch_check_finite(int64_t len, const double* x, int32_t* err, cudaStream_t s) {
-  k_check_finite<<<grid_for(len), 256, 0, s>>>(len, x, err);
   count_launch();
 }
 
