@@ -402,7 +402,11 @@ __global__ void __launch_bounds__(256, 4) k_ilu_solve(RasDev d, const double* __
       // y_k -= sum L y_j (forward) or y_k - sum U z_j (backward, block 0 is the
       // inverted pivot).  The entries of CH blocks are loaded before any of their
       // FMAs, so a row waits for one memory latency per CH blocks, not per block.
-      constexpr int CH = sizeof(T) == 8 ? 3 : 4;  // FP64: keeps 4 CTAs per SM without spills
+      // A short row reloads its last block to fill the batch; a stage is bound by
+      // its busiest warp's instruction chain, so two blocks per batch measured best
+      // (2.0M nodes: FP32 0.91 ms against 0.96 / 0.95 / 0.94 / 1.02 ms for 1 / 4 / 3
+      // / 6 blocks; FP64 1.68 ms against 1.74 / 1.70 ms for 1 / 3).
+      constexpr int CH = 2;
       for (int32_t j = fw ? 0 : 1; j < cn; j += CH) {
         const int nb = min(CH, cn - j);
         T xv[CH][5];
