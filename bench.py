@@ -39,8 +39,8 @@ FALLBACK_HBM_GBS = 6800.0
 # full launch by the units it processes (traffic grows in proportion).
 NCU_TRAFFIC = {
     ("spmv", "fp64"): (307.414e6, 1400635, "nnzb"),  # profiles/k_bsr_spmv_ontario200k.md
-    ("ilu_solve", "fp64"): (374.700e6, 1577927, "subdomain_blocks"),  # profiles/k_ilu_solve_ontario200k.md (v8)
-    ("ilu_solve", "mixed"): (204.760e6, 1577927, "subdomain_blocks"),  # same file, FP32 instantiation
+    ("ilu_solve", "fp64"): (373.090e6, 1577927, "subdomain_blocks"),  # profiles/k_ilu_solve_ontario200k.md (v9)
+    ("ilu_solve", "mixed"): (202.650e6, 1577927, "subdomain_blocks"),  # same file, FP32 instantiation (v9)
 }
 
 # kernel classes with one kernel launch per timed call, and their algorithmic
