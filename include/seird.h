@@ -368,6 +368,21 @@ int seird_bsr_spmv_f32val(int64_t n_rows, const int32_t* row_ptr, const int32_t*
 /* Number of kernels the library has launched in this process so far. */
 int64_t seird_launch_count(void);
 
+/* Host-only check of the set-up the kernels rely on (no device call, no
+ * context): builds the partition, the BSR pattern, the overlapping
+ * subdomains and the ILU(0) level schedules and solve plans for `mesh` under
+ * `opt` (NULL: defaults) and verifies their invariants: owned ranges tile the
+ * nodes, rows sorted with their diagonal, a structurally symmetric pattern,
+ * every owned node in its subdomain, every sweep a permutation of the
+ * subdomain's rows, every stage within the shared-memory rings, every
+ * dependency of a row in an earlier stage, and the row records numbering the
+ * solution entries by sweep position with each owned row written once.
+ * stats (nullable) [8]: n_nodes, n_tris, nnzb, subdomains, subdomain rows,
+ * forward stages, backward stages, violations.  Returns SEIRD_OK, SEIRD_EINVAL
+ * with the first violation in seird_last_error(NULL), or the set-up's own
+ * error for a bad mesh or partition. */
+int seird_setup_check(const seird_mesh* mesh, const seird_options* opt, int64_t* stats);
+
 /* ---- allocation-free residual --------------------------------------------
  * For callers that cannot call cudaMalloc (the paper has no counterpart): code
  * running inside a framework that owns all device memory through its own

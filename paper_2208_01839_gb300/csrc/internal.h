@@ -77,8 +77,9 @@ struct HostSetup {
     std::vector<int64_t> levblk;  // per subdomain nlev+1 entries: block boundaries (absolute)
     std::vector<int32_t> sd_lev0; // [P+1] offsets into levpos/levblk
     std::vector<int64_t> src;     // [nblocks] factor block (>= 0) or -1-R for the inverted pivot of row R
-    std::vector<int32_t> col;     // [nblocks] local column of each block (the row itself for a pivot)
-    std::vector<int32_t> info;    // [NL][4] per position: row, first block relative to its level, blocks, 0
+    std::vector<int32_t> col;     // [nblocks] sweep position of the entry each block multiplies (own for a pivot)
+    std::vector<int32_t> info;    // [NL][4] per position: forward (node, first block in its stage, blocks, 0),
+                                  // backward (forward position, first block, blocks, node if owned else -1)
     int32_t max_lev_blocks = 0;
   } sp_fwd, sp_bwd;
   // coarse space: subdomain p sits at block row cpos[p] of the banded coarse matrix
@@ -101,6 +102,7 @@ struct HostSetup {
 };
 
 int build_setup(const seird_mesh* mesh, const seird_options* opt, HostSetup& hs, std::string& err);
+int64_t check_setup(const HostSetup& hs, std::string& first);
 // Subdomain of every node: the caller's owner array (validated) or the seeded
 // recursive coordinate bisection into opt->n_subdomains parts.
 int partition_nodes(const seird_mesh* mesh, const seird_options* opt, std::vector<int32_t>& owner, int32_t& P,

@@ -550,4 +550,128 @@ int build_setup(const seird_mesh* mesh, const seird_options* opt, HostSetup& hs,
   return SEIRD_OK;
 }
 
+// Invariants of a set-up that the kernels rely on without checking them (see
+// seird_setup_check).  Returns the number of violations; `first` names the first.
+int64_t check_setup(const HostSetup& hs, std::string& first) {
+  int64_t bad = 0;
+  auto fail = [&](bool ok, const std::string& what) {
+    if (ok) return;
+    if (!bad) first = what;
+    ++bad;
+  };
+  const int64_t n = hs.n;
+  const int32_t P = hs.P;
+  // partition: owned ranges tile the internal numbering
+  fail((int32_t)hs.own_ptr.size() == P + 1 && hs.own_ptr[0] == 0 && hs.own_ptr[P] == n, "owned ranges");
+  for (int32_t q = 0; q < P && !bad; ++q) {
+    fail(hs.own_ptr[q] <= hs.own_ptr[q + 1], "owned ranges not monotone");
+    for (int32_t i = hs.own_ptr[q]; i < hs.own_ptr[q + 1]; ++i) fail(hs.owner[i] == q, "owner map");
+  }
+  // BSR pattern: sorted rows with their diagonal, structurally symmetric
+  const int64_t nnzb = (int64_t)hs.col.size();
+  fail((int64_t)hs.row_ptr.size() == n + 1 && hs.row_ptr[n] == nnzb, "row pointers");
+  for (int64_t i = 0; i < n && !bad; ++i) {
+    bool diag = false;
+    for (int32_t k = hs.row_ptr[i]; k < hs.row_ptr[i + 1]; ++k) {
+      if (k > hs.row_ptr[i]) fail(hs.col[k] > hs.col[k - 1], "columns not strictly increasing");
+      diag |= hs.col[k] == i;
+      const int32_t t = hs.tpos[k];
+      fail(t >= 0 && t < nnzb && hs.col[t] == i && hs.row_ptr[hs.col[k]] <= t && t < hs.row_ptr[hs.col[k] + 1],
+           "transpose map");
+    }
+    fail(diag, "missing diagonal block");
+  }
+  // subdomains: distinct rows covering the owned nodes, local diagonal in place
+  const int64_t NL = (int64_t)hs.sd_node.size();
+  fail((int32_t)hs.sd_row0.size() == P + 1 && hs.sd_row0[P] == NL, "subdomain row ranges");
+  std::vector<int32_t> seen(n, -1);
+  for (int32_t q = 0; q < P && !bad; ++q) {
+    const int32_t r0 = hs.sd_row0[q], r1 = hs.sd_row0[q + 1];
+    for (int32_t R = r0; R < r1; ++R) {
+      const int32_t v = hs.sd_node[R];
+      fail(v >= 0 && v < n && seen[v] != q, "subdomain rows not distinct");
+      if (v >= 0 && v < n) seen[v] = q;
+      const int64_t dg = hs.l_diag[R];
+      fail(dg >= hs.l_row_ptr[R] && dg < hs.l_row_ptr[R + 1] && hs.l_col[dg] == R - r0, "local diagonal");
+    }
+    for (int32_t i = hs.own_ptr[q]; i < hs.own_ptr[q + 1]; ++i) fail(seen[i] == q, "owned node outside its subdomain");
+  }
+  // solve plans: each stage fits the shared-memory rings, every dependency of a row
+  // lies in an earlier stage, and the records number the entries by sweep position
+  for (int dir = 0; dir < 2 && !bad; ++dir) {
+    const HostSetup::SolvePlan& sp = dir == 0 ? hs.sp_fwd : hs.sp_bwd;
+    const std::vector<int32_t>& order = dir == 0 ? hs.fwd_order : hs.bwd_order;
+    for (int32_t q = 0; q < P && !bad; ++q) {
+      const int32_t r0 = hs.sd_row0[q], nl = hs.sd_row0[q + 1] - r0;
+      std::vector<int32_t> posf(nl, -1), hit(nl, 0);
+      for (int32_t k = 0; k < nl; ++k) {
+        const int32_t i = order[r0 + k];
+        fail(i >= 0 && i < nl && hit[i]++ == 0, "sweep order is not a permutation");
+        if (i >= 0 && i < nl) posf[i] = k;
+      }
+      const int32_t v0 = sp.sd_lev0[q], v1 = sp.sd_lev0[q + 1] - 1;
+      fail(sp.levpos[v0] == 0 && sp.levpos[v1] == nl, "stage positions");
+      int32_t owned = 0;
+      for (int32_t v = v0; v < v1 && !bad; ++v) {
+        const int32_t k0 = sp.levpos[v], k1 = sp.levpos[v + 1];
+        const int64_t b0 = sp.levblk[v], nbs = sp.levblk[v + 1] - b0;
+        fail(k1 >= k0 && k1 - k0 <= SOLVE_BUF_ROWS && nbs >= 0 && nbs <= SOLVE_BUF_BLOCKS, "stage exceeds the rings");
+        for (int32_t k = k0; k < k1; ++k) {
+          const int32_t* rec = &sp.info[4 * ((int64_t)r0 + k)];
+          const int32_t i = order[r0 + k];
+          const int64_t R = (int64_t)r0 + i;
+          fail(rec[1] >= 0 && rec[2] >= 0 && rec[1] + rec[2] <= nbs, "row record outside its stage");
+          int32_t expect = 0;
+          if (dir == 0) {
+            for (int64_t a = hs.l_row_ptr[R]; a < hs.l_diag[R]; ++a) ++expect;
+            fail(rec[0] == hs.sd_node[R] && rec[3] == 0, "forward record");
+          } else {
+            expect = 1 + (int32_t)(hs.l_row_ptr[R + 1] - hs.l_diag[R] - 1);
+            const int32_t node = hs.sd_node[R];
+            const bool own = node >= hs.own_ptr[q] && node < hs.own_ptr[q + 1];
+            fail(rec[0] >= 0 && rec[0] < nl && hs.fwd_order[r0 + rec[0]] == i, "backward record: forward position");
+            fail(rec[3] == (own ? node : -1), "backward record: owned node");
+            owned += own;
+            fail(sp.src[b0 + rec[1]] == -1 - R && sp.col[b0 + rec[1]] == k, "backward pivot block");
+          }
+          fail(rec[2] == expect, "row block count");
+          for (int32_t j = dir == 0 ? 0 : 1; j < rec[2]; ++j) {
+            const int32_t pos = sp.col[b0 + rec[1] + j];
+            fail(pos >= 0 && pos < k0, "dependency not in an earlier stage");
+          }
+        }
+      }
+      if (dir == 1) fail(owned == hs.own_ptr[q + 1] - hs.own_ptr[q], "owned rows written once");
+    }
+  }
+  return bad;
+}
+
 }  // namespace seird
+
+extern "C" int seird_setup_check(const seird_mesh* mesh, const seird_options* opt, int64_t* stats) {
+  using namespace seird;
+  seird_options o;
+  if (opt) o = *opt;
+  else seird_default_options(&o);
+  HostSetup hs;
+  std::string err;
+  const int rc = build_setup(mesh, &o, hs, err);
+  if (rc) {
+    set_global_error(err);
+    return rc;
+  }
+  const int64_t bad = check_setup(hs, err);
+  if (stats) {
+    stats[0] = hs.n;
+    stats[1] = hs.m;
+    stats[2] = (int64_t)hs.col.size();
+    stats[3] = hs.P;
+    stats[4] = (int64_t)hs.sd_node.size();
+    stats[5] = (int64_t)hs.sp_fwd.levpos.size() - hs.P;  // stages (each subdomain adds one boundary entry)
+    stats[6] = (int64_t)hs.sp_bwd.levpos.size() - hs.P;
+    stats[7] = bad;
+  }
+  if (bad) set_global_error("setup check: " + std::to_string(bad) + " violations, first: " + err);
+  return bad ? SEIRD_EINVAL : SEIRD_OK;
+}

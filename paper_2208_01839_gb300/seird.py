@@ -123,6 +123,7 @@ _linear_solve = _sig("seird_linear_solve", C.c_int, [_vp, _vp, _vp, C.c_int, C.P
 _bsr_spmv = _sig("seird_bsr_spmv", C.c_int, [C.c_int64, _vp, _vp, _vp, _vp, _vp, _vp])
 _bsr_spmv_f32 = _sig("seird_bsr_spmv_f32val", C.c_int, [C.c_int64, _vp, _vp, _vp, _vp, _vp, _vp])
 _launch_count = _sig("seird_launch_count", C.c_int64, [])
+_setup_check = _sig("seird_setup_check", C.c_int, [C.POINTER(Mesh), C.POINTER(Options), C.POINTER(C.c_int64)])
 _create_ensemble = _sig("seird_create_ensemble", C.c_int,
                         [C.POINTER(Mesh), C.c_int32, C.POINTER(Params), C.POINTER(Options), C.POINTER(_vp)])
 _set_params = _sig("seird_set_params", C.c_int, [_vp, C.POINTER(Params)])
@@ -151,6 +152,27 @@ def default_options(**over) -> Options:
 
 def launch_count() -> int:
     return int(_launch_count())
+
+
+def setup_check(xy, tri, owner=None, **options) -> dict:
+    """Host-only check of the set-up the kernels rely on (seird_setup_check):
+    raises SeirdError on a violated invariant, else returns the set-up's sizes."""
+    xy = np.ascontiguousarray(xy, dtype=np.float64)
+    tri = np.ascontiguousarray(tri, dtype=np.int32)
+    mesh = Mesh(len(xy), len(tri), xy.ctypes.data_as(_dp), tri.ctypes.data_as(_ip))
+    o = default_options(**options)
+    own = None
+    if owner is not None:
+        own = np.ascontiguousarray(owner, dtype=np.int32)
+        o.owner = own.ctypes.data_as(_ip)
+        o.n_subdomains = int(own.max()) + 1
+    st = (C.c_int64 * 8)()
+    rc = _setup_check(C.byref(mesh), C.byref(o), st)
+    if rc != OK:
+        raise SeirdError(rc, _last_error(None).decode())
+    keys = ("n_nodes", "n_tris", "nnzb", "n_subdomains", "subdomain_rows", "forward_stages", "backward_stages",
+            "violations")
+    return {k: int(st[i]) for i, k in enumerate(keys)}
 
 
 def _ptr(a):

@@ -1,0 +1,78 @@
+"""Host-side set-up invariants (seird_setup_check; no GPU).
+
+The subdomain kernels trust the set-up without checking it: the ILU(0) solve
+streams each stage into fixed shared-memory rings, reads a row's dependencies
+from earlier stages with no synchronisation beyond the stage barrier, and
+writes every owned row of z exactly once.  These tests build the set-up on the
+CPU for the workload generators, geometric and non-geometric partitions and
+every overlap, and require every invariant to hold.
+"""
+import numpy as np
+import pytest
+
+from paper_2208_01839_gb300 import inputs as I
+
+from paper_2208_01839_gb300 import build as _b  # noqa: E402
+
+_b.build()
+from paper_2208_01839_gb300 import seird as S  # noqa: E402
+
+
+def _check(xy, tri, owner=None, **opts):
+    st = S.setup_check(xy, tri, owner=owner, **opts)
+    assert st["violations"] == 0
+    assert st["n_nodes"] == len(xy) and st["n_tris"] == len(tri)
+    # every subdomain has at least one forward and one backward stage
+    assert st["forward_stages"] >= st["n_subdomains"] and st["backward_stages"] >= st["n_subdomains"]
+    return st
+
+
+@pytest.mark.parametrize("overlap", [0, 1, 2])
+def test_square_default_partition(overlap):
+    wl = I.square_workload(33)
+    st = _check(wl.xy, wl.tri, n_subdomains=4, overlap=overlap)
+    assert st["n_subdomains"] == 4
+    # overlap adds rows: the subdomains hold at least every node once
+    assert st["subdomain_rows"] >= st["n_nodes"]
+    if overlap == 0:
+        assert st["subdomain_rows"] == st["n_nodes"]
+
+
+@pytest.mark.parametrize("overlap", [1, 2])
+def test_irregular_mesh_box_partition(overlap):
+    xy, tri, _ = I.irregular_mesh(3, 3000)
+    _check(xy, tri, owner=I.box_partition(xy, 3, 2), overlap=overlap)
+
+
+def test_random_partition_is_not_geometric():
+    """Subdomains scattered over the mesh (every node's owner drawn at random):
+    the level schedules and records must still hold."""
+    xy, tri, _ = I.irregular_mesh(5, 1500)
+    owner = np.random.default_rng(5).integers(0, 7, len(xy)).astype(np.int32)
+    owner[:7] = np.arange(7)  # every subdomain owns a node
+    _check(xy, tri, owner=owner, overlap=1)
+
+
+def test_ontario_like_uneven_bisection():
+    wl = I.ontario_workload(20_000, n_subdomains=16)
+    st = _check(wl.xy, wl.tri, n_subdomains=16, overlap=2, seed=3)
+    assert st["n_subdomains"] == 16
+    # a 5x5 block per node pair of the P1 graph: about 7 blocks per row
+    assert 5 * st["n_nodes"] < st["nnzb"] < 9 * st["n_nodes"]
+
+
+def test_single_subdomain_and_one_triangle():
+    wl = I.square_workload(9)
+    st = _check(wl.xy, wl.tri, n_subdomains=1, overlap=0)
+    assert st["subdomain_rows"] == st["n_nodes"]
+    xy = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]])
+    tri = np.array([[0, 1, 2]], dtype=np.int32)
+    st = _check(xy, tri, n_subdomains=1, overlap=0)
+    assert st["nnzb"] == 9
+
+
+def test_bad_mesh_is_reported_not_checked():
+    xy = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]])
+    tri = np.array([[0, 2, 1]], dtype=np.int32)  # clockwise
+    with pytest.raises(S.SeirdError, match="counter-clockwise"):
+        S.setup_check(xy, tri)
