@@ -1,12 +1,15 @@
 // Restricted additive Schwarz preconditioner (Eq. RAS) with block-ILU(0)
-// subdomain solves, and the additive coarse correction of Section 3.1 with the
+// subdomain solves, and the coarse correction of Section 3.1 with the
 // per-subdomain, per-compartment constant coarse space Z:
-//   z = sum_p R_p^T D_p (L_p U_p)^{-1} R_p r  +  Z A_c^{-1} Z^T r,  A_c = Z^T J Z.
+//   z = sum_p R_p^T D_p (L_p U_p)^{-1} R_p r  +  Z A_c^{-1} Z^T r,  A_c = Z^T J Z,
+// applied additively or, as in Eq. RAS_2L, multiplicatively (the J Z blocks
+// summed at set-up turn the second residual update into k_az_sub).
 // One CTA per subdomain for the factorization and the solves; rows of one
 // level of the ILU(0) dependency DAG are independent and run in parallel, with
-// a CTA barrier between levels.  The coarse matrix is block-banded (subdomains
-// in reverse Cuthill-McKee order) and factored by block LU with 5x5 pivot
-// blocks inverted under partial pivoting.
+// a barrier between stages, and the solve numbers a subdomain's solution
+// entries by their position in the sweep.  The coarse matrix is block-banded
+// (subdomains in reverse Cuthill-McKee order) and factored by block LU with 5x5
+// pivot blocks inverted under partial pivoting, then inverted explicitly.
 #include <cmath>
 
 #include "kernels.cuh"
