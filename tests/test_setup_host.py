@@ -76,3 +76,20 @@ def test_bad_mesh_is_reported_not_checked():
     tri = np.array([[0, 2, 1]], dtype=np.int32)  # clockwise
     with pytest.raises(S.SeirdError, match="counter-clockwise"):
         S.setup_check(xy, tri)
+
+
+def test_ensemble_union_mesh():
+    """The union mesh an ensemble is solved on: sample k's copy of the mesh with its
+    nodes offset by k n and the per-sample partition shifted by k P (block-diagonal
+    system, no block couples two samples)."""
+    xy, tri, _ = I.irregular_mesh(4, 800)
+    owner = I.box_partition(xy, 2, 2).astype(np.int32)
+    n, P, B = len(xy), int(owner.max()) + 1, 3
+    uxy = np.concatenate([xy] * B)
+    utri = np.concatenate([tri + k * n for k in range(B)]).astype(np.int32)
+    uown = np.concatenate([owner + k * P for k in range(B)]).astype(np.int32)
+    st = _check(uxy, utri, owner=uown, overlap=2)
+    one = _check(xy, tri, owner=owner, overlap=2)
+    assert st["n_subdomains"] == B * P and st["nnzb"] == B * one["nnzb"]
+    assert st["subdomain_rows"] == B * one["subdomain_rows"]
+    assert st["forward_stages"] == B * one["forward_stages"] and st["backward_stages"] == B * one["backward_stages"]
