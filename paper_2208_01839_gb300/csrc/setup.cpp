@@ -4,11 +4,13 @@
 // banded pattern of the coarse matrix Z^T J Z (Section 3.1).  Plain C++; runs
 // once per context.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <numeric>
 #include <random>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "internal.h"
@@ -122,6 +124,28 @@ int partition_nodes(const seird_mesh* mesh, const seird_options* opt, std::vecto
   return SEIRD_OK;
 }
 
+// Worker threads for the per-subdomain parts of the set-up: the host's cores, at most 16.
+static int setup_threads(int32_t units) {
+  const unsigned hw = std::thread::hardware_concurrency();
+  return (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)(hw ? hw : 1), 16, (int64_t)units}));
+}
+
+// f(i, thread) for i in [0, n) over nth threads (dynamic assignment)
+template <class F>
+static void parallel_for(int32_t n, int nth, F&& f) {
+  if (nth <= 1) {
+    for (int32_t i = 0; i < n; ++i) f(i, 0);
+    return;
+  }
+  std::atomic<int32_t> next{0};
+  std::vector<std::thread> th;
+  for (int t = 0; t < nth; ++t)
+    th.emplace_back([&, t] {
+      for (int32_t i = next.fetch_add(1); i < n; i = next.fetch_add(1)) f(i, t);
+    });
+  for (auto& x : th) x.join();
+}
+
 int build_setup(const seird_mesh* mesh, const seird_options* opt, HostSetup& hs, std::string& err) {
   const int64_t n = mesh->n_nodes, m = mesh->n_tris;
   if (n < 3 || m < 1 || !mesh->xy || !mesh->tri) {
@@ -195,27 +219,39 @@ int build_setup(const seird_mesh* mesh, const seird_options* opt, HostSetup& hs,
       for (int a = 0; a < 3; ++a) hs.tri[3 * t + a] = tri[3 * (int64_t)ord[t] + a];
   }
 
-  // ---- BSR pattern --------------------------------------------------------
+  // ---- element incidence and BSR pattern ---------------------------------
+  // node -> (t*3 + a), ordered by triangle; a row's blocks are the vertices of
+  // its incident triangles, sorted and deduplicated row by row
+  hs.node_inc_ptr.assign(n + 1, 0);
+  for (int64_t t = 0; t < m; ++t)
+    for (int a = 0; a < 3; ++a) hs.node_inc_ptr[hs.tri[3 * t + a] + 1]++;
+  for (int64_t i = 0; i < n; ++i) hs.node_inc_ptr[i + 1] += hs.node_inc_ptr[i];
+  hs.node_inc.resize(3 * m);
   {
-    std::vector<int64_t> pairs;
-    pairs.reserve(9 * m);
+    std::vector<int32_t> fill(hs.node_inc_ptr.begin(), hs.node_inc_ptr.end() - 1);
     for (int64_t t = 0; t < m; ++t)
-      for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) pairs.push_back((int64_t)hs.tri[3 * t + a] * n + hs.tri[3 * t + b]);
-    std::sort(pairs.begin(), pairs.end());
-    pairs.erase(std::unique(pairs.begin(), pairs.end()), pairs.end());
+      for (int a = 0; a < 3; ++a) hs.node_inc[fill[hs.tri[3 * t + a]]++] = (int32_t)(3 * t + a);
+  }
+  {
     hs.row_ptr.assign(n + 1, 0);
-    hs.col.resize(pairs.size());
-    for (size_t k = 0; k < pairs.size(); ++k) {
-      hs.row_ptr[pairs[k] / n + 1]++;
-      hs.col[k] = (int32_t)(pairs[k] % n);
-    }
-    for (int64_t i = 0; i < n; ++i) hs.row_ptr[i + 1] += hs.row_ptr[i];
-    for (int64_t i = 0; i < n; ++i)
-      if (hs.row_ptr[i + 1] == hs.row_ptr[i]) {
+    hs.col.clear();
+    hs.col.reserve(8 * (size_t)n);
+    std::vector<int32_t> cols;
+    for (int64_t i = 0; i < n; ++i) {
+      cols.clear();
+      for (int32_t e = hs.node_inc_ptr[i]; e < hs.node_inc_ptr[i + 1]; ++e) {
+        const int64_t t = hs.node_inc[e] / 3;
+        for (int b = 0; b < 3; ++b) cols.push_back(hs.tri[3 * t + b]);
+      }
+      if (cols.empty()) {
         err = "node " + std::to_string(hs.perm[i]) + " belongs to no triangle";
         return SEIRD_EINVAL;
       }
+      std::sort(cols.begin(), cols.end());
+      cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+      hs.col.insert(hs.col.end(), cols.begin(), cols.end());
+      hs.row_ptr[i + 1] = (int32_t)hs.col.size();
+    }
   }
   const int64_t nnzb = hs.col.size();
   auto find_blk = [&](int32_t i, int32_t j) -> int32_t {
@@ -229,16 +265,7 @@ int build_setup(const seird_mesh* mesh, const seird_options* opt, HostSetup& hs,
     for (int32_t k = hs.row_ptr[i]; k < hs.row_ptr[i + 1]; ++k) hs.tpos[k] = find_blk(hs.col[k], (int32_t)i);
 
   // ---- element gather lists (deterministic: ordered by triangle) ---------
-  hs.node_inc_ptr.assign(n + 1, 0);
-  for (int64_t t = 0; t < m; ++t)
-    for (int a = 0; a < 3; ++a) hs.node_inc_ptr[hs.tri[3 * t + a] + 1]++;
-  for (int64_t i = 0; i < n; ++i) hs.node_inc_ptr[i + 1] += hs.node_inc_ptr[i];
-  hs.node_inc.resize(3 * m);
-  {
-    std::vector<int32_t> fill(hs.node_inc_ptr.begin(), hs.node_inc_ptr.end() - 1);
-    for (int64_t t = 0; t < m; ++t)
-      for (int a = 0; a < 3; ++a) hs.node_inc[fill[hs.tri[3 * t + a]]++] = (int32_t)(3 * t + a);
-  }
+  // (the node lists were built with the pattern above)
   hs.blk_inc_ptr.assign(nnzb + 1, 0);
   std::vector<int32_t> tblk(9 * m);
   for (int64_t t = 0; t < m; ++t)
@@ -259,126 +286,199 @@ int build_setup(const seird_mesh* mesh, const seird_options* opt, HostSetup& hs,
   tblk.shrink_to_fit();
 
   // ---- overlapping subdomains, local patterns, ILU(0) maps, levels --------
+  // Subdomains are independent: each is built into its own buffers (threads over
+  // the host's cores, one node-map per thread) and the buffers are concatenated in
+  // subdomain order, so the result does not depend on the thread count.  Block
+  // indices inside a part are relative to the subdomain's first block.
   const int delta = std::max(0, opt->overlap);
-  std::vector<int32_t> loc(n, -1);   // internal node -> local row (current subdomain)
-  std::vector<int32_t> mark(n, -1);  // BFS stamp
-  hs.sd_row0.assign(P + 1, 0);
-  hs.l_row_ptr.assign(1, 0);
-  hs.sd_fwd_lev0.assign(1, 0);
-  hs.sd_bwd_lev0.assign(1, 0);
-  hs.upd_ptr.assign(1, 0);
-  std::vector<int32_t> nodes, front, next, lev, lb;
-  std::vector<int64_t> rowpos;  // local col -> absolute block index in the current row (stamp)
-  for (int32_t q = 0; q < P; ++q) {
-    nodes.clear();
-    front.clear();
-    for (int32_t i = hs.own_ptr[q]; i < hs.own_ptr[q + 1]; ++i) {
-      nodes.push_back(i);
-      front.push_back(i);
-      mark[i] = q;
-    }
-    for (int d = 0; d < delta; ++d) {
-      next.clear();
-      for (int32_t i : front)
-        for (int32_t k = hs.row_ptr[i]; k < hs.row_ptr[i + 1]; ++k) {
-          int32_t j = hs.col[k];
-          if (mark[j] != q) {
-            mark[j] = q;
-            next.push_back(j);
-            nodes.push_back(j);
-          }
-        }
-      front.swap(next);
-    }
-    std::sort(nodes.begin(), nodes.end());
-    const int32_t nl = (int32_t)nodes.size();
-    const int32_t r0 = hs.sd_row0[q];
-    hs.sd_row0[q + 1] = r0 + nl;
-    hs.max_sd_rows = std::max(hs.max_sd_rows, nl);
-    for (int32_t l = 0; l < nl; ++l) loc[nodes[l]] = l;
-    // local BSR rows (restriction of J's rows to the subdomain keeps column order)
-    const int64_t base = hs.l_row_ptr.back();
-    int64_t pos = base;
-    std::vector<int64_t> rstart(nl + 1);
-    for (int32_t l = 0; l < nl; ++l) {
-      rstart[l] = pos;
-      const int32_t g = nodes[l];
-      for (int32_t k = hs.row_ptr[g]; k < hs.row_ptr[g + 1]; ++k) {
-        int32_t j = hs.col[k];
-        if (mark[j] == q) {
-          hs.l_col.push_back(loc[j]);
-          hs.l_gblk.push_back(k);
-          if (j == g) hs.l_diag.push_back(pos);
-          ++pos;
-        }
+  struct SdPart {
+    std::vector<int32_t> nodes;          // local rows: internal nodes, ascending
+    std::vector<int64_t> rowend;         // end of each local row's blocks
+    std::vector<int32_t> l_col, l_gblk;  // local column and J block of each local block
+    std::vector<int64_t> diag;           // diagonal block of each row
+    std::vector<int64_t> upd;            // ILU(0) update pairs (destination, source)
+    std::vector<int64_t> updend;         // pairs issued up to and including each block
+    std::vector<int32_t> order[2], lb[2];
+  };
+  std::vector<SdPart> parts(P);
+  {
+    const int nth = setup_threads(P);
+    std::vector<std::vector<int32_t>> locs(nth);
+    parallel_for(P, nth, [&](int32_t q, int th) {
+      std::vector<int32_t>& loc = locs[th];  // internal node -> local row, -2 while found, -1 outside
+      if (loc.empty()) loc.assign(n, -1);
+      SdPart& S = parts[q];
+      std::vector<int32_t>& nodes = S.nodes;
+      std::vector<int32_t> front, next;
+      for (int32_t i = hs.own_ptr[q]; i < hs.own_ptr[q + 1]; ++i) {
+        nodes.push_back(i);
+        front.push_back(i);
+        loc[i] = -2;
       }
-      hs.sd_node.push_back(g);
-      hs.l_row_ptr.push_back(pos);
-    }
-    rstart[nl] = pos;
-    // ILU(0) update pairs: for lower block (i,k): every (k,j) with j > k and (i,j) present
-    rowpos.assign(nl, -1);
-    for (int32_t i = 0; i < nl; ++i) {
-      for (int64_t a = rstart[i]; a < rstart[i + 1]; ++a) rowpos[hs.l_col[a]] = a;
-      for (int64_t a = rstart[i]; a < rstart[i + 1]; ++a) {
-        const int32_t k = hs.l_col[a];
-        if (k < i) {
-          for (int64_t b = rstart[k]; b < rstart[k + 1]; ++b) {
-            const int32_t j = hs.l_col[b];
-            if (j > k && rowpos[j] >= 0) {
-              hs.upd.push_back(rowpos[j]);
-              hs.upd.push_back(b);
+      for (int d = 0; d < delta; ++d) {
+        next.clear();
+        for (int32_t i : front)
+          for (int32_t k = hs.row_ptr[i]; k < hs.row_ptr[i + 1]; ++k) {
+            const int32_t j = hs.col[k];
+            if (loc[j] == -1) {
+              loc[j] = -2;
+              next.push_back(j);
+              nodes.push_back(j);
             }
           }
-        }
-        hs.upd_ptr.push_back((int64_t)hs.upd.size() / 2);
+        front.swap(next);
       }
-      for (int64_t a = rstart[i]; a < rstart[i + 1]; ++a) rowpos[hs.l_col[a]] = -1;
-    }
-    // forward levels (lower triangle) and backward levels (upper triangle)
-    for (int dir = 0; dir < 2; ++dir) {
-      lev.assign(nl, 0);
-      int32_t nlev = 0;
-      if (dir == 0) {
-        for (int32_t i = 0; i < nl; ++i) {
-          int32_t lv = 0;
-          for (int64_t a = rstart[i]; a < rstart[i + 1]; ++a)
-            if (hs.l_col[a] < i) lv = std::max(lv, lev[hs.l_col[a]] + 1);
-          lev[i] = lv;
-          nlev = std::max(nlev, lv + 1);
+      std::sort(nodes.begin(), nodes.end());
+      const int32_t nl = (int32_t)nodes.size();
+      for (int32_t l = 0; l < nl; ++l) loc[nodes[l]] = l;
+      // local BSR rows (restriction of J's rows to the subdomain keeps column order)
+      int64_t pos = 0;
+      std::vector<int64_t> rstart(nl + 1);
+      S.rowend.resize(nl);
+      for (int32_t l = 0; l < nl; ++l) {
+        rstart[l] = pos;
+        const int32_t g = nodes[l];
+        for (int32_t k = hs.row_ptr[g]; k < hs.row_ptr[g + 1]; ++k) {
+          const int32_t j = hs.col[k];
+          if (loc[j] >= 0) {
+            S.l_col.push_back(loc[j]);
+            S.l_gblk.push_back(k);
+            if (j == g) S.diag.push_back(pos);
+            ++pos;
+          }
         }
-      } else {
-        for (int32_t i = nl - 1; i >= 0; --i) {
-          int32_t lv = 0;
-          for (int64_t a = rstart[i]; a < rstart[i + 1]; ++a)
-            if (hs.l_col[a] > i) lv = std::max(lv, lev[hs.l_col[a]] + 1);
-          lev[i] = lv;
-          nlev = std::max(nlev, lv + 1);
+        S.rowend[l] = pos;
+      }
+      rstart[nl] = pos;
+      // ILU(0) update pairs: for lower block (i,k): every (k,j) with j > k and (i,j) present
+      std::vector<int64_t> rowpos(nl, -1);  // local col -> block index in the current row
+      S.updend.reserve(pos);
+      for (int32_t i = 0; i < nl; ++i) {
+        for (int64_t a = rstart[i]; a < rstart[i + 1]; ++a) rowpos[S.l_col[a]] = a;
+        for (int64_t a = rstart[i]; a < rstart[i + 1]; ++a) {
+          const int32_t k = S.l_col[a];
+          if (k < i) {
+            for (int64_t b = rstart[k]; b < rstart[k + 1]; ++b) {
+              const int32_t j = S.l_col[b];
+              if (j > k && rowpos[j] >= 0) {
+                S.upd.push_back(rowpos[j]);
+                S.upd.push_back(b);
+              }
+            }
+          }
+          S.updend.push_back((int64_t)S.upd.size() / 2);
+        }
+        for (int64_t a = rstart[i]; a < rstart[i + 1]; ++a) rowpos[S.l_col[a]] = -1;
+      }
+      // forward levels (lower triangle) and backward levels (upper triangle)
+      std::vector<int32_t> lev(nl);
+      for (int dir = 0; dir < 2; ++dir) {
+        int32_t nlev = 0;
+        if (dir == 0) {
+          for (int32_t i = 0; i < nl; ++i) {
+            int32_t lv = 0;
+            for (int64_t a = rstart[i]; a < rstart[i + 1]; ++a)
+              if (S.l_col[a] < i) lv = std::max(lv, lev[S.l_col[a]] + 1);
+            lev[i] = lv;
+            nlev = std::max(nlev, lv + 1);
+          }
+        } else {
+          for (int32_t i = nl - 1; i >= 0; --i) {
+            int32_t lv = 0;
+            for (int64_t a = rstart[i]; a < rstart[i + 1]; ++a)
+              if (S.l_col[a] > i) lv = std::max(lv, lev[S.l_col[a]] + 1);
+            lev[i] = lv;
+            nlev = std::max(nlev, lv + 1);
+          }
+        }
+        std::vector<int32_t>& lb = S.lb[dir];
+        lb.assign(nlev + 1, 0);
+        for (int32_t i = 0; i < nl; ++i) lb[lev[i] + 1]++;
+        for (int32_t v = 0; v < nlev; ++v) lb[v + 1] += lb[v];
+        std::vector<int32_t>& order = S.order[dir];
+        order.resize(nl);
+        std::vector<int32_t> fill(lb.begin(), lb.end() - 1);
+        if (dir == 0) {
+          for (int32_t i = 0; i < nl; ++i) order[fill[lev[i]]++] = i;
+        } else {
+          for (int32_t i = nl - 1; i >= 0; --i) order[fill[lev[i]]++] = i;
         }
       }
-      hs.max_levels = std::max(hs.max_levels, nlev);
-      lb.assign(nlev + 1, 0);
-      for (int32_t i = 0; i < nl; ++i) lb[lev[i] + 1]++;
-      for (int32_t v = 0; v < nlev; ++v) lb[v + 1] += lb[v];
-      std::vector<int32_t>& order = dir == 0 ? hs.fwd_order : hs.bwd_order;
-      std::vector<int32_t>& levs = dir == 0 ? hs.fwd_lev : hs.bwd_lev;
-      std::vector<int32_t>& lev0 = dir == 0 ? hs.sd_fwd_lev0 : hs.sd_bwd_lev0;
-      const size_t o0 = order.size();
-      order.resize(o0 + nl);
-      std::vector<int32_t> fill(lb.begin(), lb.end() - 1);
-      if (dir == 0) {
-        for (int32_t i = 0; i < nl; ++i) order[o0 + fill[lev[i]]++] = i;
-      } else {
-        for (int32_t i = nl - 1; i >= 0; --i) order[o0 + fill[lev[i]]++] = i;
-      }
-      levs.insert(levs.end(), lb.begin(), lb.end());
-      lev0.push_back((int32_t)levs.size());
-    }
-    for (int32_t l = 0; l < nl; ++l) loc[nodes[l]] = -1;
+      for (int32_t l = 0; l < nl; ++l) loc[nodes[l]] = -1;
+    });
   }
-  if ((int64_t)hs.l_diag.size() != (int64_t)hs.sd_node.size()) {
-    err = "internal error: missing diagonal block in a subdomain";
-    return SEIRD_EINVAL;
+  // concatenation: every part's slice is known from prefix sums, so the parts are
+  // copied into place in parallel
+  {
+    std::vector<int64_t> roff(P + 1, 0), boff(P + 1, 0), uoff(P + 1, 0), loff[2];
+    loff[0].assign(P + 1, 0);
+    loff[1].assign(P + 1, 0);
+    for (int32_t q = 0; q < P; ++q) {
+      const SdPart& S = parts[q];
+      roff[q + 1] = roff[q] + (int64_t)S.nodes.size();
+      boff[q + 1] = boff[q] + (int64_t)S.l_col.size();
+      uoff[q + 1] = uoff[q] + (int64_t)S.upd.size() / 2;
+      for (int dir = 0; dir < 2; ++dir) {
+        loff[dir][q + 1] = loff[dir][q] + (int64_t)S.lb[dir].size();
+        hs.max_levels = std::max(hs.max_levels, (int32_t)S.lb[dir].size() - 1);
+      }
+      hs.max_sd_rows = std::max(hs.max_sd_rows, (int32_t)S.nodes.size());
+    }
+    const int64_t NLt = roff[P], NLBt = boff[P], NUt = uoff[P];
+    if (NLt > INT32_MAX || NLBt > INT32_MAX) {
+      err = "subdomains too large for 32-bit local maps";
+      return SEIRD_EINVAL;
+    }
+    hs.sd_row0.resize(P + 1);
+    for (int32_t q = 0; q <= P; ++q) hs.sd_row0[q] = (int32_t)roff[q];
+    hs.sd_node.resize(NLt);
+    hs.l_row_ptr.resize(NLt + 1);
+    hs.l_row_ptr[0] = 0;
+    hs.l_diag.resize(NLt);
+    hs.l_col.resize(NLBt);
+    hs.l_gblk.resize(NLBt);
+    hs.upd_ptr.resize(NLBt + 1);
+    hs.upd_ptr[0] = 0;
+    hs.upd.resize(2 * NUt);
+    hs.fwd_order.resize(NLt);
+    hs.bwd_order.resize(NLt);
+    hs.fwd_lev.resize(loff[0][P]);
+    hs.bwd_lev.resize(loff[1][P]);
+    hs.sd_fwd_lev0.resize(P + 1);
+    hs.sd_bwd_lev0.resize(P + 1);
+    for (int32_t q = 0; q <= P; ++q) {
+      hs.sd_fwd_lev0[q] = (int32_t)loff[0][q];
+      hs.sd_bwd_lev0[q] = (int32_t)loff[1][q];
+    }
+    bool diag_ok = true;
+    for (int32_t q = 0; q < P; ++q) diag_ok &= parts[q].diag.size() == parts[q].nodes.size();
+    if (!diag_ok) {
+      err = "internal error: missing diagonal block in a subdomain";
+      return SEIRD_EINVAL;
+    }
+    parallel_for(P, setup_threads(P), [&](int32_t q, int) {
+      SdPart& S = parts[q];
+      const int64_t r0 = roff[q], b0 = boff[q], u0 = uoff[q];
+      const int64_t nl = (int64_t)S.nodes.size();
+      std::copy(S.nodes.begin(), S.nodes.end(), hs.sd_node.begin() + r0);
+      for (int64_t l = 0; l < nl; ++l) {
+        hs.l_row_ptr[r0 + l + 1] = b0 + S.rowend[l];
+        hs.l_diag[r0 + l] = b0 + S.diag[l];
+      }
+      std::copy(S.l_col.begin(), S.l_col.end(), hs.l_col.begin() + b0);
+      std::copy(S.l_gblk.begin(), S.l_gblk.end(), hs.l_gblk.begin() + b0);
+      for (size_t a = 0; a < S.updend.size(); ++a) hs.upd_ptr[b0 + a + 1] = u0 + S.updend[a];
+      for (size_t k = 0; k < S.upd.size(); ++k) hs.upd[2 * u0 + k] = b0 + S.upd[k];
+      for (int dir = 0; dir < 2; ++dir) {
+        std::vector<int32_t>& order = dir == 0 ? hs.fwd_order : hs.bwd_order;
+        std::vector<int32_t>& levs = dir == 0 ? hs.fwd_lev : hs.bwd_lev;
+        std::copy(S.order[dir].begin(), S.order[dir].end(), order.begin() + r0);
+        std::copy(S.lb[dir].begin(), S.lb[dir].end(), levs.begin() + loff[dir][q]);
+      }
+      S = SdPart();  // release the part
+    });
+    parts.clear();
+    parts.shrink_to_fit();
   }
 
   // ---- ILU(0) solve plans ---------------------------------------------------
@@ -388,25 +488,30 @@ int build_setup(const seird_mesh* mesh, const seird_options* opt, HostSetup& hs,
   // record holds: forward (node, first block, block count, 0); backward (forward
   // position of the row, first block, block count, node if the subdomain owns it
   // else -1).
-  std::vector<int32_t> posf, posd;
+  // Built per subdomain in parallel (block indices relative to the subdomain's first
+  // solve block), then concatenated in subdomain order.
+  struct PlanPart {
+    std::vector<int32_t> levpos, row, cnt, info, col;
+    std::vector<int64_t> levblk, start, src;
+  };
   for (int dir = 0; dir < 2; ++dir) {
     HostSetup::SolvePlan& sp = dir == 0 ? hs.sp_fwd : hs.sp_bwd;
     const std::vector<int32_t>& order = dir == 0 ? hs.fwd_order : hs.bwd_order;
     const std::vector<int32_t>& levs = dir == 0 ? hs.fwd_lev : hs.bwd_lev;
     const std::vector<int32_t>& lev0 = dir == 0 ? hs.sd_fwd_lev0 : hs.sd_bwd_lev0;
-    sp.sd_lev0.assign(1, 0);
-    for (int32_t q = 0; q < P; ++q) {
+    std::vector<PlanPart> pp(P);
+    parallel_for(P, setup_threads(P), [&](int32_t q, int) {
+      PlanPart& T = pp[q];
       const int32_t r0 = hs.sd_row0[q];
       const int32_t nlq = hs.sd_row0[q + 1] - r0;
-      posf.assign(nlq, 0);
-      posd.assign(nlq, 0);
+      std::vector<int32_t> posf(nlq, 0), posd(nlq, 0);
       for (int32_t k = 0; k < nlq; ++k) {
         posf[hs.fwd_order[r0 + k]] = k;
         posd[order[r0 + k]] = k;
       }
       const int32_t nlev = lev0[q + 1] - lev0[q] - 1;
-      sp.levpos.push_back(0);
-      sp.levblk.push_back((int64_t)sp.src.size());
+      T.levpos.push_back(0);
+      T.levblk.push_back(0);
       int32_t pos = 0, in_level = 0;
       for (int32_t v = 0; v < nlev; ++v) {
         for (int32_t k = levs[lev0[q] + v]; k < levs[lev0[q] + v + 1]; ++k) {
@@ -414,47 +519,76 @@ int build_setup(const seird_mesh* mesh, const seird_options* opt, HostSetup& hs,
           const int64_t R = (int64_t)r0 + i;
           int32_t nb = 0;
           if (dir == 0) {
-            for (int64_t a = hs.l_row_ptr[R]; a < hs.l_diag[R]; ++a) ++nb;
+            nb = (int32_t)(hs.l_diag[R] - hs.l_row_ptr[R]);
           } else {
             nb = 1 + (int32_t)(hs.l_row_ptr[R + 1] - hs.l_diag[R] - 1);
           }
           if ((in_level > 0 && in_level + nb > SOLVE_BUF_BLOCKS) ||
-              pos - sp.levpos.back() >= SOLVE_BUF_ROWS) {  // split: rows of a level are independent
-            sp.levpos.push_back(pos);
-            sp.levblk.push_back((int64_t)sp.src.size());
+              pos - T.levpos.back() >= SOLVE_BUF_ROWS) {  // split: rows of a level are independent
+            T.levpos.push_back(pos);
+            T.levblk.push_back((int64_t)T.src.size());
             in_level = 0;
           }
-          sp.row.push_back(i);
-          sp.start.push_back((int64_t)sp.src.size());
-          sp.cnt.push_back(nb);
+          T.row.push_back(i);
+          T.start.push_back((int64_t)T.src.size());
+          T.cnt.push_back(nb);
           const int32_t node = hs.sd_node[R];
           const bool owned = node >= hs.own_ptr[q] && node < hs.own_ptr[q + 1];
-          sp.info.push_back(dir == 0 ? node : posf[i]);
-          sp.info.push_back((int32_t)((int64_t)sp.src.size() - sp.levblk.back()));
-          sp.info.push_back(nb);
-          sp.info.push_back(dir == 0 ? 0 : (owned ? node : -1));
+          T.info.push_back(dir == 0 ? node : posf[i]);
+          T.info.push_back((int32_t)((int64_t)T.src.size() - T.levblk.back()));
+          T.info.push_back(nb);
+          T.info.push_back(dir == 0 ? 0 : (owned ? node : -1));
           if (dir == 0) {
             for (int64_t a = hs.l_row_ptr[R]; a < hs.l_diag[R]; ++a) {
-              sp.src.push_back(a);
-              sp.col.push_back(posf[hs.l_col[a]]);
+              T.src.push_back(a);
+              T.col.push_back(posf[hs.l_col[a]]);
             }
           } else {
-            sp.src.push_back(-1 - R);
-            sp.col.push_back(posd[i]);
+            T.src.push_back(-1 - R);
+            T.col.push_back(posd[i]);
             for (int64_t a = hs.l_diag[R] + 1; a < hs.l_row_ptr[R + 1]; ++a) {
-              sp.src.push_back(a);
-              sp.col.push_back(posd[hs.l_col[a]]);
+              T.src.push_back(a);
+              T.col.push_back(posd[hs.l_col[a]]);
             }
           }
           in_level += nb;
           ++pos;
         }
-        sp.levpos.push_back(pos);
-        sp.levblk.push_back((int64_t)sp.src.size());
+        T.levpos.push_back(pos);
+        T.levblk.push_back((int64_t)T.src.size());
         in_level = 0;
       }
-      sp.sd_lev0.push_back((int32_t)sp.levpos.size());
+    });
+    // concatenation: slices from prefix sums, copied in parallel
+    std::vector<int64_t> loff(P + 1, 0), roff(P + 1, 0), soff(P + 1, 0);
+    for (int32_t q = 0; q < P; ++q) {
+      loff[q + 1] = loff[q] + (int64_t)pp[q].levpos.size();
+      roff[q + 1] = roff[q] + (int64_t)pp[q].row.size();
+      soff[q + 1] = soff[q] + (int64_t)pp[q].src.size();
     }
+    sp.sd_lev0.resize(P + 1);
+    for (int32_t q = 0; q <= P; ++q) sp.sd_lev0[q] = (int32_t)loff[q];
+    sp.levpos.resize(loff[P]);
+    sp.levblk.resize(loff[P]);
+    sp.row.resize(roff[P]);
+    sp.start.resize(roff[P]);
+    sp.cnt.resize(roff[P]);
+    sp.info.resize(4 * roff[P]);
+    sp.src.resize(soff[P]);
+    sp.col.resize(soff[P]);
+    parallel_for(P, setup_threads(P), [&](int32_t q, int) {
+      PlanPart& T = pp[q];
+      const int64_t l0 = loff[q], r0 = roff[q], s0 = soff[q];
+      std::copy(T.levpos.begin(), T.levpos.end(), sp.levpos.begin() + l0);
+      for (size_t k = 0; k < T.levblk.size(); ++k) sp.levblk[l0 + k] = s0 + T.levblk[k];
+      std::copy(T.row.begin(), T.row.end(), sp.row.begin() + r0);
+      for (size_t k = 0; k < T.start.size(); ++k) sp.start[r0 + k] = s0 + T.start[k];
+      std::copy(T.cnt.begin(), T.cnt.end(), sp.cnt.begin() + r0);
+      std::copy(T.info.begin(), T.info.end(), sp.info.begin() + 4 * r0);
+      std::copy(T.src.begin(), T.src.end(), sp.src.begin() + s0);
+      std::copy(T.col.begin(), T.col.end(), sp.col.begin() + s0);
+      T = PlanPart();
+    });
     for (int32_t q = 0; q < P; ++q)
       for (int32_t v = sp.sd_lev0[q]; v + 1 < sp.sd_lev0[q + 1]; ++v)
         sp.max_lev_blocks = std::max<int32_t>(sp.max_lev_blocks, (int32_t)(sp.levblk[v + 1] - sp.levblk[v]));
@@ -527,11 +661,18 @@ int build_setup(const seird_mesh* mesh, const seird_options* opt, HostSetup& hs,
     std::vector<int32_t> rowof(nnzb);
     for (int64_t i = 0; i < n; ++i)
       for (int32_t k = hs.row_ptr[i]; k < hs.row_ptr[i + 1]; ++k) rowof[k] = (int32_t)i;
-    hs.cseg_blk.resize(nnzb);
-    std::iota(hs.cseg_blk.begin(), hs.cseg_blk.end(), 0);
     for (int64_t k = 0; k < nnzb; ++k)
       key[k] = (int64_t)hs.cpos[hs.cunit[rowof[k]]] * P + hs.cpos[hs.cunit[hs.col[k]]];
-    std::stable_sort(hs.cseg_blk.begin(), hs.cseg_blk.end(), [&](int32_t a, int32_t b) { return key[a] < key[b]; });
+    // stable counting sort on the key's banded slot p W + (q - p + band): the same order
+    // as sorting by (p, q) and then by block id
+    {
+      std::vector<int64_t> cnt((size_t)P * W + 1, 0);
+      auto slot = [&](int64_t kk) { return (kk / P) * W + (kk % P - kk / P + band); };
+      for (int64_t k = 0; k < nnzb; ++k) cnt[slot(key[k]) + 1]++;
+      for (size_t v = 1; v < cnt.size(); ++v) cnt[v] += cnt[v - 1];
+      hs.cseg_blk.resize(nnzb);
+      for (int64_t k = 0; k < nnzb; ++k) hs.cseg_blk[cnt[slot(key[k])]++] = (int32_t)k;
+    }
     const int32_t CH = 256;  // blocks per chunk
     hs.cchunk_ptr.assign(1, 0);
     hs.cdst_ptr.assign(1, 0);
