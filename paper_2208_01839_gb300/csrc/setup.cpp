@@ -260,21 +260,25 @@ int build_setup(const seird_mesh* mesh, const seird_options* opt, HostSetup& hs,
     const int32_t* p = std::lower_bound(b, e, j);
     return (int32_t)(p - hs.col.data());
   };
+  constexpr int64_t CHUNK = 1 << 16;  // rows or triangles per task of the parallel loops below
   hs.tpos.resize(nnzb);
-  for (int64_t i = 0; i < n; ++i)
-    for (int32_t k = hs.row_ptr[i]; k < hs.row_ptr[i + 1]; ++k) hs.tpos[k] = find_blk(hs.col[k], (int32_t)i);
+  parallel_for((int32_t)((n + CHUNK - 1) / CHUNK), setup_threads(64), [&](int32_t ch, int) {
+    const int64_t i1 = std::min<int64_t>(n, (ch + 1) * CHUNK);
+    for (int64_t i = ch * CHUNK; i < i1; ++i)
+      for (int32_t k = hs.row_ptr[i]; k < hs.row_ptr[i + 1]; ++k) hs.tpos[k] = find_blk(hs.col[k], (int32_t)i);
+  });
 
   // ---- element gather lists (deterministic: ordered by triangle) ---------
   // (the node lists were built with the pattern above)
   hs.blk_inc_ptr.assign(nnzb + 1, 0);
   std::vector<int32_t> tblk(9 * m);
-  for (int64_t t = 0; t < m; ++t)
-    for (int a = 0; a < 3; ++a)
-      for (int b = 0; b < 3; ++b) {
-        int32_t k = find_blk(hs.tri[3 * t + a], hs.tri[3 * t + b]);
-        tblk[9 * t + 3 * a + b] = k;
-        hs.blk_inc_ptr[k + 1]++;
-      }
+  parallel_for((int32_t)((m + CHUNK - 1) / CHUNK), setup_threads(64), [&](int32_t ch, int) {
+    const int64_t t1 = std::min<int64_t>(m, (ch + 1) * CHUNK);
+    for (int64_t t = ch * CHUNK; t < t1; ++t)
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) tblk[9 * t + 3 * a + b] = find_blk(hs.tri[3 * t + a], hs.tri[3 * t + b]);
+  });
+  for (int64_t e = 0; e < 9 * m; ++e) hs.blk_inc_ptr[tblk[e] + 1]++;
   for (int64_t k = 0; k < nnzb; ++k) hs.blk_inc_ptr[k + 1] += hs.blk_inc_ptr[k];
   hs.blk_inc.resize(9 * m);
   {
