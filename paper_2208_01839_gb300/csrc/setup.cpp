@@ -130,19 +130,24 @@ static int setup_threads(int32_t units) {
   return (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)(hw ? hw : 1), 16, (int64_t)units}));
 }
 
-// f(i, thread) for i in [0, n) over nth threads (dynamic assignment)
+// f(i, worker) for i in [0, n): the calling thread is worker 0 and up to nth - 1
+// helper threads take items from the same counter, so the loop completes (with
+// fewer workers) even where a helper cannot be started
 template <class F>
 static void parallel_for(int32_t n, int nth, F&& f) {
-  if (nth <= 1) {
-    for (int32_t i = 0; i < n; ++i) f(i, 0);
-    return;
-  }
   std::atomic<int32_t> next{0};
+  auto work = [&](int t) {
+    for (int32_t i = next.fetch_add(1); i < n; i = next.fetch_add(1)) f(i, t);
+  };
   std::vector<std::thread> th;
-  for (int t = 0; t < nth; ++t)
-    th.emplace_back([&, t] {
-      for (int32_t i = next.fetch_add(1); i < n; i = next.fetch_add(1)) f(i, t);
-    });
+  for (int t = 1; t < nth; ++t) {
+    try {
+      th.emplace_back(work, t);
+    } catch (...) {
+      break;
+    }
+  }
+  work(0);
   for (auto& x : th) x.join();
 }
 
