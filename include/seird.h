@@ -373,6 +373,10 @@ int64_t seird_launch_count(void);
  * subdomains and the ILU(0) level schedules and solve plans for `mesh` under
  * `opt` (NULL: defaults) and verifies their invariants: owned ranges tile the
  * nodes, rows sorted with their diagonal, a structurally symmetric pattern,
+ * each node's element gather list naming its triangle corners in order and
+ * each block's naming the corner pairs that reach it, coarse units tiling the
+ * nodes, the J Z segments of the two-grid lying in their row and in one unit,
+ * the coarse segment sums visiting every block once,
  * every owned node in its subdomain, every sweep a permutation of the
  * subdomain's rows, every stage within the shared-memory rings, every
  * dependency of a row in an earlier stage, and the row records numbering the

@@ -731,6 +731,41 @@ int64_t check_setup(const HostSetup& hs, std::string& first) {
     }
     fail(diag, "missing diagonal block");
   }
+  // assembly gather lists: each node lists its (triangle, corner) entries and each block
+  // its (triangle, corner pair) entries exactly once, ascending in the triangle
+  const int64_t m = hs.m;
+  fail((int64_t)hs.node_inc.size() == 3 * m && hs.node_inc_ptr[n] == 3 * m, "node gather list sizes");
+  for (int64_t i = 0; i < n && !bad; ++i)
+    for (int32_t e = hs.node_inc_ptr[i]; e < hs.node_inc_ptr[i + 1]; ++e) {
+      fail(hs.tri[hs.node_inc[e]] == i, "node gather entry of another node");
+      if (e > hs.node_inc_ptr[i]) fail(hs.node_inc[e] > hs.node_inc[e - 1], "node gather order");
+    }
+  fail((int64_t)hs.blk_inc.size() == 9 * m && hs.blk_inc_ptr[nnzb] == 9 * m, "block gather list sizes");
+  for (int64_t i = 0; i < n && !bad; ++i)
+    for (int32_t k = hs.row_ptr[i]; k < hs.row_ptr[i + 1]; ++k)
+      for (int32_t e = hs.blk_inc_ptr[k]; e < hs.blk_inc_ptr[k + 1]; ++e) {
+        const int32_t v = hs.blk_inc[e], t = v / 9, a = (v % 9) / 3, b = v % 3;
+        fail(hs.tri[3 * (int64_t)t + a] == i && hs.tri[3 * (int64_t)t + b] == hs.col[k], "block gather entry");
+        if (e > hs.blk_inc_ptr[k]) fail(v > hs.blk_inc[e - 1], "block gather order");
+      }
+  // coarse space: units tile the nodes; the J Z segments of a row are the runs of its
+  // blocks in one unit; the segment sums visit every J block once
+  fail((int32_t)hs.cunit_ptr.size() == hs.Pc + 1 && hs.cunit_ptr[0] == 0 && hs.cunit_ptr[hs.Pc] == n, "coarse units");
+  for (int32_t u = 0; u < hs.Pc && !bad; ++u)
+    for (int32_t i = hs.cunit_ptr[u]; i < hs.cunit_ptr[u + 1]; ++i) fail(hs.cunit[i] == u, "coarse unit map");
+  if (!hs.az_ptr.empty()) {
+    for (int64_t i = 0; i < n && !bad; ++i)
+      for (int64_t s = hs.az_ptr[i]; s < hs.az_ptr[i + 1]; ++s) {
+        fail(hs.az_blk[s] >= hs.row_ptr[i] && hs.az_blk[s + 1] <= hs.row_ptr[i + 1] && hs.az_blk[s] < hs.az_blk[s + 1],
+             "J Z segment outside its row");
+        for (int32_t k = hs.az_blk[s]; k < hs.az_blk[s + 1]; ++k)
+          fail(hs.cunit[hs.col[k]] == hs.az_unit[s], "J Z segment mixes coarse units");
+      }
+  }
+  if (!hs.cseg_blk.empty()) {
+    std::vector<uint8_t> hit(nnzb, 0);
+    for (int32_t k : hs.cseg_blk) fail(k >= 0 && k < nnzb && hit[k]++ == 0, "coarse segment order not a permutation");
+  }
   // subdomains: distinct rows covering the owned nodes, local diagonal in place
   const int64_t NL = (int64_t)hs.sd_node.size();
   fail((int32_t)hs.sd_row0.size() == P + 1 && hs.sd_row0[P] == NL, "subdomain row ranges");

@@ -55,7 +55,7 @@ def test_random_partition_is_not_geometric():
 
 def test_ontario_like_uneven_bisection():
     wl = I.ontario_workload(20_000, n_subdomains=16)
-    st = _check(wl.xy, wl.tri, n_subdomains=16, overlap=2, seed=3)
+    st = _check(wl.xy, wl.tri, n_subdomains=16, overlap=2, seed=3, coarse=2)  # with the J Z segments
     assert st["n_subdomains"] == 16
     # a 5x5 block per node pair of the P1 graph: about 7 blocks per row
     assert 5 * st["n_nodes"] < st["nnzb"] < 9 * st["n_nodes"]
@@ -88,8 +88,8 @@ def test_ensemble_union_mesh():
     uxy = np.concatenate([xy] * B)
     utri = np.concatenate([tri + k * n for k in range(B)]).astype(np.int32)
     uown = np.concatenate([owner + k * P for k in range(B)]).astype(np.int32)
-    st = _check(uxy, utri, owner=uown, overlap=2)
-    one = _check(xy, tri, owner=owner, overlap=2)
+    st = _check(uxy, utri, owner=uown, overlap=2, coarse=2)
+    one = _check(xy, tri, owner=owner, overlap=2, coarse=2)
     assert st["n_subdomains"] == B * P and st["nnzb"] == B * one["nnzb"]
     assert st["subdomain_rows"] == B * one["subdomain_rows"]
     assert st["forward_stages"] == B * one["forward_stages"] and st["backward_stages"] == B * one["backward_stages"]
