@@ -38,7 +38,9 @@
  * Errors.  Every int-returning call returns SEIRD_OK (0) or a negative
  * SEIRD_E* code; seird_last_error() gives a message.  The library never traps
  * or aborts, never waits without bound, and leaves the state at u^n when a
- * step fails.  A context is used by one host thread at a time.
+ * step fails.  No C++ exception crosses this interface: a failed host
+ * allocation returns SEIRD_ENOMEM like a failed device one.  A context is
+ * used by one host thread at a time.
  */
 #ifndef SEIRD_H
 #define SEIRD_H

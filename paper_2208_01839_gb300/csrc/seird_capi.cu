@@ -11,6 +11,8 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <memory>
+#include <stdexcept>
 #include <string>
 #include <vector>
 
@@ -60,6 +62,36 @@ int fail(seird_ctx* ctx, int code, const std::string& msg) {
     }                      \
   } while (0)
 
+// Host exceptions end as error codes and never cross the C ABI: chiefly a failed
+// host allocation (the set-up of a paper-scale mesh holds several GB of host
+// arrays), reported as SEIRD_ENOMEM.
+void note_error(seird_ctx* ctx, const char* msg) noexcept {
+  try {
+    if (ctx) ctx->last_error = msg;
+    else g_create_error = msg;
+  } catch (...) {
+  }
+}
+
+template <class F>
+int host_guard(seird_ctx* ctx, F&& body) noexcept {
+  try {
+    return body();
+  } catch (const std::bad_alloc&) {
+    note_error(ctx, "host allocation failed");
+    return SEIRD_ENOMEM;
+  } catch (const std::length_error&) {
+    note_error(ctx, "host allocation failed (size beyond the container limit)");
+    return SEIRD_ENOMEM;
+  } catch (const std::exception& e) {
+    note_error(ctx, e.what());
+    return SEIRD_EINVAL;
+  } catch (...) {
+    note_error(ctx, "unknown host exception");
+    return SEIRD_EINVAL;
+  }
+}
+
 template <class T>
 int dalloc(seird_ctx* ctx, T** p, size_t count) {
   if (count == 0) count = 1;
@@ -69,7 +101,13 @@ int dalloc(seird_ctx* ctx, T** p, size_t count) {
     return fail(ctx, SEIRD_ENOMEM, "cudaMalloc of " + std::to_string(sizeof(T) * count) + " bytes: " +
                                        cudaGetErrorString(e));
   }
-  ctx->allocations.push_back((void*)*p);
+  try {
+    ctx->allocations.push_back((void*)*p);
+  } catch (...) {
+    cudaFree(*p);
+    *p = nullptr;
+    throw;
+  }
   ctx->device_bytes += (int64_t)(sizeof(T) * count);
   return SEIRD_OK;
 }
@@ -1414,7 +1452,7 @@ int seird_create(const seird_mesh* mesh, const seird_params* params, const seird
   ctx->params.beta_field = nullptr;  // copied to the device, never retained
   if (opt) ctx->opt = *opt;
   else seird_default_options(&ctx->opt);
-  int rc = create_impl(ctx, mesh, params);
+  int rc = host_guard(ctx, [&]() -> int { return create_impl(ctx, mesh, params); });
   ctx->opt.owner = nullptr;  // read during create only, never retained
   if (rc) {
     g_create_error = ctx->last_error;
@@ -1431,148 +1469,164 @@ int seird_create_ensemble(const seird_mesh* mesh, int32_t n_samples, const seird
   *out = nullptr;
   if (!mesh || !params || !mesh->xy || !mesh->tri) return fail(nullptr, SEIRD_EINVAL, "mesh and params must not be NULL");
   if (n_samples < 1) return fail(nullptr, SEIRD_EINVAL, "n_samples must be >= 1");
-  seird_options o;
-  if (opt) o = *opt;
-  else seird_default_options(&o);
-  const int64_t n = mesh->n_nodes, m = mesh->n_tris, B = n_samples;
-  if (n < 3 || m < 1) return fail(nullptr, SEIRD_EINVAL, "mesh needs at least 3 nodes and 1 triangle");
-  if (B * n > (int64_t)INT32_MAX / 8 || B * m > (int64_t)INT32_MAX / 9)
-    return fail(nullptr, SEIRD_EINVAL, "ensemble too large for 32-bit element maps");
-  // one partition of the mesh, repeated for every sample: sample k owns
-  // subdomains [k P, (k+1) P), so its nodes are one contiguous internal range
-  std::vector<int32_t> own;
-  int32_t P = 0;
-  std::string err;
-  int rc = partition_nodes(mesh, &o, own, P, err);
-  if (rc) return fail(nullptr, rc, err);
-  std::vector<double> xy(2 * B * n);
-  std::vector<int32_t> tri(3 * B * m), owner(B * n);
-  for (int64_t k = 0; k < B; ++k) {
-    std::copy(mesh->xy, mesh->xy + 2 * n, xy.begin() + 2 * k * n);
-    for (int64_t q = 0; q < 3 * m; ++q) tri[3 * k * m + q] = (int32_t)(mesh->tri[q] + k * n);
-    for (int64_t i = 0; i < n; ++i) owner[k * n + i] = (int32_t)(own[i] + k * P);
-  }
-  std::vector<double> bf;
-  seird_params p0 = params[0];
-  if (p0.beta_field) {
-    bf.resize(B * n);
-    for (int64_t k = 0; k < B; ++k) std::copy(p0.beta_field, p0.beta_field + n, bf.begin() + k * n);
-    p0.beta_field = bf.data();
-  }
-  o.owner = owner.data();
-  o.n_subdomains = (int32_t)(B * P);
-  if (o.coarse_group == 0) {
-    // coarse units must not span two samples: the group size divides the per-sample partition
-    int32_t G = 1;
-    auto fits = [&](int32_t g) {
-      const int64_t units = B * (P / g);
-      return 5 * units <= DENSE_COARSE_MAX && units <= COARSE_BLOCKCOL_MAX;
-    };
-    while (G < P && !(P % G == 0 && fits(G))) ++G;
-    o.coarse_group = G;
-  }
-  seird_mesh um{B * n, B * m, xy.data(), tri.data()};
-  seird_ctx* ctx = nullptr;
-  rc = seird_create(&um, &p0, &o, &ctx);
-  if (rc) return rc;
-  std::vector<double> rows(RATE_ROW * B);
-  for (int64_t k = 0; k < B; ++k) {
-    const seird_params& q = params[k];
-    const double v[RATE_ROW] = {q.A,     q.beta_i, q.beta_e, q.sigma, q.gamma_e, q.gamma_r, q.gamma_d,
-                                q.alpha, q.mu,     q.nu[0],  q.nu[1], q.nu[2],   q.nu[3]};
-    std::copy(v, v + RATE_ROW, rows.begin() + RATE_ROW * k);
-  }
-  rc = upload(ctx, &ctx->rtab, rows);
-  if (rc) {
-    g_create_error = ctx->last_error;
-    seird_destroy(ctx);
-    return rc;
-  }
-  ctx->n_samples = n_samples;
-  ctx->n_per_sample = n;
-  // internal triangles are ordered by their smallest node, so each sample's are one range
-  ctx->sample_tri_ptr.assign(B + 1, 0);
-  for (int64_t t = 0; t < B * m; ++t) {
-    const int32_t* v = ctx->hs.tri.data() + 3 * t;
-    ctx->sample_tri_ptr[std::min({v[0], v[1], v[2]}) / n + 1]++;
-  }
-  for (int64_t k = 0; k < B; ++k) ctx->sample_tri_ptr[k + 1] += ctx->sample_tri_ptr[k];
-  *out = ctx;
-  return SEIRD_OK;
+  return host_guard(nullptr, [&]() -> int {
+    seird_options o;
+    if (opt) o = *opt;
+    else seird_default_options(&o);
+    const int64_t n = mesh->n_nodes, m = mesh->n_tris, B = n_samples;
+    if (n < 3 || m < 1) return fail(nullptr, SEIRD_EINVAL, "mesh needs at least 3 nodes and 1 triangle");
+    if (B * n > (int64_t)INT32_MAX / 8 || B * m > (int64_t)INT32_MAX / 9)
+      return fail(nullptr, SEIRD_EINVAL, "ensemble too large for 32-bit element maps");
+    // one partition of the mesh, repeated for every sample: sample k owns
+    // subdomains [k P, (k+1) P), so its nodes are one contiguous internal range
+    std::vector<int32_t> own;
+    int32_t P = 0;
+    std::string err;
+    int rc = partition_nodes(mesh, &o, own, P, err);
+    if (rc) return fail(nullptr, rc, err);
+    std::vector<double> xy(2 * B * n);
+    std::vector<int32_t> tri(3 * B * m), owner(B * n);
+    for (int64_t k = 0; k < B; ++k) {
+      std::copy(mesh->xy, mesh->xy + 2 * n, xy.begin() + 2 * k * n);
+      for (int64_t q = 0; q < 3 * m; ++q) tri[3 * k * m + q] = (int32_t)(mesh->tri[q] + k * n);
+      for (int64_t i = 0; i < n; ++i) owner[k * n + i] = (int32_t)(own[i] + k * P);
+    }
+    std::vector<double> bf;
+    seird_params p0 = params[0];
+    if (p0.beta_field) {
+      bf.resize(B * n);
+      for (int64_t k = 0; k < B; ++k) std::copy(p0.beta_field, p0.beta_field + n, bf.begin() + k * n);
+      p0.beta_field = bf.data();
+    }
+    o.owner = owner.data();
+    o.n_subdomains = (int32_t)(B * P);
+    if (o.coarse_group == 0) {
+      // coarse units must not span two samples: the group size divides the per-sample partition
+      int32_t G = 1;
+      auto fits = [&](int32_t g) {
+        const int64_t units = B * (P / g);
+        return 5 * units <= DENSE_COARSE_MAX && units <= COARSE_BLOCKCOL_MAX;
+      };
+      while (G < P && !(P % G == 0 && fits(G))) ++G;
+      o.coarse_group = G;
+    }
+    seird_mesh um{B * n, B * m, xy.data(), tri.data()};
+    seird_ctx* ctx = nullptr;
+    rc = seird_create(&um, &p0, &o, &ctx);
+    if (rc) return rc;
+    std::unique_ptr<seird_ctx, void (*)(seird_ctx*)> hold(ctx, seird_destroy);  // destroyed unless completed
+    std::vector<double> rows(RATE_ROW * B);
+    for (int64_t k = 0; k < B; ++k) {
+      const seird_params& q = params[k];
+      const double v[RATE_ROW] = {q.A,     q.beta_i, q.beta_e, q.sigma, q.gamma_e, q.gamma_r, q.gamma_d,
+                                  q.alpha, q.mu,     q.nu[0],  q.nu[1], q.nu[2],   q.nu[3]};
+      std::copy(v, v + RATE_ROW, rows.begin() + RATE_ROW * k);
+    }
+    rc = upload(ctx, &ctx->rtab, rows);
+    if (rc) {
+      g_create_error = ctx->last_error;
+      return rc;
+    }
+    ctx->n_samples = n_samples;
+    ctx->n_per_sample = n;
+    // internal triangles are ordered by their smallest node, so each sample's are one range
+    ctx->sample_tri_ptr.assign(B + 1, 0);
+    for (int64_t t = 0; t < B * m; ++t) {
+      const int32_t* v = ctx->hs.tri.data() + 3 * t;
+      ctx->sample_tri_ptr[std::min({v[0], v[1], v[2]}) / n + 1]++;
+    }
+    for (int64_t k = 0; k < B; ++k) ctx->sample_tri_ptr[k + 1] += ctx->sample_tri_ptr[k];
+    *out = hold.release();
+    return SEIRD_OK;
+  });
 }
 
 int seird_set_state(seird_ctx* ctx, const double* u, int on_device, double t) {
-  if (!ctx || !u) return fail(ctx, SEIRD_EINVAL, "NULL argument");
-  TRY(to_internal(ctx, u, on_device, ctx->U));
-  ctx->t = t;
-  ctx->have_prev = false;
-  return SEIRD_OK;
+  return host_guard(ctx, [&]() -> int {
+    if (!ctx || !u) return fail(ctx, SEIRD_EINVAL, "NULL argument");
+    TRY(to_internal(ctx, u, on_device, ctx->U));
+    ctx->t = t;
+    ctx->have_prev = false;
+    return SEIRD_OK;
+  });
 }
 
 int seird_get_state(const seird_ctx* cctx, double* u, int on_device, double* t) {
-  seird_ctx* ctx = const_cast<seird_ctx*>(cctx);
-  if (!ctx || !u) return fail(ctx, SEIRD_EINVAL, "NULL argument");
-  TRY(from_internal(ctx, ctx->U, u, on_device));
-  if (t) *t = ctx->t;
-  return SEIRD_OK;
+  return host_guard(const_cast<seird_ctx*>(cctx), [&]() -> int {
+    seird_ctx* ctx = const_cast<seird_ctx*>(cctx);
+    if (!ctx || !u) return fail(ctx, SEIRD_EINVAL, "NULL argument");
+    TRY(from_internal(ctx, ctx->U, u, on_device));
+    if (t) *t = ctx->t;
+    return SEIRD_OK;
+  });
 }
 
 int seird_step(seird_ctx* ctx, seird_stats* stats) {
-  if (!ctx) return fail(nullptr, SEIRD_EINVAL, "NULL context");
-  return newton_step(ctx, stats);
+  return host_guard(ctx, [&]() -> int {
+    if (!ctx) return fail(nullptr, SEIRD_EINVAL, "NULL context");
+    return newton_step(ctx, stats);
+  });
 }
 
 int seird_run(seird_ctx* ctx, int32_t n_steps, seird_stats* per_step) {
-  if (!ctx || n_steps < 0) return fail(ctx, SEIRD_EINVAL, "bad argument");
-  for (int32_t k = 0; k < n_steps; ++k) TRY(newton_step(ctx, per_step ? per_step + k : nullptr));
-  return SEIRD_OK;
+  return host_guard(ctx, [&]() -> int {
+    if (!ctx || n_steps < 0) return fail(ctx, SEIRD_EINVAL, "bad argument");
+    for (int32_t k = 0; k < n_steps; ++k) TRY(newton_step(ctx, per_step ? per_step + k : nullptr));
+    return SEIRD_OK;
+  });
 }
 
 int seird_set_params(seird_ctx* ctx, const seird_params* params) {
-  if (!ctx || !params) return fail(ctx, SEIRD_EINVAL, "NULL argument");
-  if (ctx->rtab) return fail(ctx, SEIRD_EINVAL, "set_params: an ensemble's rates are fixed at creation");
-  ctx->have_prev = false;  // the previous step's residual belongs to the old rates
-  ctx->params = *params;
-  ctx->params.beta_field = nullptr;
-  if (params->beta_field) {
-    const HostSetup& hs = ctx->hs;
-    std::vector<double> bf(hs.n);
-    for (int64_t k = 0; k < hs.n; ++k) bf[k] = params->beta_field[hs.perm[k]];
-    if (!ctx->bfield) TRY(dalloc(ctx, &ctx->bfield, hs.n));
-    CK(cudaMemcpy(ctx->bfield, bf.data(), sizeof(double) * hs.n, cudaMemcpyHostToDevice));
-  }
-  ctx->pc_ready = false;
-  return SEIRD_OK;
+  return host_guard(ctx, [&]() -> int {
+    if (!ctx || !params) return fail(ctx, SEIRD_EINVAL, "NULL argument");
+    if (ctx->rtab) return fail(ctx, SEIRD_EINVAL, "set_params: an ensemble's rates are fixed at creation");
+    ctx->have_prev = false;  // the previous step's residual belongs to the old rates
+    ctx->params = *params;
+    ctx->params.beta_field = nullptr;
+    if (params->beta_field) {
+      const HostSetup& hs = ctx->hs;
+      std::vector<double> bf(hs.n);
+      for (int64_t k = 0; k < hs.n; ++k) bf[k] = params->beta_field[hs.perm[k]];
+      if (!ctx->bfield) TRY(dalloc(ctx, &ctx->bfield, hs.n));
+      CK(cudaMemcpy(ctx->bfield, bf.data(), sizeof(double) * hs.n, cudaMemcpyHostToDevice));
+    }
+    ctx->pc_ready = false;
+    return SEIRD_OK;
+  });
 }
 
 int seird_set_beta_schedule(seird_ctx* ctx, const seird_beta_schedule* sched) {
-  if (!ctx) return fail(ctx, SEIRD_EINVAL, "NULL context");
-  if (ctx->rtab) return fail(ctx, SEIRD_EINVAL, "beta schedule: not available on an ensemble");
-  ctx->have_prev = false;
-  if (!sched) {
-    ctx->sched_on = false;
+  return host_guard(ctx, [&]() -> int {
+    if (!ctx) return fail(ctx, SEIRD_EINVAL, "NULL context");
+    if (ctx->rtab) return fail(ctx, SEIRD_EINVAL, "beta schedule: not available on an ensemble");
+    ctx->have_prev = false;
+    if (!sched) {
+      ctx->sched_on = false;
+      ctx->pc_ready = false;
+      return SEIRD_OK;
+    }
+    const double v[10] = {sched->b0,        sched->b1,        sched->t_mid,     sched->beta_central, sched->beta_eastern,
+                          sched->beta_western, sched->x_eastern, sched->x_western, sched->k_eastern,   sched->k_western};
+    for (double x : v)
+      if (!std::isfinite(x)) return fail(ctx, SEIRD_EINVAL, "beta schedule: non-finite value");
+    if (!ctx->bsched) TRY(dalloc(ctx, &ctx->bsched, ctx->hs.n));
+    launch_beta_field(ctx->hs.n, ctx->xy, *sched, ctx->bsched, ctx->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->sched = *sched;
+    ctx->sched_on = true;
     ctx->pc_ready = false;
     return SEIRD_OK;
-  }
-  const double v[10] = {sched->b0,        sched->b1,        sched->t_mid,     sched->beta_central, sched->beta_eastern,
-                        sched->beta_western, sched->x_eastern, sched->x_western, sched->k_eastern,   sched->k_western};
-  for (double x : v)
-    if (!std::isfinite(x)) return fail(ctx, SEIRD_EINVAL, "beta schedule: non-finite value");
-  if (!ctx->bsched) TRY(dalloc(ctx, &ctx->bsched, ctx->hs.n));
-  launch_beta_field(ctx->hs.n, ctx->xy, *sched, ctx->bsched, ctx->stream);
-  CK(cudaGetLastError());
-  CK(cudaStreamSynchronize(ctx->stream));
-  ctx->sched = *sched;
-  ctx->sched_on = true;
-  ctx->pc_ready = false;
-  return SEIRD_OK;
+  });
 }
 
 int seird_adjoint(seird_ctx* ctx, const seird_misfit* spec, double* misfit, double* grad, double* grad_field) {
-  if (!ctx || !spec) return fail(ctx, SEIRD_EINVAL, "NULL argument");
-  if (ctx->sched_on) return fail(ctx, SEIRD_EINVAL, "adjoint: turn the beta schedule off first (constant rates only)");
+  return host_guard(ctx, [&]() -> int {
+    if (!ctx || !spec) return fail(ctx, SEIRD_EINVAL, "NULL argument");
+    if (ctx->sched_on) return fail(ctx, SEIRD_EINVAL, "adjoint: turn the beta schedule off first (constant rates only)");
 
-  return adjoint_impl(ctx, spec, misfit, grad, grad_field);
+    return adjoint_impl(ctx, spec, misfit, grad, grad_field);
+  });
 }
 
 int seird_get_info(const seird_ctx* ctx, seird_info* info) {
@@ -1594,85 +1648,99 @@ int seird_get_info(const seird_ctx* ctx, seird_info* info) {
 }
 
 int seird_eval_residual(seird_ctx* ctx, const double* u, const double* u_prev, double* F, int on_device) {
-  if (!ctx || !u || !u_prev || !F) return fail(ctx, SEIRD_EINVAL, "NULL argument");
-  TRY(to_internal(ctx, u, on_device, ctx->Ut));
-  TRY(to_internal(ctx, u_prev, on_device, ctx->stage2));
-  double fn;
-  TRY(residual(ctx, ctx->Ut, ctx->stage2, ctx->Ft, &fn));
-  return from_internal(ctx, ctx->Ft, F, on_device);
+  return host_guard(ctx, [&]() -> int {
+    if (!ctx || !u || !u_prev || !F) return fail(ctx, SEIRD_EINVAL, "NULL argument");
+    TRY(to_internal(ctx, u, on_device, ctx->Ut));
+    TRY(to_internal(ctx, u_prev, on_device, ctx->stage2));
+    double fn;
+    TRY(residual(ctx, ctx->Ut, ctx->stage2, ctx->Ft, &fn));
+    return from_internal(ctx, ctx->Ft, F, on_device);
+  });
 }
 
 int seird_eval_jacobian(seird_ctx* ctx, const double* u, int on_device) {
-  if (!ctx || !u) return fail(ctx, SEIRD_EINVAL, "NULL argument");
-  TRY(to_internal(ctx, u, on_device, ctx->Ut));
-  TRY(jacobian(ctx, ctx->Ut, ctx->opt.nonlinear == 1));
-  return check_flags(ctx, "jacobian");
+  return host_guard(ctx, [&]() -> int {
+    if (!ctx || !u) return fail(ctx, SEIRD_EINVAL, "NULL argument");
+    TRY(to_internal(ctx, u, on_device, ctx->Ut));
+    TRY(jacobian(ctx, ctx->Ut, ctx->opt.nonlinear == 1));
+    return check_flags(ctx, "jacobian");
+  });
 }
 
 int seird_get_jacobian(const seird_ctx* cctx, int32_t* row_ptr, int32_t* col, double* val) {
-  seird_ctx* ctx = const_cast<seird_ctx*>(cctx);
-  if (!ctx || !row_ptr || !col || !val) return fail(ctx, SEIRD_EINVAL, "NULL argument");
-  if (!ctx->jac_ready) return fail(ctx, SEIRD_EINVAL, "no Jacobian assembled");
-  const HostSetup& hs = ctx->hs;
-  const int64_t nnzb = (int64_t)hs.col.size();
-  std::vector<double> v(25 * nnzb);
-  CK(cudaStreamSynchronize(ctx->stream));
-  if (mixed(ctx)) {  // the mixed path keeps only the FP32 copy
-    std::vector<float> v32(25 * nnzb);
-    CK(cudaMemcpy(v32.data(), ctx->val32, sizeof(float) * v32.size(), cudaMemcpyDeviceToHost));
-    for (size_t q = 0; q < v.size(); ++q) v[q] = v32[q];
-  } else {
-    CK(cudaMemcpy(v.data(), ctx->val, sizeof(double) * v.size(), cudaMemcpyDeviceToHost));
-  }
-  row_ptr[0] = 0;
-  std::vector<std::pair<int32_t, int32_t>> ent;
-  int64_t pos = 0;
-  for (int64_t i = 0; i < hs.n; ++i) {
-    const int32_t k = hs.iperm[i];
-    ent.clear();
-    for (int32_t b = hs.row_ptr[k]; b < hs.row_ptr[k + 1]; ++b) ent.push_back({hs.perm[hs.col[b]], b});
-    std::sort(ent.begin(), ent.end());
-    for (auto& e : ent) {
-      col[pos] = e.first;
-      std::memcpy(val + 25 * pos, v.data() + 25 * (int64_t)e.second, 25 * sizeof(double));
-      ++pos;
+  return host_guard(const_cast<seird_ctx*>(cctx), [&]() -> int {
+    seird_ctx* ctx = const_cast<seird_ctx*>(cctx);
+    if (!ctx || !row_ptr || !col || !val) return fail(ctx, SEIRD_EINVAL, "NULL argument");
+    if (!ctx->jac_ready) return fail(ctx, SEIRD_EINVAL, "no Jacobian assembled");
+    const HostSetup& hs = ctx->hs;
+    const int64_t nnzb = (int64_t)hs.col.size();
+    std::vector<double> v(25 * nnzb);
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (mixed(ctx)) {  // the mixed path keeps only the FP32 copy
+      std::vector<float> v32(25 * nnzb);
+      CK(cudaMemcpy(v32.data(), ctx->val32, sizeof(float) * v32.size(), cudaMemcpyDeviceToHost));
+      for (size_t q = 0; q < v.size(); ++q) v[q] = v32[q];
+    } else {
+      CK(cudaMemcpy(v.data(), ctx->val, sizeof(double) * v.size(), cudaMemcpyDeviceToHost));
     }
-    row_ptr[i + 1] = (int32_t)pos;
-  }
-  return SEIRD_OK;
+    row_ptr[0] = 0;
+    std::vector<std::pair<int32_t, int32_t>> ent;
+    int64_t pos = 0;
+    for (int64_t i = 0; i < hs.n; ++i) {
+      const int32_t k = hs.iperm[i];
+      ent.clear();
+      for (int32_t b = hs.row_ptr[k]; b < hs.row_ptr[k + 1]; ++b) ent.push_back({hs.perm[hs.col[b]], b});
+      std::sort(ent.begin(), ent.end());
+      for (auto& e : ent) {
+        col[pos] = e.first;
+        std::memcpy(val + 25 * pos, v.data() + 25 * (int64_t)e.second, 25 * sizeof(double));
+        ++pos;
+      }
+      row_ptr[i + 1] = (int32_t)pos;
+    }
+    return SEIRD_OK;
+  });
 }
 
 int seird_apply_jacobian(seird_ctx* ctx, const double* x, double* y, int on_device) {
-  if (!ctx || !x || !y) return fail(ctx, SEIRD_EINVAL, "NULL argument");
-  if (!ctx->jac_ready) return fail(ctx, SEIRD_EINVAL, "no Jacobian assembled");
-  TRY(to_internal(ctx, x, on_device, ctx->stage2));
-  TRY(spmv(ctx, ctx->stage2, ctx->Ft));
-  return from_internal(ctx, ctx->Ft, y, on_device);
+  return host_guard(ctx, [&]() -> int {
+    if (!ctx || !x || !y) return fail(ctx, SEIRD_EINVAL, "NULL argument");
+    if (!ctx->jac_ready) return fail(ctx, SEIRD_EINVAL, "no Jacobian assembled");
+    TRY(to_internal(ctx, x, on_device, ctx->stage2));
+    TRY(spmv(ctx, ctx->stage2, ctx->Ft));
+    return from_internal(ctx, ctx->Ft, y, on_device);
+  });
 }
 
 int seird_precond_setup(seird_ctx* ctx) {
-  if (!ctx) return fail(nullptr, SEIRD_EINVAL, "NULL context");
-  return pc_setup(ctx);
+  return host_guard(ctx, [&]() -> int {
+    if (!ctx) return fail(nullptr, SEIRD_EINVAL, "NULL context");
+    return pc_setup(ctx);
+  });
 }
 
 int seird_precond_apply(seird_ctx* ctx, const double* r, double* z, int on_device) {
-  if (!ctx || !r || !z) return fail(ctx, SEIRD_EINVAL, "NULL argument");
-  if (!ctx->pc_ready) return fail(ctx, SEIRD_EINVAL, "preconditioner not set up");
-  TRY(to_internal(ctx, r, on_device, ctx->stage2));
-  TRY(pc_apply(ctx, ctx->stage2, ctx->Ft));
-  return from_internal(ctx, ctx->Ft, z, on_device);
+  return host_guard(ctx, [&]() -> int {
+    if (!ctx || !r || !z) return fail(ctx, SEIRD_EINVAL, "NULL argument");
+    if (!ctx->pc_ready) return fail(ctx, SEIRD_EINVAL, "preconditioner not set up");
+    TRY(to_internal(ctx, r, on_device, ctx->stage2));
+    TRY(pc_apply(ctx, ctx->stage2, ctx->Ft));
+    return from_internal(ctx, ctx->Ft, z, on_device);
+  });
 }
 
 int seird_linear_solve(seird_ctx* ctx, const double* b, double* x, int on_device, int32_t* its) {
-  if (!ctx || !b || !x) return fail(ctx, SEIRD_EINVAL, "NULL argument");
-  if (!ctx->pc_ready) return fail(ctx, SEIRD_EINVAL, "preconditioner not set up");
-  TRY(to_internal(ctx, b, on_device, ctx->stage2));
-  int k = 0;
-  bool conv = false;
-  TRY(gmres(ctx, ctx->stage2, ctx->dU, ctx->opt.gmres_rtol, &k, &conv));
-  if (its) *its = k;
-  TRY(from_internal(ctx, ctx->dU, x, on_device));
-  return conv ? SEIRD_OK : fail(ctx, SEIRD_EGMRES, "gmres: iteration limit reached");
+  return host_guard(ctx, [&]() -> int {
+    if (!ctx || !b || !x) return fail(ctx, SEIRD_EINVAL, "NULL argument");
+    if (!ctx->pc_ready) return fail(ctx, SEIRD_EINVAL, "preconditioner not set up");
+    TRY(to_internal(ctx, b, on_device, ctx->stage2));
+    int k = 0;
+    bool conv = false;
+    TRY(gmres(ctx, ctx->stage2, ctx->dU, ctx->opt.gmres_rtol, &k, &conv));
+    if (its) *its = k;
+    TRY(from_internal(ctx, ctx->dU, x, on_device));
+    return conv ? SEIRD_OK : fail(ctx, SEIRD_EGMRES, "gmres: iteration limit reached");
+  });
 }
 
 int seird_bsr_spmv(int64_t n_rows, const int32_t* row_ptr, const int32_t* col, const double* val, const double* x,

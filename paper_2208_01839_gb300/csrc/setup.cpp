@@ -7,8 +7,11 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <exception>
+#include <mutex>
 #include <numeric>
 #include <random>
+#include <stdexcept>
 #include <string>
 #include <thread>
 #include <vector>
@@ -132,12 +135,22 @@ static int setup_threads(int32_t units) {
 
 // f(i, worker) for i in [0, n): the calling thread is worker 0 and up to nth - 1
 // helper threads take items from the same counter, so the loop completes (with
-// fewer workers) even where a helper cannot be started
+// fewer workers) even where a helper cannot be started.  An exception in any
+// worker (a failed allocation) stops the hand-out and is rethrown to the caller
+// once every worker has returned.
 template <class F>
 static void parallel_for(int32_t n, int nth, F&& f) {
   std::atomic<int32_t> next{0};
+  std::exception_ptr first;
+  std::mutex first_mu;
   auto work = [&](int t) {
-    for (int32_t i = next.fetch_add(1); i < n; i = next.fetch_add(1)) f(i, t);
+    try {
+      for (int32_t i = next.fetch_add(1); i < n; i = next.fetch_add(1)) f(i, t);
+    } catch (...) {
+      next.store(n);
+      std::lock_guard<std::mutex> lk(first_mu);
+      if (!first) first = std::current_exception();
+    }
   };
   std::vector<std::thread> th;
   for (int t = 1; t < nth; ++t) {
@@ -149,6 +162,7 @@ static void parallel_for(int32_t n, int nth, F&& f) {
   }
   work(0);
   for (auto& x : th) x.join();
+  if (first) std::rethrow_exception(first);
 }
 
 int build_setup(const seird_mesh* mesh, const seird_options* opt, HostSetup& hs, std::string& err) {
@@ -841,12 +855,19 @@ extern "C" int seird_setup_check(const seird_mesh* mesh, const seird_options* op
   else seird_default_options(&o);
   HostSetup hs;
   std::string err;
-  const int rc = build_setup(mesh, &o, hs, err);
-  if (rc) {
-    set_global_error(err);
-    return rc;
+  int64_t bad = 0;
+  try {  // host exceptions (a failed allocation) end as an error code, as in every other entry point
+    const int rc = build_setup(mesh, &o, hs, err);
+    if (rc) {
+      set_global_error(err);
+      return rc;
+    }
+    bad = check_setup(hs, err);
+  } catch (const std::exception& e) {
+    const bool nomem = dynamic_cast<const std::bad_alloc*>(&e) || dynamic_cast<const std::length_error*>(&e);
+    set_global_error(nomem ? "host allocation failed" : e.what());
+    return nomem ? SEIRD_ENOMEM : SEIRD_EINVAL;
   }
-  const int64_t bad = check_setup(hs, err);
   if (stats) {
     stats[0] = hs.n;
     stats[1] = hs.m;
