@@ -188,6 +188,27 @@ def _ptr(a):
     raise TypeError("expected a numpy array or a torch tensor")
 
 
+def _arr(a, count, dtype, name):
+    """(address, on_device) of a contiguous numpy array or torch tensor holding
+    exactly ``count`` values of ``dtype`` ("float64" or "int32"): the library
+    reads and writes that many values behind the pointer, so a wrong size or
+    type is refused here, before the call."""
+    p, dev = _ptr(a)
+    dt = str(a.dtype)
+    if dt not in (dtype, "torch." + dtype):
+        raise TypeError("%s: expected %s values, got %s" % (name, dtype, dt))
+    size = a.size if isinstance(a, np.ndarray) else a.numel()
+    if size != count:
+        raise ValueError("%s: expected %d values, got %d" % (name, count, size))
+    return p, dev
+
+
+def _same_place(devs, names):
+    if len(set(devs)) != 1:
+        raise ValueError("%s must all be host arrays or all device tensors" % ", ".join(names))
+    return devs[0]
+
+
 def _stream_handle(stream):
     if stream is None:
         return None
@@ -199,7 +220,15 @@ def _stream_handle(stream):
 def bsr_spmv(row_ptr, col, val, x, y, stream=None):
     """y = A x for 5x5-block BSR device tensors (val float64 or float32)."""
     n_rows = row_ptr.numel() - 1
-    fn = _bsr_spmv if str(val.dtype).endswith("float64") else _bsr_spmv_f32
+    nnzb = col.numel()
+    f32 = str(val.dtype).endswith("float32")
+    fn = _bsr_spmv_f32 if f32 else _bsr_spmv
+    args = [_arr(row_ptr, n_rows + 1, "int32", "row_ptr"), _arr(col, nnzb, "int32", "col"),
+            _arr(val, 25 * nnzb, "float32" if f32 else "float64", "val"), _arr(y, 5 * n_rows, "float64", "y")]
+    if not all(dev for _, dev in args) or not (hasattr(x, "is_cuda") and x.is_cuda):
+        raise ValueError("bsr_spmv: every array must be a CUDA tensor")
+    if str(x.dtype) != "torch.float64":
+        raise TypeError("x: expected float64 values, got %s" % x.dtype)
     rc = fn(n_rows, row_ptr.data_ptr(), col.data_ptr(), val.data_ptr(), x.data_ptr(), y.data_ptr(),
             _stream_handle(stream))
     if rc != OK:
@@ -224,6 +253,16 @@ def residual_noalloc(xy, tri, inc_ptr, inc, params, u, u_prev, F, dt, quadrature
     All array arguments are CUDA tensors; ``inc_ptr``/``inc`` give each node's
     incident (3*t + a) entries, ascending in t."""
     p = params_struct(params)
+    n, m = xy.shape[0], tri.shape[0]
+    checks = [(xy, 2 * n, "float64", "xy"), (tri, 3 * m, "int32", "tri"), (inc_ptr, n + 1, "int32", "inc_ptr"),
+              (inc, 3 * m, "int32", "inc"), (u, 5 * n, "float64", "u"), (u_prev, 5 * n, "float64", "u_prev"),
+              (F, 5 * n, "float64", "F")]
+    if beta_field is not None:
+        checks.append((beta_field, n, "float64", "beta_field"))
+    if norm2 is not None:
+        checks.append((norm2, 1, "float64", "norm2"))
+    if not all(_arr(*ck)[1] for ck in checks):
+        raise ValueError("residual_noalloc: every array must be a CUDA tensor")
     rc = _residual_noalloc(xy.shape[0], tri.shape[0], xy.data_ptr(), tri.data_ptr(), inc_ptr.data_ptr(),
                            inc.data_ptr(), C.byref(p), None if beta_field is None else beta_field.data_ptr(),
                            float(dt), int(quadrature), u.data_ptr(), u_prev.data_ptr(), F.data_ptr(),
@@ -243,6 +282,8 @@ class Solver:
                  **opt_over):
         self._xy = np.ascontiguousarray(xy, dtype=np.float64)
         self._tri = np.ascontiguousarray(tri, dtype=np.int32)
+        if self._xy.ndim != 2 or self._xy.shape[1] != 2 or self._tri.ndim != 2 or self._tri.shape[1] != 3:
+            raise ValueError("xy must be [n, 2] and tri [m, 3], got %s and %s" % (self._xy.shape, self._tri.shape))
         mesh = Mesh(len(self._xy), len(self._tri), self._xy.ctypes.data_as(_dp), self._tri.ctypes.data_as(_ip))
         samples = list(params) if isinstance(params, (list, tuple)) else None
         self.n_samples = len(samples) if samples is not None else 1
@@ -255,6 +296,7 @@ class Solver:
         self._bf = None
         if beta_field is not None:
             self._bf = np.ascontiguousarray(beta_field, dtype=np.float64)
+            _arr(self._bf, len(self._xy), "float64", "beta_field")
             p0.beta_field = self._bf.ctypes.data_as(_dp)
         o = options if options is not None else default_options()
         for k, v in opt_over.items():
@@ -262,6 +304,7 @@ class Solver:
         self._owner = None
         if owner is not None:
             self._owner = np.ascontiguousarray(owner, dtype=np.int32)
+            _arr(self._owner, len(self._xy), "int32", "owner")
             o.owner = self._owner.ctypes.data_as(_ip)
         if stream is not None:
             o.stream = _stream_handle(stream)
@@ -299,13 +342,13 @@ class Solver:
 
     # -- state
     def set_state(self, u, t=0.0):
-        p, dev = _ptr(u)
+        p, dev = _arr(u, 5 * self.n, "float64", "u")
         self._check(_set_state(self._h, p, dev, float(t)))
 
     def get_state(self, out=None):
         if out is None:
             out = np.empty((self.n, 5))
-        p, dev = _ptr(out)
+        p, dev = _arr(out, 5 * self.n, "float64", "out")
         t = C.c_double()
         self._check(_get_state(self._h, p, dev, C.byref(t)))
         self.t = t.value
@@ -325,6 +368,7 @@ class Solver:
         p = params_struct(params)
         if beta_field is not None:
             self._bf = np.ascontiguousarray(beta_field, dtype=np.float64)
+            _arr(self._bf, self.n, "float64", "beta_field")
             p.beta_field = self._bf.ctypes.data_as(_dp)
         self._check(_set_params(self._h, C.byref(p)))
 
@@ -345,6 +389,8 @@ class Solver:
         steps = np.ascontiguousarray(obs_steps, dtype=np.int32)
         Ih = np.ascontiguousarray(I_hat, dtype=np.float64)
         Dh = np.ascontiguousarray(D_hat, dtype=np.float64)
+        _arr(Ih, len(steps) * len(nodes), "float64", "I_hat")
+        _arr(Dh, len(steps) * len(nodes), "float64", "D_hat")
         spec = Misfit(int(n_steps), int(checkpoint_every), len(nodes), nodes.ctypes.data_as(_ip), len(steps),
                       steps.ctypes.data_as(_ip), Ih.ctypes.data_as(_dp), Dh.ctypes.data_as(_dp), float(lin_rtol))
         j = C.c_double()
@@ -363,14 +409,15 @@ class Solver:
     def residual(self, u, u_prev, out=None):
         if out is None:
             out = np.empty((self.n, 5)) if isinstance(u, np.ndarray) else u.new_empty(u.shape)
-        a, dev = _ptr(u)
-        b, _ = _ptr(u_prev)
-        c, _ = _ptr(out)
+        a, d0 = _arr(u, 5 * self.n, "float64", "u")
+        b, d1 = _arr(u_prev, 5 * self.n, "float64", "u_prev")
+        c, d2 = _arr(out, 5 * self.n, "float64", "out")
+        dev = _same_place((d0, d1, d2), ("u", "u_prev", "out"))
         self._check(_eval_residual(self._h, a, b, c, dev))
         return out
 
     def jacobian(self, u):
-        a, dev = _ptr(u)
+        a, dev = _arr(u, 5 * self.n, "float64", "u")
         self._check(_eval_jacobian(self._h, a, dev))
 
     def get_jacobian(self):
@@ -384,8 +431,9 @@ class Solver:
     def apply_jacobian(self, x, out=None):
         if out is None:
             out = np.empty_like(x) if isinstance(x, np.ndarray) else x.new_empty(x.shape)
-        a, dev = _ptr(x)
-        b, _ = _ptr(out)
+        a, d0 = _arr(x, 5 * self.n, "float64", "x")
+        b, d1 = _arr(out, 5 * self.n, "float64", "out")
+        dev = _same_place((d0, d1), ("x", "out"))
         self._check(_apply_jacobian(self._h, a, b, dev))
         return out
 
@@ -395,16 +443,18 @@ class Solver:
     def precond_apply(self, r, out=None):
         if out is None:
             out = np.empty_like(r) if isinstance(r, np.ndarray) else r.new_empty(r.shape)
-        a, dev = _ptr(r)
-        b, _ = _ptr(out)
+        a, d0 = _arr(r, 5 * self.n, "float64", "r")
+        b, d1 = _arr(out, 5 * self.n, "float64", "out")
+        dev = _same_place((d0, d1), ("r", "out"))
         self._check(_precond_apply(self._h, a, b, dev))
         return out
 
     def linear_solve(self, b, out=None):
         if out is None:
             out = np.empty_like(b) if isinstance(b, np.ndarray) else b.new_empty(b.shape)
-        a, dev = _ptr(b)
-        c, _ = _ptr(out)
+        a, d0 = _arr(b, 5 * self.n, "float64", "b")
+        c, d1 = _arr(out, 5 * self.n, "float64", "out")
+        dev = _same_place((d0, d1), ("b", "out"))
         its = C.c_int32()
         self._check(_linear_solve(self._h, a, c, dev, C.byref(its)))
         return out, its.value

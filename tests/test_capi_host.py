@@ -73,3 +73,57 @@ def test_bad_meshes_are_rejected_before_any_device_call():
     with pytest.raises(S.SeirdError) as e:
         S.Solver(xy, tri, I.params_square(), owner=owner)
     assert "owns no node" in str(e.value)
+
+
+class _FakeDeviceTensor:
+    """Stands in for a CUDA tensor in the placement check; its address is never used."""
+    dtype = "torch.float64"
+    is_cuda = True
+
+    def __init__(self, n):
+        self.n = n
+
+    def data_ptr(self):
+        return 16
+
+    def is_contiguous(self):
+        return True
+
+    def numel(self):
+        return self.n
+
+
+def test_binding_refuses_wrong_sizes_types_and_placements_before_the_call():
+    """The library reads and writes 5 n values behind each state pointer; the
+    binding refuses anything else before it calls the library."""
+    import numpy as np
+    from paper_2208_01839_gb300 import inputs as I
+    from paper_2208_01839_gb300 import seird as S
+    xy, tri = I.structured_mesh(4)
+    n = len(xy)
+    with pytest.raises(ValueError, match="xy must be"):
+        S.Solver(xy[:, :1], tri, I.params_square())
+    with pytest.raises(ValueError, match="beta_field"):
+        S.Solver(xy, tri, I.params_square(), beta_field=np.ones(n - 1))
+    with pytest.raises(ValueError, match="owner"):
+        S.Solver(xy, tri, I.params_square(), owner=np.zeros(n + 1, np.int32))
+    sv = S.Solver.__new__(S.Solver)  # no context: whatever passes the checks reaches the library's NULL check
+    sv.n, sv.n_samples, sv._h = n, 1, None
+    u = np.ones((n, 5))
+    with pytest.raises(ValueError, match="expected %d values, got %d" % (5 * n, 5 * n - 5)):
+        sv.set_state(u[:-1])
+    with pytest.raises(TypeError, match="float64"):
+        sv.set_state(u.astype(np.float32))
+    with pytest.raises(ValueError, match="C-contiguous"):
+        sv.set_state(np.asfortranarray(u))
+    with pytest.raises(ValueError, match="out"):
+        sv.get_state(np.empty((n, 4)))
+    with pytest.raises(ValueError, match="all be host arrays or all device tensors"):
+        sv.residual(u, u, out=_FakeDeviceTensor(5 * n))
+    with pytest.raises(ValueError, match="all be host arrays or all device tensors"):
+        sv.linear_solve(_FakeDeviceTensor(5 * n), out=u.copy())
+    with pytest.raises(ValueError, match="I_hat"):
+        sv.adjoint(4, [0, 1], [2, 4], np.zeros((2, 3)), np.zeros((2, 2)))
+    with pytest.raises(S.SeirdError) as e:  # well-formed arguments reach the library
+        sv.set_state(u)
+    assert e.value.code == -1
