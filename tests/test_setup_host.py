@@ -93,3 +93,12 @@ def test_ensemble_union_mesh():
     assert st["n_subdomains"] == B * P and st["nnzb"] == B * one["nnzb"]
     assert st["subdomain_rows"] == B * one["subdomain_rows"]
     assert st["forward_stages"] == B * one["forward_stages"] and st["backward_stages"] == B * one["backward_stages"]
+
+
+@pytest.mark.parametrize("group", [2, 3, 4, 16])
+def test_coarse_units_spanning_several_subdomains(group):
+    """Coarse units of `group` consecutive subdomains (the grouping the paper-scale
+    partition uses): units tile the nodes and every J Z segment stays in one unit."""
+    wl = I.ontario_workload(20_000, n_subdomains=16)
+    st = _check(wl.xy, wl.tri, n_subdomains=16, overlap=2, seed=3, coarse=2, coarse_group=group)
+    assert st["n_subdomains"] == 16
