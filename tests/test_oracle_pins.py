@@ -474,3 +474,106 @@ def test_multiplicative_two_grid_matches_the_expanded_operator():
     P5 = P1 + P2 + P3 - P2 @ A @ P1 - P3 @ A @ P1 - P3 @ A @ P2 + P3 @ A @ P2 @ A @ P1
     z = O.ras_apply(rp, col, val, owner, 1, r, multiplicative=True)
     assert np.allclose(z, P5 @ r, rtol=1e-10, atol=1e-12 * np.abs(P5 @ r).max())
+
+
+# ---------------------------------------------------------------------------
+# sampled residual and the restricted prolongation of Eq. RAS
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("rule", ["deg5", "vertex"])
+def test_residual_at_nodes_equals_the_whole_mesh_residual(rule):
+    """F at a node list from only the triangles incident to those nodes equals the
+    whole-mesh F at the same nodes (Eq. weakform: row i of F integrates over the
+    support of phi_i only).  Nodes include boundary nodes, corners of the
+    structured square, interior nodes and unsorted, repeated entries."""
+    rng = np.random.default_rng(11)
+    xy, tri, _ = I.irregular_mesh(5, 900)
+    sq_xy, sq_tri = I.structured_mesh(9)
+    p = I.params_ontario(40.0)
+    for xyv, triv in ((xy, tri), (sq_xy, sq_tri)):
+        n = len(xyv)
+        U = 1.0 + rng.random((n, 5)) * np.array([30.0, 2.0, 2.0, 1.0, 0.5])
+        Un = U * (1.0 + 0.05 * rng.standard_normal((n, 5)))
+        bf = 0.5 + rng.random(n)
+        # boundary nodes: endpoints of edges used by exactly one triangle
+        e = np.sort(np.concatenate([triv[:, [0, 1]], triv[:, [1, 2]], triv[:, [2, 0]]]), axis=1)
+        ue, cnt = np.unique(e, axis=0, return_counts=True)
+        bnd = np.unique(ue[cnt == 1])
+        inner = np.setdiff1d(np.arange(n), bnd)
+        corners = [int(np.argmin(xyv[:, 0] + xyv[:, 1])), int(np.argmax(xyv[:, 0] + xyv[:, 1])),
+                   int(np.argmin(xyv[:, 0] - xyv[:, 1])), int(np.argmax(xyv[:, 0] - xyv[:, 1]))]
+        nodes = np.concatenate([rng.choice(bnd, 12, replace=False), corners, rng.choice(inner, 12, replace=False),
+                                [corners[0], int(inner[0])]])
+        full = O.residual(xyv, triv, p, 0.5, U, Un, bf, rule)
+        part = O.residual_at_nodes(xyv, triv, p, 0.5, U, Un, nodes, bfield=bf, rule=rule)
+        scale = np.abs(full).max()
+        assert part.shape == (len(nodes), 5)
+        assert np.abs(part - full[nodes]).max() <= 1e-14 * scale
+        # a wrong triangle selection is visible: dropping one incident triangle changes the row
+        k = int(inner[len(inner) // 2])
+        drop = np.nonzero((triv == k).any(axis=1))[0][0]
+        keep = np.delete(np.arange(len(triv)), drop)
+        other = O.residual(xyv, triv[keep], p, 0.5, U, Un, bf, rule)
+        assert np.abs(other[k] - full[k]).max() > 1e-6 * scale
+
+
+def _chain_parts(nblk, sizes):
+    """Owner array of a chain split into consecutive parts of the given sizes."""
+    assert sum(sizes) == nblk
+    return np.repeat(np.arange(len(sizes), dtype=np.int32), sizes)
+
+
+def _dense_schwarz(A, owner, delta, restricted):
+    """sum_p R_p^T D_p (R_p A R_p^T)^{-1} R_p for a chain of 5x5 blocks, written
+    out densely (Eq. ASM, Eq. RAS): subdomain p covers its owned blocks and
+    delta neighbours on either side; D_p keeps its owned rows (RAS) or all of
+    them (ASM, restricted=False)."""
+    nb = len(owner)
+    M = np.zeros_like(A)
+    for q in range(int(owner.max()) + 1):
+        own = np.nonzero(owner == q)[0]
+        lo, hi = max(0, own.min() - delta), min(nb, own.max() + 1 + delta)
+        blocks = np.arange(lo, hi)
+        idx = (5 * blocks[:, None] + np.arange(5)).ravel()
+        inv = np.linalg.inv(A[np.ix_(idx, idx)])
+        keep = np.isin(blocks, own) if restricted else np.ones(len(blocks), dtype=bool)
+        rows = (5 * blocks[keep][:, None] + np.arange(5)).ravel()
+        sel = np.repeat(keep, 5)
+        M[np.ix_(rows, idx)] += inv[sel]
+    return M
+
+
+@pytest.mark.parametrize("sizes,delta", [((4, 5, 3), 1), ((3, 3, 4, 2), 2), ((6, 6), 2)])
+def test_multi_subdomain_ras_against_dense_restricted_schwarz(sizes, delta):
+    """Eq. RAS with several overlapping subdomains: on a block-tridiagonal chain
+    (block ILU(0) of a block-tridiagonal matrix has no dropped fill, so each
+    subdomain solve is exact) the oracle's RAS apply equals the dense
+    sum_p R_p^T D_p (R_p A R_p^T)^{-1} R_p r with D_p the owned rows, the ASM
+    form (every overlap row written) differs from it, and the additive and
+    multiplicative two-level forms (Section 3.1, Eq. RAS_2L) equal their dense
+    counterparts with a hand-built constant coarse space."""
+    nb = sum(sizes)
+    rp, col, val = _chain_bsr(nb, seed=len(sizes) + delta)
+    A = sp.bsr_matrix((val, col, rp), shape=(5 * nb, 5 * nb)).toarray()
+    owner = _chain_parts(nb, sizes)
+    r = np.random.default_rng(7).standard_normal(5 * nb)
+    Mras = _dense_schwarz(A, owner, delta, True)
+    Masm = _dense_schwarz(A, owner, delta, False)
+    z = O.ras_apply(rp, col, val, owner, delta, r, coarse=False)
+    ref = Mras @ r
+    assert np.abs(z - ref).max() <= 1e-12 * np.abs(ref).max()
+    assert np.abs(Masm @ r - ref).max() > 1e-3 * np.abs(ref).max()
+    # constant coarse space by hand: Z[5 i + c, 5 q + c] = 1 for the blocks i that q owns
+    P = len(sizes)
+    Z = np.zeros((5 * nb, 5 * P))
+    for i in range(nb):
+        Z[5 * i:5 * i + 5, 5 * owner[i]:5 * owner[i] + 5] = np.eye(5)
+    Q = Z @ np.linalg.solve(Z.T @ A @ Z, Z.T)
+    z2 = O.ras_apply(rp, col, val, owner, delta, r, coarse=True)
+    ref2 = (Mras + Q) @ r
+    assert np.abs(z2 - ref2).max() <= 1e-11 * np.abs(ref2).max()
+    u = Mras @ r
+    u = u + Q @ (r - A @ u)
+    u = u + Mras @ (r - A @ u)
+    z3 = O.ras_apply(rp, col, val, owner, delta, r, multiplicative=True)
+    assert np.abs(z3 - u).max() <= 1e-11 * np.abs(u).max()
