@@ -188,6 +188,10 @@ typedef struct {
   double ms_total;
   double kernel_ms[8];    /* device time per kernel class (options.timing = 1) */
   int32_t kernel_calls[8];
+  double alg_bytes[8];    /* algorithmic bytes per kernel class in this step (always counted): what
+                             each launch must move at least, every array it needs read or written
+                             once at the precision it runs in, summed over the step's launches;
+                             scratch kept between a class's own kernels is not counted */
 } seird_stats;
 
 /* Sizes of a created context. */
@@ -351,6 +355,17 @@ int seird_precond_setup(seird_ctx* ctx);
 /* z = M^{-1} r with the last preconditioner built (caller numbering). */
 int seird_precond_apply(seird_ctx* ctx, const double* r, double* z, int on_device);
 
+/* Failure detection of the bounded device waits (the library never waits
+ * without bound).  The subdomain solves of the RAS apply stream each stage's
+ * factor blocks through shared memory, and every wait for a stage's data or
+ * for ring space polls an mbarrier at most `polls` times (default 2^20) before
+ * it gives up; the CTA then stops at the same stage in all its warps, lets
+ * every copy it issued land (that wait keeps its fixed bound) and sets the
+ * context's error word, and the call returns SEIRD_ETIMEOUT (the step leaves
+ * the state at u^n).  polls = 0 restores the default; polls < 0 makes every
+ * such wait give up at once, which exercises this path without a fault. */
+int seird_set_wait_limit(seird_ctx* ctx, int32_t polls);
+
 /* Solves J x = b with the preconditioned (F)GMRES of the step (x starts at 0),
  * using the context's Jacobian and last preconditioner.  its may be NULL. */
 int seird_linear_solve(seird_ctx* ctx, const double* b, double* x, int on_device, int32_t* its);
@@ -390,14 +405,14 @@ int64_t seird_launch_count(void);
 int seird_setup_check(const seird_mesh* mesh, const seird_options* opt, int64_t* stats);
 
 /* ---- allocation-free residual --------------------------------------------
- * For callers that cannot call cudaMalloc (the paper has no counterpart): code
- * running inside a framework that owns all device memory through its own
- * arena, or inside a loop that must not allocate (allocation can block, fail
- * or synchronise).  Such a caller cannot create a context, because
- * seird_create allocates.  This entry point evaluates F(u; u_prev) of Eq.
- * weakform -- the same two-phase element/gather computation as
- * seird_eval_residual -- on a mesh held entirely in caller-owned device
- * memory, and allocates nothing: its scratch is one fixed file-scope device
+ * The paper has no counterpart to this entry point.  It serves callers that
+ * cannot call cudaMalloc: code running inside a framework that owns all device
+ * memory through its own arena, or inside a loop that must not allocate
+ * (allocation can block, fail or synchronise).  Such a caller cannot create a
+ * context, because seird_create allocates.  This entry point evaluates the
+ * same residual as seird_eval_residual, by the same two-phase element/gather
+ * computation, on a mesh held entirely in caller-owned device memory, and
+ * allocates nothing: its scratch is one fixed file-scope device
  * array of SEIRD_NOALLOC_MAX_TRIS element vectors (15 doubles each) and
  * SEIRD_NOALLOC_MAX_NODES node terms (8 doubles each), about 12 MB, which
  * every GPU that loads the library keeps until the process exits.
@@ -413,10 +428,12 @@ int seird_setup_check(const seird_mesh* mesh, const seird_options* opt, int64_t*
  *   receives ||F||_2^2.  quadrature as in seird_options.
  * Limits: n_tris <= SEIRD_NOALLOC_MAX_TRIS and n_nodes <= SEIRD_NOALLOC_MAX_NODES,
  * else SEIRD_EINVAL with a message in seird_last_error(NULL).
- * Behaviour: runs on `stream` and synchronises it before returning, then
+ * Behaviour: runs on `stream` on the current device (every pointer must be
+ * memory of that device) and synchronises the stream before returning, then
  * returns SEIRD_ENONFINITE if N <= 0 at a quadrature point.  The first call
- * on a device looks up the scratch array's device address (a one-time set-up
- * per device, with that device current); make that first call before any
+ * on a device looks up the scratch array's device address and uploads the
+ * quadrature tables (a one-time set-up per device, with that device current,
+ * ending in a device synchronisation); make that first call before any
  * stream capture.  Every call shares the one scratch array, whose contents
  * are left over from the last call; calls that overlap on the GPU (other
  * streams, other host threads) race on it and must be serialised by the caller. */

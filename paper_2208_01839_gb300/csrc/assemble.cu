@@ -35,7 +35,7 @@ __constant__ double cQC[2][7][6];
 __constant__ double cORB[21];
 __constant__ float cORBf[21];  // the same in FP32 (FP32 Jacobian record)
 
-void upload_quadrature() {
+cudaError_t upload_quadrature() {
   double L[2][7][3] = {};
   double W[2][7] = {};
   const double r = std::sqrt(15.0);
@@ -58,9 +58,9 @@ void upload_quadrature() {
   for (int rule = 0; rule < 2; ++rule)
     for (int q = 0; q < 7; ++q)
       for (int s = 0; s < 6; ++s) Cw[rule][q][s] = W[rule][q] * L[rule][q][pa[s]] * L[rule][q][pb[s]];
-  cudaMemcpyToSymbol(cQL, L, sizeof(L));
-  cudaMemcpyToSymbol(cQW, W, sizeof(W));
-  cudaMemcpyToSymbol(cQC, Cw, sizeof(Cw));
+  cudaError_t e = cudaMemcpyToSymbol(cQL, L, sizeof(L));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(cQW, W, sizeof(W));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(cQC, Cw, sizeof(Cw));
   // orbit form of the same table: point 1 + k (4 + k) has its larger (smaller) coordinate at vertex k
   double O[21];
   const double A1 = L[0][1][1], B1 = L[0][1][0], A2 = L[0][4][1], B2 = L[0][4][0];
@@ -74,8 +74,12 @@ void upload_quadrature() {
     O[k] = orb[k];
     Of[k] = (float)orb[k];
   }
-  cudaMemcpyToSymbol(cORB, O, sizeof(O));
-  cudaMemcpyToSymbol(cORBf, Of, sizeof(Of));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(cORB, O, sizeof(O));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(cORBf, Of, sizeof(Of));
+  // copies from pageable memory may return before their DMA has landed: a kernel on
+  // a non-blocking stream is ordered after the tables only once the device is idle
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  return e;
 }
 
 namespace {
@@ -1078,8 +1082,11 @@ extern "C" int seird_residual_noalloc(int64_t n_nodes, int64_t n_tris, const dou
       if (e != cudaSuccess)
         return fail(SEIRD_ECUDA, std::string("seird_residual_noalloc: cudaGetSymbolAddress: ") +
                                      cudaGetErrorString(e));
-      upload_quadrature();
-      g_noalloc_ptr[dev] = static_cast<double*>(p);
+      e = upload_quadrature();  // checked copies, then a device synchronisation
+      if (e != cudaSuccess)
+        return fail(SEIRD_ECUDA, std::string("seird_residual_noalloc: quadrature tables: ") +
+                                     cudaGetErrorString(e));
+      g_noalloc_ptr[dev] = static_cast<double*>(p);  // cached only once both steps succeeded
     }
     base = g_noalloc_ptr[dev];
   }

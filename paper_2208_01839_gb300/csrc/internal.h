@@ -247,6 +247,9 @@ struct seird_ctx {
   float* cy32 = nullptr;    // [5P] FP32 copy of the coarse solution (mixed path)
   double* ainvT = nullptr;  // [5P][5P] explicit coarse inverse (transposed)
   bool pc_ready = false;
+  int32_t wait_polls = seird::SOLVE_WAIT_POLLS_DEFAULT;  // seird_set_wait_limit
+  // algorithmic bytes per kernel class since the step began (seird_stats.alg_bytes)
+  double abytes[SEIRD_K_COUNT] = {};
   // launch shapes (options.autotune)
   int spmv_tb = 256, cgs_tile = 0, sms = 1;
   bool tuned = false;
@@ -255,6 +258,7 @@ struct seird_ctx {
   cudaGraphExec_t cycle_exec = nullptr;
   int cycle_m = 0;
   std::vector<int64_t> cycle_launches;  // kernels of the first j captured iterations, j <= m
+  std::vector<double> cycle_bytes;      // [(m+1)][SEIRD_K_COUNT] their algorithmic bytes, cumulative
   int* cyc_ctl = nullptr;              // device [4]: iterations run, limit, outcome
   int* h_cyc = nullptr;                // pinned [8]: [0, 4) uploaded, [4, 8) read back
   bool eager_cycles = false;           // while the adjoint has J^T swapped in

@@ -60,7 +60,7 @@ int64_t launch_total();
 void set_global_error(const std::string& msg);
 
 // quadrature tables are uploaded once per process (degree-5 and vertex rules)
-void upload_quadrature();
+cudaError_t upload_quadrature();  // quadrature tables to constant memory (checked, synchronised)
 
 // ---- launchers (defined in the .cu files) ----
 // geo: per-triangle |T| and hat-function gradients (8 doubles each) from launch_tri_geometry,
@@ -164,7 +164,12 @@ struct RasDev {
   double* bU;
   float* fL32;
   float* bU32;
+  // polls of each bounded wait on a stage's data or ring space in the solve (<= 0:
+  // none, so every wait gives up at once); the final wait for issued copies to land
+  // keeps the fixed bound SOLVE_DRAIN_POLLS
+  int32_t wait_polls;
 };
+constexpr int32_t SOLVE_WAIT_POLLS_DEFAULT = 1 << 20;
 void launch_ilu_factor(const RasDev& d, const double* val, const float* val32, int32_t* err, bool fp32,
                        cudaStream_t s);
 void launch_ilu_reorg(const RasDev& d, int64_t nfwd, int64_t nbwd, const int64_t* fsrc, const int32_t* fcol,

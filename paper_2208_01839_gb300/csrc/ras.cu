@@ -240,12 +240,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// bounded wait: gives up after a fixed number of polls and reports it
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (int it = 0; it < (1 << 20); ++it)
+// bounded wait: gives up after `polls` polls (none when polls <= 0) and reports it
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int polls) {
+  for (int it = 0; it < polls; ++it)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
+// the wait for issued copies to land before a CTA exits: never shortened, so no bulk
+// copy is in flight into the shared memory of a CTA that has left
+constexpr int SOLVE_DRAIN_POLLS = 1 << 20;
 
 // Stage data of one subdomain stream through two rings in shared memory: the
 // factor blocks (SolveRing<T>::blocks) and the per-row records (SOLVE_RING_ROWS).
@@ -335,7 +338,7 @@ __global__ void __launch_bounds__(256, 4) k_ilu_solve(RasDev d, const double* __
       // release stages (in order) until this one fits and its slot is free
       while (oldest < gi &&
              (gi - oldest >= NS || sb + nb - slot_vb[oldest % NS] > RB || sr + nr - slot_vr[oldest % NS] > RR)) {
-        if (!mbar_wait(&empty[oldest % NS], (uint32_t)((oldest / NS) & 1)) ||
+        if (!mbar_wait(&empty[oldest % NS], (uint32_t)((oldest / NS) & 1), d.wait_polls) ||
             *(volatile int*)&abort_at != INT_MAX) {
           ok = false;
           break;
@@ -360,7 +363,8 @@ __global__ void __launch_bounds__(256, 4) k_ilu_solve(RasDev d, const double* __
     if (!ok) atomicOr(err, 8);
     // every issued copy lands before the CTA can exit (the last stage issued on
     // each slot is the only one whose phase is still open)
-    for (int k = gi - 1; k >= 0 && k >= gi - NS; --k) mbar_wait(&full[k % NS], (uint32_t)((k / NS) & 1));
+    for (int k = gi - 1; k >= 0 && k >= gi - NS; --k)
+      mbar_wait(&full[k % NS], (uint32_t)((k / NS) & 1), SOLVE_DRAIN_POLLS);
     return;
   }
 
@@ -379,7 +383,7 @@ __global__ void __launch_bounds__(256, 4) k_ilu_solve(RasDev d, const double* __
   for (int g = 0; g < nstage; ++g) {
     const bool fw = g < nF;
     const int sl = g % NS;
-    const bool landed = __all_sync(FULL, mbar_wait(&full[sl], (uint32_t)((g / NS) & 1)));
+    const bool landed = __all_sync(FULL, mbar_wait(&full[sl], (uint32_t)((g / NS) & 1), d.wait_polls));
     if (!landed && lane == 0) atomicMin(&abort_at, g);
     const T* B = ring + (size_t)(slot_vb[sl] % RB) * BS;
     const int4* inf = info + slot_vr[sl] % RR;

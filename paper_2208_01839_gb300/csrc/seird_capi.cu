@@ -194,12 +194,14 @@ struct KTimer {
 void timing_reset(seird_ctx* ctx) {
   ctx->ev_used = 0;
   ctx->ev_class.clear();
+  for (int k = 0; k < SEIRD_K_COUNT; ++k) ctx->abytes[k] = 0.0;
 }
 
 void timing_collect(seird_ctx* ctx, seird_stats* S) {
   for (int k = 0; k < SEIRD_K_COUNT; ++k) {
     S->kernel_ms[k] = 0.0;
     S->kernel_calls[k] = 0;
+    S->alg_bytes[k] = ctx->abytes[k];
   }
   if (!ctx->opt.timing) return;
   cudaStreamSynchronize(ctx->stream);
@@ -213,6 +215,57 @@ void timing_collect(seird_ctx* ctx, seird_stats* S) {
   timing_reset(ctx);
 }
 
+// ---- algorithmic bytes per kernel class (seird_stats.alg_bytes) ---------------
+// What each launch group must move at least: every array it needs, read or
+// written once, at the precision it runs in (w = 4 for the mixed path's FP32
+// matrix, factors and preconditioned basis); scratch that a class keeps between
+// its own kernels (element vectors, work vectors of the sweeps) is not counted.
+// Vectors of the state are 5n doubles = 40n bytes.
+
+double wv(const seird_ctx* c) { return c->opt.precision == 1 ? 4.0 : 8.0; }
+void add_bytes(seird_ctx* c, int cls, double b) { c->abytes[cls] += b; }
+double nnzb_of(const seird_ctx* c) { return (double)c->hs.col.size(); }
+// U and u^n read (80n), xy (16n), triangles (12m), F written (40n)
+double bytes_residual(const seird_ctx* c) { return 136.0 * c->hs.n + 12.0 * c->hs.m; }
+// U (40n) and xy (16n) read, triangles (12m) and block incidence lists (36m), blocks written
+double bytes_jacobian(const seird_ctx* c) { return 56.0 * c->hs.n + 48.0 * c->hs.m + 25.0 * wv(c) * nnzb_of(c); }
+// J blocks gathered with their global ids and local columns, factor blocks and inverted pivots written
+double bytes_ilu_factor(const seird_ctx* c) {
+  return (double)c->hs.l_col.size() * (50.0 * wv(c) + 8.0) + (double)c->hs.sd_node.size() * 25.0 * wv(c);
+}
+// J blocks read once with their segment order, plus the J Z blocks written for the two-grid
+double bytes_coarse_setup(const seird_ctx* c) {
+  return nnzb_of(c) * (25.0 * wv(c) + 4.0) + (c->opt.coarse >= 2 ? 25.0 * wv(c) * c->hs.az_unit.size() : 0.0);
+}
+// values with column indices, row pointers, x once (wx), y written, b read when fused (y = b - J x)
+double bytes_spmv(const seird_ctx* c, double wx, bool fused) {
+  const double n = (double)c->hs.n;
+  return nnzb_of(c) * (25.0 * wv(c) + 4.0) + 4.0 * (n + 1) + 5.0 * n * wx + 40.0 * n + (fused ? 40.0 * n : 0.0);
+}
+// every local block once (strictly lower, inverted pivots, strictly upper) with its column,
+// two 16-byte row records, r read per local row, z written per owned row (wz)
+double bytes_ilu_solve(const seird_ctx* c, double wz) {
+  return (double)c->hs.l_col.size() * (25.0 * wv(c) + 4.0) + 72.0 * c->hs.sd_node.size() + 5.0 * c->hs.n * wz;
+}
+// Z^T r (r read), A_c^{-1} (explicit inverse or band factors read once), z += Z y (read and
+// written at wz, unit map), and with J Z: its blocks and segment maps read, t read and written
+double bytes_coarse_solve(const seird_ctx* c) {
+  const double nc = 5.0 * c->hs.Pc;
+  const double inv = c->ainvT ? nc * nc * 8.0 : (double)c->hs.Pc * (2.0 * c->hs.cband + 2.0) * 200.0;
+  return 40.0 * c->hs.n + inv;
+}
+double bytes_coarse_prolong(const seird_ctx* c, double wz) { return 10.0 * c->hs.n * wz + 4.0 * c->hs.n; }
+double bytes_az_sub(const seird_ctx* c, double wa) {
+  return (double)c->hs.az_unit.size() * (25.0 * wa + 4.0) + 8.0 * c->hs.n + 80.0 * c->hs.n;
+}
+// Arnoldi iteration with nv basis vectors: one classical Gram-Schmidt pass reads V and w
+// (dots), then V and w again and writes w (update and norm), then w -> v_{nv}; CGS2 adds a
+// fused update-and-dots pass
+double bytes_arnoldi(const seird_ctx* c, int nv) {
+  const double vec = 40.0 * c->hs.n;
+  return (c->opt.gmres_one_pass == 1 ? 2.0 * nv + 5.0 : 3.0 * nv + 7.0) * vec;
+}
+
 // ---- building blocks --------------------------------------------------------
 
 // F = F(U; Un), returns ||F||_2 in *fn (synchronises)
@@ -220,6 +273,7 @@ int residual(seird_ctx* ctx, const double* U, const double* Un, double* F, doubl
   const HostSetup& hs = ctx->hs;
   {
     KTimer kt_(ctx, SEIRD_K_RESIDUAL);
+    add_bytes(ctx, SEIRD_K_RESIDUAL, bytes_residual(ctx));
     launch_residual(hs.n, hs.m, ctx->tri, ctx->xy, ctx->geo, U, Un, bfield_of(ctx), make_rates(ctx),
                     ctx->opt.quadrature, ctx->nodebuf, ctx->elem, ctx->node_inc_ptr, ctx->node_inc, F, ctx->partial,
                     ctx->scal, ctx->err, ctx->stream);
@@ -238,6 +292,7 @@ int residual(seird_ctx* ctx, const double* U, const double* Un, double* F, doubl
 int jacobian(seird_ctx* ctx, const double* U, bool picard = false) {
   const HostSetup& hs = ctx->hs;
   KTimer kt_(ctx, SEIRD_K_JACOBIAN);
+  add_bytes(ctx, SEIRD_K_JACOBIAN, bytes_jacobian(ctx));
   // the mixed path assembles the Jacobian straight into its FP32 copy (FP32
   // arithmetic); it only feeds the FP32 operator and the FP32 factors
   launch_jacobian((int64_t)hs.col.size(), hs.m, ctx->tri, ctx->xy, ctx->geo, U, bfield_of(ctx), make_rates(ctx),
@@ -291,6 +346,7 @@ RasDev ras_dev(seird_ctx* ctx) {
   d.bU = ctx->bU;
   d.fL32 = ctx->fL32;
   d.bU32 = ctx->bU32;
+  d.wait_polls = ctx->wait_polls;
   return d;
 }
 
@@ -320,6 +376,7 @@ int pc_setup(seird_ctx* ctx) {
   if (!ctx->jac_ready) return fail(ctx, SEIRD_EINVAL, "preconditioner setup needs an assembled Jacobian");
   {
     KTimer kt_(ctx, SEIRD_K_ILU_FACTOR);
+    add_bytes(ctx, SEIRD_K_ILU_FACTOR, bytes_ilu_factor(ctx));
     const RasDev d = ras_dev(ctx);
     launch_ilu_factor(d, ctx->val, ctx->val32, ctx->err, mixed(ctx), ctx->stream);
     launch_ilu_reorg(d, (int64_t)ctx->hs.sp_fwd.src.size(), (int64_t)ctx->hs.sp_bwd.src.size(), ctx->pf.src,
@@ -328,6 +385,7 @@ int pc_setup(seird_ctx* ctx) {
   CK(cudaGetLastError());
   if (ctx->opt.coarse) {
     KTimer kt_(ctx, SEIRD_K_COARSE_SETUP);
+    add_bytes(ctx, SEIRD_K_COARSE_SETUP, bytes_coarse_setup(ctx));
     const CoarseDev c = coarse_dev(ctx);
     launch_coarse_assemble(c, ctx->val, ctx->val32, ctx->stream);
     if (!ctx->coarse_graph) {
@@ -375,6 +433,7 @@ int pc_apply32(seird_ctx* ctx, const double* r, float* z) {
     const CoarseDev cd = coarse_dev(ctx);
     {
       KTimer kt_(ctx, SEIRD_K_COARSE_APPLY);
+      add_bytes(ctx, SEIRD_K_COARSE_APPLY, bytes_coarse_solve(ctx) + 80.0 * ctx->hs.n + bytes_az_sub(ctx, 4.0));
       launch_coarse_solve(cd, r, ctx->stream);
       launch_coarse_y32(cd, ctx->stream);
       CK(cudaMemcpyAsync(ctx->pct, r, sizeof(double) * len, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -382,10 +441,12 @@ int pc_apply32(seird_ctx* ctx, const double* r, float* z) {
     }
     {
       KTimer kt_(ctx, SEIRD_K_ILU_SOLVE);
+      add_bytes(ctx, SEIRD_K_ILU_SOLVE, bytes_ilu_solve(ctx, 4.0));
       launch_ilu_solve32(ras_dev(ctx), ctx->pct, z, ctx->err, ctx->stream);
     }
     {
       KTimer kt_(ctx, SEIRD_K_COARSE_APPLY);
+      add_bytes(ctx, SEIRD_K_COARSE_APPLY, bytes_coarse_prolong(ctx, 4.0));
       launch_coarse_prolong32(cd, ctx->hs.n, z, ctx->stream);
     }
     CK(cudaGetLastError());
@@ -393,10 +454,12 @@ int pc_apply32(seird_ctx* ctx, const double* r, float* z) {
   }
   {
     KTimer kt_(ctx, SEIRD_K_ILU_SOLVE);
+    add_bytes(ctx, SEIRD_K_ILU_SOLVE, bytes_ilu_solve(ctx, 4.0));
     launch_ilu_solve32(ras_dev(ctx), r, z, ctx->err, ctx->stream);
   }
   if (ctx->opt.coarse == 1) {
     KTimer kt_(ctx, SEIRD_K_COARSE_APPLY);
+    add_bytes(ctx, SEIRD_K_COARSE_APPLY, bytes_coarse_solve(ctx) + bytes_coarse_prolong(ctx, 4.0));
     const CoarseDev cd = coarse_dev(ctx);
     launch_coarse_solve(cd, r, ctx->stream);
     launch_coarse_y32(cd, ctx->stream);
@@ -405,6 +468,8 @@ int pc_apply32(seird_ctx* ctx, const double* r, float* z) {
     TRY(spmv32(ctx, z, ctx->pct, r));  // r - J z
     {
       KTimer kt_(ctx, SEIRD_K_COARSE_APPLY);
+      add_bytes(ctx, SEIRD_K_COARSE_APPLY,
+                bytes_coarse_solve(ctx) + bytes_coarse_prolong(ctx, 4.0) + bytes_az_sub(ctx, 4.0));
       const CoarseDev cd = coarse_dev(ctx);
       launch_coarse_solve(cd, ctx->pct, ctx->stream);
       launch_coarse_y32(cd, ctx->stream);
@@ -414,6 +479,7 @@ int pc_apply32(seird_ctx* ctx, const double* r, float* z) {
     }
     {
       KTimer kt_(ctx, SEIRD_K_ILU_SOLVE);
+      add_bytes(ctx, SEIRD_K_ILU_SOLVE, bytes_ilu_solve(ctx, 4.0));
       launch_ilu_solve32(ras_dev(ctx), ctx->pct, ctx->pcu32, ctx->err, ctx->stream);
     }
     launch_add32(len, ctx->pcu32, z, ctx->stream);
@@ -437,16 +503,19 @@ int pc_apply(seird_ctx* ctx, const double* r, double* z) {
     const CoarseDev cd = coarse_dev(ctx);
     {
       KTimer kt_(ctx, SEIRD_K_COARSE_APPLY);
+      add_bytes(ctx, SEIRD_K_COARSE_APPLY, bytes_coarse_solve(ctx) + 80.0 * ctx->hs.n + bytes_az_sub(ctx, 8.0));
       launch_coarse_solve(cd, r, ctx->stream);
       CK(cudaMemcpyAsync(ctx->pct, r, sizeof(double) * len, cudaMemcpyDeviceToDevice, ctx->stream));
       launch_az_sub(cd, ctx->hs.n, ctx->az_ptr, ctx->az_unit, ctx->azval, ctx->azval32, false, ctx->pct, ctx->stream);
     }
     {
       KTimer kt_(ctx, SEIRD_K_ILU_SOLVE);
+      add_bytes(ctx, SEIRD_K_ILU_SOLVE, bytes_ilu_solve(ctx, 8.0));
       launch_ilu_solve(ras_dev(ctx), ctx->pct, z, ctx->err, ctx->stream);
     }
     {
       KTimer kt_(ctx, SEIRD_K_COARSE_APPLY);
+      add_bytes(ctx, SEIRD_K_COARSE_APPLY, bytes_coarse_prolong(ctx, 8.0));
       launch_coarse_prolong<double>(cd, ctx->hs.n, z, ctx->stream);
     }
     CK(cudaGetLastError());
@@ -454,16 +523,20 @@ int pc_apply(seird_ctx* ctx, const double* r, double* z) {
   }
   {
     KTimer kt_(ctx, SEIRD_K_ILU_SOLVE);
+    add_bytes(ctx, SEIRD_K_ILU_SOLVE, bytes_ilu_solve(ctx, 8.0));
     launch_ilu_solve(ras_dev(ctx), r, z, ctx->err, ctx->stream);
   }
   if (ctx->opt.coarse == 1) {
     KTimer kt_(ctx, SEIRD_K_COARSE_APPLY);
+    add_bytes(ctx, SEIRD_K_COARSE_APPLY, bytes_coarse_solve(ctx) + bytes_coarse_prolong(ctx, 8.0));
     launch_coarse_apply_add<double>(coarse_dev(ctx), ctx->hs.n, r, z, ctx->stream);
   } else if (ctx->opt.coarse == 2) {  // Eq. RAS_2L: coarse on r - J z, then RAS on the new residual
     const int64_t len = vlen(ctx);
     TRY(spmv(ctx, z, ctx->pct, r));  // r - J z
     {
       KTimer kt_(ctx, SEIRD_K_COARSE_APPLY);
+      add_bytes(ctx, SEIRD_K_COARSE_APPLY,
+                bytes_coarse_solve(ctx) + bytes_coarse_prolong(ctx, 8.0) + bytes_az_sub(ctx, 8.0));
       const CoarseDev cd = coarse_dev(ctx);
       launch_coarse_apply_add<double>(cd, ctx->hs.n, ctx->pct, z, ctx->stream);
       // r - J (z + Z y) = (r - J z) - (J Z) y, with J Z summed at set-up
@@ -471,6 +544,7 @@ int pc_apply(seird_ctx* ctx, const double* r, double* z) {
     }
     {
       KTimer kt_(ctx, SEIRD_K_ILU_SOLVE);
+      add_bytes(ctx, SEIRD_K_ILU_SOLVE, bytes_ilu_solve(ctx, 8.0));
       launch_ilu_solve(ras_dev(ctx), ctx->pct, ctx->pcu, ctx->err, ctx->stream);
     }
     launch_axpby(len, 1.0, z, 1.0, ctx->pcu, z, ctx->stream);
@@ -482,6 +556,7 @@ int pc_apply(seird_ctx* ctx, const double* r, double* z) {
 // y = J x, or y = b - J x when b != NULL
 int spmv(seird_ctx* ctx, const double* x, double* y, const double* b) {
   KTimer kt_(ctx, SEIRD_K_SPMV);
+  add_bytes(ctx, SEIRD_K_SPMV, bytes_spmv(ctx, 8.0, b != nullptr));
   if (mixed(ctx))
     launch_spmv<float>(ctx->hs.n, ctx->row_ptr, ctx->col, ctx->val32, x, y, ctx->stream, ctx->spmv_tb, b);
   else launch_spmv<double>(ctx->hs.n, ctx->row_ptr, ctx->col, ctx->val, x, y, ctx->stream, ctx->spmv_tb, b);
@@ -492,6 +567,7 @@ int spmv(seird_ctx* ctx, const double* x, double* y, const double* b) {
 // y = J x (or b - J x) with the FP32 matrix copy and FP32 x (mixed path)
 int spmv32(seird_ctx* ctx, const float* x, double* y, const double* b) {
   KTimer kt_(ctx, SEIRD_K_SPMV);
+  add_bytes(ctx, SEIRD_K_SPMV, bytes_spmv(ctx, 4.0, b != nullptr));
   launch_spmv32(ctx->hs.n, ctx->row_ptr, ctx->col, ctx->val32, x, y, ctx->stream, ctx->spmv_tb, b);
   CK(cudaGetLastError());
   return SEIRD_OK;
@@ -501,6 +577,17 @@ int read_scalars(seird_ctx* ctx, int first, int count) {
   CK(cudaMemcpyAsync(ctx->h_scal + first, ctx->scal + first, sizeof(double) * count, cudaMemcpyDeviceToHost,
                      ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
+  return SEIRD_OK;
+}
+
+// read_scalars plus the device error word in the same synchronisation: a set flag
+// (a subdomain solve that timed out, a singular pivot) ends the caller's loop at once
+int read_scalars_checked(seird_ctx* ctx, int first, int count, const char* where) {
+  CK(cudaMemcpyAsync(ctx->h_scal + first, ctx->scal + first, sizeof(double) * count, cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CK(cudaMemcpyAsync(ctx->h_err, ctx->err, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (*ctx->h_err) return check_flags(ctx, where);
   return SEIRD_OK;
 }
 
@@ -600,6 +687,7 @@ static int arnoldi_iteration(seird_ctx* ctx, int j, const CycleCtl& cc) {
     TRY(spmv(ctx, Zj, ctx->w));
   }
   KTimer kt_(ctx, SEIRD_K_KRYLOV);
+  add_bytes(ctx, SEIRD_K_KRYLOV, bytes_arnoldi(ctx, j + 1));
   launch_mdot(len, j + 1, ctx->V, len, ctx->w, ctx->partial, ctx->red_grid, h1, s, ctx->cgs_tile);
   if (ctx->opt.gmres_one_pass == 1) {
     launch_update_norm(len, j + 1, ctx->V, len, h1, ctx->w, ctx->partial, ctx->red_grid, ctx->scal + 5, s);
@@ -630,10 +718,13 @@ static int build_cycle_graph(seird_ctx* ctx) {
   cudaError_t e = cudaGraphCreate(&g, 0);
   cudaGraphConditionalHandle hnd = 0;
   if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hnd, g, 1u, cudaGraphCondAssignDefault);
-  const cudaStream_t saved = ctx->stream;
+  const cudaStream_t saved_stream = ctx->stream;
   ctx->stream = cs;  // the launchers capture on the context's stream
   int rc = SEIRD_OK;
   std::vector<int64_t> launches(1, 0);
+  double saved[SEIRD_K_COUNT];
+  for (int c = 0; c < SEIRD_K_COUNT; ++c) saved[c] = ctx->abytes[c];
+  std::vector<double> cbytes((size_t)(m + 1) * SEIRD_K_COUNT, 0.0);
   cudaGraph_t parent = g;
   cudaGraphNode_t dep = nullptr;  // node j's predecessor inside its parent
   for (int j = 0; j < m && e == cudaSuccess && rc == SEIRD_OK; ++j) {
@@ -660,6 +751,7 @@ static int build_cycle_graph(seird_ctx* ctx) {
     rc = arnoldi_iteration(ctx, j, cc);
     launches.push_back(launches.back() + launch_total() - k0);
     count_launches(k0 - launch_total());  // captured, not run
+    for (int c = 0; c < SEIRD_K_COUNT; ++c) cbytes[(size_t)(j + 1) * SEIRD_K_COUNT + c] = ctx->abytes[c] - saved[c];
     cudaStreamCaptureStatus st;
     const cudaGraphNode_t* last = nullptr;
     size_t nlast = 0;
@@ -671,7 +763,8 @@ static int build_cycle_graph(seird_ctx* ctx) {
     parent = body;
     hnd = cc.next;
   }
-  ctx->stream = saved;
+  ctx->stream = saved_stream;
+  for (int c = 0; c < SEIRD_K_COUNT; ++c) ctx->abytes[c] = saved[c];  // counted per replay instead
   if (e == cudaSuccess && rc == SEIRD_OK) e = cudaGraphInstantiate(&ctx->cycle_exec, g, 0);
   if (g) cudaGraphDestroy(g);
   cudaStreamDestroy(cs);
@@ -684,6 +777,7 @@ static int build_cycle_graph(seird_ctx* ctx) {
   }
   ctx->cycle_m = m;
   ctx->cycle_launches = launches;
+  ctx->cycle_bytes = cbytes;
   return SEIRD_OK;
 }
 
@@ -738,11 +832,12 @@ int gmres(seird_ctx* ctx, const double* b, double* x, double rtol, int* its_out,
       CK(cudaMemcpyAsync(ctx->cyc_ctl, hin, 4 * sizeof(int), cudaMemcpyHostToDevice, s));
       CK(cudaGraphLaunch(ctx->cycle_exec, s));
       CK(cudaMemcpyAsync(hout, ctx->cyc_ctl, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
-      TRY(read_scalars(ctx, 2, 2));
+      TRY(read_scalars_checked(ctx, 2, 2, "gmres"));
       k = hout[0];
       its += k;
       if (k < 1 || k > m) return fail(ctx, SEIRD_ECUDA, "gmres: captured cycle reported no iterations");
       count_launches(ctx->cycle_launches[k]);
+      for (int c = 0; c < SEIRD_K_COUNT; ++c) ctx->abytes[c] += ctx->cycle_bytes[(size_t)k * SEIRD_K_COUNT + c];
       if (hout[2] == 2) {
         if (!std::isfinite(ctx->h_scal[2])) return fail(ctx, SEIRD_ENONFINITE, "gmres: non-finite residual estimate");
         return fail(ctx, SEIRD_EGMRES, "gmres: diverged (dtol)");
@@ -751,7 +846,7 @@ int gmres(seird_ctx* ctx, const double* b, double* x, double rtol, int* its_out,
     } else {
       for (int j = 0; j < m; ++j) {
         TRY(arnoldi_iteration(ctx, j, CycleCtl()));
-        TRY(read_scalars(ctx, 2, 2));
+        TRY(read_scalars_checked(ctx, 2, 2, "gmres"));
         ++its;
         k = j + 1;
         const double res = ctx->h_scal[2], hn = ctx->h_scal[3];
@@ -764,9 +859,14 @@ int gmres(seird_ctx* ctx, const double* b, double* x, double rtol, int* its_out,
         if (its >= ctx->opt.gmres_maxit) break;
       }
     }
-    launch_hsolve(k, ctx->gm, ldh, s);
-    if (mixed(ctx)) launch_multi_axpy32(len, k, ctx->Z32, len, gbuf + ldh, x, s);
-    else launch_multi_axpy(len, k, ctx->Z, len, gbuf + ldh, x, s);  // y lives right after g
+    {
+      KTimer kt_(ctx, SEIRD_K_KRYLOV);
+      // x += Z y: k preconditioned vectors read, x read and written
+      add_bytes(ctx, SEIRD_K_KRYLOV, (5.0 * k * wv(ctx) + 80.0) * ctx->hs.n);
+      launch_hsolve(k, ctx->gm, ldh, s);
+      if (mixed(ctx)) launch_multi_axpy32(len, k, ctx->Z32, len, gbuf + ldh, x, s);
+      else launch_multi_axpy(len, k, ctx->Z, len, gbuf + ldh, x, s);  // y lives right after g
+    }
     CK(cudaGetLastError());
     if (done) {
       *converged = true;
@@ -784,7 +884,8 @@ int gmres(seird_ctx* ctx, const double* b, double* x, double rtol, int* its_out,
     r = ctx->w;
   }
   *its_out = its;
-  return SEIRD_OK;
+  // a subdomain solve whose bounded wait gave up (or a singular pivot) fails the solve here
+  return check_flags(ctx, "gmres");
 }
 
 bool verbose() {
@@ -1298,7 +1399,7 @@ static int create_impl(seird_ctx* ctx, const seird_mesh* mesh, const seird_param
     CK(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
     ctx->own_stream = true;
   }
-  upload_quadrature();
+  CK(upload_quadrature());
   cgs_init();
   coarse_init();
   CK(cudaGetLastError());
@@ -1725,8 +1826,19 @@ int seird_precond_apply(seird_ctx* ctx, const double* r, double* z, int on_devic
     if (!ctx->pc_ready) return fail(ctx, SEIRD_EINVAL, "preconditioner not set up");
     TRY(to_internal(ctx, r, on_device, ctx->stage2));
     TRY(pc_apply(ctx, ctx->stage2, ctx->Ft));
+    TRY(check_flags(ctx, "preconditioner apply"));
     return from_internal(ctx, ctx->Ft, z, on_device);
   });
+}
+
+int seird_set_wait_limit(seird_ctx* ctx, int32_t polls) {
+  if (!ctx) return SEIRD_EINVAL;
+  ctx->wait_polls = polls == 0 ? SOLVE_WAIT_POLLS_DEFAULT : std::max<int32_t>(polls, 0);
+  if (ctx->cycle_exec) {  // a captured restart cycle holds the old limit in its kernel arguments
+    cudaGraphExecDestroy(ctx->cycle_exec);
+    ctx->cycle_exec = nullptr;
+  }
+  return SEIRD_OK;
 }
 
 int seird_linear_solve(seird_ctx* ctx, const double* b, double* x, int on_device, int32_t* its) {

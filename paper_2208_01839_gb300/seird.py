@@ -68,12 +68,13 @@ class Stats(C.Structure):
                 ("pc_setups", C.c_int32), ("res0", C.c_double), ("res_final", C.c_double),
                 ("eps_update", C.c_double), ("ms_assemble", C.c_double), ("ms_setup", C.c_double),
                 ("ms_solve", C.c_double), ("ms_total", C.c_double), ("kernel_ms", C.c_double * 8),
-                ("kernel_calls", C.c_int32 * 8)]
+                ("kernel_calls", C.c_int32 * 8), ("alg_bytes", C.c_double * 8)]
 
     def as_dict(self):
-        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("kernel_ms", "kernel_calls")}
-        d["kernel_ms"] = {KERNEL_CLASSES[i]: self.kernel_ms[i] for i in range(8)}
-        d["kernel_calls"] = {KERNEL_CLASSES[i]: self.kernel_calls[i] for i in range(8)}
+        arrays = ("kernel_ms", "kernel_calls", "alg_bytes")
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in arrays}
+        for a in arrays:
+            d[a] = {KERNEL_CLASSES[i]: getattr(self, a)[i] for i in range(8)}
         return d
 
 
@@ -129,6 +130,7 @@ _create_ensemble = _sig("seird_create_ensemble", C.c_int,
 _set_params = _sig("seird_set_params", C.c_int, [_vp, C.POINTER(Params)])
 _set_beta_schedule = _sig("seird_set_beta_schedule", C.c_int, [_vp, C.POINTER(BetaSchedule)])
 _adjoint = _sig("seird_adjoint", C.c_int, [_vp, C.POINTER(Misfit), C.POINTER(C.c_double), _vp, _vp])
+_set_wait_limit = _sig("seird_set_wait_limit", C.c_int, [_vp, C.c_int32])
 _residual_noalloc = _sig("seird_residual_noalloc", C.c_int,
                          [C.c_int64, C.c_int64, _vp, _vp, _vp, _vp, C.POINTER(Params), _vp, C.c_double, C.c_int32,
                           _vp, _vp, _vp, _vp, _vp])
@@ -250,8 +252,11 @@ def residual_noalloc(xy, tri, inc_ptr, inc, params, u, u_prev, F, dt, quadrature
                      stream=None):
     """F(u; u_prev) on a mesh held in caller-owned device tensors, without any
     device allocation by the library (see seird_residual_noalloc in seird.h).
-    All array arguments are CUDA tensors; ``inc_ptr``/``inc`` give each node's
-    incident (3*t + a) entries, ascending in t."""
+    All array arguments are CUDA tensors on one device; ``inc_ptr``/``inc`` give
+    each node's incident (3*t + a) entries, ascending in t.  The call runs with
+    that device current, on ``stream`` or, by default, on torch's current stream
+    of that device (so it is ordered after the work that wrote the inputs)."""
+    import torch
     p = params_struct(params)
     n, m = xy.shape[0], tri.shape[0]
     checks = [(xy, 2 * n, "float64", "xy"), (tri, 3 * m, "int32", "tri"), (inc_ptr, n + 1, "int32", "inc_ptr"),
@@ -263,10 +268,17 @@ def residual_noalloc(xy, tri, inc_ptr, inc, params, u, u_prev, F, dt, quadrature
         checks.append((norm2, 1, "float64", "norm2"))
     if not all(_arr(*ck)[1] for ck in checks):
         raise ValueError("residual_noalloc: every array must be a CUDA tensor")
-    rc = _residual_noalloc(xy.shape[0], tri.shape[0], xy.data_ptr(), tri.data_ptr(), inc_ptr.data_ptr(),
-                           inc.data_ptr(), C.byref(p), None if beta_field is None else beta_field.data_ptr(),
-                           float(dt), int(quadrature), u.data_ptr(), u_prev.data_ptr(), F.data_ptr(),
-                           None if norm2 is None else norm2.data_ptr(), _stream_handle(stream))
+    # the library launches on the current device: every tensor must live there
+    devs = {ck[0].device for ck in checks}
+    if len(devs) != 1:
+        raise ValueError("residual_noalloc: tensors on several devices: %s" % sorted(str(d) for d in devs))
+    dev = devs.pop()
+    with torch.cuda.device(dev):
+        sh = _stream_handle(stream) if stream is not None else torch.cuda.current_stream(dev).cuda_stream
+        rc = _residual_noalloc(xy.shape[0], tri.shape[0], xy.data_ptr(), tri.data_ptr(), inc_ptr.data_ptr(),
+                               inc.data_ptr(), C.byref(p), None if beta_field is None else beta_field.data_ptr(),
+                               float(dt), int(quadrature), u.data_ptr(), u_prev.data_ptr(), F.data_ptr(),
+                               None if norm2 is None else norm2.data_ptr(), sh)
     if rc != OK:
         raise SeirdError(rc, _last_error(None).decode())
 
@@ -399,6 +411,11 @@ class Solver:
         self._check(_adjoint(self._h, C.byref(spec), C.byref(j), g.ctypes.data,
                              None if gf is None else gf.ctypes.data))
         return j.value, (g if self.n_samples == 1 else g.reshape(self.n_samples, 10)), gf
+
+    def set_wait_limit(self, polls):
+        """Polls of each bounded wait in the subdomain solves (seird_set_wait_limit):
+        0 restores the default, a negative value makes every wait give up at once."""
+        self._check(_set_wait_limit(self._h, int(polls)))
 
     def info(self):
         inf = Info()

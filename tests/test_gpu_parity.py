@@ -415,6 +415,29 @@ def test_automatic_coarse_groups_beyond_the_explicit_inverse_limit():
     assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
 
 
+def test_coarse_space_of_4096_ungrouped_units_matches_oracle():
+    """4096 box subdomains, one coarse unit each (coarse_group = 1): 20,480 coarse
+    unknowns, beyond the explicit inverse, so every coarse solve runs through the
+    banded block-LU factors.  The preconditioner equals the oracle's RAS with the
+    additive coarse correction of Section 3.1 (dense A_c of 20,480 unknowns)."""
+    xy, tri = I.structured_mesh(128)
+    dens = I.urban_density(11)
+    U0 = I.urban_ic(xy, dens, 11)
+    p = I.params_ontario(float(U0.sum(axis=1).max()))
+    owner = I.box_partition(xy, 64, 64)
+    assert owner.max() + 1 == 4096
+    J = O.jacobian(xy, tri, p, 0.5, U0)
+    rp, col, val = O.to_bsr(J)
+    r = np.random.default_rng(13).standard_normal(5 * len(xy))
+    ref = O.ras_apply(rp, col, val, owner, 1, r, coarse=True)
+    with S.Solver(xy, tri, p, owner=owner, dt=0.5, overlap=1, coarse=1, coarse_group=1) as sv:
+        assert sv.info()["coarse_units"] == 4096
+        sv.jacobian(U0)
+        sv.precond_setup()
+        got = sv.precond_apply(r.reshape(-1, 5)).ravel()
+    assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
 def test_extrapolation_predictor_reaches_the_same_roots():
     """options.predictor = 1 starts Newton from 2 u^n - u^{n-1}: the iterates
     change, the roots (and the stopping test, relative to ||F(u^n)||) do not."""

@@ -5,11 +5,13 @@ through its own arena, or a loop that must never allocate.  They cannot create
 a context (creating one allocates), so the library gives them one entry point
 that evaluates the residual F(u; u_prev) on a mesh held in their own device
 memory and keeps its scratch in a fixed device array.  These tests call it
-through the C ABI and compare it with the context-based seird_eval_residual,
-within the residual tolerance of the parity tests, on two calls in a row (the
-second call reuses the scratch the first one left behind).  This file is
-collected last so that a failure here stops a -x run only after every other
-test has run.
+through the C ABI, for both quadrature rules, and compare it with the
+context-based seird_eval_residual and with the CPU oracle, within the residual
+tolerance of the parity tests, on two calls in a row (the second call reuses
+the scratch the first one left behind); one call runs on a side stream, and a
+state with N <= 0 returns SEIRD_ENONFINITE without spoiling the next call.
+This file is collected last so that a failure here stops a -x run only after
+every other test has run.
 """
 import numpy as np
 import pytest
@@ -54,13 +56,15 @@ def _cases():
             ("irregular3k", xy, tri, p, U0, 0.5, I.smooth_field(xy, 3))]
 
 
+@pytest.mark.parametrize("quadrature", [0, 1], ids=["deg5", "vertex"])
 @pytest.mark.parametrize("case", _cases(), ids=lambda c: c[0])
-def test_noalloc_residual_matches_context_residual_on_two_calls(case):
+def test_noalloc_residual_matches_context_and_oracle_on_two_calls(case, quadrature):
     name, xy, tri, params, U0, dt, bf = case
+    rule = "deg5" if quadrature == 0 else "vertex"
     rng = np.random.default_rng(11)
     U1 = U0 * (1.0 + 0.05 * rng.standard_normal(U0.shape)) + 1.0
     U2 = U1 * (1.0 + 0.05 * rng.standard_normal(U0.shape)) + 0.5
-    with S.Solver(xy, tri, params, beta_field=bf, dt=dt, n_subdomains=3) as sv:
+    with S.Solver(xy, tri, params, beta_field=bf, dt=dt, n_subdomains=3, quadrature=quadrature) as sv:
         ref1 = sv.residual(U1, U0)
         ref2 = sv.residual(U2, U1)
     d = lambda a: torch.tensor(np.ascontiguousarray(a), device="cuda")
@@ -70,13 +74,48 @@ def test_noalloc_residual_matches_context_residual_on_two_calls(case):
     F = torch.full((len(xy), 5), np.nan, dtype=torch.float64, device="cuda")
     nrm = torch.zeros(1, dtype=torch.float64, device="cuda")
     for U, Up, ref in ((U1, U0, ref1), (U2, U1, ref2)):
-        S.residual_noalloc(xy_d, tri_d, ptr_d, inc_d, params, d(U), d(Up), F, dt, beta_field=bf_d, norm2=nrm)
+        S.residual_noalloc(xy_d, tri_d, ptr_d, inc_d, params, d(U), d(Up), F, dt, quadrature=quadrature,
+                           beta_field=bf_d, norm2=nrm)
         got = F.cpu().numpy()
-        assert np.abs(got - ref).max() <= 1e-12 * scale(xy, tri, params, U, dt), name
+        tol = 1e-12 * scale(xy, tri, params, U, dt)
+        assert np.abs(got - ref).max() <= tol, name
+        orc = O.residual(xy, tri, params, dt, U, Up, bf, rule)
+        assert np.abs(got - orc).max() <= tol, name
         assert abs(nrm.item() - float((ref ** 2).sum())) <= 1e-10 * float((ref ** 2).sum())
     # without a norm output the call still fills F
-    S.residual_noalloc(xy_d, tri_d, ptr_d, inc_d, params, d(U1), d(U0), F, dt, beta_field=bf_d)
+    S.residual_noalloc(xy_d, tri_d, ptr_d, inc_d, params, d(U1), d(U0), F, dt, quadrature=quadrature,
+                       beta_field=bf_d)
     assert np.abs(F.cpu().numpy() - ref1).max() <= 1e-12 * scale(xy, tri, params, U1, dt)
+
+
+def test_noalloc_on_a_side_stream_and_after_a_nonpositive_density():
+    """Inputs written on a non-blocking side stream and the call made on that
+    stream; then a state whose density vanishes on a patch of triangles gives
+    SEIRD_ENONFINITE (1/N undefined), and the next call with a valid state
+    succeeds and matches the oracle again (the error word starts at zero on
+    every call)."""
+    name, xy, tri, params, U0, dt, bf = _cases()[1]
+    U1 = U0 * 1.02 + 0.5
+    d = lambda a: torch.tensor(np.ascontiguousarray(a), device="cuda")
+    ptr, inc = incidence(len(xy), tri)
+    tol = 1e-12 * scale(xy, tri, params, U1, dt)
+    ref = O.residual(xy, tri, params, dt, U1, U0, bf)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        xy_d, tri_d, ptr_d, inc_d = d(xy), d(tri.astype(np.int32)), d(ptr), d(inc)
+        bf_d, u_d, up_d = d(bf), d(U1), d(U0)
+        F = torch.full((len(xy), 5), np.nan, dtype=torch.float64, device="cuda")
+        S.residual_noalloc(xy_d, tri_d, ptr_d, inc_d, params, u_d, up_d, F, dt, beta_field=bf_d, stream=side)
+    side.synchronize()
+    assert np.abs(F.cpu().numpy() - ref).max() <= tol
+    # host-prepared bad state: every compartment zero on the nodes of a few triangles
+    bad = U1.copy()
+    bad[np.unique(tri[:40])] = 0.0
+    with pytest.raises(S.SeirdError) as ei:
+        S.residual_noalloc(xy_d, tri_d, ptr_d, inc_d, params, d(bad), up_d, F, dt, beta_field=bf_d)
+    assert ei.value.code == -7
+    S.residual_noalloc(xy_d, tri_d, ptr_d, inc_d, params, u_d, up_d, F, dt, beta_field=bf_d)
+    assert np.abs(F.cpu().numpy() - ref).max() <= tol
 
 
 def test_noalloc_rejects_meshes_beyond_its_scratch():
