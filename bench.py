@@ -1,13 +1,20 @@
 """Benchmark of the SEIRD backward-Euler Newton-Krylov-Schwarz step on GB300.
 
 Metric: implicit DOF*steps/s at a 1e-8 relative Newton residual (DOF = 5 x
-nodes), on the Southern-Ontario-like workload: a seeded 24-gon meshed to 2.0M
-P1 nodes (10M unknowns), urban-Gaussian density, 5 infection seeds, dt = 0.5
-day, RAS with 512 uneven subdomains, overlap 2, plus the constant coarse space.
+nodes).  Headline workload: the paper-scale Southern-Ontario-like mesh, a
+seeded 24-gon meshed to 18.4M P1 nodes (92M unknowns, the size of the paper's
+Section 4.2 scalability run), urban-Gaussian density, 5 infection seeds,
+dt = 0.5 day, RAS with 4096 uneven subdomains, overlap 2, the paper's
+multiplicative two-grid with the constant coarse space, FGMRES(30) with CGS2.
 A "step" is one backward-Euler time step (assembly, preconditioner set-up,
-GMRES, line search) of that whole mesh.
+GMRES, line search) of that whole mesh.  The same line carries the
+mixed-precision path on that workload, the 2.0M-node workload (10M unknowns,
+512 subdomains), a 64-sample ensemble, the discrete adjoint and the oracle
+timed on the host cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --cpu-ladder      (the oracle on a ladder of square meshes)
+  python bench.py --fp64-probe      (FP64 FMA and DGEMM rates of this GPU)
 
 --impl reference times the CPU oracle (test infrastructure, not the product)
 on the host cores, on a bounded sample of the same workload.  Under torchrun
@@ -18,6 +25,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -32,30 +40,29 @@ UNIT = "DOF·steps/s"
 FALLBACK_HBM_GBS = 6800.0
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from the committed ncu
-# capture of each kernel class at this workload (profiles/); None until captured
-# or after the kernel changed.
-# (kernel class, precision) -> (bytes per launch at the captured small case,
-# units processed there, seird_get_info key of those units); scaled to the
-# full launch by the units it processes (traffic grows in proportion).
+# capture of each kernel class (profiles/), as (bytes per launch at the captured
+# small case, units processed there, seird_get_info key of those units); scaled
+# to a full launch by the units it processes (traffic grows in proportion).
+# Entries are removed when the kernel changes and restored by the next capture.
 NCU_TRAFFIC = {
     ("spmv", "fp64"): (307.414e6, 1400635, "nnzb"),  # profiles/k_bsr_spmv_ontario200k.md
-    ("ilu_solve", "fp64"): (373.090e6, 1577927, "subdomain_blocks"),  # profiles/k_ilu_solve_ontario200k.md (v9)
-    ("ilu_solve", "mixed"): (202.650e6, 1577927, "subdomain_blocks"),  # same file, FP32 instantiation (v9)
 }
 
-# kernel classes with one kernel launch per timed call, and their algorithmic
-# bytes per launch
-SINGLE_KERNEL = ("spmv", "ilu_solve", "ilu_factor")
+# kernel classes with one kernel launch per timed call
+SINGLE_KERNEL = ("spmv", "ilu_solve")
+
+PAPER_SCALE_NODES = 18_400_000
+PAPER_SCALE_SUBDOMAINS = 4096
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--nodes", type=int, default=2_000_000)
-    ap.add_argument("--subdomains", type=int, default=512)
+    ap.add_argument("--nodes", type=int, default=PAPER_SCALE_NODES)
+    ap.add_argument("--subdomains", type=int, default=PAPER_SCALE_SUBDOMAINS)
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--forcing", choices=["fixed", "ew"], default="ew")
     ap.add_argument("--pc-lag", type=int, default=20)
@@ -65,46 +72,67 @@ def parse():
     ap.add_argument("--coarse", type=int, choices=[1, 2, 3], default=2,
                     help="1 additive coarse correction, 2 the paper's multiplicative two-grid (Eq. RAS_2L), "
                          "3 coarse correction then RAS")
+    ap.add_argument("--coarse-group", type=int, default=0, help="subdomains per coarse unit (0: automatic)")
     ap.add_argument("--no-mixed", action="store_true")
-    ap.add_argument("--cgs2", action="store_true", help="re-orthogonalise (CGS2) instead of PETSc's single pass")
+    ap.add_argument("--one-pass", action="store_true",
+                    help="one classical Gram-Schmidt pass (PETSc's default) instead of CGS2")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-2m", action="store_true", help="skip the 2.0M-node (10M-unknown) object")
     ap.add_argument("--ensemble", type=int, default=64, help="samples of the ensemble line (0: skip it)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint timing line")
     ap.add_argument("--no-autotune", action="store_true", help="fixed launch shapes instead of the autotuner's")
+    ap.add_argument("--cpu-ladder", action="store_true", help="time the oracle on the square-mesh ladder and exit")
+    ap.add_argument("--fp64-probe", action="store_true", help="measure the FP64 FMA and DGEMM rates and exit")
     ap.add_argument("--oracle-sample", type=str, default=None, help=argparse.SUPPRESS)
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
-def workload_config(wl, args):
+def solver_options(args, precision, subdomains):
+    return dict(n_subdomains=subdomains, overlap=2, coarse=args.coarse, coarse_group=args.coarse_group,
+                pc_keep_steps=args.pc_keep, predictor=args.predictor, newton_rtol=1e-8, gmres_rtol=1e-5,
+                gmres_restart=30, gmres_maxit=200, precision=1 if precision == "mixed" else 0, seed=args.seed,
+                gmres_forcing=1 if args.forcing == "ew" else 0, pc_lag=args.pc_lag,
+                gmres_one_pass=1 if args.one_pass else 0)
+
+
+def workload_config(wl, args, subdomains):
     return {
         "workload": "%s (Southern-Ontario-like 24-gon, %d P1 nodes, %d unknowns)" % (wl.name, wl.n, 5 * wl.n),
         "n_nodes": wl.n, "n_tris": int(len(wl.tri)), "dof": 5 * wl.n, "dt_days": wl.dt,
-        "subdomains": args.subdomains, "overlap": 2,
+        "subdomains": subdomains, "overlap": 2,
         "coarse": {1: "additive", 2: "multiplicative two-grid (Eq. RAS_2L)",
                    3: "coarse correction, then RAS"}[args.coarse] + ", constant per subdomain and compartment",
         "subdomain_solver": "block ILU(0)",
         "krylov": "FGMRES(30) right-preconditioned, %s, rtol 1e-5" % (
-            "CGS2" if args.cgs2 else "classical Gram-Schmidt single pass (PETSc default)"),
+            "classical Gram-Schmidt single pass (PETSc default)" if args.one_pass else "CGS2"),
+        "forcing": "Eisenstat-Walker" if args.forcing == "ew" else "fixed rtol 1e-5",
+        "pc_lag": args.pc_lag, "pc_keep_steps": args.pc_keep, "predictor": args.predictor,
         "newton_rtol": 1e-8, "quadrature": "degree-5 seven-point", "seed": args.seed,
         "l2": "inputs larger than L2 (the FP64 Jacobian alone is > 2.7 GB)",
     }
 
 
 # ---------------------------------------------------------------------------
-# CPU oracle sample (run in a child process with one BLAS thread)
+# CPU oracle (run in a child process with one BLAS thread)
 # ---------------------------------------------------------------------------
 
-SAMPLE_NODES = 20_000
+CPU_BASELINE_NODES = 20_000   # one step: about 20-25 s of one core
+REFERENCE_NODES = 5_000       # per step about 3 s: a --steps 20 --warmup 5 run ends in a few minutes
 
 
 def oracle_sample_child(spec):
-    """Times the oracle (as it stands) on the same generator at SAMPLE_NODES."""
+    """Times the oracle (as it stands) on the workload generator named in spec."""
     from oracle import seird_oracle as O
     from paper_2208_01839_gb300 import inputs as I
     d = json.loads(spec)
-    wl = I.ontario_workload(d["nodes"], seed=d["seed"])
+    if d.get("nside"):
+        wl = I.ontario_workload(d["nside"] ** 2, seed=d["seed"], structured=True, nside=d["nside"])
+    elif d.get("square"):
+        wl = I.square_workload(d["square"])
+    else:
+        wl = I.ontario_workload(d["nodes"], seed=d["seed"])
     U = wl.U0
     times = []
     for k in range(d["warmup"] + d["steps"]):
@@ -112,24 +140,57 @@ def oracle_sample_child(spec):
         U, info = O.newton_step(wl.xy, wl.tri, wl.params, wl.dt, U, rtol=1e-8)
         if k >= d["warmup"]:
             times.append(time.perf_counter() - t0)
-    print(json.dumps({"n": wl.n, "dof": 5 * wl.n, "times": times}))
+    print(json.dumps({"n": wl.n, "dof": 5 * wl.n, "times": times, "name": wl.name}))
 
 
-def run_oracle_sample(nodes, steps, warmup, seed):
+def run_oracle(spec):
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
         env[k] = "1"
-    spec = json.dumps({"nodes": nodes, "steps": steps, "warmup": warmup, "seed": seed})
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", spec], env=env,
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", json.dumps(spec)], env=env,
                        capture_output=True, text=True, cwd=ROOT)
     if r.returncode != 0:
         raise RuntimeError("oracle sample failed: %s" % r.stderr[-2000:])
-    out = json.loads(r.stdout.strip().splitlines()[-1])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def run_oracle_sample(nodes, steps, warmup, seed):
+    out = run_oracle({"nodes": nodes, "steps": steps, "warmup": warmup, "seed": seed})
     tot = sum(out["times"])
-    return {"value": out["dof"] * len(out["times"]) / tot, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d steps of the same generator at %d nodes (%d DOF), Newton to 1e-8 with a SuperLU "
-                      "direct solve, one thread" % (len(out["times"]), out["n"], out["dof"]),
+    return {"value": out["dof"] * len(out["times"]) / tot, "unit": UNIT, "cores": 1,
+            "host_cores": os.cpu_count(), "kind": "oracle",
+            "sample": "%d step(s) of the same generator at %d nodes (%d DOF), Newton to 1e-8 with a SuperLU "
+                      "direct solve, one thread of the host's %d" % (len(out["times"]), out["n"], out["dof"],
+                                                                     os.cpu_count() or 0),
             "s_per_step": tot / len(out["times"])}
+
+
+def run_cpu_ladder(args):
+    """The oracle on the 33x33 square (config 1) and on the urban-square ladder
+    65^2, 129^2, 257^2 (steps bounded so that each rung takes minutes), then a
+    power-law fit of seconds per step against nodes, extrapolated (and labelled
+    so) to the 2.0M-node and 18.4M-node workloads."""
+    rungs = [({"square": 33}, 10), ({"nside": 65}, 10), ({"nside": 129}, 3), ({"nside": 257}, 1)]
+    out = []
+    for spec, steps in rungs:
+        d = run_oracle(dict(spec, steps=steps, warmup=0, seed=args.seed))
+        sps = sum(d["times"]) / len(d["times"])
+        out.append({"workload": d["name"], "nodes": d["n"], "steps": len(d["times"]), "s_per_step": sps,
+                    "dof_steps_per_s": d["dof"] / sps})
+    # fit log(s) = a + b log(n) on the urban-square rungs (same generator family as the workloads)
+    pts = [(math.log(r["nodes"]), math.log(r["s_per_step"])) for r in out[1:]]
+    mx = sum(p[0] for p in pts) / len(pts)
+    my = sum(p[1] for p in pts) / len(pts)
+    b = sum((x - mx) * (y - my) for x, y in pts) / sum((x - mx) ** 2 for x, _ in pts)
+    a = my - b * mx
+    extra = {}
+    for name, n in (("ontario_like_2001k", 2_001_952), ("ontario_like_18408k", 18_408_616)):
+        s = math.exp(a + b * math.log(n))
+        extra[name] = {"nodes": n, "s_per_step": s, "dof_steps_per_s": 5 * n / s, "kind": "extrapolated",
+                       "s_per_180_steps": 180 * s}
+    print(json.dumps({"cpu_ladder": out, "fit": {"exponent": b, "s_per_step_at_1e5_nodes": math.exp(a + b * math.log(1e5))},
+                      "extrapolated": extra, "cores": 1, "host_cores": os.cpu_count(),
+                      "note": "oracle (NumPy assembly, SuperLU), one thread"}))
 
 
 # ---------------------------------------------------------------------------
@@ -204,47 +265,88 @@ def aggregate_value(dof, steps, seconds, world):
     return world * dof * steps / seconds
 
 
-def hbm_peak():
+def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         with open(path) as f:
-            return float(json.load(f)["hbm_gbs"]), "measured"
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
     except Exception:
-        return FALLBACK_HBM_GBS, "fallback"
+        return FALLBACK_HBM_GBS, "fallback (profiling recipe)"
 
 
-def algorithmic_bytes(cls, info, precision="fp64"):
-    """Bytes each launch of a kernel class must move at least (each array the
-    kernel needs, read or written once); the mixed path stores matrix values,
-    factors and the preconditioned basis in FP32."""
-    n, nnzb = info["n_nodes"], info["nnzb"]
-    nl, nlb = info["subdomain_rows"], info["subdomain_blocks"]
-    w = 4 if precision == "mixed" else 8
-    if cls == "spmv":  # values + column indices + row pointers + x once + y once (FP64)
-        return nnzb * (25 * w + 4) + (n + 1) * 4 + 5 * n * w + 5 * n * 8
-    if cls == "ilu_solve":  # factor blocks + columns + inverse diagonals + r gathered + z written
-        return nlb * (25 * w + 4) + nl * (25 * w + 8 + 16) + nl * 5 * 8 + 5 * n * w
-    if cls == "ilu_factor":  # J blocks gathered (FP64), factor blocks written, inverse diagonals written
-        return nlb * (25 * 8 + 25 * w + 4 + 4) + nl * 25 * w
+# GB300's FP64 rate: the recipe's nominal 1.25 TFLOP/s; this pool's measured FMA loop
+# (bench.py --fp64-probe, profiles/fp64_rate_gb300.md) gives 1.20
+FP64_PEAK_TFLOPS = 1.25
+
+
+def algorithmic_fma(cls, info):
+    """FP64 FMAs one launch must perform: 25 per 5x5 block product."""
+    if cls == "spmv":
+        return 25 * info["nnzb"]
+    if cls == "ilu_solve":  # forward L blocks + backward U blocks + the inverted pivots = every local block
+        return 25 * info["subdomain_blocks"]
     return None
+
+
+def class_sums(S, stats):
+    """Per kernel class over the timed steps: device ms, launches, algorithmic bytes (library counts)."""
+    kms = {k: sum(s["kernel_ms"][k] for s in stats) for k in S.KERNEL_CLASSES}
+    kcalls = {k: sum(s["kernel_calls"][k] for s in stats) for k in S.KERNEL_CLASSES}
+    kbytes = {k: sum(s["alg_bytes"][k] for s in stats) for k in S.KERNEL_CLASSES}
+    return kms, kcalls, kbytes
+
+
+def roofline(S, res, precision):
+    """Dominant single-kernel class against the HBM peak, the SpMV, and the whole step:
+    achieved = the library's algorithmic bytes / CUDA-event time on the context's stream."""
+    kms, kcalls, kbytes = class_sums(S, res["stats"])
+    info = res["info"]
+    peak, peak_kind = peaks()
+    dom = max(SINGLE_KERNEL, key=lambda k: kms[k])
+    ab = kbytes[dom] / max(kcalls[dom], 1)
+    avg_ms = kms[dom] / max(kcalls[dom], 1)
+    achieved = ab / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else 0.0
+    traffic = None
+    tr = NCU_TRAFFIC.get((dom, precision))
+    if tr is not None:
+        bytes_small, units_small, unit_key = tr
+        traffic = bytes_small * info[unit_key] / units_small
+    sp_ms = kms["spmv"] / max(kcalls["spmv"], 1)
+    sp_ab = kbytes["spmv"] / max(kcalls["spmv"], 1)
+    sp_gbs = sp_ab / (sp_ms * 1e-3) / 1e9 if kcalls["spmv"] and sp_ms > 0 else None
+    fma = algorithmic_fma(dom, info) if precision == "fp64" else None
+    alu = None
+    if fma is not None and avg_ms > 0:
+        tf = 2.0 * fma / (avg_ms * 1e-3) / 1e12
+        alu = {"achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tf / FP64_PEAK_TFLOPS,
+               "peak_kind": "nominal FP64 (profiling recipe)", "fma_per_launch": fma}
+    step_s = res["ms_per_step"] * len(res["stats"]) * 1e-3
+    total = sum(kbytes.values())
+    step = {"bytes_per_step": total / max(len(res["stats"]), 1), "achieved": total / step_s / 1e9 if step_s else None,
+            "peak": peak, "unit": "GB/s", "frac": (total / step_s / 1e9) / peak if step_s else None,
+            "peak_kind": peak_kind,
+            "bytes_by_class": {k: v / max(len(res["stats"]), 1) for k, v in kbytes.items()},
+            "note": "sum of the library's algorithmic bytes over the timed steps / their device time"}
+    return ({"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+             "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
+             "algorithmic_bytes_per_launch": ab, "avg_launch_ms": avg_ms, "launches": kcalls[dom],
+             "fp64_alu": alu},
+            {"gbs": sp_gbs, "frac_of_hbm": (sp_gbs / peak) if sp_gbs else None, "avg_launch_ms": sp_ms,
+             "launches": kcalls["spmv"], "algorithmic_bytes": sp_ab},
+            step, kms, kcalls)
 
 
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 
-def measure(S, wl, args, stream, precision, forcing, pc_lag, world, local, e2e=True):
+def measure(S, wl, args, stream, precision, subdomains, world, local, e2e=True):
     """Warm-up, then K device-timed steps (and K end-to-end steps) of one variant."""
     import torch
     import torch.distributed as dist
     t_create = time.perf_counter()
-    sv = S.Solver(wl.xy, wl.tri, wl.params, stream=stream, dt=wl.dt, n_subdomains=args.subdomains, overlap=2,
-                  coarse=args.coarse, pc_keep_steps=args.pc_keep, predictor=args.predictor, newton_rtol=1e-8,
-                  gmres_rtol=1e-5,
-                  gmres_restart=30, gmres_maxit=200,
-                  precision=1 if precision == "mixed" else 0, seed=args.seed, timing=1,
-                  gmres_forcing=1 if forcing == "ew" else 0, pc_lag=pc_lag, gmres_one_pass=0 if args.cgs2 else 1,
-                  autotune=0 if args.no_autotune else 1)
+    sv = S.Solver(wl.xy, wl.tri, wl.params, stream=stream, dt=wl.dt, timing=1,
+                  autotune=0 if args.no_autotune else 1, **solver_options(args, precision, subdomains))
     info = sv.info()
     t_create = time.perf_counter() - t_create  # partition, patterns, level schedules, upload
     sv.set_state(torch.tensor(wl.U0, device="cuda"))
@@ -272,8 +374,7 @@ def measure(S, wl, args, stream, precision, forcing, pc_lag, world, local, e2e=T
     ms = max_over_ranks(ms, world)
     dof = 5 * wl.n
     out = {"value": aggregate_value(dof, args.steps, ms * 1e-3, world), "ms_per_step": ms / args.steps,
-           "launches": launches, "create_s": t_create,
-           "clocks": clk.summary(), "info": info, "stats": stats}
+           "launches": launches, "create_s": t_create, "clocks": clk.summary(), "info": info, "stats": stats}
     if e2e:
         hbuf = torch.empty((wl.n, 5), dtype=torch.float64, pin_memory=True)
         sv.get_state(hbuf.numpy())
@@ -288,45 +389,64 @@ def measure(S, wl, args, stream, precision, forcing, pc_lag, world, local, e2e=T
         torch.cuda.synchronize()
         wall = max_over_ranks(time.perf_counter() - t0, world)
         out["e2e"] = {"value": aggregate_value(dof, args.steps, wall, world), "unit": UNIT,
-                      "h2d_bytes_per_step": dof * 8,
-                      "d2h_bytes_per_step": dof * 8}
+                      "h2d_bytes_per_step": dof * 8, "d2h_bytes_per_step": dof * 8}
     sv.close()
+    return out
+
+
+def summarize(S, res, precision, wl=None, args=None, subdomains=None):
+    roof, spmv, step, kms, kcalls = roofline(S, res, precision)
+    nits = [s["newton_its"] for s in res["stats"]]
+    gits = [s["gmres_its"] for s in res["stats"]]
+    out = {"value": res["value"], "unit": UNIT, "ms_per_step": res["ms_per_step"],
+           "dtype": "f64" if precision == "fp64" else "f64+f32", "roofline": roof, "spmv": spmv,
+           "step_roofline": step, "kernel_ms": {k: round(v, 3) for k, v in kms.items()}, "kernel_calls": kcalls,
+           "newton_its_per_step": sum(nits) / len(nits), "gmres_its_per_step": sum(gits) / len(gits),
+           "pc_setups": sum(s["pc_setups"] for s in res["stats"]), "gpu_launches": res["launches"],
+           "clocks": res["clocks"], "create_s": round(res["create_s"], 2),
+           "launch_shapes": {k: res["info"][k] for k in ("spmv_threads", "cgs_ctas", "cgs_tile")},
+           "device_bytes": res["info"]["device_bytes"], "coarse_units": res["info"]["coarse_units"]}
+    if wl is not None:
+        out["config"] = workload_config(wl, args, subdomains)
     return out
 
 
 def measure_ensemble(S, I, args, stream, world, local):
     """An ensemble of args.ensemble rate samples (each of the ten calibrated rates log-uniform within
     +-50% of the base) on the 256x256 urban square, 16 subdomains per sample: one context, one
-    block-diagonal system, every kernel launch covers all samples.  Device-timed like the main line."""
+    block-diagonal system, every kernel launch covers all samples.  The GMRES restart cycles run as
+    replays of a captured CUDA graph (options.graph); the eager loop is timed beside it."""
     import numpy as np
     import torch
     import torch.distributed as dist
     wl = I.ontario_workload(256 * 256, seed=args.seed, structured=True, nside=256)
     samples = I.rate_samples(wl.params, args.ensemble, args.seed)
-    sv = S.Solver(wl.xy, wl.tri, samples, stream=stream, dt=wl.dt, n_subdomains=16, overlap=2, coarse=args.coarse,
-                  pc_keep_steps=args.pc_keep, predictor=args.predictor, newton_rtol=1e-8, gmres_rtol=1e-5,
-                  gmres_restart=30, gmres_maxit=200,
-                  seed=args.seed, gmres_forcing=1, pc_lag=args.pc_lag, gmres_one_pass=0 if args.cgs2 else 1)
-    sv.set_state(torch.tensor(np.concatenate([wl.U0] * len(samples)), device="cuda"))
-    for _ in range(args.warmup):
-        sv.step()
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    launches0 = S.launch_count()
-    e0.record(stream)
-    stats = [sv.step() for _ in range(args.steps)]
-    e1.record(stream)
-    torch.cuda.synchronize()
-    launches = S.launch_count() - launches0
-    ms = max_over_ranks(e0.elapsed_time(e1), world)
-    sv.close()
+    u0 = torch.tensor(np.concatenate([wl.U0] * len(samples)), device="cuda")
+    res = {}
+    for mode in ("eager", "graph"):
+        sv = S.Solver(wl.xy, wl.tri, samples, stream=stream, dt=wl.dt, graph=1 if mode == "graph" else 0,
+                      **solver_options(args, "fp64", 16))
+        sv.set_state(u0)
+        for _ in range(args.warmup):
+            sv.step()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        launches0 = S.launch_count()
+        e0.record(stream)
+        stats = [sv.step() for _ in range(args.steps)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res[mode] = (max_over_ranks(e0.elapsed_time(e1), world), S.launch_count() - launches0, stats)
+        sv.close()
+    ms, launches, stats = res["graph"]
     dof = 5 * wl.n * len(samples)
     return {"workload": "ensemble of %d rate samples on the 256x256 urban square (%d unknowns)" % (len(samples), dof),
-            "value": aggregate_value(dof, args.steps, ms * 1e-3, world), "unit": UNIT,
-            "ms_per_step": ms / args.steps, "n_samples": len(samples), "dtype": "f64", "gpu_launches": launches,
+            "value": aggregate_value(dof, args.steps, ms * 1e-3, world), "unit": UNIT, "graph": True,
+            "ms_per_step": ms / args.steps, "eager_ms_per_step": res["eager"][0] / args.steps,
+            "n_samples": len(samples), "dtype": "f64", "gpu_launches": launches,
             "newton_its_per_step": sum(s["newton_its"] for s in stats) / len(stats),
             "gmres_its_per_step": sum(s["gmres_its"] for s in stats) / len(stats)}
 
@@ -342,9 +462,9 @@ def measure_adjoint(S, I, args, stream):
     nodes = np.sort(rng.choice(wl.n, 50, replace=False)).astype(np.int32)
     steps = np.arange(2, 61, 2, dtype=np.int32)
     field = np.ones(wl.n)
-    sv = S.Solver(wl.xy, wl.tri, wl.params, beta_field=field, stream=stream, dt=wl.dt, n_subdomains=16, overlap=2,
-                  coarse=args.coarse, newton_rtol=1e-8, gmres_rtol=1e-5, gmres_restart=30, gmres_maxit=200,
-                  seed=args.seed, gmres_forcing=1, pc_lag=args.pc_lag, gmres_one_pass=0 if args.cgs2 else 1)
+    opts = solver_options(args, "fp64", 16)
+    opts.update(pc_keep_steps=0, predictor=0)
+    sv = S.Solver(wl.xy, wl.tri, wl.params, beta_field=field, stream=stream, dt=wl.dt, **opts)
     u0 = torch.tensor(wl.U0, device="cuda")
     sv.set_state(u0)
     obs = []
@@ -371,62 +491,6 @@ def measure_adjoint(S, I, args, stream):
             "misfit": j, "gradient_entries": int(g.size + gb.size)}
 
 
-def kernel_summary(S, res):
-    stats, info = res["stats"], res["info"]
-    kms = {k: sum(s["kernel_ms"][k] for s in stats) for k in S.KERNEL_CLASSES}
-    kcalls = {k: sum(s["kernel_calls"][k] for s in stats) for k in S.KERNEL_CLASSES}
-    return kms, kcalls
-
-
-# GB300's nominal FP64 rate (no FP64 tensor path beyond the FP64 pipe's 1.25 TFLOP/s)
-FP64_PEAK_TFLOPS = 1.25
-
-
-def algorithmic_fma(cls, info):
-    """FP64 FMAs one launch must perform: 25 per 5x5 block product."""
-    if cls == "spmv":
-        return 25 * info["nnzb"]
-    if cls == "ilu_solve":  # forward L blocks + backward U blocks + the inverted pivots = every local block
-        return 25 * info["subdomain_blocks"]
-    return None
-
-
-def roofline(S, res, precision, coarse=2):
-    kms, kcalls = kernel_summary(S, res)
-    info = res["info"]
-    peak, peak_kind = hbm_peak()
-    dom = max(SINGLE_KERNEL, key=lambda k: kms[k])
-    ab = algorithmic_bytes(dom, info, precision)
-    avg_ms = kms[dom] / max(kcalls[dom], 1)
-    achieved = ab / (avg_ms * 1e-3) / 1e9
-    traffic = None
-    tr = NCU_TRAFFIC.get((dom, precision))
-    if tr is not None:
-        bytes_small, units_small, unit_key = tr
-        traffic = bytes_small * info[unit_key] / units_small
-    sp_ab = algorithmic_bytes("spmv", info, precision)
-    # with the multiplicative two-grid every coarse application follows an SpMV that also
-    # reads r (it computes r - J z): those launches move 5n FP64 values more
-    fused = kcalls["coarse_apply"] if coarse == 2 else 0
-    if kcalls["spmv"]:
-        sp_ab = sp_ab + min(fused, kcalls["spmv"]) / kcalls["spmv"] * 5 * info["n_nodes"] * 8
-    sp_ms = kms["spmv"] / max(kcalls["spmv"], 1)
-    sp_gbs = sp_ab / (sp_ms * 1e-3) / 1e9 if kcalls["spmv"] else None
-    fma = algorithmic_fma(dom, info) if precision == "fp64" else None
-    alu = None
-    if fma is not None:
-        tf = 2.0 * fma / (avg_ms * 1e-3) / 1e12
-        alu = {"achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tf / FP64_PEAK_TFLOPS,
-               "peak_kind": "nominal FP64 (profiling recipe)", "fma_per_launch": fma}
-    return ({"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-             "frac": achieved / peak, "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind ==
-             "measured" else peak_kind, "traffic": traffic, "algorithmic_bytes_per_launch": ab,
-             "avg_launch_ms": avg_ms, "launches": kcalls[dom], "fp64_alu": alu},
-            {"gbs": sp_gbs, "frac_of_hbm": (sp_gbs / peak) if sp_gbs else None, "avg_launch_ms": sp_ms,
-             "launches": kcalls["spmv"], "algorithmic_bytes": sp_ab},
-            kms, kcalls)
-
-
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -447,12 +511,23 @@ def run_ours(args):
     t_setup = time.perf_counter()
     wl = I.ontario_workload(args.nodes, seed=args.seed, n_subdomains=args.subdomains)
     t_gen = time.perf_counter() - t_setup
+    cfg_main = workload_config(wl, args, args.subdomains)
 
-    res = measure(S, wl, args, stream, args.precision, args.forcing, args.pc_lag, world, local,
-                  e2e=not args.no_e2e)
+    res = measure(S, wl, args, stream, args.precision, args.subdomains, world, local, e2e=not args.no_e2e)
     other = None
     if not args.no_mixed and args.precision == "fp64":
-        other = measure(S, wl, args, stream, "mixed", args.forcing, args.pc_lag, world, local, e2e=False)
+        other = measure(S, wl, args, stream, "mixed", args.subdomains, world, local, e2e=False)
+    del wl
+
+    two = None
+    if not args.no_2m and args.nodes != 2_000_000:
+        wl2 = I.ontario_workload(2_000_000, seed=args.seed, n_subdomains=512)
+        r64 = measure(S, wl2, args, stream, "fp64", 512, world, local, e2e=False)
+        r32 = measure(S, wl2, args, stream, "mixed", 512, world, local, e2e=False)
+        two = summarize(S, r64, "fp64", wl2, args, 512)
+        two["mixed"] = summarize(S, r32, "mixed")
+        two["mixed"]["speedup_vs_fp64"] = r32["value"] / r64["value"]
+        del wl2
 
     ens = None
     if args.ensemble > 0:
@@ -464,39 +539,36 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            cpu = run_oracle_sample(SAMPLE_NODES, 2, 0, args.seed)
+            cpu = run_oracle_sample(CPU_BASELINE_NODES, 1, 0, args.seed)
         except Exception as ex:  # reported, never fatal
             cpu = {"error": str(ex)[:300]}
 
     if rank == 0:
-        roof, spmv, kms, kcalls = roofline(S, res, args.precision, args.coarse)
-        nits = [s["newton_its"] for s in res["stats"]]
-        gits = [s["gmres_its"] for s in res["stats"]]
+        main = summarize(S, res, args.precision)
         line = {
             "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
+            "scaling": "weak", "vs_baseline": None, "dtype": main["dtype"],
             "data": "synthetic (seeded Southern-Ontario-like mesh, density and infection seeds)",
-            "config": dict(workload_config(wl, args), precision=args.precision,
-                           forcing="Eisenstat-Walker" if args.forcing == "ew" else "fixed rtol 1e-5",
-                           pc_lag=args.pc_lag, pc_keep_steps=args.pc_keep, predictor=args.predictor,
+            "config": dict(cfg_main, precision=args.precision,
                            parallelism="replicas" if world > 1 else "single GPU"),
-            "roofline": roof, "spmv": spmv, "cpu_baseline": cpu, "e2e": res.get("e2e"),
-            "gpu_launches": res["launches"], "clocks": res["clocks"],
-            "kernel_ms": {k: round(v, 3) for k, v in kms.items()}, "kernel_calls": kcalls,
-            "newton_its_per_step": sum(nits) / len(nits), "gmres_its_per_step": sum(gits) / len(gits),
+            "roofline": main["roofline"], "spmv": main["spmv"], "step_roofline": main["step_roofline"],
+            "cpu_baseline": cpu, "e2e": res.get("e2e"), "gpu_launches": res["launches"], "clocks": res["clocks"],
+            "kernel_ms": main["kernel_ms"], "kernel_calls": main["kernel_calls"],
+            "newton_its_per_step": main["newton_its_per_step"], "gmres_its_per_step": main["gmres_its_per_step"],
+            "pc_setups": main["pc_setups"],
             "setup_s": {"generate": round(t_gen, 2), "create": round(res["create_s"], 2)},
-            "launch_shapes": {k: res["info"][k] for k in ("spmv_threads", "cgs_ctas", "cgs_tile")},
-            "device_bytes": res["info"]["device_bytes"],
+            "launch_shapes": main["launch_shapes"], "device_bytes": main["device_bytes"],
+            "coarse_units": main["coarse_units"],
+            "paper_context": "the paper's 92.57M-unknown Southern Ontario forecast: 3 months 'within 7 hours' on "
+                             "1780 processes (extrapolated there from scaling runs; Section 4.2)",
         }
         if other is not None:
-            r2, s2, k2, c2 = roofline(S, other, "mixed", args.coarse)
-            g2 = [s["gmres_its"] for s in other["stats"]]
-            line["mixed"] = {"value": other["value"], "ms_per_step": other["ms_per_step"],
-                             "speedup_vs_fp64": other["value"] / res["value"], "dtype": "f64+f32",
-                             "roofline": r2, "spmv": s2, "kernel_ms": {k: round(v, 3) for k, v in k2.items()},
-                             "gmres_its_per_step": sum(g2) / len(g2), "gpu_launches": other["launches"],
-                             "clocks": other["clocks"]}
+            m = summarize(S, other, "mixed")
+            m["speedup_vs_fp64"] = other["value"] / res["value"]
+            line["mixed"] = m
+        if two is not None:
+            line["ontario_2m"] = two
         if ens is not None:
             line["ensemble"] = ens
         if adj is not None:
@@ -515,23 +587,88 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    res = run_oracle_sample(SAMPLE_NODES, args.steps, args.warmup, args.seed)
+    res = run_oracle_sample(REFERENCE_NODES, args.steps, args.warmup, args.seed)
     line = {
         "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * res["s_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
         "config": {"workload": "Southern-Ontario-like 24-gon, %d P1 nodes (timed on a %d-node sample)"
-                               % (args.nodes, SAMPLE_NODES), "dt_days": 0.5, "newton_rtol": 1e-8},
-        "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": res["sample"], "value": res["value"], "unit": UNIT},
+                               % (args.nodes, REFERENCE_NODES), "dt_days": 0.5, "newton_rtol": 1e-8},
+        "cpu_baseline": {"kind": "oracle", "cores": 1, "host_cores": os.cpu_count(), "sample": res["sample"],
+                         "value": res["value"], "unit": UNIT},
         "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+# FP64 rates of the GPU (the measurement behind the no-tensor-core decision)
+# ---------------------------------------------------------------------------
+
+def run_fp64_probe(args):
+    """FP64 FMA rate (an elementwise kernel of 1024 dependent-chain-free FMA groups per
+    element, compiled at run time by torch's jiterator) and torch.matmul float64
+    (cuBLAS DGEMM) TFLOP/s, best of 5, CUDA events, clocks sampled meanwhile."""
+    import torch
+    torch.cuda.set_device(0)
+    out = {}
+    with ClockSampler(0) as clk:
+        # DGEMM
+        n = 8192
+        a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+        b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+        torch.matmul(a, b)
+        best = 1e30
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        out["dgemm"] = {"n": n, "ms": best, "tflops": 2.0 * n ** 3 / (best * 1e-3) / 1e12}
+        del a, b
+        # FMA loop: eight independent chains per element, 128 FMAs each
+        code = """
+        template <typename T> T fma_probe(T x, T y) {
+          T a0 = x, a1 = x + 1, a2 = x + 2, a3 = x + 3, a4 = x + 4, a5 = x + 5, a6 = x + 6, a7 = x + 7;
+          for (int i = 0; i < 128; ++i) {
+            a0 = a0 * y + x; a1 = a1 * y + x; a2 = a2 * y + x; a3 = a3 * y + x;
+            a4 = a4 * y + x; a5 = a5 * y + x; a6 = a6 * y + x; a7 = a7 * y + x;
+          }
+          return a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
+        }"""
+        fn = torch.cuda.jiterator._create_jit_fn(code)
+        m = 1 << 26
+        x = torch.rand(m, dtype=torch.float64, device="cuda")
+        y = torch.full((m,), 0.999, dtype=torch.float64, device="cuda")
+        fn(x, y)
+        best = 1e30
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn(x, y)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        fmas = m * 8 * 128
+        out["fma_loop"] = {"elements": m, "fma_per_element": 1024, "ms": best,
+                           "tflops": 2.0 * fmas / (best * 1e-3) / 1e12}
+    out["clocks"] = clk.summary()
+    out["gpu"] = torch.cuda.get_device_name(0)
+    print(json.dumps({"fp64_probe": out}))
 
 
 def main():
     args = parse()
     if args.oracle_sample:
         oracle_sample_child(args.oracle_sample)
+        return
+    if args.cpu_ladder:
+        run_cpu_ladder(args)
+        return
+    if args.fp64_probe:
+        run_fp64_probe(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "internal.h"
+#include <nvtx3/nvToolsExt.h>
 #include "kernels.cuh"
 
 namespace seird {
@@ -165,6 +166,16 @@ int check_flags(seird_ctx* ctx, const char* where) {
   return fail(ctx, SEIRD_ENONFINITE, std::string(where) + ": non-finite value");
 }
 
+// ---- tracing ------------------------------------------------------------------
+
+// NVTX range around a phase of the step (no-op unless a profiler is attached)
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
+
 // ---- kernel-class timing ----------------------------------------------------
 
 // Records a start event on construction and an end event on destruction, on the
@@ -270,6 +281,7 @@ double bytes_arnoldi(const seird_ctx* c, int nv) {
 
 // F = F(U; Un), returns ||F||_2 in *fn (synchronises)
 int residual(seird_ctx* ctx, const double* U, const double* Un, double* F, double* fn) {
+  Range rg_("seird residual");
   const HostSetup& hs = ctx->hs;
   {
     KTimer kt_(ctx, SEIRD_K_RESIDUAL);
@@ -290,6 +302,7 @@ int residual(seird_ctx* ctx, const double* U, const double* Un, double* F, doubl
 // Assembles dF/dU at U (picard = false) or the Picard matrix of Eq.
 // weak_vec_implicit with its coefficients frozen at U (picard = true).
 int jacobian(seird_ctx* ctx, const double* U, bool picard = false) {
+  Range rg_("seird jacobian");
   const HostSetup& hs = ctx->hs;
   KTimer kt_(ctx, SEIRD_K_JACOBIAN);
   add_bytes(ctx, SEIRD_K_JACOBIAN, bytes_jacobian(ctx));
@@ -373,6 +386,7 @@ CoarseDev coarse_dev(seird_ctx* ctx) {
 }
 
 int pc_setup(seird_ctx* ctx) {
+  Range rg_("seird preconditioner setup");
   if (!ctx->jac_ready) return fail(ctx, SEIRD_EINVAL, "preconditioner setup needs an assembled Jacobian");
   {
     KTimer kt_(ctx, SEIRD_K_ILU_FACTOR);
@@ -782,6 +796,7 @@ static int build_cycle_graph(seird_ctx* ctx) {
 }
 
 int gmres(seird_ctx* ctx, const double* b, double* x, double rtol, int* its_out, bool* converged) {
+  Range rg_("seird gmres");
   const int64_t len = vlen(ctx);
   const int m = ctx->opt.gmres_restart;
   const int ldh = m + 1;
@@ -984,6 +999,7 @@ int picard_step(seird_ctx* ctx, seird_stats* st) {
 }
 
 int newton_step(seird_ctx* ctx, seird_stats* st) {
+  Range rg_("seird step");
   if (ctx->opt.nonlinear == 1) return picard_step(ctx, st);
   using clk = std::chrono::steady_clock;
   const auto t_begin = clk::now();
