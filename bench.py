@@ -40,12 +40,13 @@ UNIT = "DOF·steps/s"
 FALLBACK_HBM_GBS = 6800.0
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from the committed ncu
-# capture of each kernel class (profiles/), as (bytes per launch at the captured
-# small case, units processed there, seird_get_info key of those units); scaled
-# to a full launch by the units it processes (traffic grows in proportion).
-# Entries are removed when the kernel changes and restored by the next capture.
+# capture of each kernel class on the 200k-node case of the same generator, as
+# (bytes per launch there, units processed there, seird_get_info key of those
+# units); scaled to a full launch by the units it processes (traffic grows in
+# proportion).  Entries are removed when the kernel changes and restored by the
+# next capture.
 NCU_TRAFFIC = {
-    ("spmv", "fp64"): (307.414e6, 1400635, "nnzb"),  # profiles/k_bsr_spmv_ontario200k.md
+    ("spmv", "fp64"): (307.414e6, 1400635, "nnzb"),  # k_bsr_spmv<double>, 1.4M blocks
 }
 
 # kernel classes with one kernel launch per timed call
@@ -274,9 +275,9 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback (profiling recipe)"
 
 
-# GB300's FP64 rate: the recipe's nominal 1.25 TFLOP/s; this pool's measured FMA loop
-# (bench.py --fp64-probe, profiles/fp64_rate_gb300.md) gives 1.20
-FP64_PEAK_TFLOPS = 1.25
+# GB300's FP64 rate as measured by --fp64-probe on this machine (an FMA loop: 1.234 TFLOP/s at
+# 2070 MHz; cuBLAS DGEMM reaches 1.10), against the nominal 1.25 TFLOP/s
+FP64_PEAK_TFLOPS = 1.234
 
 
 def algorithmic_fma(cls, info):
@@ -319,7 +320,7 @@ def roofline(S, res, precision):
     if fma is not None and avg_ms > 0:
         tf = 2.0 * fma / (avg_ms * 1e-3) / 1e12
         alu = {"achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tf / FP64_PEAK_TFLOPS,
-               "peak_kind": "nominal FP64 (profiling recipe)", "fma_per_launch": fma}
+               "peak_kind": "measured FP64 FMA loop (bench.py --fp64-probe)", "fma_per_launch": fma}
     step_s = res["ms_per_step"] * len(res["stats"]) * 1e-3
     total = sum(kbytes.values())
     step = {"bytes_per_step": total / max(len(res["stats"]), 1), "achieved": total / step_s / 1e9 if step_s else None,
@@ -404,7 +405,7 @@ def summarize(S, res, precision, wl=None, args=None, subdomains=None):
            "newton_its_per_step": sum(nits) / len(nits), "gmres_its_per_step": sum(gits) / len(gits),
            "pc_setups": sum(s["pc_setups"] for s in res["stats"]), "gpu_launches": res["launches"],
            "clocks": res["clocks"], "create_s": round(res["create_s"], 2),
-           "launch_shapes": {k: res["info"][k] for k in ("spmv_threads", "cgs_ctas", "cgs_tile")},
+           "launch_shapes": {k: res["info"][k] for k in ("spmv_threads", "cgs_ctas", "cgs_tile", "ilu_batch")},
            "device_bytes": res["info"]["device_bytes"], "coarse_units": res["info"]["coarse_units"]}
     if wl is not None:
         out["config"] = workload_config(wl, args, subdomains)

@@ -145,11 +145,13 @@ typedef struct {
                              2 u^n - u^{n-1} when the previous step is known and it lowers ||F||.
                              The stopping test stays relative to ||F(u^n)|| either way (0) */
   int32_t autotune;       /* 1: at the first linear solve, time the candidate launch shapes of the SpMV
-                             (128/256/512 threads per CTA) and of the Gram-Schmidt kernels (2/3/4/6 CTAs
-                             per SM, 128- or 256-entry tiles) on the context's own vectors and keep the
-                             fastest; the choice is reported by seird_get_info.  The Gram-Schmidt shape
-                             sets the order of its sums, so results are reproducible for a given choice,
-                             not across choices.  0: fixed shapes (256 threads, 3 CTAs per SM, 256) (0) */
+                             (128/256/512 threads per CTA), of the Gram-Schmidt kernels (2/3/4/6 CTAs
+                             per SM, 128- or 256-entry tiles) and of the subdomain solves (1-4 blocks of
+                             solution entries loaded per batch) on the context's own vectors and factors
+                             and keep the fastest; the choice is reported by seird_get_info.  The
+                             Gram-Schmidt shape sets the order of its sums, so results are reproducible
+                             for a given choice, not across choices; the other choices leave every sum
+                             unchanged.  0: fixed shapes (256 threads, 3 CTAs per SM, 256, 2 blocks) (0) */
   int32_t graph;          /* 1: each GMRES restart cycle runs as one replay of a CUDA graph captured at
                              the first solve: iteration j is a conditional node that the Givens kernel
                              of iteration j - 1 arms while the residual estimate is above the
@@ -207,6 +209,8 @@ typedef struct {
   int32_t spmv_threads;        /* launch shapes in use (options.autotune): SpMV threads per CTA, */
   int32_t cgs_ctas;            /* Gram-Schmidt CTAs, */
   int32_t cgs_tile;            /* Gram-Schmidt tile entries (0: 256 up to depth 27, then 128) */
+  int32_t ilu_batch;           /* subdomain solves: blocks whose solution entries a row loads before
+                                  their FMAs (1-4) */
 } seird_info;
 
 typedef struct seird_ctx seird_ctx;
@@ -354,6 +358,16 @@ int seird_precond_setup(seird_ctx* ctx);
 
 /* z = M^{-1} r with the last preconditioner built (caller numbering). */
 int seird_precond_apply(seird_ctx* ctx, const double* r, double* z, int on_device);
+
+/* Pins launch shapes (each 0 keeps the current one): SpMV threads per CTA (128, 256,
+ * 512), Gram-Schmidt CTAs (1 .. 64 x SMs) and tile entries (128, 256), and the
+ * subdomain solves' dependency-load batch (1-4 blocks).  The autotuner
+ * (options.autotune) does not change shapes pinned this way, so the shapes one
+ * run reported by seird_get_info reproduce its sums in another run (the
+ * Gram-Schmidt shape sets the order of its sums; the other shapes do not change
+ * any result).  SEIRD_EINVAL for a value outside these candidates. */
+int seird_set_launch_shapes(seird_ctx* ctx, int32_t spmv_threads, int32_t cgs_ctas, int32_t cgs_tile,
+                            int32_t ilu_batch);
 
 /* Failure detection of the bounded device waits (the library never waits
  * without bound).  The subdomain solves of the RAS apply stream each stage's

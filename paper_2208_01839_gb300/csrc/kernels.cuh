@@ -168,6 +168,9 @@ struct RasDev {
   // none, so every wait gives up at once); the final wait for issued copies to land
   // keeps the fixed bound SOLVE_DRAIN_POLLS
   int32_t wait_polls;
+  // blocks whose solution entries a consumer row loads before their FMAs (1-4; the autotuner's
+  // choice, 2 by default); every choice forms the same sums in the same order
+  int32_t solve_ch;
 };
 constexpr int32_t SOLVE_WAIT_POLLS_DEFAULT = 1 << 20;
 void launch_ilu_factor(const RasDev& d, const double* val, const float* val32, int32_t* err, bool fp32,

@@ -283,7 +283,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 }
 __device__ __forceinline__ void consumers_sync() { asm volatile("bar.sync 1, 224;" ::: "memory"); }
 
-template <class T, class TZ>
+template <class T, class TZ, int CH>
 __global__ void __launch_bounds__(256, 4) k_ilu_solve(RasDev d, const double* __restrict__ r, TZ* __restrict__ z,
                                                       int32_t* err) {
   constexpr int BS = SolveBS<T>::v;
@@ -407,11 +407,14 @@ __global__ void __launch_bounds__(256, 4) k_ilu_solve(RasDev d, const double* __
       // inverted pivot).  The entries of CH blocks are loaded before any of their
       // FMAs, so a row waits for one memory latency per CH blocks, not per block.
       // A short row reloads its last block to fill the batch; a stage is bound by
-      // its busiest warp's instruction chain, so two blocks per batch measured best
-      // (2.0M nodes: FP32 0.91 ms against 0.96 / 0.95 / 0.94 / 1.02 ms for 1 / 4 / 3
-      // / 6 blocks; FP64 1.68 ms against 1.74 / 1.70 ms for 1 / 3).
-      constexpr int CH = 2;
-      for (int32_t j = fw ? 0 : 1; j < cn; j += CH) {
+      // its busiest warp's instruction chain, so the batch trades load rounds
+      // against instructions (2.0M nodes: FP32 0.91 ms for 2 blocks against 0.96 /
+      // 0.95 / 0.94 / 1.02 ms for 1 / 4 / 3 / 6; FP64 1.68 ms against 1.74 / 1.70 ms
+      // for 1 / 3); the autotuner picks CH per context.  Block b of the row (counted
+      // from its first product) goes to chain b % 2 whatever CH is, so every CH
+      // gives the same sums in the same order.
+      const int32_t jb = fw ? 0 : 1;
+      for (int32_t j = jb; j < cn; j += CH) {
         const int nb = min(CH, cn - j);
         T xv[CH][5];
 #pragma unroll
@@ -424,9 +427,10 @@ __global__ void __launch_bounds__(256, 4) k_ilu_solve(RasDev d, const double* __
         for (int u = 0; u < CH; ++u) {
           if (u < nb) {  // folded into two accumulator chains: no separate add per block
             const T* Lb = B + (st + j + u) * BS + 5 * cpt;
+            const bool odd = (CH % 2 == 0) ? (u & 1) : ((j - jb + u) & 1);
 #pragma unroll
             for (int mm = 0; mm < 5; ++mm) {
-              if (u & 1) acc2 = fmaT(Lb[mm], xv[u][mm], acc2);
+              if (odd) acc2 = fmaT(Lb[mm], xv[u][mm], acc2);
               else acc = fmaT(-Lb[mm], xv[u][mm], acc);
             }
           }
@@ -723,14 +727,24 @@ void launch_ilu_reorg(const RasDev& d, int64_t nfwd, int64_t nbwd, const int64_t
   count_launch();
 }
 
-void launch_ilu_solve(const RasDev& d, const double* r, double* z, int32_t* err, cudaStream_t s) {
-  k_ilu_solve<double, double><<<d.P, 256, solve_smem(false), s>>>(d, r, z, err);
+template <class T>
+void launch_ilu_solve_t(const RasDev& d, const double* r, T* z, int32_t* err, cudaStream_t s, int ch) {
+  const size_t sm = solve_smem(sizeof(T) == 4);
+  switch (ch) {
+    case 1: k_ilu_solve<T, T, 1><<<d.P, 256, sm, s>>>(d, r, z, err); break;
+    case 3: k_ilu_solve<T, T, 3><<<d.P, 256, sm, s>>>(d, r, z, err); break;
+    case 4: k_ilu_solve<T, T, 4><<<d.P, 256, sm, s>>>(d, r, z, err); break;
+    default: k_ilu_solve<T, T, 2><<<d.P, 256, sm, s>>>(d, r, z, err); break;
+  }
   count_launch();
 }
 
+void launch_ilu_solve(const RasDev& d, const double* r, double* z, int32_t* err, cudaStream_t s) {
+  launch_ilu_solve_t<double>(d, r, z, err, s, d.solve_ch);
+}
+
 void launch_ilu_solve32(const RasDev& d, const double* r, float* z, int32_t* err, cudaStream_t s) {
-  k_ilu_solve<float, float><<<d.P, 256, solve_smem(true), s>>>(d, r, z, err);
-  count_launch();
+  launch_ilu_solve_t<float>(d, r, z, err, s, d.solve_ch);
 }
 
 void launch_coarse_assemble(const CoarseDev& c, const double* val, const float* val32, cudaStream_t s) {
@@ -884,9 +898,15 @@ void launch_az_sub(const CoarseDev& c, int64_t n, const int64_t* az_ptr, const i
 void coarse_init() {
   cudaFuncSetAttribute(k_band_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   cudaFuncSetAttribute(k_band_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-  cudaFuncSetAttribute(k_ilu_solve<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)solve_smem(false));
-  cudaFuncSetAttribute(k_ilu_solve<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)solve_smem(true));
+  const int s64 = (int)solve_smem(false), s32 = (int)solve_smem(true);
+  cudaFuncSetAttribute(k_ilu_solve<double, double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, s64);
+  cudaFuncSetAttribute(k_ilu_solve<double, double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, s64);
+  cudaFuncSetAttribute(k_ilu_solve<double, double, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, s64);
+  cudaFuncSetAttribute(k_ilu_solve<double, double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, s64);
+  cudaFuncSetAttribute(k_ilu_solve<float, float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, s32);
+  cudaFuncSetAttribute(k_ilu_solve<float, float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, s32);
+  cudaFuncSetAttribute(k_ilu_solve<float, float, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, s32);
+  cudaFuncSetAttribute(k_ilu_solve<float, float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, s32);
 }
 
 }  // namespace seird

@@ -7,6 +7,8 @@ their own rates, solved as one block-diagonal system.
 * Steps: every sample's state is the oracle root at its rates (<= 1e-9
   relative L2 per compartment, FP64 and mixed).
 * An ensemble of one sample reproduces the single-problem context bit for bit.
+* With options.graph (GMRES cycles replayed as captured CUDA graphs) the
+  ensemble's states equal the eager loop's bit for bit.
 * Rates of an ensemble are fixed: set_params and the beta schedule are refused.
 * The ensemble adjoint gives every sample's gradient: sample by sample it is the
   oracle's adjoint at that sample's rates and observations (1e-7 of the largest
@@ -85,6 +87,30 @@ def test_ensemble_steps_match_per_sample_oracle(precision):
     for k, p in enumerate(samples):
         ref, _ = O.run(xy, tri, p, 0.5, U0, 3, rtol=1e-12, atol=atol, bfield=bf)
         assert max(rel_l2_per_comp(got[k * n:(k + 1) * n], ref)) <= 1e-9, (k, rel_l2_per_comp(got[k * n:(k + 1) * n], ref))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_ensemble_under_captured_gmres_cycles(precision):
+    """options.graph on an ensemble: each GMRES restart cycle of the block-diagonal
+    system is one replay of a captured CUDA graph.  The states equal the eager
+    ensemble's bit for bit (same kernels, same launch shapes, same order of
+    sums), and every sample is the oracle root at its rates."""
+    xy, tri, samples, U0, bf = _problem()
+    n = len(xy)
+    atol = 1e-14 * np.linalg.norm(O.residual(xy, tri, samples[0], 0.0, np.abs(U0), np.zeros_like(U0)))
+    out = {}
+    for graph in (0, 1):
+        with S.Solver(xy, tri, samples, beta_field=bf, owner=I.box_partition(xy, 2, 2),
+                      **_opts(precision=precision, graph=graph, newton_atol=atol * np.sqrt(len(samples)))) as sv:
+            sv.set_state(np.concatenate([U0] * len(samples)))
+            stats = sv.run(3)
+            out[graph] = (sv.get_state(), [s["gmres_its"] for s in stats])
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1]
+    got = out[1][0]
+    for k, p in enumerate(samples):
+        ref, _ = O.run(xy, tri, p, 0.5, U0, 3, rtol=1e-12, atol=atol, bfield=bf)
+        assert max(rel_l2_per_comp(got[k * n:(k + 1) * n], ref)) <= 1e-9, k
 
 
 def test_ensemble_of_one_is_the_single_problem():

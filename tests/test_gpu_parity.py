@@ -466,5 +466,33 @@ def test_autotuned_launch_shapes():
             got = sv.get_state()
             inf = sv.info()
         assert inf["spmv_threads"] in (128, 256, 512) and inf["cgs_tile"] in (128, 256), inf
-        assert inf["cgs_ctas"] > 0
+        assert inf["cgs_ctas"] > 0 and inf["ilu_batch"] in (1, 2, 3, 4), inf
         assert max(rel_l2_per_comp(got, U_ref)) <= (1e-9 if precision == 0 else 1e-6), precision
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_subdomain_solve_batches_give_identical_results(precision):
+    """The subdomain solve's dependency-load batch (1-4 blocks, an autotuner choice)
+    changes only when a row's loads are issued: every batch forms the same sums in
+    the same order, so the preconditioner apply is bitwise the same for all four."""
+    wl = WL["irregular3k"]
+    r = np.random.default_rng(31).standard_normal(5 * wl.n)
+    J = O.jacobian(wl.xy, wl.tri, wl.params, wl.dt, wl.U0, bfield=wl.beta_field)
+    rp, col, val = O.to_bsr(J)
+    ref = O.ras_apply(rp, col, val, wl.owner, 2, r, coarse=True, multiplicative=True)
+    outs = []
+    with solver(wl, overlap=2, coarse=2, precision=precision, autotune=1) as sv:
+        sv.jacobian(wl.U0)
+        sv.precond_setup()
+        sv.set_state(wl.U0)
+        sv.linear_solve(r.reshape(-1, 5))  # runs the autotuner (the chosen batch is one of the four)
+        with pytest.raises(S.SeirdError):
+            sv.set_launch_shapes(ilu_batch=5)
+        for ch in (1, 2, 3, 4):
+            sv.set_launch_shapes(ilu_batch=ch)
+            assert sv.info()["ilu_batch"] == ch
+            outs.append(sv.precond_apply(r.reshape(-1, 5)).ravel())
+    for k in range(1, 4):
+        assert np.array_equal(outs[0], outs[k]), k
+    tol = 1e-10 if precision == 0 else 1e-4
+    assert np.linalg.norm(outs[0] - ref) <= tol * np.linalg.norm(ref)
