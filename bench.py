@@ -405,7 +405,7 @@ def summarize(S, res, precision, wl=None, args=None, subdomains=None):
            "newton_its_per_step": sum(nits) / len(nits), "gmres_its_per_step": sum(gits) / len(gits),
            "pc_setups": sum(s["pc_setups"] for s in res["stats"]), "gpu_launches": res["launches"],
            "clocks": res["clocks"], "create_s": round(res["create_s"], 2),
-           "launch_shapes": {k: res["info"][k] for k in ("spmv_threads", "cgs_ctas", "cgs_tile", "ilu_batch")},
+           "launch_shapes": {k: res["info"][k] for k in ("spmv_threads", "cgs_ctas", "cgs_tile", "ilu_batch", "ilu_warps")},
            "device_bytes": res["info"]["device_bytes"], "coarse_units": res["info"]["coarse_units"]}
     if wl is not None:
         out["config"] = workload_config(wl, args, subdomains)

@@ -252,7 +252,8 @@ struct seird_ctx {
   double abytes[SEIRD_K_COUNT] = {};
   // launch shapes (options.autotune)
   int spmv_tb = 256, cgs_tile = 0, sms = 1;
-  int ilu_ch = 2;  // dependency-load batch of the subdomain solves (options.autotune)
+  int ilu_ch = 2;     // dependency-load batch of the subdomain solves (options.autotune)
+  int ilu_warps = 7;  // their consumer warps per CTA (7 or 3)
   bool tuned = false;
   double* tune_buf = nullptr;
   // GMRES restart cycle captured into a CUDA graph (options.graph)

@@ -171,6 +171,7 @@ struct RasDev {
   // blocks whose solution entries a consumer row loads before their FMAs (1-4; the autotuner's
   // choice, 2 by default); every choice forms the same sums in the same order
   int32_t solve_ch;
+  int32_t solve_warps;  // consumer warps per subdomain CTA: 7 (256 threads) or 3 (128 threads)
 };
 constexpr int32_t SOLVE_WAIT_POLLS_DEFAULT = 1 << 20;
 void launch_ilu_factor(const RasDev& d, const double* val, const float* val32, int32_t* err, bool fp32,

@@ -273,7 +273,6 @@ struct SolveRing<float> {
 };
 constexpr int SOLVE_RING_ROWS = 2 * SOLVE_BUF_ROWS_DEV;
 constexpr int SOLVE_SLOTS = 8;
-constexpr int SOLVE_CONSUMERS = 224;  // warps 0-6
 
 __device__ __forceinline__ void mbar_init_count(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
@@ -281,11 +280,19 @@ __device__ __forceinline__ void mbar_init_count(uint64_t* bar, uint32_t count) {
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
-__device__ __forceinline__ void consumers_sync() { asm volatile("bar.sync 1, 224;" ::: "memory"); }
+// named barrier 1 over the NCW consumer warps (the producer warp does not take part)
+template <int NCW>
+__device__ __forceinline__ void consumers_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(32 * NCW) : "memory");
+}
 
-template <class T, class TZ, int CH>
-__global__ void __launch_bounds__(256, 4) k_ilu_solve(RasDev d, const double* __restrict__ r, TZ* __restrict__ z,
-                                                      int32_t* err) {
+// NCW consumer warps (7 or 3) and one producer warp.  Seven consumers take up to 42
+// rows of a stage in one round; three take 18, but their CTA of 128 threads needs half
+// the registers, so where shared memory allows (the FP32 rings) twice as many
+// subdomains run on an SM at once.  Every row's arithmetic is the same either way.
+template <class T, class TZ, int CH, int NCW>
+__global__ void __launch_bounds__(32 * (NCW + 1), NCW <= 3 ? 7 : 4)
+    k_ilu_solve(RasDev d, const double* __restrict__ r, TZ* __restrict__ z, int32_t* err) {
   constexpr int BS = SolveBS<T>::v;
   constexpr int RB = SolveRing<T>::blocks;
   constexpr int RR = SOLVE_RING_ROWS;
@@ -316,7 +323,7 @@ __global__ void __launch_bounds__(256, 4) k_ilu_solve(RasDev d, const double* __
   }
   __syncthreads();
 
-  if (warp == 7) {
+  if (warp == NCW) {
     // ---- producer: stage g < nF is forward level g, otherwise backward level
     // g - nF; it uses slot g % NS, whose barriers complete phase (g / NS) & 1 for it.
     if (lane != 0) return;
@@ -390,7 +397,7 @@ __global__ void __launch_bounds__(256, 4) k_ilu_solve(RasDev d, const double* __
     const int nrows = landed ? slot_n[sl] : 0;
     const int k0 = slot_k0[sl];
     T* vec = fw ? y : zz;
-    for (int qb = warp * 6; qb < nrows; qb += 6 * (SOLVE_CONSUMERS / 32)) {
+    for (int qb = warp * 6; qb < nrows; qb += 6 * NCW) {
       const int q = qb + rw;
       const bool act = lane < 30 && q < nrows;
       int32_t st = 0, cn = 0, onode = -1;
@@ -411,8 +418,10 @@ __global__ void __launch_bounds__(256, 4) k_ilu_solve(RasDev d, const double* __
       // against instructions (2.0M nodes: FP32 0.91 ms for 2 blocks against 0.96 /
       // 0.95 / 0.94 / 1.02 ms for 1 / 4 / 3 / 6; FP64 1.68 ms against 1.74 / 1.70 ms
       // for 1 / 3); the autotuner picks CH per context.  Block b of the row (counted
-      // from its first product) goes to chain b % 2 whatever CH is, so every CH
-      // gives the same sums in the same order.
+      // from its first product) goes to chain b % 2 whatever CH is: both chains
+      // subtract, the slot of a batch's block u is fixed (u % 2), and after a batch
+      // of odd size the two chains trade slots, so every CH gives the same sums in
+      // the same order with no run-time choice of chain per FMA.
       const int32_t jb = fw ? 0 : 1;
       for (int32_t j = jb; j < cn; j += CH) {
         const int nb = min(CH, cn - j);
@@ -427,16 +436,23 @@ __global__ void __launch_bounds__(256, 4) k_ilu_solve(RasDev d, const double* __
         for (int u = 0; u < CH; ++u) {
           if (u < nb) {  // folded into two accumulator chains: no separate add per block
             const T* Lb = B + (st + j + u) * BS + 5 * cpt;
-            const bool odd = (CH % 2 == 0) ? (u & 1) : ((j - jb + u) & 1);
 #pragma unroll
             for (int mm = 0; mm < 5; ++mm) {
-              if (odd) acc2 = fmaT(Lb[mm], xv[u][mm], acc2);
+              if (u & 1) acc2 = fmaT(-Lb[mm], xv[u][mm], acc2);
               else acc = fmaT(-Lb[mm], xv[u][mm], acc);
             }
           }
         }
+        if (CH % 2 == 1) {  // the next batch starts on the other chain
+          const T t = acc;
+          acc = acc2;
+          acc2 = t;
+        }
       }
-      acc -= acc2;
+      // the chain that started from r (or y) and the other one; FP addition commutes, so
+      // whichever register holds which chain the sum is the same (and -fma(a, b, c) =
+      // fma(-a, b, -c) exactly, so this equals the r - sum_even - (sum_odd) of a chain that adds)
+      acc += acc2;
       const int kq = k0 + q;  // this row's position
       T v = acc;
       if (!fw) {
@@ -454,7 +470,7 @@ __global__ void __launch_bounds__(256, 4) k_ilu_solve(RasDev d, const double* __
         if (!fw && onode >= 0) z[5 * (int64_t)onode + cpt] = (TZ)v;
       }
     }
-    consumers_sync();  // every row of this stage is written; the stage's ring space is free
+    consumers_sync<NCW>();  // every row of this stage is written; the stage's ring space is free
     if (*(volatile int*)&abort_at <= g) {
       aborted = true;
       break;
@@ -727,24 +743,39 @@ void launch_ilu_reorg(const RasDev& d, int64_t nfwd, int64_t nbwd, const int64_t
   count_launch();
 }
 
-template <class T>
-void launch_ilu_solve_t(const RasDev& d, const double* r, T* z, int32_t* err, cudaStream_t s, int ch) {
+template <class T, int NCW>
+void launch_ilu_solve_w(const RasDev& d, const double* r, T* z, int32_t* err, cudaStream_t s, int ch) {
   const size_t sm = solve_smem(sizeof(T) == 4);
+  constexpr int tb = 32 * (NCW + 1);
   switch (ch) {
-    case 1: k_ilu_solve<T, T, 1><<<d.P, 256, sm, s>>>(d, r, z, err); break;
-    case 3: k_ilu_solve<T, T, 3><<<d.P, 256, sm, s>>>(d, r, z, err); break;
-    case 4: k_ilu_solve<T, T, 4><<<d.P, 256, sm, s>>>(d, r, z, err); break;
-    default: k_ilu_solve<T, T, 2><<<d.P, 256, sm, s>>>(d, r, z, err); break;
+    case 1: k_ilu_solve<T, T, 1, NCW><<<d.P, tb, sm, s>>>(d, r, z, err); break;
+    case 3: k_ilu_solve<T, T, 3, NCW><<<d.P, tb, sm, s>>>(d, r, z, err); break;
+    case 4: k_ilu_solve<T, T, 4, NCW><<<d.P, tb, sm, s>>>(d, r, z, err); break;
+    default: k_ilu_solve<T, T, 2, NCW><<<d.P, tb, sm, s>>>(d, r, z, err); break;
   }
   count_launch();
 }
 
+template <class T>
+void launch_ilu_solve_t(const RasDev& d, const double* r, T* z, int32_t* err, cudaStream_t s) {
+  if (d.solve_warps == 3) launch_ilu_solve_w<T, 3>(d, r, z, err, s, d.solve_ch);
+  else launch_ilu_solve_w<T, 7>(d, r, z, err, s, d.solve_ch);
+}
+
 void launch_ilu_solve(const RasDev& d, const double* r, double* z, int32_t* err, cudaStream_t s) {
-  launch_ilu_solve_t<double>(d, r, z, err, s, d.solve_ch);
+  launch_ilu_solve_t<double>(d, r, z, err, s);
 }
 
 void launch_ilu_solve32(const RasDev& d, const double* r, float* z, int32_t* err, cudaStream_t s) {
-  launch_ilu_solve_t<float>(d, r, z, err, s, d.solve_ch);
+  launch_ilu_solve_t<float>(d, r, z, err, s);
+}
+
+template <class T, int NCW>
+void solve_attrs(int smem) {
+  cudaFuncSetAttribute(k_ilu_solve<T, T, 1, NCW>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_ilu_solve<T, T, 2, NCW>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_ilu_solve<T, T, 3, NCW>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_ilu_solve<T, T, 4, NCW>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
 void launch_coarse_assemble(const CoarseDev& c, const double* val, const float* val32, cudaStream_t s) {
@@ -899,14 +930,10 @@ void coarse_init() {
   cudaFuncSetAttribute(k_band_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   cudaFuncSetAttribute(k_band_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   const int s64 = (int)solve_smem(false), s32 = (int)solve_smem(true);
-  cudaFuncSetAttribute(k_ilu_solve<double, double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, s64);
-  cudaFuncSetAttribute(k_ilu_solve<double, double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, s64);
-  cudaFuncSetAttribute(k_ilu_solve<double, double, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, s64);
-  cudaFuncSetAttribute(k_ilu_solve<double, double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, s64);
-  cudaFuncSetAttribute(k_ilu_solve<float, float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, s32);
-  cudaFuncSetAttribute(k_ilu_solve<float, float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, s32);
-  cudaFuncSetAttribute(k_ilu_solve<float, float, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, s32);
-  cudaFuncSetAttribute(k_ilu_solve<float, float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, s32);
+  solve_attrs<double, 7>(s64);
+  solve_attrs<double, 3>(s64);
+  solve_attrs<float, 7>(s32);
+  solve_attrs<float, 3>(s32);
 }
 
 }  // namespace seird

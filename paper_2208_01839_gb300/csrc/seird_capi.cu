@@ -361,6 +361,7 @@ RasDev ras_dev(seird_ctx* ctx) {
   d.bU32 = ctx->bU32;
   d.wait_polls = ctx->wait_polls;
   d.solve_ch = ctx->ilu_ch;
+  d.solve_warps = ctx->ilu_warps;
   return d;
 }
 
@@ -674,31 +675,38 @@ int autotune(seird_ctx* ctx) {
       }
     }
   }
-  // subdomain solves: the dependency-load batch, on the context's own factors with
-  // V[0] as the right-hand side (every batch forms the same sums; only the time differs)
+  // subdomain solves: the dependency-load batch and the consumer warps per CTA, on the
+  // context's own factors with V[0] as the right-hand side (every choice forms the same
+  // sums; only the time differs)
   if (ctx->pc_ready) {
     tbest = 1e30f;
-    const int keep = ctx->ilu_ch;
-    for (int ch : {1, 2, 3, 4}) {
-      ctx->ilu_ch = ch;
-      const RasDev d = ras_dev(ctx);
-      const float t = best_of([&] {
-        if (mixed(ctx)) launch_ilu_solve32(d, ctx->V, reinterpret_cast<float*>(ctx->tune_buf), ctx->err, s);
-        else launch_ilu_solve(d, ctx->V, ctx->tune_buf, ctx->err, s);
-      });
-      if (t < tbest) {
-        tbest = t;
-        best_ch = ch;
+    const int keep_ch = ctx->ilu_ch, keep_w = ctx->ilu_warps;
+    int best_w = 0;
+    for (int nw : {7, 3}) {
+      for (int ch : {1, 2, 3, 4}) {
+        ctx->ilu_ch = ch;
+        ctx->ilu_warps = nw;
+        const RasDev d = ras_dev(ctx);
+        const float t = best_of([&] {
+          if (mixed(ctx)) launch_ilu_solve32(d, ctx->V, reinterpret_cast<float*>(ctx->tune_buf), ctx->err, s);
+          else launch_ilu_solve(d, ctx->V, ctx->tune_buf, ctx->err, s);
+        });
+        if (t < tbest) {
+          tbest = t;
+          best_ch = ch;
+          best_w = nw;
+        }
       }
     }
-    ctx->ilu_ch = best_ch > 0 ? best_ch : keep;
+    ctx->ilu_ch = best_ch > 0 ? best_ch : keep_ch;
+    ctx->ilu_warps = best_w > 0 ? best_w : keep_w;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   CK(cudaGetLastError());
   if (verbose())
-    std::fprintf(stderr, "[seird] autotune: spmv %d threads, gram-schmidt %d CTAs, tile %d, ilu batch %d\n",
-                 ctx->spmv_tb, ctx->red_grid, ctx->cgs_tile, ctx->ilu_ch);
+    std::fprintf(stderr, "[seird] autotune: spmv %d threads, gram-schmidt %d CTAs, tile %d, ilu batch %d warps %d\n",
+                 ctx->spmv_tb, ctx->red_grid, ctx->cgs_tile, ctx->ilu_ch, ctx->ilu_warps);
   return SEIRD_OK;
 }
 
@@ -1783,6 +1791,7 @@ int seird_get_info(const seird_ctx* ctx, seird_info* info) {
   info->cgs_ctas = ctx->red_grid;
   info->cgs_tile = ctx->cgs_tile;
   info->ilu_batch = ctx->ilu_ch;
+  info->ilu_warps = ctx->ilu_warps;
   return SEIRD_OK;
 }
 
@@ -1870,16 +1879,17 @@ int seird_precond_apply(seird_ctx* ctx, const double* r, double* z, int on_devic
 }
 
 int seird_set_launch_shapes(seird_ctx* ctx, int32_t spmv_threads, int32_t cgs_ctas, int32_t cgs_tile,
-                            int32_t ilu_batch) {
+                            int32_t ilu_batch, int32_t ilu_warps) {
   if (!ctx) return SEIRD_EINVAL;
   if ((spmv_threads && spmv_threads != 128 && spmv_threads != 256 && spmv_threads != 512) || cgs_ctas < 0 ||
       cgs_ctas > 64 * ctx->sms || (cgs_tile && cgs_tile != 128 && cgs_tile != 256) || ilu_batch < 0 ||
-      ilu_batch > 4)
+      ilu_batch > 4 || (ilu_warps && ilu_warps != 3 && ilu_warps != 7))
     return fail(ctx, SEIRD_EINVAL, "set_launch_shapes: a shape outside its candidates");
   if (spmv_threads) ctx->spmv_tb = spmv_threads;
   if (cgs_ctas) ctx->red_grid = cgs_ctas;
   if (cgs_tile) ctx->cgs_tile = cgs_tile;
   if (ilu_batch) ctx->ilu_ch = ilu_batch;
+  if (ilu_warps) ctx->ilu_warps = ilu_warps;
   ctx->tuned = true;  // the autotuner keeps these
   if (ctx->cycle_exec) {  // a captured restart cycle holds the old shapes
     cudaGraphExecDestroy(ctx->cycle_exec);

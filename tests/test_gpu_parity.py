@@ -466,15 +466,16 @@ def test_autotuned_launch_shapes():
             got = sv.get_state()
             inf = sv.info()
         assert inf["spmv_threads"] in (128, 256, 512) and inf["cgs_tile"] in (128, 256), inf
-        assert inf["cgs_ctas"] > 0 and inf["ilu_batch"] in (1, 2, 3, 4), inf
+        assert inf["cgs_ctas"] > 0 and inf["ilu_batch"] in (1, 2, 3, 4) and inf["ilu_warps"] in (3, 7), inf
         assert max(rel_l2_per_comp(got, U_ref)) <= (1e-9 if precision == 0 else 1e-6), precision
 
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_subdomain_solve_batches_give_identical_results(precision):
-    """The subdomain solve's dependency-load batch (1-4 blocks, an autotuner choice)
-    changes only when a row's loads are issued: every batch forms the same sums in
-    the same order, so the preconditioner apply is bitwise the same for all four."""
+    """The subdomain solve's dependency-load batch (1-4 blocks) and consumer warps per
+    CTA (7 or 3), both autotuner choices, change only when a row's loads are issued
+    and which warp takes it: every choice forms the same sums in the same order, so
+    the preconditioner apply is bitwise the same for all eight."""
     wl = WL["irregular3k"]
     r = np.random.default_rng(31).standard_normal(5 * wl.n)
     J = O.jacobian(wl.xy, wl.tri, wl.params, wl.dt, wl.U0, bfield=wl.beta_field)
@@ -488,11 +489,15 @@ def test_subdomain_solve_batches_give_identical_results(precision):
         sv.linear_solve(r.reshape(-1, 5))  # runs the autotuner (the chosen batch is one of the four)
         with pytest.raises(S.SeirdError):
             sv.set_launch_shapes(ilu_batch=5)
-        for ch in (1, 2, 3, 4):
-            sv.set_launch_shapes(ilu_batch=ch)
-            assert sv.info()["ilu_batch"] == ch
-            outs.append(sv.precond_apply(r.reshape(-1, 5)).ravel())
-    for k in range(1, 4):
+        for nw in (7, 3):
+            for ch in (1, 2, 3, 4):
+                sv.set_launch_shapes(ilu_batch=ch, ilu_warps=nw)
+                inf = sv.info()
+                assert inf["ilu_batch"] == ch and inf["ilu_warps"] == nw
+                outs.append(sv.precond_apply(r.reshape(-1, 5)).ravel())
+        with pytest.raises(S.SeirdError):
+            sv.set_launch_shapes(ilu_warps=5)
+    for k in range(1, len(outs)):
         assert np.array_equal(outs[0], outs[k]), k
     tol = 1e-10 if precision == 0 else 1e-4
     assert np.linalg.norm(outs[0] - ref) <= tol * np.linalg.norm(ref)
