@@ -405,7 +405,7 @@ def summarize(S, res, precision, wl=None, args=None, subdomains=None):
            "newton_its_per_step": sum(nits) / len(nits), "gmres_its_per_step": sum(gits) / len(gits),
            "pc_setups": sum(s["pc_setups"] for s in res["stats"]), "gpu_launches": res["launches"],
            "clocks": res["clocks"], "create_s": round(res["create_s"], 2),
-           "launch_shapes": {k: res["info"][k] for k in ("spmv_threads", "cgs_ctas", "cgs_tile", "ilu_batch", "ilu_warps")},
+           "launch_shapes": {k: res["info"][k] for k in ("spmv_threads", "cgs_ctas", "cgs_tile", "ilu_batch", "ilu_warps", "ilu_ring")},
            "device_bytes": res["info"]["device_bytes"], "coarse_units": res["info"]["coarse_units"]}
     if wl is not None:
         out["config"] = workload_config(wl, args, subdomains)
@@ -561,8 +561,8 @@ def run_ours(args):
             "setup_s": {"generate": round(t_gen, 2), "create": round(res["create_s"], 2)},
             "launch_shapes": main["launch_shapes"], "device_bytes": main["device_bytes"],
             "coarse_units": main["coarse_units"],
-            "paper_context": "the paper's 92.57M-unknown Southern Ontario forecast: 3 months 'within 7 hours' on "
-                             "1780 processes (extrapolated there from scaling runs; Section 4.2)",
+            "paper_context": "the paper's 92.57M-unknown Southern Ontario forecast: three months in under seven "
+                             "hours on 1780 processes (its estimate from scaling runs; Section 4.2)",
         }
         if other is not None:
             m = summarize(S, other, "mixed")

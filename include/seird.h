@@ -147,8 +147,8 @@ typedef struct {
   int32_t autotune;       /* 1: at the first linear solve, time the candidate launch shapes of the SpMV
                              (128/256/512 threads per CTA), of the Gram-Schmidt kernels (2/3/4/6 CTAs
                              per SM, 128- or 256-entry tiles) and of the subdomain solves (1-4 blocks of
-                             solution entries loaded per batch, 7 or 3 consumer warps per CTA) on the
-                             context's own vectors and factors
+                             solution entries loaded per batch, 7 or 3 consumer warps per CTA, a factor
+                             ring of two stages or one) on the context's own vectors and factors
                              and keep the fastest; the choice is reported by seird_get_info.  The
                              Gram-Schmidt shape sets the order of its sums, so results are reproducible
                              for a given choice, not across choices; the other choices leave every sum
@@ -212,7 +212,8 @@ typedef struct {
   int32_t cgs_tile;            /* Gram-Schmidt tile entries (0: 256 up to depth 27, then 128) */
   int32_t ilu_batch;           /* subdomain solves: blocks whose solution entries a row loads before
                                   their FMAs (1-4), */
-  int32_t ilu_warps;           /* and consumer warps per subdomain CTA (7, or 3 in CTAs of 128 threads) */
+  int32_t ilu_warps;           /* consumer warps per subdomain CTA (7, or 3 in CTAs of 128 threads), */
+  int32_t ilu_ring;            /* and factor blocks in the shared-memory ring (236: two stages, 118: one) */
 } seird_info;
 
 typedef struct seird_ctx seird_ctx;
@@ -363,13 +364,14 @@ int seird_precond_apply(seird_ctx* ctx, const double* r, double* z, int on_devic
 
 /* Pins launch shapes (each 0 keeps the current one): SpMV threads per CTA (128, 256,
  * 512), Gram-Schmidt CTAs (1 .. 64 x SMs) and tile entries (128, 256), and the
- * subdomain solves' dependency-load batch (1-4 blocks) and consumer warps (7 or 3).  The autotuner
+ * subdomain solves' dependency-load batch (1-4 blocks), consumer warps (7 or 3)
+ * and factor-ring size (236 or 118 blocks; 118 only when every stage fits it).  The autotuner
  * (options.autotune) does not change shapes pinned this way, so the shapes one
  * run reported by seird_get_info reproduce its sums in another run (the
  * Gram-Schmidt shape sets the order of its sums; the other shapes do not change
  * any result).  SEIRD_EINVAL for a value outside these candidates. */
 int seird_set_launch_shapes(seird_ctx* ctx, int32_t spmv_threads, int32_t cgs_ctas, int32_t cgs_tile,
-                            int32_t ilu_batch, int32_t ilu_warps);
+                            int32_t ilu_batch, int32_t ilu_warps, int32_t ilu_ring);
 
 /* Failure detection of the bounded device waits (the library never waits
  * without bound).  The subdomain solves of the RAS apply stream each stage's

@@ -254,6 +254,7 @@ struct seird_ctx {
   int spmv_tb = 256, cgs_tile = 0, sms = 1;
   int ilu_ch = 2;     // dependency-load batch of the subdomain solves (options.autotune)
   int ilu_warps = 7;  // their consumer warps per CTA (7 or 3)
+  int ilu_ring = seird::SOLVE_RING_FULL;  // and factor-ring blocks (two stages or one)
   bool tuned = false;
   double* tune_buf = nullptr;
   // GMRES restart cycle captured into a CUDA graph (options.graph)

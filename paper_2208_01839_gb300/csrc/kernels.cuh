@@ -172,7 +172,10 @@ struct RasDev {
   // choice, 2 by default); every choice forms the same sums in the same order
   int32_t solve_ch;
   int32_t solve_warps;  // consumer warps per subdomain CTA: 7 (256 threads) or 3 (128 threads)
+  int32_t solve_ring;   // blocks in the factor ring: SOLVE_RING_FULL (two stages) or SOLVE_RING_HALF (one)
 };
+constexpr int32_t SOLVE_RING_FULL = 2 * SOLVE_BUF_BLOCKS_DEV;
+constexpr int32_t SOLVE_RING_HALF = SOLVE_BUF_BLOCKS_DEV;
 constexpr int32_t SOLVE_WAIT_POLLS_DEFAULT = 1 << 20;
 void launch_ilu_factor(const RasDev& d, const double* val, const float* val32, int32_t* err, bool fp32,
                        cudaStream_t s);

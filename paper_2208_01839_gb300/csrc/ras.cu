@@ -261,16 +261,11 @@ constexpr int SOLVE_DRAIN_POLLS = 1 << 20;
 // ring's end: the producer skips the tail.  Every wait is bounded; on a
 // timeout the kernel sets bit 3 of *err, lets every issued copy land and
 // returns.
-template <class T>
-struct SolveRing;
-template <>
-struct SolveRing<double> {
-  static constexpr int blocks = 2 * SOLVE_BUF_BLOCKS_DEV;  // 236 x 208 B
-};
-template <>
-struct SolveRing<float> {
-  static constexpr int blocks = 2 * SOLVE_BUF_BLOCKS_DEV;  // 236 x 112 B: a larger ring measured 6% slower
-};
+// Ring of factor blocks: two stages (236 blocks: 49 KB in FP64, 26 KB in FP32) so that
+// the next stage streams in while one is consumed, or one stage (118 blocks), which
+// halves a CTA's shared memory so that more subdomains share an SM and hide each
+// other's latency instead (SOLVE_RING_FULL / SOLVE_RING_HALF; a 354-block FP32 ring
+// measured 6% slower).
 constexpr int SOLVE_RING_ROWS = 2 * SOLVE_BUF_ROWS_DEV;
 constexpr int SOLVE_SLOTS = 8;
 
@@ -290,11 +285,10 @@ __device__ __forceinline__ void consumers_sync() {
 // rows of a stage in one round; three take 18, but their CTA of 128 threads needs half
 // the registers, so where shared memory allows (the FP32 rings) twice as many
 // subdomains run on an SM at once.  Every row's arithmetic is the same either way.
-template <class T, class TZ, int CH, int NCW>
+template <class T, class TZ, int CH, int NCW, int RB>
 __global__ void __launch_bounds__(32 * (NCW + 1), NCW <= 3 ? 7 : 4)
     k_ilu_solve(RasDev d, const double* __restrict__ r, TZ* __restrict__ z, int32_t* err) {
   constexpr int BS = SolveBS<T>::v;
-  constexpr int RB = SolveRing<T>::blocks;
   constexpr int RR = SOLVE_RING_ROWS;
   constexpr int NS = SOLVE_SLOTS;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -724,9 +718,9 @@ void launch_ilu_factor(const RasDev& d, const double* val, const float* val32, i
   count_launch();
 }
 
-size_t solve_smem(bool fp32) {
-  return fp32 ? (size_t)SolveRing<float>::blocks * SolveBS<float>::v * sizeof(float)
-              : (size_t)SolveRing<double>::blocks * SolveBS<double>::v * sizeof(double);
+size_t solve_smem(bool fp32, int ring_blocks) {
+  return fp32 ? (size_t)ring_blocks * SolveBS<float>::v * sizeof(float)
+              : (size_t)ring_blocks * SolveBS<double>::v * sizeof(double);
 }
 
 void launch_ilu_reorg(const RasDev& d, int64_t nfwd, int64_t nbwd, const int64_t* fsrc, const int32_t* fcol,
@@ -743,23 +737,29 @@ void launch_ilu_reorg(const RasDev& d, int64_t nfwd, int64_t nbwd, const int64_t
   count_launch();
 }
 
-template <class T, int NCW>
+template <class T, int NCW, int RB>
 void launch_ilu_solve_w(const RasDev& d, const double* r, T* z, int32_t* err, cudaStream_t s, int ch) {
-  const size_t sm = solve_smem(sizeof(T) == 4);
+  const size_t sm = solve_smem(sizeof(T) == 4, RB);
   constexpr int tb = 32 * (NCW + 1);
   switch (ch) {
-    case 1: k_ilu_solve<T, T, 1, NCW><<<d.P, tb, sm, s>>>(d, r, z, err); break;
-    case 3: k_ilu_solve<T, T, 3, NCW><<<d.P, tb, sm, s>>>(d, r, z, err); break;
-    case 4: k_ilu_solve<T, T, 4, NCW><<<d.P, tb, sm, s>>>(d, r, z, err); break;
-    default: k_ilu_solve<T, T, 2, NCW><<<d.P, tb, sm, s>>>(d, r, z, err); break;
+    case 1: k_ilu_solve<T, T, 1, NCW, RB><<<d.P, tb, sm, s>>>(d, r, z, err); break;
+    case 3: k_ilu_solve<T, T, 3, NCW, RB><<<d.P, tb, sm, s>>>(d, r, z, err); break;
+    case 4: k_ilu_solve<T, T, 4, NCW, RB><<<d.P, tb, sm, s>>>(d, r, z, err); break;
+    default: k_ilu_solve<T, T, 2, NCW, RB><<<d.P, tb, sm, s>>>(d, r, z, err); break;
   }
   count_launch();
 }
 
 template <class T>
 void launch_ilu_solve_t(const RasDev& d, const double* r, T* z, int32_t* err, cudaStream_t s) {
-  if (d.solve_warps == 3) launch_ilu_solve_w<T, 3>(d, r, z, err, s, d.solve_ch);
-  else launch_ilu_solve_w<T, 7>(d, r, z, err, s, d.solve_ch);
+  const bool half = d.solve_ring == SOLVE_RING_HALF;
+  if (d.solve_warps == 3) {
+    if (half) launch_ilu_solve_w<T, 3, SOLVE_RING_HALF>(d, r, z, err, s, d.solve_ch);
+    else launch_ilu_solve_w<T, 3, SOLVE_RING_FULL>(d, r, z, err, s, d.solve_ch);
+  } else {
+    if (half) launch_ilu_solve_w<T, 7, SOLVE_RING_HALF>(d, r, z, err, s, d.solve_ch);
+    else launch_ilu_solve_w<T, 7, SOLVE_RING_FULL>(d, r, z, err, s, d.solve_ch);
+  }
 }
 
 void launch_ilu_solve(const RasDev& d, const double* r, double* z, int32_t* err, cudaStream_t s) {
@@ -770,12 +770,20 @@ void launch_ilu_solve32(const RasDev& d, const double* r, float* z, int32_t* err
   launch_ilu_solve_t<float>(d, r, z, err, s);
 }
 
-template <class T, int NCW>
-void solve_attrs(int smem) {
-  cudaFuncSetAttribute(k_ilu_solve<T, T, 1, NCW>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  cudaFuncSetAttribute(k_ilu_solve<T, T, 2, NCW>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  cudaFuncSetAttribute(k_ilu_solve<T, T, 3, NCW>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  cudaFuncSetAttribute(k_ilu_solve<T, T, 4, NCW>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+template <class T, int NCW, int RB>
+void solve_attrs() {
+  const int smem = (int)solve_smem(sizeof(T) == 4, RB);
+  cudaFuncSetAttribute(k_ilu_solve<T, T, 1, NCW, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_ilu_solve<T, T, 2, NCW, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_ilu_solve<T, T, 3, NCW, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_ilu_solve<T, T, 4, NCW, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+template <class T>
+void solve_attrs_all() {
+  solve_attrs<T, 7, SOLVE_RING_FULL>();
+  solve_attrs<T, 3, SOLVE_RING_FULL>();
+  solve_attrs<T, 7, SOLVE_RING_HALF>();
+  solve_attrs<T, 3, SOLVE_RING_HALF>();
 }
 
 void launch_coarse_assemble(const CoarseDev& c, const double* val, const float* val32, cudaStream_t s) {
@@ -929,11 +937,8 @@ void launch_az_sub(const CoarseDev& c, int64_t n, const int64_t* az_ptr, const i
 void coarse_init() {
   cudaFuncSetAttribute(k_band_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   cudaFuncSetAttribute(k_band_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-  const int s64 = (int)solve_smem(false), s32 = (int)solve_smem(true);
-  solve_attrs<double, 7>(s64);
-  solve_attrs<double, 3>(s64);
-  solve_attrs<float, 7>(s32);
-  solve_attrs<float, 3>(s32);
+  solve_attrs_all<double>();
+  solve_attrs_all<float>();
 }
 
 }  // namespace seird

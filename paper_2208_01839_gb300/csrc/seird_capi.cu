@@ -362,6 +362,7 @@ RasDev ras_dev(seird_ctx* ctx) {
   d.wait_polls = ctx->wait_polls;
   d.solve_ch = ctx->ilu_ch;
   d.solve_warps = ctx->ilu_warps;
+  d.solve_ring = ctx->ilu_ring;
   return d;
 }
 
@@ -621,6 +622,11 @@ int norm2(seird_ctx* ctx, const double* x, double* out) {
 // *converged = false (Newton then takes the inexact step).
 bool verbose();
 
+// Largest stage of the solve plans in blocks (a stage has to fit the factor ring).
+int64_t solve_max_stage_blocks(const seird_ctx* ctx) {
+  return std::max<int64_t>(ctx->hs.sp_fwd.max_lev_blocks, ctx->hs.sp_bwd.max_lev_blocks);
+}
+
 // Launch-shape autotuner (options.autotune): times the candidates on the context's own
 // vectors (V[0] holds the first Krylov vector; the Gram-Schmidt candidates run at depth 8
 // with V[1..7] set to copies of it, which GMRES overwrites later) and keeps the fastest.
@@ -680,33 +686,40 @@ int autotune(seird_ctx* ctx) {
   // sums; only the time differs)
   if (ctx->pc_ready) {
     tbest = 1e30f;
-    const int keep_ch = ctx->ilu_ch, keep_w = ctx->ilu_warps;
-    int best_w = 0;
-    for (int nw : {7, 3}) {
-      for (int ch : {1, 2, 3, 4}) {
-        ctx->ilu_ch = ch;
-        ctx->ilu_warps = nw;
-        const RasDev d = ras_dev(ctx);
-        const float t = best_of([&] {
-          if (mixed(ctx)) launch_ilu_solve32(d, ctx->V, reinterpret_cast<float*>(ctx->tune_buf), ctx->err, s);
-          else launch_ilu_solve(d, ctx->V, ctx->tune_buf, ctx->err, s);
-        });
-        if (t < tbest) {
-          tbest = t;
-          best_ch = ch;
-          best_w = nw;
+    const int keep_ch = ctx->ilu_ch, keep_w = ctx->ilu_warps, keep_r = ctx->ilu_ring;
+    int best_w = 0, best_r = 0;
+    const bool half_ok = solve_max_stage_blocks(ctx) <= SOLVE_RING_HALF;
+    for (int ring : {SOLVE_RING_FULL, SOLVE_RING_HALF}) {
+      if (ring == SOLVE_RING_HALF && !half_ok) continue;
+      for (int nw : {7, 3}) {
+        for (int ch : {1, 2, 3, 4}) {
+          ctx->ilu_ch = ch;
+          ctx->ilu_warps = nw;
+          ctx->ilu_ring = ring;
+          const RasDev d = ras_dev(ctx);
+          const float t = best_of([&] {
+            if (mixed(ctx)) launch_ilu_solve32(d, ctx->V, reinterpret_cast<float*>(ctx->tune_buf), ctx->err, s);
+            else launch_ilu_solve(d, ctx->V, ctx->tune_buf, ctx->err, s);
+          });
+          if (t < tbest) {
+            tbest = t;
+            best_ch = ch;
+            best_w = nw;
+            best_r = ring;
+          }
         }
       }
     }
     ctx->ilu_ch = best_ch > 0 ? best_ch : keep_ch;
     ctx->ilu_warps = best_w > 0 ? best_w : keep_w;
+    ctx->ilu_ring = best_r > 0 ? best_r : keep_r;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   CK(cudaGetLastError());
   if (verbose())
-    std::fprintf(stderr, "[seird] autotune: spmv %d threads, gram-schmidt %d CTAs, tile %d, ilu batch %d warps %d\n",
-                 ctx->spmv_tb, ctx->red_grid, ctx->cgs_tile, ctx->ilu_ch, ctx->ilu_warps);
+    std::fprintf(stderr, "[seird] autotune: spmv %d threads, gram-schmidt %d CTAs, tile %d, ilu batch %d warps %d "
+                 "ring %d\n", ctx->spmv_tb, ctx->red_grid, ctx->cgs_tile, ctx->ilu_ch, ctx->ilu_warps, ctx->ilu_ring);
   return SEIRD_OK;
 }
 
@@ -1438,6 +1451,11 @@ static int create_impl(seird_ctx* ctx, const seird_mesh* mesh, const seird_param
   HostSetup& hs = ctx->hs;
   if (o.coarse && 5 * (int64_t)hs.Pc * 8 > 200 * 1024)
     return fail(ctx, SEIRD_EINVAL, "coarse space supports at most 5120 coarse units (options.coarse_group)");
+  // a stage of the subdomain solves must fit the factor ring (only a row with more blocks than
+  // the ring, a node with hundreds of neighbours, can make one larger)
+  if (solve_max_stage_blocks(ctx) > SOLVE_RING_FULL)
+    return fail(ctx, SEIRD_EINVAL, "a subdomain row has more blocks than the solve's shared-memory ring holds (" +
+                                       std::to_string(SOLVE_RING_FULL) + ")");
   if (o.stream) {
     ctx->stream = (cudaStream_t)o.stream;
   } else {
@@ -1792,6 +1810,7 @@ int seird_get_info(const seird_ctx* ctx, seird_info* info) {
   info->cgs_tile = ctx->cgs_tile;
   info->ilu_batch = ctx->ilu_ch;
   info->ilu_warps = ctx->ilu_warps;
+  info->ilu_ring = ctx->ilu_ring;
   return SEIRD_OK;
 }
 
@@ -1879,12 +1898,16 @@ int seird_precond_apply(seird_ctx* ctx, const double* r, double* z, int on_devic
 }
 
 int seird_set_launch_shapes(seird_ctx* ctx, int32_t spmv_threads, int32_t cgs_ctas, int32_t cgs_tile,
-                            int32_t ilu_batch, int32_t ilu_warps) {
+                            int32_t ilu_batch, int32_t ilu_warps, int32_t ilu_ring) {
   if (!ctx) return SEIRD_EINVAL;
   if ((spmv_threads && spmv_threads != 128 && spmv_threads != 256 && spmv_threads != 512) || cgs_ctas < 0 ||
       cgs_ctas > 64 * ctx->sms || (cgs_tile && cgs_tile != 128 && cgs_tile != 256) || ilu_batch < 0 ||
-      ilu_batch > 4 || (ilu_warps && ilu_warps != 3 && ilu_warps != 7))
+      ilu_batch > 4 || (ilu_warps && ilu_warps != 3 && ilu_warps != 7) ||
+      (ilu_ring && ilu_ring != SOLVE_RING_FULL && ilu_ring != SOLVE_RING_HALF))
     return fail(ctx, SEIRD_EINVAL, "set_launch_shapes: a shape outside its candidates");
+  if (ilu_ring == SOLVE_RING_HALF && solve_max_stage_blocks(ctx) > SOLVE_RING_HALF)
+    return fail(ctx, SEIRD_EINVAL, "set_launch_shapes: a solve stage is larger than a one-stage ring");
+  if (ilu_ring) ctx->ilu_ring = ilu_ring;
   if (spmv_threads) ctx->spmv_tb = spmv_threads;
   if (cgs_ctas) ctx->red_grid = cgs_ctas;
   if (cgs_tile) ctx->cgs_tile = cgs_tile;

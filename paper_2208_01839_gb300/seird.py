@@ -92,7 +92,7 @@ class Info(C.Structure):
                 ("subdomain_rows", C.c_int64), ("subdomain_blocks", C.c_int64), ("max_levels", C.c_int32),
                 ("coarse_band", C.c_int32), ("device_bytes", C.c_int64), ("coarse_units", C.c_int32),
                 ("spmv_threads", C.c_int32), ("cgs_ctas", C.c_int32), ("cgs_tile", C.c_int32),
-                ("ilu_batch", C.c_int32), ("ilu_warps", C.c_int32)]
+                ("ilu_batch", C.c_int32), ("ilu_warps", C.c_int32), ("ilu_ring", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -133,7 +133,7 @@ _set_beta_schedule = _sig("seird_set_beta_schedule", C.c_int, [_vp, C.POINTER(Be
 _adjoint = _sig("seird_adjoint", C.c_int, [_vp, C.POINTER(Misfit), C.POINTER(C.c_double), _vp, _vp])
 _set_wait_limit = _sig("seird_set_wait_limit", C.c_int, [_vp, C.c_int32])
 _set_launch_shapes = _sig("seird_set_launch_shapes", C.c_int,
-                          [_vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32])
+                          [_vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32])
 _residual_noalloc = _sig("seird_residual_noalloc", C.c_int,
                          [C.c_int64, C.c_int64, _vp, _vp, _vp, _vp, C.POINTER(Params), _vp, C.c_double, C.c_int32,
                           _vp, _vp, _vp, _vp, _vp])
@@ -415,10 +415,10 @@ class Solver:
                              None if gf is None else gf.ctypes.data))
         return j.value, (g if self.n_samples == 1 else g.reshape(self.n_samples, 10)), gf
 
-    def set_launch_shapes(self, spmv_threads=0, cgs_ctas=0, cgs_tile=0, ilu_batch=0, ilu_warps=0):
+    def set_launch_shapes(self, spmv_threads=0, cgs_ctas=0, cgs_tile=0, ilu_batch=0, ilu_warps=0, ilu_ring=0):
         """Pins launch shapes (seird_set_launch_shapes); 0 keeps a shape as it is."""
         self._check(_set_launch_shapes(self._h, int(spmv_threads), int(cgs_ctas), int(cgs_tile), int(ilu_batch),
-                                       int(ilu_warps)))
+                                       int(ilu_warps), int(ilu_ring)))
 
     def set_wait_limit(self, polls):
         """Polls of each bounded wait in the subdomain solves (seird_set_wait_limit):

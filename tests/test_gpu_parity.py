@@ -467,15 +467,17 @@ def test_autotuned_launch_shapes():
             inf = sv.info()
         assert inf["spmv_threads"] in (128, 256, 512) and inf["cgs_tile"] in (128, 256), inf
         assert inf["cgs_ctas"] > 0 and inf["ilu_batch"] in (1, 2, 3, 4) and inf["ilu_warps"] in (3, 7), inf
+        assert inf["ilu_ring"] in (118, 236), inf
         assert max(rel_l2_per_comp(got, U_ref)) <= (1e-9 if precision == 0 else 1e-6), precision
 
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_subdomain_solve_batches_give_identical_results(precision):
-    """The subdomain solve's dependency-load batch (1-4 blocks) and consumer warps per
-    CTA (7 or 3), both autotuner choices, change only when a row's loads are issued
-    and which warp takes it: every choice forms the same sums in the same order, so
-    the preconditioner apply is bitwise the same for all eight."""
+    """The subdomain solve's dependency-load batch (1-4 blocks), consumer warps per
+    CTA (7 or 3) and factor-ring size (two stages or one), all autotuner choices,
+    change only when a row's loads are issued, which warp takes it and how far the
+    copies run ahead: every choice forms the same sums in the same order, so the
+    preconditioner apply is bitwise the same for all sixteen."""
     wl = WL["irregular3k"]
     r = np.random.default_rng(31).standard_normal(5 * wl.n)
     J = O.jacobian(wl.xy, wl.tri, wl.params, wl.dt, wl.U0, bfield=wl.beta_field)
@@ -489,14 +491,17 @@ def test_subdomain_solve_batches_give_identical_results(precision):
         sv.linear_solve(r.reshape(-1, 5))  # runs the autotuner (the chosen batch is one of the four)
         with pytest.raises(S.SeirdError):
             sv.set_launch_shapes(ilu_batch=5)
-        for nw in (7, 3):
-            for ch in (1, 2, 3, 4):
-                sv.set_launch_shapes(ilu_batch=ch, ilu_warps=nw)
-                inf = sv.info()
-                assert inf["ilu_batch"] == ch and inf["ilu_warps"] == nw
-                outs.append(sv.precond_apply(r.reshape(-1, 5)).ravel())
+        for ring in (236, 118):
+            for nw in (7, 3):
+                for ch in (1, 2, 3, 4):
+                    sv.set_launch_shapes(ilu_batch=ch, ilu_warps=nw, ilu_ring=ring)
+                    inf = sv.info()
+                    assert inf["ilu_batch"] == ch and inf["ilu_warps"] == nw and inf["ilu_ring"] == ring
+                    outs.append(sv.precond_apply(r.reshape(-1, 5)).ravel())
         with pytest.raises(S.SeirdError):
             sv.set_launch_shapes(ilu_warps=5)
+        with pytest.raises(S.SeirdError):
+            sv.set_launch_shapes(ilu_ring=100)
     for k in range(1, len(outs)):
         assert np.array_equal(outs[0], outs[k]), k
     tol = 1e-10 if precision == 0 else 1e-4
