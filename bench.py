@@ -47,6 +47,8 @@ FALLBACK_HBM_GBS = 6800.0
 # next capture.
 NCU_TRAFFIC = {
     ("spmv", "fp64"): (307.414e6, 1400635, "nnzb"),  # k_bsr_spmv<double>, 1.4M blocks
+    ("ilu_solve", "fp64"): (372.44e6, 1577927, "subdomain_blocks"),  # k_ilu_solve<double>, 64 subdomains
+    ("ilu_solve", "mixed"): (202.53e6, 1577927, "subdomain_blocks"),  # k_ilu_solve<float>, 64 subdomains
 }
 
 # kernel classes with one kernel launch per timed call

@@ -35,7 +35,12 @@ def test_dominant_kernel_and_achieved_bandwidth():
     assert roof["algorithmic_bytes_per_launch"] == pytest.approx(3.5e9)
     assert roof["achieved"] == pytest.approx(3.5e9 / 1.7e-3 / 1e9)
     assert roof["frac"] == pytest.approx(roof["achieved"] / roof["peak"])
-    assert roof["traffic"] is None  # no capture of this kernel since it last changed
+    b_small, units_small, key = bench.NCU_TRAFFIC[("ilu_solve", "fp64")]
+    assert roof["traffic"] == pytest.approx(b_small * res["info"][key] / units_small)
+    roof32, _, _, _, _ = bench.roofline(_S, res, "mixed")
+    b32, u32, k32 = bench.NCU_TRAFFIC[("ilu_solve", "mixed")]
+    assert roof32["traffic"] == pytest.approx(b32 * res["info"][k32] / u32)
+    assert roof32["fp64_alu"] is None  # the FP64 rate applies to the FP64 path only
     assert roof["fp64_alu"]["fma_per_launch"] == 25 * res["info"]["subdomain_blocks"]
     assert spmv["gbs"] == pytest.approx(3.0e9 / 0.58e-3 / 1e9)
 
