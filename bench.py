@@ -70,8 +70,9 @@ def parse(argv=None):
     ap.add_argument("--forcing", choices=["fixed", "ew"], default="ew")
     ap.add_argument("--pc-lag", type=int, default=20)
     ap.add_argument("--pc-keep", type=int, default=3, help="steps a preconditioner may be carried over")
-    ap.add_argument("--predictor", type=int, choices=[0, 1], default=1,
-                    help="Newton's first iterate: 0 u^n, 1 the extrapolation 2 u^n - u^{n-1}")
+    ap.add_argument("--predictor", type=int, choices=[0, 1, 2, 3, 4, 5, 6], default=5,
+                    help="Newton's first iterate: 0 u^n, p = 1-6 the degree-p extrapolation through u^n and the "
+                         "p previous states")
     ap.add_argument("--coarse", type=int, choices=[1, 2, 3], default=2,
                     help="1 additive coarse correction, 2 the paper's multiplicative two-grid (Eq. RAS_2L), "
                          "3 coarse correction then RAS")
@@ -355,6 +356,10 @@ def measure(S, wl, args, stream, precision, subdomains, world, local, e2e=True):
     sv.set_state(torch.tensor(wl.U0, device="cuda"))
     for _ in range(args.warmup):
         sv.step()
+    if e2e:  # where the timed steps start: the e2e loop replays the same steps from here
+        hstart = torch.empty((wl.n, 5), dtype=torch.float64, pin_memory=True)
+        sv.get_state(hstart.numpy())
+        t_start = sv.t
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -379,14 +384,18 @@ def measure(S, wl, args, stream, precision, subdomains, world, local, e2e=True):
     out = {"value": aggregate_value(dof, args.steps, ms * 1e-3, world), "ms_per_step": ms / args.steps,
            "launches": launches, "create_s": t_create, "clocks": clk.summary(), "info": info, "stats": stats}
     if e2e:
-        hbuf = torch.empty((wl.n, 5), dtype=torch.float64, pin_memory=True)
-        sv.get_state(hbuf.numpy())
+        # The same K steps again, from the state the timed steps started from, through the C ABI with host
+        # buffers: every step copies its input in and its result out.  The first set_state is a new state
+        # (the step history is dropped, so that step runs without the predictor); later ones hand back the
+        # state the context holds, which keeps the history.
+        hbuf = hstart
+        sv.t = t_start
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            sv.set_state(hbuf.numpy())
+            sv.set_state(hbuf.numpy(), t=sv.t)  # the step's input, at the context's time
             sv.step()
             sv.get_state(hbuf.numpy())
         torch.cuda.synchronize()

@@ -141,9 +141,13 @@ typedef struct {
                              (Z's column (g, c) = indicator of the nodes the group owns in compartment c).
                              0 chooses 1 unless 5 x units would exceed 8192 or units 1160 (the sizes of
                              the explicit coarse inverse), else the smallest group that fits (0) */
-  int32_t predictor;      /* Newton's first iterate: 0 u^n (Section 2.2); 1 the linear extrapolation
-                             2 u^n - u^{n-1} when the previous step is known and it lowers ||F||.
-                             The stopping test stays relative to ||F(u^n)|| either way (0) */
+  int32_t predictor;      /* Newton's first iterate: 0 u^n (Section 2.2); p = 1-6 the polynomial
+                             extrapolation of degree p (or lower while fewer earlier steps are known)
+                             through u^n and the p previous states, one step ahead:
+                             sum_k (-1)^k C(p+1, k+1) u^{n-k}, e.g. 2 u^n - u^{n-1} (p = 1),
+                             4 u^n - 6 u^{n-1} + 4 u^{n-2} - u^{n-3} (p = 3); used when it is
+                             admissible and lowers ||F||.  The stopping test stays relative to
+                             ||F(u^n)|| either way.  Each degree keeps one more state (5n doubles) (0) */
   int32_t autotune;       /* 1: at the first linear solve, time the candidate launch shapes of the SpMV
                              (128/256/512 threads per CTA), of the Gram-Schmidt kernels (2/3/4/6 CTAs
                              per SM, 128- or 256-entry tiles) and of the subdomain solves (1-4 blocks of
@@ -251,7 +255,10 @@ void seird_destroy(seird_ctx* ctx);
  * when ctx is NULL).  Valid until the next call on the context. */
 const char* seird_last_error(const seird_ctx* ctx);
 
-/* Sets the state u^n (caller numbering, [n_nodes][5] float64) and time t. */
+/* Sets the state u^n (caller numbering, [n_nodes][5] float64) and time t.  A new
+ * state drops the step history the predictor and the residual reuse; setting the
+ * state the context already holds, bit for bit and at its own time (a caller that
+ * passes each step's result through its own memory), keeps it. */
 int seird_set_state(seird_ctx* ctx, const double* u, int on_device, double t);
 
 /* Copies the current state out (caller numbering) and its time (t may be NULL). */

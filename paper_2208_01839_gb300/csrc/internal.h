@@ -22,6 +22,7 @@ enum : int {
 };
 
 constexpr int MAX_RESTART = 64;
+constexpr int MAX_PREDICTOR = 6;  // highest degree of the Newton predictor's extrapolation
 // coarse problems up to this many unknowns (5 x subdomains) keep an explicit
 // inverse (applied as a GEMV); larger ones are solved through the band factors
 constexpr int64_t DENSE_COARSE_MAX = 8192;
@@ -167,7 +168,12 @@ struct seird_ctx {
   // state and Newton vectors [n][5]
   double* U = nullptr;
   double* Un = nullptr;
-  double* Uprev = nullptr;  // u^{n-1} for the predictor (options.predictor)
+  // earlier states for the predictor (options.predictor = p): Uhist[k] holds u^{n-1-k}, k < p, the
+  // buffers rotating as steps complete; Uprev aliases Uhist[0] (u^{n-1})
+  double* Uhist[seird::MAX_PREDICTOR] = {};
+  int n_hist = 0;
+  double* Uprev = nullptr;
+  int hist_depth = 0;        // earlier states held (1: u^{n-1} ... p); valid while have_prev
   double* Flast = nullptr;  // F(u^n; u^{n-1}), the previous step's last residual
   bool have_prev = false;
   double* F = nullptr;
@@ -189,6 +195,8 @@ struct seird_ctx {
   double* h_scal = nullptr; // pinned host mirror
   int32_t* err = nullptr;   // device error flags
   int32_t* h_err = nullptr; // pinned
+  int* dflag = nullptr;      // device flag of seird_set_state's comparison with the held state
+  int* h_flag = nullptr;     // pinned
   int red_grid = 0;
   // RAS
   int32_t* sd_row0 = nullptr;

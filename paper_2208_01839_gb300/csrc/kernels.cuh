@@ -189,6 +189,8 @@ void launch_multi_axpy32(int64_t len, int nv, const float* Zs, int64_t ld, const
                          cudaStream_t s);
 void launch_f32_to_f64(int64_t n, const float* src, double* dst, cudaStream_t s);
 void launch_add32(int64_t len, const float* u, float* z, cudaStream_t s);
+// *flag = 1 if a and b differ in any bit pattern, else 0 (flag is cleared first)
+void launch_differs(int64_t len, const double* a, const double* b, int* flag, cudaStream_t s);
 
 struct CoarseDev {
   int32_t P, band;

@@ -89,6 +89,14 @@ __global__ void k_bsr_transpose(int64_t nnzb, const int32_t* __restrict__ tpos, 
   }
 }
 
+// *flag |= 1 when a and b differ in any bit pattern (so NaNs and signed zeros count as they are stored)
+__global__ void k_differs(int64_t len, const double* __restrict__ a, const double* __restrict__ b, int* flag) {
+  bool d = false;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
+    d |= __double_as_longlong(a[i]) != __double_as_longlong(b[i]);
+  if (__any_sync(0xffffffffu, d) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+}
+
 __global__ void k_add32(int64_t len, const float* __restrict__ u, float* __restrict__ z) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
     z[i] += u[i];
@@ -406,6 +414,12 @@ void launch_multi_axpy32(int64_t len, int nv, const float* Zs, int64_t ld, const
 
 void launch_bsr_transpose(int64_t nnzb, const int32_t* tpos, const double* val, double* valT, cudaStream_t s) {
   k_bsr_transpose<<<grid_for(25 * nnzb), 256, 0, s>>>(nnzb, tpos, val, valT);
+  count_launch();
+}
+
+void launch_differs(int64_t len, const double* a, const double* b, int* flag, cudaStream_t s) {
+  cudaMemsetAsync(flag, 0, sizeof(int), s);
+  k_differs<<<grid_for(len), 256, 0, s>>>(len, a, b, flag);
   count_launch();
 }
 

@@ -1070,10 +1070,21 @@ int newton_step(seird_ctx* ctx, seird_stats* st) {
   if (rc) return rc;
   const double f0 = f;  // the stopping test is relative to ||F(u^n)||
   S.res0 = f0;
-  if (ctx->opt.predictor == 1 && ctx->have_prev && ctx->Uprev) {
-    // first iterate 2 u^n - u^{n-1}, kept only if it is admissible and lowers ||F||
+  if (ctx->opt.predictor >= 1 && ctx->have_prev && ctx->Uprev) {
+    // first iterate: the polynomial through u^n and the earlier states held (up to
+    // options.predictor of them) evaluated one step ahead: sum_k (-1)^k C(p+1, k+1) u^{n-k},
+    // e.g. 2 u^n - u^{n-1} or 4 u^n - 6 u^{n-1} + 4 u^{n-2} - u^{n-3}; kept only if it is
+    // admissible and lowers ||F||
     t0 = clk::now();
-    launch_axpby(len, 2.0, ctx->Un, -1.0, ctx->Uprev, ctx->Ut, s);
+    const int deg = std::max(1, std::min<int>(ctx->opt.predictor, ctx->hist_depth));
+    // coefficient of u^{n-k} in the degree-deg extrapolation: (-1)^k C(deg+1, k+1)
+    auto coef = [deg](int k) {
+      double c = 1.0;
+      for (int i = 0; i < k + 1; ++i) c = c * (deg + 1 - i) / (i + 1);
+      return (k % 2 ? -1.0 : 1.0) * c;
+    };
+    launch_axpby(len, coef(0), ctx->Un, coef(1), ctx->Uhist[0], ctx->Ut, s);
+    for (int k = 2; k <= deg; ++k) launch_axpby(len, 1.0, ctx->Ut, coef(k), ctx->Uhist[k - 1], ctx->Ut, s);
     double fp = 0.0;
     rc = residual(ctx, ctx->Ut, ctx->Un, ctx->Ft, &fp);
     S.ms_assemble += ms_since(t0);
@@ -1177,6 +1188,15 @@ int newton_step(seird_ctx* ctx, seird_stats* st) {
   ctx->t += ctx->opt.dt;
   ctx->pc_age_steps++;
   if (ctx->Uprev) {
+    // the held states move one step back by rotating the buffers (u^{n-k} -> u^{n-k-1}, the oldest
+    // buffer is reused for u^n -> u^{n-1}): one copy per step whatever the degree
+    const int depth = ctx->have_prev ? ctx->hist_depth : 0;
+    const int nh = ctx->n_hist;
+    double* recycled = ctx->Uhist[nh - 1];
+    for (int k = nh - 1; k > 0; --k) ctx->Uhist[k] = ctx->Uhist[k - 1];
+    ctx->Uhist[0] = recycled;
+    ctx->Uprev = recycled;
+    ctx->hist_depth = std::min(depth + 1, std::max(1, (int)ctx->opt.predictor));
     CK(cudaMemcpyAsync(ctx->Uprev, ctx->Un, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(ctx->Flast, ctx->F, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
     ctx->have_prev = true;
@@ -1430,6 +1450,7 @@ void seird_destroy(seird_ctx* ctx) {
   for (void* p : ctx->allocations) cudaFree(p);
   if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
   if (ctx->h_cyc) cudaFreeHost(ctx->h_cyc);
+  if (ctx->h_flag) cudaFreeHost(ctx->h_flag);
   if (ctx->h_err) cudaFreeHost(ctx->h_err);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
@@ -1442,7 +1463,7 @@ static int create_impl(seird_ctx* ctx, const seird_mesh* mesh, const seird_param
       (o.quadrature != 0 && o.quadrature != 1) || (o.precision != 0 && o.precision != 1) ||
       (o.gmres_forcing != 0 && o.gmres_forcing != 1) || (o.nonlinear != 0 && o.nonlinear != 1) ||
       (o.gmres_one_pass != 0 && o.gmres_one_pass != 1) || o.pc_keep_steps < 0 ||
-      (o.predictor != 0 && o.predictor != 1) || (o.autotune != 0 && o.autotune != 1) || (o.graph != 0 && o.graph != 1) ||
+      (o.predictor < 0 || o.predictor > seird::MAX_PREDICTOR) || (o.autotune != 0 && o.autotune != 1) || (o.graph != 0 && o.graph != 1) ||
       !(o.picard_tol >= 0))
     return fail(ctx, SEIRD_EINVAL, "invalid option value");
   std::string err;
@@ -1499,8 +1520,10 @@ static int create_impl(seird_ctx* ctx, const seird_mesh* mesh, const seird_param
   TRY(dalloc(ctx, &ctx->rec, (size_t)REC * m));
   double** vecs[] = {&ctx->U, &ctx->Un, &ctx->F, &ctx->Ft, &ctx->dU, &ctx->Ut, &ctx->stage, &ctx->stage2, &ctx->w};
   for (double** v : vecs) TRY(dalloc(ctx, v, len));
-  if (o.predictor == 1) {
-    TRY(dalloc(ctx, &ctx->Uprev, len));
+  if (o.predictor >= 1) {
+    ctx->n_hist = o.predictor;
+    for (int k = 0; k < ctx->n_hist; ++k) TRY(dalloc(ctx, &ctx->Uhist[k], len));
+    ctx->Uprev = ctx->Uhist[0];
     TRY(dalloc(ctx, &ctx->Flast, len));
   }
   const bool mix = o.precision == 1;
@@ -1528,6 +1551,8 @@ static int create_impl(seird_ctx* ctx, const seird_mesh* mesh, const seird_param
   }
   CK(cudaMallocHost((void**)&ctx->h_err, sizeof(int32_t)));
   *ctx->h_err = 0;
+  TRY(dalloc(ctx, &ctx->dflag, 1));
+  CK(cudaMallocHost((void**)&ctx->h_flag, sizeof(int)));
   // RAS
   TRY(upload(ctx, &ctx->sd_row0, hs.sd_row0));
   TRY(upload(ctx, &ctx->sd_node, hs.sd_node));
@@ -1708,6 +1733,17 @@ int seird_create_ensemble(const seird_mesh* mesh, int32_t n_samples, const seird
 int seird_set_state(seird_ctx* ctx, const double* u, int on_device, double t) {
   return host_guard(ctx, [&]() -> int {
     if (!ctx || !u) return fail(ctx, SEIRD_EINVAL, "NULL argument");
+    if (ctx->have_prev && t == ctx->t) {
+      // the state the context already holds, at its own time (a caller that round-trips the
+      // state through its memory between steps): the step history stays valid
+      TRY(to_internal(ctx, u, on_device, ctx->Ut));
+      launch_differs(vlen(ctx), ctx->Ut, ctx->U, ctx->dflag, ctx->stream);
+      CK(cudaMemcpyAsync(ctx->h_flag, ctx->dflag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaMemcpyAsync(ctx->U, ctx->Ut, sizeof(double) * vlen(ctx), cudaMemcpyDeviceToDevice, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      ctx->have_prev = *ctx->h_flag == 0;
+      return SEIRD_OK;
+    }
     TRY(to_internal(ctx, u, on_device, ctx->U));
     ctx->t = t;
     ctx->have_prev = false;
