@@ -40,15 +40,16 @@ UNIT = "DOF·steps/s"
 FALLBACK_HBM_GBS = 6800.0
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from the committed ncu
-# capture of each kernel class on the 200k-node case of the same generator, as
-# (bytes per launch there, units processed there, seird_get_info key of those
-# units); scaled to a full launch by the units it processes (traffic grows in
-# proportion).  Entries are removed when the kernel changes and restored by the
-# next capture.
+# capture of each kernel class, as (bytes per launch there, units processed there,
+# seird_get_info key of those units); scaled to a launch by the units it processes
+# (traffic grows in proportion).  The SpMV was captured on the 200k-node case of the
+# same generator, the subdomain solve at full size (18.4M nodes, 4096 subdomains,
+# the autotuned variants).  Entries are removed when the kernel changes and restored
+# by the next capture.
 NCU_TRAFFIC = {
     ("spmv", "fp64"): (307.414e6, 1400635, "nnzb"),  # k_bsr_spmv<double>, 1.4M blocks
-    ("ilu_solve", "fp64"): (372.44e6, 1577927, "subdomain_blocks"),  # k_ilu_solve<double>, 64 subdomains
-    ("ilu_solve", "mixed"): (202.53e6, 1577927, "subdomain_blocks"),  # k_ilu_solve<float>, 64 subdomains
+    ("ilu_solve", "fp64"): (35.25e9, 143961429, "subdomain_blocks"),  # k_ilu_solve<double, double, 2, 3, 118>
+    ("ilu_solve", "mixed"): (19.54e9, 143961429, "subdomain_blocks"),  # k_ilu_solve<float, float, 2, 3, 236>
 }
 
 # kernel classes with one kernel launch per timed call

@@ -164,6 +164,10 @@ typedef struct {
                              per iteration.  Same kernels and arithmetic as 0 (results identical).
                              Needs a driver with conditional graph nodes (CUDA 12.4+); ignored while
                              timing = 1 and in the adjoint's transposed solves (0) */
+  double forcing_first;   /* gmres_forcing = 1: the forcing term of each step's first Newton iteration
+                             (0 means 0.1, the usual Eisenstat-Walker start).  A Newton iteration that
+                             starts close to the root (a good predictor) can afford a smaller one, so
+                             that the next iteration already reaches the Newton target (0) */
 } seird_options;
 
 /* Kernel classes of seird_stats.kernel_ms / kernel_calls. */

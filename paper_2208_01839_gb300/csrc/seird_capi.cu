@@ -1126,7 +1126,8 @@ int newton_step(seird_ctx* ctx, seird_stats* st) {
     if (ctx->opt.gmres_forcing == 1) {
       // Eisenstat-Walker choice 2 with the usual safeguard, capped at 0.5, and
       // no tighter than what brings ||F|| to the Newton target
-      double e = its == 0 ? 0.1 : 0.9 * (f / f_prev) * (f / f_prev);
+      const double first = ctx->opt.forcing_first > 0.0 ? ctx->opt.forcing_first : 0.1;
+      double e = its == 0 ? first : 0.9 * (f / f_prev) * (f / f_prev);
       if (its > 0 && 0.9 * eta * eta > 0.1) e = std::max(e, 0.9 * eta * eta);
       // near the Newton target, solve just far enough to finish in this iteration
       const double tgt = (ctx->opt.newton_rtol * f0 + ctx->opt.newton_atol) / f;
@@ -1463,7 +1464,7 @@ static int create_impl(seird_ctx* ctx, const seird_mesh* mesh, const seird_param
       (o.quadrature != 0 && o.quadrature != 1) || (o.precision != 0 && o.precision != 1) ||
       (o.gmres_forcing != 0 && o.gmres_forcing != 1) || (o.nonlinear != 0 && o.nonlinear != 1) ||
       (o.gmres_one_pass != 0 && o.gmres_one_pass != 1) || o.pc_keep_steps < 0 ||
-      (o.predictor < 0 || o.predictor > seird::MAX_PREDICTOR) || (o.autotune != 0 && o.autotune != 1) || (o.graph != 0 && o.graph != 1) ||
+      (o.predictor < 0 || o.predictor > seird::MAX_PREDICTOR) || !(o.forcing_first >= 0.0 && o.forcing_first < 1.0) || (o.autotune != 0 && o.autotune != 1) || (o.graph != 0 && o.graph != 1) ||
       !(o.picard_tol >= 0))
     return fail(ctx, SEIRD_EINVAL, "invalid option value");
   std::string err;
