@@ -279,9 +279,11 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback (profiling recipe)"
 
 
-# GB300's FP64 rate as measured by --fp64-probe on this machine (an FMA loop: 1.234 TFLOP/s at
-# 2070 MHz; cuBLAS DGEMM reaches 1.10), against the nominal 1.25 TFLOP/s
-FP64_PEAK_TFLOPS = 1.234
+# GB300's FP64 peak from its unit counts and clock: 152 SMs x 2 FP64 FMA per clock x 2 flop x
+# 2.070 GHz = 1.259 TFLOP/s (the part's nominal 1.25).  --fp64-probe measures 1.234 TFLOP/s with
+# an FMA loop at 2070 MHz (98%) and 1.10 with cuBLAS DGEMM.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+FP64_PEAK_KIND = "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.070 GHz (an FMA loop measures 1.234)"
 
 
 def algorithmic_fma(cls, info):
@@ -302,8 +304,13 @@ def class_sums(S, stats):
 
 
 def roofline(S, res, precision):
-    """Dominant single-kernel class against the HBM peak, the SpMV, and the whole step:
-    achieved = the library's algorithmic bytes / CUDA-event time on the context's stream."""
+    """Dominant single-kernel class against its roofline, the SpMV, and the whole step.
+
+    achieved = the library's algorithmic bytes (or, for FP64 work, 2 x its FMAs) / CUDA-event time on
+    the context's stream.  The bound is whichever of the HBM time (bytes / HBM peak) and the FP64
+    time (FMAs / FP64 peak) is longer: an FP64 5x5 block product moves 204 bytes per 25 FMAs, more
+    work per byte than GB300's FP64 pipe keeps up with at full bandwidth, so the FP64 SpMV and
+    subdomain solve are bound by the pipe ("alu"), their FP32 forms by HBM."""
     kms, kcalls, kbytes = class_sums(S, res["stats"])
     info = res["info"]
     peak, peak_kind = peaks()
@@ -324,7 +331,9 @@ def roofline(S, res, precision):
     if fma is not None and avg_ms > 0:
         tf = 2.0 * fma / (avg_ms * 1e-3) / 1e12
         alu = {"achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tf / FP64_PEAK_TFLOPS,
-               "peak_kind": "measured FP64 FMA loop (bench.py --fp64-probe)", "fma_per_launch": fma}
+               "peak_kind": FP64_PEAK_KIND, "fma_per_launch": fma}
+    sp_fma = algorithmic_fma("spmv", info) if precision == "fp64" else None
+    sp_alu = (2.0 * sp_fma / (sp_ms * 1e-3) / 1e12) / FP64_PEAK_TFLOPS if sp_fma and sp_ms > 0 else None
     step_s = res["ms_per_step"] * len(res["stats"]) * 1e-3
     total = sum(kbytes.values())
     step = {"bytes_per_step": total / max(len(res["stats"]), 1), "achieved": total / step_s / 1e9 if step_s else None,
@@ -332,12 +341,17 @@ def roofline(S, res, precision):
             "peak_kind": peak_kind,
             "bytes_by_class": {k: v / max(len(res["stats"]), 1) for k, v in kbytes.items()},
             "note": "sum of the library's algorithmic bytes over the timed steps / their device time"}
-    return ({"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-             "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
-             "algorithmic_bytes_per_launch": ab, "avg_launch_ms": avg_ms, "launches": kcalls[dom],
-             "fp64_alu": alu},
-            {"gbs": sp_gbs, "frac_of_hbm": (sp_gbs / peak) if sp_gbs else None, "avg_launch_ms": sp_ms,
-             "launches": kcalls["spmv"], "algorithmic_bytes": sp_ab},
+    hbm = {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind}
+    common = {"kernel": dom, "traffic": traffic, "algorithmic_bytes_per_launch": ab, "avg_launch_ms": avg_ms,
+              "launches": kcalls[dom]}
+    if alu is not None and 2.0 * fma / (FP64_PEAK_TFLOPS * 1e12) > ab / (peak * 1e9):
+        roof = dict({"bound": "alu"}, **{k: alu[k] for k in ("achieved", "peak", "unit", "frac", "peak_kind")},
+                    **common, fma_per_launch=fma, hbm=hbm)
+    else:
+        roof = dict({"bound": "hbm"}, **hbm, **common, fp64_alu=alu)
+    return (roof,
+            {"gbs": sp_gbs, "frac_of_hbm": (sp_gbs / peak) if sp_gbs else None, "frac_of_fp64": sp_alu,
+             "avg_launch_ms": sp_ms, "launches": kcalls["spmv"], "algorithmic_bytes": sp_ab},
             step, kms, kcalls)
 
 

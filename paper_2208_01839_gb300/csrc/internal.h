@@ -31,6 +31,12 @@ constexpr int32_t COARSE_BLOCKCOL_MAX = 1160;
 // blocks per ILU-solve level buffer (two buffers of 24 KB in FP64 at 26 doubles per block)
 constexpr int32_t SOLVE_BUF_BLOCKS = SOLVE_BUF_BLOCKS_DEV;
 constexpr int32_t SOLVE_BUF_ROWS = SOLVE_BUF_ROWS_DEV;
+// a stage of the subdomain solve costs about as much as this many blocks (its barrier and
+// the latency of its first dependency loads), for the launch order of the subdomain CTAs
+constexpr int64_t SOLVE_STAGE_WEIGHT = 40;
+// solve work of subdomain q that orders the subdomain CTAs: blocks + SOLVE_STAGE_WEIGHT x stages
+struct HostSetup;
+int64_t solve_work(const HostSetup& hs, int32_t q);
 
 // Host-side products of the setup phase (all indices in the internal numbering,
 // where nodes are sorted by (subdomain, caller index)).
@@ -83,6 +89,10 @@ struct HostSetup {
                                   // backward (forward position, first block, blocks, node if owned else -1)
     int32_t max_lev_blocks = 0;
   } sp_fwd, sp_bwd;
+  // launch order of the per-subdomain kernels (factor and solve): subdomains by
+  // descending solve work (blocks + SOLVE_STAGE_WEIGHT x stages, both sweeps), ties in
+  // index order, so the longest start first and the grid's tail holds the short ones
+  std::vector<int32_t> sd_sched;    // [P]
   // coarse space: subdomain p sits at block row cpos[p] of the banded coarse matrix
   // coarse units: groups of cG consecutive subdomains (cG = 1 unless the coarse matrix would be too
   // large for its explicit inverse); unit u owns the internal nodes [cunit_ptr[u], cunit_ptr[u+1])
@@ -215,6 +225,7 @@ struct seird_ctx {
   int32_t* sd_bwd_lev0 = nullptr;
   int32_t* own_ptr = nullptr;
   int32_t* owner = nullptr;
+  int32_t* sd_sched = nullptr;
   double* fval = nullptr;   // [NLB][25] factor blocks
   float* fval32 = nullptr;
   double* dinv = nullptr;   // [NL][25] inverted U diagonal blocks

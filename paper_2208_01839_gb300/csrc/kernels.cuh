@@ -136,6 +136,7 @@ struct SolvePlanDev {
 };
 struct RasDev {
   int32_t P;
+  const int32_t* sd_sched;  // CTA b of a per-subdomain kernel works on subdomain sd_sched[b]
   const int32_t* sd_row0;
   const int32_t* sd_node;
   const int64_t* l_row_ptr;

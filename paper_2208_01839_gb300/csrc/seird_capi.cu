@@ -319,6 +319,7 @@ int jacobian(seird_ctx* ctx, const double* U, bool picard = false) {
 RasDev ras_dev(seird_ctx* ctx) {
   RasDev d;
   d.P = ctx->hs.P;
+  d.sd_sched = ctx->sd_sched;
   d.sd_row0 = ctx->sd_row0;
   d.sd_node = ctx->sd_node;
   d.l_row_ptr = ctx->l_row_ptr;
@@ -1571,6 +1572,7 @@ static int create_impl(seird_ctx* ctx, const seird_mesh* mesh, const seird_param
   TRY(upload(ctx, &ctx->sd_bwd_lev0, hs.sd_bwd_lev0));
   TRY(upload(ctx, &ctx->own_ptr, hs.own_ptr));
   TRY(upload(ctx, &ctx->owner, hs.owner));
+  TRY(upload(ctx, &ctx->sd_sched, hs.sd_sched));
   const int64_t NL = (int64_t)hs.sd_node.size();
   const int64_t NLB = (int64_t)hs.l_col.size();
   for (int dir = 0; dir < 2; ++dir) {

@@ -617,6 +617,18 @@ int build_setup(const seird_mesh* mesh, const seird_options* opt, HostSetup& hs,
         sp.max_lev_blocks = std::max<int32_t>(sp.max_lev_blocks, (int32_t)(sp.levblk[v + 1] - sp.levblk[v]));
   }
 
+  // ---- launch order of the subdomain CTAs ------------------------------------
+  // Subdomains differ in size (2k-8k nodes at 4096 subdomains) and several waves of
+  // CTAs share the SMs; launched longest first (a list schedule), the short ones fill
+  // the tail instead of a long one starting last.
+  {
+    std::vector<int64_t> w(P);
+    for (int32_t q = 0; q < P; ++q) w[q] = solve_work(hs, q);
+    hs.sd_sched.resize(P);
+    for (int32_t q = 0; q < P; ++q) hs.sd_sched[q] = q;
+    std::stable_sort(hs.sd_sched.begin(), hs.sd_sched.end(), [&](int32_t a, int32_t b) { return w[a] > w[b]; });
+  }
+
   // ---- coarse units: groups of consecutive subdomains -----------------------
   // The bisection numbers spatial neighbours consecutively, so a group of G
   // consecutive subdomains is a compact region.  G = options.coarse_group, or
@@ -712,6 +724,16 @@ int build_setup(const seird_mesh* mesh, const seird_options* opt, HostSetup& hs,
     }
   }
   return SEIRD_OK;
+}
+
+int64_t solve_work(const HostSetup& hs, int32_t q) {
+  int64_t w = 0;
+  for (int dir = 0; dir < 2; ++dir) {
+    const HostSetup::SolvePlan& sp = dir == 0 ? hs.sp_fwd : hs.sp_bwd;
+    const int32_t v0 = sp.sd_lev0[q], v1 = sp.sd_lev0[q + 1] - 1;
+    w += sp.levblk[v1] - sp.levblk[v0] + SOLVE_STAGE_WEIGHT * (int64_t)(v1 - v0);
+  }
+  return w;
 }
 
 // Invariants of a set-up that the kernels rely on without checking them (see
@@ -841,6 +863,17 @@ int64_t check_setup(const HostSetup& hs, std::string& first) {
         }
       }
       if (dir == 1) fail(owned == hs.own_ptr[q + 1] - hs.own_ptr[q], "owned rows written once");
+    }
+  }
+  // launch order: every subdomain once (each CTA writes only the nodes its subdomain
+  // owns), longest first
+  fail((int32_t)hs.sd_sched.size() == P, "launch order size");
+  if (!bad) {
+    std::vector<int32_t> hit(P, 0);
+    for (int32_t b = 0; b < P; ++b) {
+      const int32_t q = hs.sd_sched[b];
+      fail(q >= 0 && q < P && hit[q]++ == 0, "launch order is not a permutation");
+      if (!bad && b > 0) fail(solve_work(hs, hs.sd_sched[b - 1]) >= solve_work(hs, q), "launch order not longest first");
     }
   }
   return bad;
