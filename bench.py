@@ -48,8 +48,8 @@ FALLBACK_HBM_GBS = 6800.0
 # by the next capture.
 NCU_TRAFFIC = {
     ("spmv", "fp64"): (307.414e6, 1400635, "nnzb"),  # k_bsr_spmv<double>, 1.4M blocks
-    ("ilu_solve", "fp64"): (35.25e9, 143961429, "subdomain_blocks"),  # k_ilu_solve<double, double, 2, 3, 118>
-    ("ilu_solve", "mixed"): (19.54e9, 143961429, "subdomain_blocks"),  # k_ilu_solve<float, float, 2, 3, 236>
+    ("ilu_solve", "fp64"): (35.42e9, 143961429, "subdomain_blocks"),  # k_ilu_solve<double, double, 2, 3, 118>
+    ("ilu_solve", "mixed"): (19.62e9, 143961429, "subdomain_blocks"),  # k_ilu_solve<float, float, 2, 3, 236>
 }
 
 # kernel classes with one kernel launch per timed call
