@@ -1,4 +1,5 @@
-"""Full-size workloads in the benchmark's launch configuration.
+"""Full-size workloads in the benchmark's launch configuration (bench.py's solver
+options and autotuner, its workload sizes).
 
 The whole-mesh oracle cannot run at these sizes, so the GPU states are checked
 through quantities the oracle can compute one by one and through properties
@@ -8,9 +9,11 @@ that hold at any size:
   * total population is conserved (alpha = mu = 0, no-flux boundary, Section 2.1);
   * d^{n+1} = d^n + dt gamma_D i^{n+1} node by node (degree-5 rule, Eq. seird5);
   * every compartment stays nonnegative;
-  * (config 3) the mixed-precision path agrees with the FP64 path to 1e-6
-    relative L2 per compartment at the 1e-8 Newton tolerance.
+  * the mixed-precision path agrees with the FP64 path to 1e-6 relative L2 per
+    compartment at the 1e-8 Newton tolerance (config 3 and the paper-scale mesh).
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -28,8 +31,14 @@ from paper_2208_01839_gb300 import build as _b  # noqa: E402
 _b.build()
 from paper_2208_01839_gb300 import seird as S  # noqa: E402
 
-BENCH_OPTS = dict(overlap=2, coarse=1, newton_rtol=1e-8, gmres_rtol=1e-5, gmres_restart=30, gmres_maxit=200,
-                  gmres_forcing=1, pc_lag=20)
+import bench  # noqa: E402
+
+_ARGS = bench.parse([])
+
+
+def bench_opts(precision, subdomains):
+    """The options bench.py times: solver_options of its default arguments, autotuner on."""
+    return dict(bench.solver_options(_ARGS, "mixed" if precision else "fp64", subdomains), autotune=1)
 
 
 def _node_mass(xy, tri):
@@ -39,7 +48,7 @@ def _node_mass(xy, tri):
     return w
 
 
-def _check_step_properties(wl, Un, U, n_samples=300, seed=0):
+def _check_step_properties(wl, Un, U, n_samples=300, seed=0, res_final=None):
     rng = np.random.default_rng(seed)
     # sampled residual from the oracle, near the infection seeds and anywhere
     hot = np.argsort(-Un[:, 2])[:n_samples // 2]
@@ -52,7 +61,12 @@ def _check_step_properties(wl, Un, U, n_samples=300, seed=0):
     assert np.abs(F).max() <= 1e-7 * np.abs(Ms).max(), (np.abs(F).max(), np.abs(Ms).max())
     w = _node_mass(wl.xy, wl.tri)
     tot0, tot1 = w @ Un.sum(axis=1), w @ U.sum(axis=1)
-    assert abs(tot1 - tot0) <= 1e-8 * tot0
+    if res_final is None:
+        assert abs(tot1 - tot0) <= 1e-8 * tot0
+    else:
+        # sum_{i,c} F_ic = tot1 - tot0 exactly (sum_i phi_i = 1, the reaction terms sum to
+        # zero over the compartments), so |tot1 - tot0| <= sqrt(5 n) ||F||
+        assert abs(tot1 - tot0) <= math.sqrt(5 * wl.n) * res_final * 1.01 + 1e-13 * tot0, (tot1 - tot0, res_final)
     # d - d^n - dt gamma_D i = M^{-1} F_D: small at the Newton tolerance, O(1) for a wrong term
     drow = U[:, 4] - Un[:, 4] - wl.dt * wl.params.gamma_d * U[:, 2]
     assert np.abs(drow).max() <= 1e-3 * np.abs(U[:, 4] - Un[:, 4]).max()
@@ -63,7 +77,7 @@ def _check_step_properties(wl, Un, U, n_samples=300, seed=0):
 def test_ontario_2m_steps(precision):
     """Config 2: 2.0M-node Ontario-like mesh, 512 subdomains, overlap 2, coarse on."""
     wl = I.ontario_workload(2_000_000)
-    with S.Solver(wl.xy, wl.tri, wl.params, dt=wl.dt, n_subdomains=512, precision=precision, **BENCH_OPTS) as sv:
+    with S.Solver(wl.xy, wl.tri, wl.params, dt=wl.dt, **bench_opts(precision, 512)) as sv:
         sv.set_state(wl.U0)
         sv.run(2)
         U1 = sv.get_state()
@@ -79,8 +93,7 @@ def test_mixed_vs_fp64_on_the_1024_square():
     wl = I.ontario_workload(1024 * 1024, structured=True, nside=1024, n_subdomains=512)
     out = {}
     for precision in (0, 1):
-        with S.Solver(wl.xy, wl.tri, wl.params, dt=wl.dt, n_subdomains=512, precision=precision,
-                      **BENCH_OPTS) as sv:
+        with S.Solver(wl.xy, wl.tri, wl.params, dt=wl.dt, **bench_opts(precision, 512)) as sv:
             sv.set_state(wl.U0)
             sv.run(3)
             Un = sv.get_state()
@@ -88,6 +101,29 @@ def test_mixed_vs_fp64_on_the_1024_square():
             out[precision] = (Un, sv.get_state())
     for precision in (0, 1):
         _check_step_properties(wl, *out[precision], seed=precision)
+    a, b = out[1][1], out[0][1]
+    rel = [np.linalg.norm(a[:, c] - b[:, c]) / np.linalg.norm(b[:, c]) for c in range(5)]
+    assert max(rel) <= 1e-6, rel
+
+
+def test_paper_scale_steps_fp64_and_mixed():
+    """The headline workload: 18.4M nodes (92M unknowns), 4096 subdomains, the bench's
+    options, FP64 and mixed precision from the same start; each step's properties,
+    and the two paths' states against each other."""
+    wl = I.ontario_workload(bench.PAPER_SCALE_NODES, seed=_ARGS.seed, n_subdomains=bench.PAPER_SCALE_SUBDOMAINS)
+    out = {}
+    for precision in (0, 1):
+        with S.Solver(wl.xy, wl.tri, wl.params, dt=wl.dt,
+                      **bench_opts(precision, bench.PAPER_SCALE_SUBDOMAINS)) as sv:
+            assert sv.info()["n_subdomains"] == bench.PAPER_SCALE_SUBDOMAINS
+            sv.set_state(wl.U0)
+            sv.run(2)
+            Un = sv.get_state()
+            st = sv.step()
+            out[precision] = (Un, sv.get_state(), st["res_final"])
+    for precision in (0, 1):
+        Un, U, res = out[precision]
+        _check_step_properties(wl, Un, U, seed=precision, res_final=res)
     a, b = out[1][1], out[0][1]
     rel = [np.linalg.norm(a[:, c] - b[:, c]) / np.linalg.norm(b[:, c]) for c in range(5)]
     assert max(rel) <= 1e-6, rel
