@@ -78,6 +78,8 @@ def parse(argv=None):
                     help="1 additive coarse correction, 2 the paper's multiplicative two-grid (Eq. RAS_2L), "
                          "3 coarse correction then RAS")
     ap.add_argument("--coarse-group", type=int, default=0, help="subdomains per coarse unit (0: automatic)")
+    ap.add_argument("--ilu-fill", type=int, default=0, choices=range(0, 9),
+                    help="levels of fill k of the block ILU(k) subdomain factors")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--one-pass", action="store_true",
                     help="one classical Gram-Schmidt pass (PETSc's default) instead of CGS2")
@@ -99,7 +101,7 @@ def solver_options(args, precision, subdomains):
                 pc_keep_steps=args.pc_keep, predictor=args.predictor, newton_rtol=1e-8, gmres_rtol=1e-5,
                 gmres_restart=30, gmres_maxit=200, precision=1 if precision == "mixed" else 0, seed=args.seed,
                 gmres_forcing=1 if args.forcing == "ew" else 0, pc_lag=args.pc_lag,
-                gmres_one_pass=1 if args.one_pass else 0)
+                gmres_one_pass=1 if args.one_pass else 0, ilu_fill=args.ilu_fill)
 
 
 def workload_config(wl, args, subdomains):
@@ -109,7 +111,7 @@ def workload_config(wl, args, subdomains):
         "subdomains": subdomains, "overlap": 2,
         "coarse": {1: "additive", 2: "multiplicative two-grid (Eq. RAS_2L)",
                    3: "coarse correction, then RAS"}[args.coarse] + ", constant per subdomain and compartment",
-        "subdomain_solver": "block ILU(0)",
+        "subdomain_solver": "block ILU(%d)" % args.ilu_fill,
         "krylov": "FGMRES(30) right-preconditioned, %s, rtol 1e-5" % (
             "classical Gram-Schmidt single pass (PETSc default)" if args.one_pass else "CGS2"),
         "forcing": "Eisenstat-Walker" if args.forcing == "ew" else "fixed rtol 1e-5",

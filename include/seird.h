@@ -18,7 +18,7 @@
  *     (options.gmres_one_pass); stopping rules of Section 3.2 (rtol, atol,
  *     dtol against ||b||_2).
  *   - Preconditioner: restricted additive Schwarz (Eq. RAS) with overlapping
- *     subdomains and block-ILU(0) subdomain solves, plus (optionally) the
+ *     subdomains and block-ILU(k) subdomain solves (options.ilu_fill), plus (optionally) the
  *     additive coarse correction M_2^{-1} = M_RAS^{-1} + Z A_c^{-1} Z^T
  *     (Section 3.1) with Z the per-subdomain, per-compartment constant space.
  *
@@ -168,13 +168,21 @@ typedef struct {
                              (0 means 0.1, the usual Eisenstat-Walker start).  A Newton iteration that
                              starts close to the root (a good predictor) can afford a smaller one, so
                              that the next iteration already reaches the Newton target (0) */
+  int32_t ilu_fill;       /* subdomain factors: block ILU(k) with k = ilu_fill levels of fill, 0-8
+                             (Saad, Iterative Methods for Sparse Linear Systems, Section 10.3.3).  Entry
+                             (i, j) of a subdomain's factors is kept when lev(i, j) <= k, where
+                             lev(i, j) = 0 on the pattern of R_p J R_p^T and every elimination step
+                             through a pivot row m < min(i, j) offers lev(i, m) + lev(m, j) + 1.  The
+                             factors agree with R_p J R_p^T on every kept entry; 0 is ILU(0), PETSc's
+                             default subdomain solver.  More fill costs memory and solve time per
+                             application and buys fewer GMRES iterations where diffusion dominates (0) */
 } seird_options;
 
 /* Kernel classes of seird_stats.kernel_ms / kernel_calls. */
 enum {
   SEIRD_K_RESIDUAL = 0,     /* residual assembly (element + gather + norm) */
   SEIRD_K_JACOBIAN = 1,     /* Jacobian assembly (records + block gather) */
-  SEIRD_K_ILU_FACTOR = 2,   /* subdomain block-ILU(0) factorisation */
+  SEIRD_K_ILU_FACTOR = 2,   /* subdomain block-ILU(k) factorisation */
   SEIRD_K_COARSE_SETUP = 3, /* Z^T J Z and its banded block LU */
   SEIRD_K_SPMV = 4,         /* BSR SpMV */
   SEIRD_K_ILU_SOLVE = 5,    /* subdomain triangular solves (RAS apply) */
@@ -210,8 +218,8 @@ typedef struct {
   int64_t n_nodes, n_tris, nnzb;
   int32_t n_subdomains;
   int64_t subdomain_rows;      /* sum over subdomains of overlapped node counts */
-  int64_t subdomain_blocks;    /* sum over subdomains of local BSR blocks */
-  int32_t max_levels;          /* deepest ILU(0) level schedule */
+  int64_t subdomain_blocks;    /* sum over subdomains of factor blocks (the local pattern and its fill) */
+  int32_t max_levels;          /* deepest level schedule of the subdomain factors */
   int32_t coarse_band;         /* half bandwidth (in coarse units) of the coarse matrix */
   int64_t device_bytes;        /* device memory held by the context */
   int32_t coarse_units;        /* units of the coarse space (groups of options.coarse_group subdomains) */
@@ -231,7 +239,7 @@ void seird_default_options(seird_options* opt);
 
 /* Builds a context: validates the mesh (indices in range, positive areas),
  * partitions and renumbers nodes, builds the BSR pattern, element maps,
- * overlapping subdomains (Eq. RAS), ILU(0) level schedules and the coarse
+ * overlapping subdomains (Eq. RAS), ILU(k) patterns and level schedules and the coarse
  * pattern, and uploads everything.  The state is set to zero at t = 0.
  * Returns SEIRD_EINVAL for a bad mesh/option, SEIRD_ENOMEM, SEIRD_ECUDA. */
 int seird_create(const seird_mesh* mesh, const seird_params* params, const seird_options* opt,
@@ -366,7 +374,7 @@ int seird_get_jacobian(const seird_ctx* ctx, int32_t* row_ptr, int32_t* col, dou
 /* y = J x with the context's Jacobian (caller numbering). */
 int seird_apply_jacobian(seird_ctx* ctx, const double* x, double* y, int on_device);
 
-/* Builds the preconditioner (subdomain block-ILU(0) factors and, if enabled,
+/* Builds the preconditioner (subdomain block-ILU(k) factors and, if enabled,
  * the coarse matrix Z^T J Z and its factors) from the context's Jacobian. */
 int seird_precond_setup(seird_ctx* ctx);
 
@@ -416,14 +424,15 @@ int64_t seird_launch_count(void);
 
 /* Host-only check of the set-up the kernels rely on (no device call, no
  * context): builds the partition, the BSR pattern, the overlapping
- * subdomains and the ILU(0) level schedules and solve plans for `mesh` under
+ * subdomains, the ILU(k) patterns, level schedules and solve plans for `mesh` under
  * `opt` (NULL: defaults) and verifies their invariants: owned ranges tile the
  * nodes, rows sorted with their diagonal, a structurally symmetric pattern,
  * each node's element gather list naming its triangle corners in order and
  * each block's naming the corner pairs that reach it, coarse units tiling the
  * nodes, the J Z segments of the two-grid lying in their row and in one unit,
- * the coarse segment sums visiting every block once,
- * every owned node in its subdomain, every sweep a permutation of the
+ * the coarse segment sums visiting every block once, every subdomain's factor
+ * pattern symmetric with its diagonal and each block naming its J block (or
+ * none, for fill), every owned node in its subdomain, every sweep a permutation of the
  * subdomain's rows, every stage within the shared-memory rings, every
  * dependency of a row in an earlier stage, and the row records numbering the
  * solution entries by sweep position with each owned row written once.

@@ -36,7 +36,9 @@ What it computes (the discrete system both sides solve):
 
 Component functions used for kernel parity: the 5x5-block BSR form of the
 Jacobian and its product with a vector, the restricted additive Schwarz
-preconditioner of Eq. RAS with block ILU(0) subdomain solves, and the additive
+preconditioner of Eq. RAS with block ILU(0) or ILU(k) subdomain solves (the
+paper leaves the subdomain solver open; ILU(k) by levels of fill as in Saad,
+Iterative Methods for Sparse Linear Systems, Section 10.3.3), and the additive
 coarse correction Q = Z A_c^{-1} Z^T of Section 3.1 with the per-subdomain,
 per-compartment constant coarse space Z.
 """
@@ -432,6 +434,59 @@ def block_ilu0_solve(row_ptr, col, F, r):
     return z.ravel()
 
 
+def iluk_levels(row_ptr, col, k):
+    """Pattern of block ILU(k) by levels of fill (Saad, Iterative Methods for Sparse
+    Linear Systems, Section 10.3.3), in the matrix's own row order: for every row a
+    dict column -> level.  The row's own blocks have level 0; eliminating with pivot
+    row m < i (in increasing m, fill included) gives each block (m, j), j > m, of row
+    m's upper part the level lev(i, m) + lev(m, j) + 1, and a block belongs to row i
+    when its least level is at most k."""
+    n = len(row_ptr) - 1
+    lev = []
+    for i in range(n):
+        row = {int(c): 0 for c in col[row_ptr[i]:row_ptr[i + 1]]}
+        done = set()
+        while True:
+            pending = [c for c in row if c < i and c not in done]
+            if not pending:
+                break
+            m = min(pending)
+            done.add(m)
+            for j, lmj in lev[m].items():
+                if j > m:
+                    lv = row[m] + lmj + 1
+                    if lv <= k and lv < row.get(j, k + 1):
+                        row[j] = lv
+        lev.append(row)
+    return lev
+
+
+def block_iluk(row_ptr, col, val, k):
+    """Block ILU(k) of a 5x5-block BSR matrix in its own row order (IKJ form on the
+    pattern of ``iluk_levels``; fill blocks start at zero).  Returns (row_ptr, col, F)
+    of the factors with sorted columns: strictly lower blocks hold L (unit block
+    diagonal implied), the diagonal and upper blocks hold U.  k = 0 is ``block_ilu0``."""
+    n = len(row_ptr) - 1
+    lev = iluk_levels(row_ptr, col, k)
+    F = []
+    for i in range(n):
+        own = {int(col[q]): q for q in range(row_ptr[i], row_ptr[i + 1])}
+        F.append({j: (val[own[j]].copy() if j in own else np.zeros((5, 5))) for j in sorted(lev[i])})
+    for i in range(n):
+        for m in sorted(c for c in F[i] if c < i):
+            F[i][m] = F[i][m] @ np.linalg.inv(F[m][m])
+            for j, b in F[m].items():
+                if j > m and j in F[i]:
+                    F[i][j] = F[i][j] - F[i][m] @ b
+    rp = np.zeros(n + 1, dtype=np.int64)
+    cc, vv = [], []
+    for i in range(n):
+        cc.extend(F[i].keys())
+        vv.extend(F[i].values())
+        rp[i + 1] = len(cc)
+    return rp, np.array(cc, dtype=np.int64), np.array(vv).reshape(-1, 5, 5)
+
+
 def submatrix_bsr(row_ptr, col, val, nodes):
     """R_p A R_p^T in BSR form for the ordered node list ``nodes``."""
     loc = {int(g): l for l, g in enumerate(nodes)}
@@ -459,10 +514,12 @@ def coarse_matrix(row_ptr, col, val, owner):
     return (Z.T @ A @ Z).toarray(), Z
 
 
-def ras_apply(row_ptr, col, val, owner, delta, r, coarse=True, multiplicative=False, coarse_owner=None):
+def ras_apply(row_ptr, col, val, owner, delta, r, coarse=True, multiplicative=False, coarse_owner=None,
+              ilu_fill=0):
     """z = M^{-1} r for the restricted additive Schwarz preconditioner (Eq. RAS)
-    with block-ILU(0) subdomain solves on R_p A R_p^T (local unknowns numbered
-    by (owner, node index)), plus, if ``coarse``, the additive coarse term
+    with block-ILU(k) subdomain solves (k = ``ilu_fill``; 0 is ILU(0)) on
+    R_p A R_p^T (local unknowns numbered by (owner, node index)), plus, if
+    ``coarse``, the additive coarse term
     Z A_c^{-1} Z^T r (M_2^{-1} = M_RAS^{-1} + Q, Section 3.1).  ``coarse_owner``
     (default: ``owner``) assigns the nodes to the coarse space's units when
     several subdomains share one unit.
@@ -479,14 +536,15 @@ def ras_apply(row_ptr, col, val, owner, delta, r, coarse=True, multiplicative=Fa
         A = sp.bsr_matrix((val, col, row_ptr), shape=(5 * n, 5 * n)).tocsr()
         Ac, Z = coarse_matrix(row_ptr, col, val, cown)
         u = Z @ np.linalg.solve(Ac, Z.T @ r)
-        return u + ras_apply(row_ptr, col, val, owner, delta, r - A @ u, coarse=False)
+        return u + ras_apply(row_ptr, col, val, owner, delta, r - A @ u, coarse=False, ilu_fill=ilu_fill)
     if multiplicative:
         n = len(row_ptr) - 1
         A = sp.bsr_matrix((val, col, row_ptr), shape=(5 * n, 5 * n)).tocsr()
         Ac, Z = coarse_matrix(row_ptr, col, val, cown)
-        u = ras_apply(row_ptr, col, val, owner, delta, r, coarse=False)          # u^{1/3} = P1 f
-        u = u + Z @ np.linalg.solve(Ac, Z.T @ (r - A @ u))                       # u^{2/3} = u + P2 (f - A u)
-        u = u + ras_apply(row_ptr, col, val, owner, delta, r - A @ u, coarse=False)  # u^1 = u + P3 (f - A u)
+        u = ras_apply(row_ptr, col, val, owner, delta, r, coarse=False, ilu_fill=ilu_fill)  # u^{1/3} = P1 f
+        u = u + Z @ np.linalg.solve(Ac, Z.T @ (r - A @ u))                        # u^{2/3} = u + P2 (f - A u)
+        u = u + ras_apply(row_ptr, col, val, owner, delta, r - A @ u, coarse=False,
+                          ilu_fill=ilu_fill)                                      # u^1 = u + P3 (f - A u)
         return u
     n = len(row_ptr) - 1
     rank = np.empty(n, dtype=np.int64)
@@ -498,7 +556,10 @@ def ras_apply(row_ptr, col, val, owner, delta, r, coarse=True, multiplicative=Fa
     for q in range(len(owned)):
         nodes = over[q][np.argsort(rank[over[q]], kind="stable")]
         rp, cc, vv = submatrix_bsr(row_ptr, col, val, nodes)
-        Fq = block_ilu0(rp, cc, vv)
+        if ilu_fill:
+            rp, cc, Fq = block_iluk(rp, cc, vv, ilu_fill)
+        else:
+            Fq = block_ilu0(rp, cc, vv)
         zq = block_ilu0_solve(rp, cc, Fq, rr[nodes].ravel()).reshape(-1, 5)
         mine = owner[nodes] == q
         zz[nodes[mine]] = zq[mine]

@@ -71,6 +71,7 @@ struct HostSetup {
   std::vector<int32_t> bwd_order, bwd_lev, sd_bwd_lev0;
   int32_t max_levels = 0;
   int32_t max_sd_rows = 0;
+  int32_t ilu_fill = 0;             // levels of fill of the subdomain factors (options.ilu_fill)
   // ILU(0) solve plans: the solve reads factor blocks from a copy laid out in
   // level order (forward: each row's strictly lower blocks; backward: each row's
   // inverted pivot block, then its upper blocks), so that every level is one

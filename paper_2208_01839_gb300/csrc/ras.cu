@@ -114,8 +114,9 @@ __device__ __forceinline__ const double* solve_bwd<double>(const RasDev& d) { re
 template <>
 __device__ __forceinline__ const float* solve_bwd<float>(const RasDev& d) { return d.bU32; }
 
-// Block ILU(0) of R_p J R_p^T (IKJ form), rows in forward-level order, in the
-// arithmetic of T (FP64, or FP32 for the mixed-precision path).
+// Block ILU(k) of R_p J R_p^T on the set-up's pattern (ILU(0): the pattern of R_p J R_p^T;
+// fill blocks start at zero), IKJ form, rows in forward-level order, in the arithmetic of T
+// (FP64, or FP32 for the mixed-precision path).
 template <class T, class TV>
 __global__ void __launch_bounds__(256) k_ilu_factor(RasDev d, const TV* __restrict__ val, int32_t* err) {
   T* fval = fvals<T>(d);
@@ -127,7 +128,8 @@ __global__ void __launch_bounds__(256) k_ilu_factor(RasDev d, const TV* __restri
   for (int64_t idx = threadIdx.x; idx < (b1 - b0) * 25; idx += blockDim.x) {
     const int64_t blk = b0 + idx / 25;
     const int e = (int)(idx % 25);
-    fval[25 * blk + e] = (T)val[25 * (int64_t)d.l_gblk[blk] + e];
+    const int32_t g = d.l_gblk[blk];  // -1: a fill block of ILU(k), zero before the factorisation
+    fval[25 * blk + e] = g >= 0 ? (T)val[25 * (int64_t)g + e] : T(0);
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;

@@ -1466,7 +1466,7 @@ static int create_impl(seird_ctx* ctx, const seird_mesh* mesh, const seird_param
       (o.gmres_forcing != 0 && o.gmres_forcing != 1) || (o.nonlinear != 0 && o.nonlinear != 1) ||
       (o.gmres_one_pass != 0 && o.gmres_one_pass != 1) || o.pc_keep_steps < 0 ||
       (o.predictor < 0 || o.predictor > seird::MAX_PREDICTOR) || !(o.forcing_first >= 0.0 && o.forcing_first < 1.0) || (o.autotune != 0 && o.autotune != 1) || (o.graph != 0 && o.graph != 1) ||
-      !(o.picard_tol >= 0))
+      o.ilu_fill < 0 || o.ilu_fill > 8 || !(o.picard_tol >= 0))
     return fail(ctx, SEIRD_EINVAL, "invalid option value");
   std::string err;
   int rc = build_setup(mesh, &o, ctx->hs, err);

@@ -10,6 +10,7 @@
 #include <exception>
 #include <mutex>
 #include <numeric>
+#include <queue>
 #include <random>
 #include <stdexcept>
 #include <string>
@@ -165,6 +166,78 @@ static void parallel_for(int32_t n, int nth, F&& f) {
   if (first) std::rethrow_exception(first);
 }
 
+// Symbolic block ILU(k) of one subdomain (level of fill; Saad, Iterative Methods for
+// Sparse Linear Systems, Section 10.3.3), row by row in the local order: the row's
+// own blocks have level 0; eliminating with pivot row m < i, in increasing m, offers
+// every block (m, j), j > m, of row m's upper part the level lev(i, m) + lev(m, j) + 1,
+// and a block joins row i when its level is at most k.  Replaces the local pattern
+// (row ends, columns, J blocks with -1 for fill, diagonal positions) in place; rows
+// stay sorted by column.
+static void iluk_pattern(int k, int32_t nl, std::vector<int64_t>& rstart, std::vector<int64_t>& rowend,
+                         std::vector<int32_t>& l_col, std::vector<int32_t>& l_gblk, std::vector<int64_t>& diag) {
+  std::vector<int32_t> ncol, ngblk;
+  ncol.reserve(l_col.size() * 2);
+  ngblk.reserve(l_col.size() * 2);
+  std::vector<int64_t> nend(nl), ndiag(nl);
+  // the upper part of every finished row with its levels, for the rows below it
+  std::vector<int64_t> uptr(nl + 1, 0);
+  std::vector<int32_t> ucol;
+  std::vector<int8_t> ulev;
+  std::vector<int8_t> lev(nl, -1);  // level of each column in the current row (-1: absent)
+  std::vector<int32_t> gb(nl, -1);  // J block of each column in the current row
+  std::vector<int32_t> cols;
+  std::priority_queue<int32_t, std::vector<int32_t>, std::greater<int32_t>> pivots;
+  for (int32_t i = 0; i < nl; ++i) {
+    cols.clear();
+    for (int64_t a = rstart[i]; a < rstart[i + 1]; ++a) {
+      const int32_t c = l_col[a];
+      lev[c] = 0;
+      gb[c] = l_gblk[a];
+      cols.push_back(c);
+      if (c < i) pivots.push(c);
+    }
+    while (!pivots.empty()) {
+      const int32_t m = pivots.top();
+      pivots.pop();
+      const int lim = lev[m];
+      if (lim >= k) continue;  // every block it offers would have a level above k
+      for (int64_t b = uptr[m]; b < uptr[m + 1]; ++b) {
+        const int32_t j = ucol[b];
+        const int l = lim + ulev[b] + 1;
+        if (l > k) continue;
+        if (lev[j] < 0) {
+          lev[j] = (int8_t)l;
+          gb[j] = -1;
+          cols.push_back(j);
+          if (j < i) pivots.push(j);  // j > m: popped after m
+        } else if (l < lev[j]) {
+          lev[j] = (int8_t)l;
+        }
+      }
+    }
+    std::sort(cols.begin(), cols.end());
+    for (int32_t c : cols) {
+      if (c == i) ndiag[i] = (int64_t)ncol.size();
+      if (c > i) {
+        ucol.push_back(c);
+        ulev.push_back(lev[c]);
+      }
+      ncol.push_back(c);
+      ngblk.push_back(gb[c]);
+      lev[c] = -1;
+      gb[c] = -1;
+    }
+    uptr[i + 1] = (int64_t)ucol.size();
+    nend[i] = (int64_t)ncol.size();
+  }
+  l_col.swap(ncol);
+  l_gblk.swap(ngblk);
+  rowend.swap(nend);
+  diag.swap(ndiag);
+  rstart[0] = 0;
+  for (int32_t i = 0; i < nl; ++i) rstart[i + 1] = rowend[i];
+}
+
 int build_setup(const seird_mesh* mesh, const seird_options* opt, HostSetup& hs, std::string& err) {
   const int64_t n = mesh->n_nodes, m = mesh->n_tris;
   if (n < 3 || m < 1 || !mesh->xy || !mesh->tri) {
@@ -200,6 +273,11 @@ int build_setup(const seird_mesh* mesh, const seird_options* opt, HostSetup& hs,
   const int prc = partition_nodes(mesh, opt, owner_c, P, err);
   if (prc) return prc;
   hs.P = P;
+  if (opt->ilu_fill < 0 || opt->ilu_fill > 8) {
+    err = "ilu_fill must be 0-8";
+    return SEIRD_EINVAL;
+  }
+  hs.ilu_fill = opt->ilu_fill;
 
   // ---- internal numbering: nodes sorted by (owner, caller index) ----------
   hs.own_ptr.assign(P + 1, 0);
@@ -373,7 +451,8 @@ int build_setup(const seird_mesh* mesh, const seird_options* opt, HostSetup& hs,
         S.rowend[l] = pos;
       }
       rstart[nl] = pos;
-      // ILU(0) update pairs: for lower block (i,k): every (k,j) with j > k and (i,j) present
+      if (opt->ilu_fill > 0) iluk_pattern(opt->ilu_fill, nl, rstart, S.rowend, S.l_col, S.l_gblk, S.diag);
+      // update pairs of the factorisation: for lower block (i,k): every (k,j) with j > k and (i,j) present
       std::vector<int64_t> rowpos(nl, -1);  // local col -> block index in the current row
       S.updend.reserve(pos);
       for (int32_t i = 0; i < nl; ++i) {
@@ -814,6 +893,34 @@ int64_t check_setup(const HostSetup& hs, std::string& first) {
       if (v >= 0 && v < n) seen[v] = q;
       const int64_t dg = hs.l_diag[R];
       fail(dg >= hs.l_row_ptr[R] && dg < hs.l_row_ptr[R + 1] && hs.l_col[dg] == R - r0, "local diagonal");
+    }
+    // factor pattern: rows sorted, structurally symmetric (the ILU(k) pattern of a symmetric
+    // pattern is symmetric), every block of R_p J R_p^T present and naming its J block, and
+    // only fill blocks (allowed with ilu_fill > 0) naming none
+    for (int32_t R = r0; R < r1 && !bad; ++R) {
+      const int32_t v = hs.sd_node[R];
+      std::vector<int32_t> jcols;  // local columns of J's row v inside the subdomain
+      for (int32_t k = hs.row_ptr[v]; k < hs.row_ptr[v + 1]; ++k) {
+        const int32_t c = hs.col[k];
+        if (seen[c] == q) jcols.push_back(c);
+      }
+      size_t found = 0;
+      for (int64_t a = hs.l_row_ptr[R]; a < hs.l_row_ptr[R + 1]; ++a) {
+        const int32_t lc = hs.l_col[a];
+        fail(lc >= 0 && lc < r1 - r0 && (a == hs.l_row_ptr[R] || hs.l_col[a - 1] < lc), "factor row not sorted");
+        if (bad) break;
+        const int32_t g = hs.l_gblk[a];
+        if (g >= 0) {
+          fail(g >= hs.row_ptr[v] && g < hs.row_ptr[v + 1] && hs.col[g] == hs.sd_node[r0 + lc], "factor block names the wrong J block");
+          ++found;
+        } else {
+          fail(hs.ilu_fill > 0, "fill block without ilu_fill");
+        }
+        // the transposed block (lc, R - r0)
+        const int64_t t0 = hs.l_row_ptr[r0 + lc], t1 = hs.l_row_ptr[r0 + lc + 1];
+        fail(std::binary_search(hs.l_col.begin() + t0, hs.l_col.begin() + t1, R - r0), "factor pattern not symmetric");
+      }
+      fail(found == jcols.size(), "a block of R_p J R_p^T is missing from the factor pattern");
     }
     for (int32_t i = hs.own_ptr[q]; i < hs.own_ptr[q + 1]; ++i) fail(seen[i] == q, "owned node outside its subdomain");
   }

@@ -51,7 +51,7 @@ class Options(C.Structure):
                 ("timing", C.c_int32), ("gmres_forcing", C.c_int32), ("nonlinear", C.c_int32),
                 ("gmres_one_pass", C.c_int32), ("picard_tol", C.c_double), ("pc_keep_steps", C.c_int32),
                 ("coarse_group", C.c_int32), ("predictor", C.c_int32), ("autotune", C.c_int32),
-                ("graph", C.c_int32), ("forcing_first", C.c_double)]
+                ("graph", C.c_int32), ("forcing_first", C.c_double), ("ilu_fill", C.c_int32)]
 
 
 class BetaSchedule(C.Structure):

@@ -328,6 +328,61 @@ def test_mixed_precision_square_step_by_step():
 
 
 # ---------------------------------------------------------------------------
+# block ILU(k) subdomain factors (options.ilu_fill)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("fill", [1, 2])
+@pytest.mark.parametrize("coarse,precision", [(0, 0), (2, 0), (1, 1)])
+def test_iluk_preconditioner_matches_oracle(fill, coarse, precision):
+    """RAS with block ILU(k) subdomain solves, one-level, the multiplicative two-grid and the
+    FP32 factors, against the oracle's ILU(k) (FP64: 1e-10; FP32 factors: 1e-4)."""
+    wl = I.square_workload(17)
+    owner = I.box_partition(wl.xy, 3, 2)
+    J = O.jacobian(wl.xy, wl.tri, wl.params, wl.dt, wl.U0)
+    rp, col, val = O.to_bsr(J)
+    r = np.random.default_rng(31 + fill).standard_normal(5 * wl.n)
+    ref = O.ras_apply(rp, col, val, owner, 2, r, coarse=coarse == 1, multiplicative=coarse == 2, ilu_fill=fill)
+    ref0 = O.ras_apply(rp, col, val, owner, 2, r, coarse=coarse == 1, multiplicative=coarse == 2)
+    with solver(wl, owner=owner, overlap=2, coarse=coarse, precision=precision, ilu_fill=fill) as sv:
+        sv.jacobian(wl.U0)
+        sv.precond_setup()
+        got = sv.precond_apply(r.reshape(-1, 5)).ravel()
+        assert sv.info()["subdomain_blocks"] > 0
+    tol = 1e-4 if precision else 1e-10
+    assert np.linalg.norm(got - ref) <= tol * np.linalg.norm(ref)
+    assert np.linalg.norm(ref - ref0) > 100 * tol * np.linalg.norm(ref)  # the fill changes the result
+
+
+def test_iluk_on_a_non_geometric_partition_matches_oracle():
+    """ILU(1) where the subdomains are scattered node sets (long fill chains, deep level
+    schedules) on the irregular mesh with the transmission field."""
+    wl = WL["irregular3k"]
+    owner = I.random_partition(wl.n, 4, 5)
+    J = O.jacobian(wl.xy, wl.tri, wl.params, wl.dt, wl.U0, bfield=wl.beta_field)
+    rp, col, val = O.to_bsr(J)
+    r = np.random.default_rng(33).standard_normal(5 * wl.n)
+    ref = O.ras_apply(rp, col, val, owner, 1, r, coarse=True, ilu_fill=1)
+    with solver(wl, owner=owner, overlap=1, coarse=1, ilu_fill=1) as sv:
+        sv.jacobian(wl.U0)
+        sv.precond_setup()
+        got = sv.precond_apply(r.reshape(-1, 5)).ravel()
+    assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_iluk_steps_match_oracle(precision):
+    """Three steps with ILU(2) subdomain factors and the two-grid reach the oracle's roots."""
+    wl = WL["irregular3k"]
+    U_ref, _ = O.run(wl.xy, wl.tri, wl.params, wl.dt, wl.U0, 3, rtol=1e-12, atol=newton_floor(wl),
+                     bfield=wl.beta_field)
+    with solver(wl, coarse=2, precision=precision, ilu_fill=2) as sv:
+        sv.set_state(wl.U0)
+        sv.run(3)
+        got = sv.get_state()
+    assert max(rel_l2_per_comp(got, U_ref)) <= 1e-9
+
+
+# ---------------------------------------------------------------------------
 # the paper's multiplicative two-grid preconditioner (Eq. RAS_2L), coarse = 2
 # ---------------------------------------------------------------------------
 

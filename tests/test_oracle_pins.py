@@ -7,8 +7,9 @@ deceased-row identity, the homogeneous-start reduction to the ODE and its
 first-order convergence (Appendix B.4, Table order_time), closed-form
 identities of the ODE, manufactured-solution spatial order 2 (Appendix B.1/B.3,
 Table ord_spatial_2), brute-force dense Newton, finite-difference Jacobians,
-mesh symmetry, and the defining properties of ILU(0), RAS and the coarse
-space (Section 3).
+mesh symmetry, and the defining properties of ILU(0), ILU(k) (its pattern
+against the fill-path characterisation, its product against the matrix on the
+pattern, its exact limit), RAS and the coarse space (Section 3).
 """
 import json
 import math
@@ -356,6 +357,119 @@ def test_block_ilu0_reproduces_matrix_on_its_pattern():
     r = np.random.default_rng(0).standard_normal(5 * n)
     z = O.block_ilu0_solve(rp, col, Fk, r)
     assert np.allclose(Ld @ (Ud @ z), r, atol=1e-9)
+
+
+def _dense_factors(rp, col, Fk):
+    n = len(rp) - 1
+    Ld = np.eye(5 * n)
+    Ud = np.zeros((5 * n, 5 * n))
+    for i in range(n):
+        for k in range(rp[i], rp[i + 1]):
+            j = col[k]
+            (Ld if j < i else Ud)[5 * i:5 * i + 5, 5 * j:5 * j + 5] = Fk[k]
+    return Ld, Ud
+
+
+def _fill_path_levels(rp, col):
+    """Level of every (i, j) from its fill paths (Hysom and Pothen, SIAM J. Sci.
+    Comput. 22 (2001)): a path i = v_0, ..., v_l = j of the matrix graph whose
+    interior vertices are all numbered below min(i, j) gives (i, j) the level
+    l - 1; the least such level wins.  Brute force: one breadth-first search per
+    (i, j) through the vertices below min(i, j)."""
+    n = len(rp) - 1
+    adj = [set(int(c) for c in col[rp[i]:rp[i + 1]]) - {i} for i in range(n)]
+    lev = {}
+    for i in range(n):
+        for j in range(n):
+            if i == j:
+                lev[i, j] = 0
+                continue
+            lo = min(i, j)
+            dist = {i: 0}
+            front = [i]
+            best = None
+            while front and best is None:
+                nxt = []
+                for v in front:
+                    for w in adj[v]:
+                        if w == j:
+                            best = dist[v] + 1
+                        elif w < lo and w not in dist:
+                            dist[w] = dist[v] + 1
+                            nxt.append(w)
+                front = nxt
+            if best is not None:
+                lev[i, j] = best - 1
+    return lev
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_iluk_levels_are_the_fill_path_levels(k):
+    """The symbolic ILU(k) pattern and levels equal the fill-path characterisation
+    (an independent, graph-theoretic definition) on an irregular 5x5-block pattern."""
+    wl, (rp, col, val) = _assembled(6)
+    # a non-geometric row order, so that fill is not confined to a band
+    perm = np.random.default_rng(3).permutation(len(rp) - 1)
+    A = sp.bsr_matrix((val, col, rp), shape=(5 * (len(rp) - 1),) * 2).tocsr()
+    idx = (5 * perm[:, None] + np.arange(5)).ravel()
+    rp2, col2, val2 = O.to_bsr(A[idx][:, idx])
+    lev = O.iluk_levels(rp2, col2, k)
+    ref = _fill_path_levels(rp2, col2)
+    n = len(rp2) - 1
+    for i in range(n):
+        want = {j: ref[i, j] for j in range(n) if (i, j) in ref and ref[i, j] <= k}
+        assert lev[i] == want, i
+    # the pattern grows with k and ILU(0) is the matrix's own pattern
+    lev0 = O.iluk_levels(rp2, col2, 0)
+    assert all(set(lev0[i]) == set(int(c) for c in col2[rp2[i]:rp2[i + 1]]) for i in range(n))
+    assert sum(len(r) for r in lev) > sum(len(r) for r in lev0)
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_block_iluk_reproduces_matrix_on_its_pattern(k):
+    """Defining property of an incomplete factorisation on a pattern: (L U)_ij = A_ij for
+    every (i, j) the pattern holds (fill blocks included, where A_ij = 0); off the pattern
+    L U differs from A."""
+    wl, (rp, col, val) = _assembled(6)
+    n = len(rp) - 1
+    A = sp.bsr_matrix((val, col, rp), shape=(5 * n, 5 * n)).toarray()
+    frp, fcol, Fk = O.block_iluk(rp, col, val, k)
+    assert len(fcol) > len(col)
+    Ld, Ud = _dense_factors(frp, fcol, Fk)
+    P = Ld @ Ud
+    scale = np.abs(val).max()
+    on = np.zeros((n, n), dtype=bool)
+    for i in range(n):
+        for q in range(frp[i], frp[i + 1]):
+            j = fcol[q]
+            on[i, j] = True
+            assert np.abs(P[5 * i:5 * i + 5, 5 * j:5 * j + 5] - A[5 * i:5 * i + 5, 5 * j:5 * j + 5]).max() <= 1e-11 * scale
+    off = max(np.abs(P - A)[5 * i:5 * i + 5, 5 * j:5 * j + 5].max() for i in range(n) for j in range(n) if not on[i, j])
+    assert off > 1e-8 * scale
+    r = np.random.default_rng(0).standard_normal(5 * n)
+    z = O.block_ilu0_solve(frp, fcol, Fk, r)
+    assert np.allclose(Ld @ (Ud @ z), r, atol=1e-9)
+
+
+def test_block_iluk_limits():
+    """k = 0 is block ILU(0) (the same operations, bit for bit); with every level
+    allowed nothing is dropped and the factors are the exact block LU: L U = A and
+    the solve is A^{-1}, so RAS with one subdomain and ILU(n) is the exact inverse."""
+    wl, (rp, col, val) = _assembled(5)
+    n = len(rp) - 1
+    frp, fcol, F0 = O.block_iluk(rp, col, val, 0)
+    assert np.array_equal(frp, rp) and np.array_equal(fcol, col)
+    assert np.array_equal(F0, O.block_ilu0(rp, col, val))
+    A = sp.bsr_matrix((val, col, rp), shape=(5 * n, 5 * n)).toarray()
+    frp, fcol, Fn = O.block_iluk(rp, col, val, n)
+    Ld, Ud = _dense_factors(frp, fcol, Fn)
+    assert np.abs(Ld @ Ud - A).max() <= 1e-11 * np.abs(A).max()
+    r = np.random.default_rng(2).standard_normal(5 * n)
+    x = np.linalg.solve(A, r)
+    assert np.allclose(O.block_ilu0_solve(frp, fcol, Fn, r), x, rtol=1e-9, atol=1e-12 * np.abs(x).max())
+    owner = np.zeros(n, dtype=np.int32)
+    z = O.ras_apply(rp, col, val, owner, 0, r, coarse=False, ilu_fill=n)
+    assert np.allclose(z, x, rtol=1e-9, atol=1e-12 * np.abs(x).max())
 
 
 def _chain_bsr(n, seed=0):

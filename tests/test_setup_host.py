@@ -102,3 +102,21 @@ def test_coarse_units_spanning_several_subdomains(group):
     wl = I.ontario_workload(20_000, n_subdomains=16)
     st = _check(wl.xy, wl.tri, n_subdomains=16, overlap=2, seed=3, coarse=2, coarse_group=group)
     assert st["n_subdomains"] == 16
+
+
+@pytest.mark.parametrize("fill", [1, 2, 3])
+def test_iluk_factor_patterns(fill):
+    """Block ILU(k) patterns: symmetric, holding R_p J R_p^T, fill naming no J block,
+    and every invariant of the solve plans on the larger pattern; the level schedules
+    deepen with k.  A fill level outside 0-8 is refused."""
+    wl = I.ontario_workload(20_000, seed=1, n_subdomains=16)
+    st0 = _check(wl.xy, wl.tri, n_subdomains=16, overlap=2, coarse=2)
+    st = _check(wl.xy, wl.tri, n_subdomains=16, overlap=2, coarse=2, ilu_fill=fill)
+    assert st["subdomain_rows"] == st0["subdomain_rows"]
+    assert st["forward_stages"] > st0["forward_stages"] and st["backward_stages"] > st0["backward_stages"]
+    # an owner array that is not geometric makes long fill chains
+    owner = np.random.default_rng(fill).integers(0, 4, size=len(wl.xy)).astype(np.int32)
+    _check(wl.xy, wl.tri, owner=owner, n_subdomains=4, overlap=1, ilu_fill=fill)
+    for bad in (-1, 9):
+        with pytest.raises(S.SeirdError):
+            S.setup_check(wl.xy, wl.tri, n_subdomains=16, ilu_fill=bad)
