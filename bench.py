@@ -4,13 +4,14 @@ Metric: implicit DOF*steps/s at a 1e-8 relative Newton residual (DOF = 5 x
 nodes).  Headline workload: the paper-scale Southern-Ontario-like mesh, a
 seeded 24-gon meshed to 18.4M P1 nodes (92M unknowns, the size of the paper's
 Section 4.2 scalability run), urban-Gaussian density, 5 infection seeds,
-dt = 0.5 day, RAS with 4096 uneven subdomains, overlap 2, the paper's
-multiplicative two-grid with the constant coarse space, FGMRES(30) with CGS2.
+dt = 0.5 day, RAS with 4096 uneven subdomains, overlap 2, block ILU(2)
+subdomain factors, the paper's multiplicative two-grid with the constant coarse
+space, FGMRES(30) with CGS2.
 A "step" is one backward-Euler time step (assembly, preconditioner set-up,
 GMRES, line search) of that whole mesh.  The same line carries the
 mixed-precision path on that workload, the 2.0M-node workload (10M unknowns,
-512 subdomains), a 64-sample ensemble, the discrete adjoint and the oracle
-timed on the host cores.
+512 subdomains, block ILU(1)), a 64-sample ensemble and the discrete adjoint
+(256^2 mesh, block ILU(0)) and the oracle timed on the host cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
   python bench.py --cpu-ladder      (the oracle on a ladder of square meshes)
@@ -78,8 +79,10 @@ def parse(argv=None):
                     help="1 additive coarse correction, 2 the paper's multiplicative two-grid (Eq. RAS_2L), "
                          "3 coarse correction then RAS")
     ap.add_argument("--coarse-group", type=int, default=0, help="subdomains per coarse unit (0: automatic)")
-    ap.add_argument("--ilu-fill", type=int, default=0, choices=range(0, 9),
-                    help="levels of fill k of the block ILU(k) subdomain factors")
+    ap.add_argument("--ilu-fill", type=int, default=2, choices=range(0, 9),
+                    help="levels of fill k of the block ILU(k) subdomain factors (headline workload)")
+    ap.add_argument("--ilu-fill-2m", type=int, default=1, choices=range(0, 9),
+                    help="levels of fill of the 2.0M-node object's subdomain factors")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--one-pass", action="store_true",
                     help="one classical Gram-Schmidt pass (PETSc's default) instead of CGS2")
@@ -96,12 +99,14 @@ def parse(argv=None):
     return ap.parse_args(argv)
 
 
-def solver_options(args, precision, subdomains):
+def solver_options(args, precision, subdomains, ilu_fill=None):
+    """Options of one measured context; ilu_fill defaults to the headline workload's."""
     return dict(n_subdomains=subdomains, overlap=2, coarse=args.coarse, coarse_group=args.coarse_group,
                 pc_keep_steps=args.pc_keep, predictor=args.predictor, newton_rtol=1e-8, gmres_rtol=1e-5,
                 gmres_restart=30, gmres_maxit=200, precision=1 if precision == "mixed" else 0, seed=args.seed,
                 gmres_forcing=1 if args.forcing == "ew" else 0, pc_lag=args.pc_lag,
-                gmres_one_pass=1 if args.one_pass else 0, ilu_fill=args.ilu_fill)
+                gmres_one_pass=1 if args.one_pass else 0,
+                ilu_fill=args.ilu_fill if ilu_fill is None else ilu_fill)
 
 
 def workload_config(wl, args, subdomains):
@@ -454,7 +459,7 @@ def measure_ensemble(S, I, args, stream, world, local):
     res = {}
     for mode in ("eager", "graph"):
         sv = S.Solver(wl.xy, wl.tri, samples, stream=stream, dt=wl.dt, graph=1 if mode == "graph" else 0,
-                      **solver_options(args, "fp64", 16))
+                      **solver_options(args, "fp64", 16, ilu_fill=0))
         sv.set_state(u0)
         for _ in range(args.warmup):
             sv.step()
@@ -491,7 +496,7 @@ def measure_adjoint(S, I, args, stream):
     nodes = np.sort(rng.choice(wl.n, 50, replace=False)).astype(np.int32)
     steps = np.arange(2, 61, 2, dtype=np.int32)
     field = np.ones(wl.n)
-    opts = solver_options(args, "fp64", 16)
+    opts = solver_options(args, "fp64", 16, ilu_fill=0)
     opts.update(pc_keep_steps=0, predictor=0)
     sv = S.Solver(wl.xy, wl.tri, wl.params, beta_field=field, stream=stream, dt=wl.dt, **opts)
     u0 = torch.tensor(wl.U0, device="cuda")
@@ -551,9 +556,11 @@ def run_ours(args):
     two = None
     if not args.no_2m and args.nodes != 2_000_000:
         wl2 = I.ontario_workload(2_000_000, seed=args.seed, n_subdomains=512)
-        r64 = measure(S, wl2, args, stream, "fp64", 512, world, local, e2e=False)
-        r32 = measure(S, wl2, args, stream, "mixed", 512, world, local, e2e=False)
-        two = summarize(S, r64, "fp64", wl2, args, 512)
+        args2 = argparse.Namespace(**vars(args))
+        args2.ilu_fill = args.ilu_fill_2m
+        r64 = measure(S, wl2, args2, stream, "fp64", 512, world, local, e2e=False)
+        r32 = measure(S, wl2, args2, stream, "mixed", 512, world, local, e2e=False)
+        two = summarize(S, r64, "fp64", wl2, args2, 512)
         two["mixed"] = summarize(S, r32, "mixed")
         two["mixed"]["speedup_vs_fp64"] = r32["value"] / r64["value"]
         del wl2

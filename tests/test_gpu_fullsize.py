@@ -36,9 +36,9 @@ import bench  # noqa: E402
 _ARGS = bench.parse([])
 
 
-def bench_opts(precision, subdomains):
+def bench_opts(precision, subdomains, ilu_fill=None):
     """The options bench.py times: solver_options of its default arguments, autotuner on."""
-    return dict(bench.solver_options(_ARGS, "mixed" if precision else "fp64", subdomains), autotune=1)
+    return dict(bench.solver_options(_ARGS, "mixed" if precision else "fp64", subdomains, ilu_fill), autotune=1)
 
 
 def _node_mass(xy, tri):
@@ -77,7 +77,7 @@ def _check_step_properties(wl, Un, U, n_samples=300, seed=0, res_final=None):
 def test_ontario_2m_steps(precision):
     """Config 2: 2.0M-node Ontario-like mesh, 512 subdomains, overlap 2, coarse on."""
     wl = I.ontario_workload(2_000_000)
-    with S.Solver(wl.xy, wl.tri, wl.params, dt=wl.dt, **bench_opts(precision, 512)) as sv:
+    with S.Solver(wl.xy, wl.tri, wl.params, dt=wl.dt, **bench_opts(precision, 512, _ARGS.ilu_fill_2m)) as sv:
         sv.set_state(wl.U0)
         sv.run(2)
         U1 = sv.get_state()
