@@ -5,8 +5,8 @@ nodes).  Headline workload: the paper-scale Southern-Ontario-like mesh, a
 seeded 24-gon meshed to 18.4M P1 nodes (92M unknowns, the size of the paper's
 Section 4.2 scalability run), urban-Gaussian density, 5 infection seeds,
 dt = 0.5 day, RAS with 4096 uneven subdomains, overlap 2, block ILU(2)
-subdomain factors, the paper's multiplicative two-grid with the constant coarse
-space, FGMRES(30) with CGS2.
+subdomain factors (ILU(3) on the mixed-precision path), the paper's
+multiplicative two-grid with the constant coarse space, FGMRES(30) with CGS2.
 A "step" is one backward-Euler time step (assembly, preconditioner set-up,
 GMRES, line search) of that whole mesh.  The same line carries the
 mixed-precision path on that workload, the 2.0M-node workload (10M unknowns,
@@ -81,8 +81,10 @@ def parse(argv=None):
     ap.add_argument("--coarse-group", type=int, default=0, help="subdomains per coarse unit (0: automatic)")
     ap.add_argument("--ilu-fill", type=int, default=2, choices=range(0, 9),
                     help="levels of fill k of the block ILU(k) subdomain factors (headline workload)")
+    ap.add_argument("--ilu-fill-mixed", type=int, default=3, choices=range(0, 9),
+                    help="levels of fill of the headline workload's mixed-precision subdomain factors")
     ap.add_argument("--ilu-fill-2m", type=int, default=1, choices=range(0, 9),
-                    help="levels of fill of the 2.0M-node object's subdomain factors")
+                    help="levels of fill of the 2.0M-node object's subdomain factors (both precisions)")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--one-pass", action="store_true",
                     help="one classical Gram-Schmidt pass (PETSc's default) instead of CGS2")
@@ -100,13 +102,15 @@ def parse(argv=None):
 
 
 def solver_options(args, precision, subdomains, ilu_fill=None):
-    """Options of one measured context; ilu_fill defaults to the headline workload's."""
+    """Options of one measured context; ilu_fill defaults to the headline workload's for the precision."""
+    if ilu_fill is None:
+        ilu_fill = args.ilu_fill_mixed if precision == "mixed" else args.ilu_fill
     return dict(n_subdomains=subdomains, overlap=2, coarse=args.coarse, coarse_group=args.coarse_group,
                 pc_keep_steps=args.pc_keep, predictor=args.predictor, newton_rtol=1e-8, gmres_rtol=1e-5,
                 gmres_restart=30, gmres_maxit=200, precision=1 if precision == "mixed" else 0, seed=args.seed,
                 gmres_forcing=1 if args.forcing == "ew" else 0, pc_lag=args.pc_lag,
                 gmres_one_pass=1 if args.one_pass else 0,
-                ilu_fill=args.ilu_fill if ilu_fill is None else ilu_fill)
+                ilu_fill=ilu_fill)
 
 
 def workload_config(wl, args, subdomains):
@@ -557,7 +561,7 @@ def run_ours(args):
     if not args.no_2m and args.nodes != 2_000_000:
         wl2 = I.ontario_workload(2_000_000, seed=args.seed, n_subdomains=512)
         args2 = argparse.Namespace(**vars(args))
-        args2.ilu_fill = args.ilu_fill_2m
+        args2.ilu_fill = args2.ilu_fill_mixed = args.ilu_fill_2m
         r64 = measure(S, wl2, args2, stream, "fp64", 512, world, local, e2e=False)
         r32 = measure(S, wl2, args2, stream, "mixed", 512, world, local, e2e=False)
         two = summarize(S, r64, "fp64", wl2, args2, 512)
@@ -602,6 +606,7 @@ def run_ours(args):
         if other is not None:
             m = summarize(S, other, "mixed")
             m["speedup_vs_fp64"] = other["value"] / res["value"]
+            m["subdomain_solver"] = "block ILU(%d)" % args.ilu_fill_mixed
             line["mixed"] = m
         if two is not None:
             line["ontario_2m"] = two
