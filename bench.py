@@ -45,12 +45,12 @@ FALLBACK_HBM_GBS = 6800.0
 # seird_get_info key of those units); scaled to a launch by the units it processes
 # (traffic grows in proportion).  The SpMV was captured on the 200k-node case of the
 # same generator, the subdomain solve at full size (18.4M nodes, 4096 subdomains,
-# block ILU(2) factors, the autotuned variants).  Entries are removed when the kernel
+# block ILU(2) factors in FP64 and ILU(3) in FP32, the autotuned variants).  Entries are removed when the kernel
 # changes and restored by the next capture.
 NCU_TRAFFIC = {
     ("spmv", "fp64"): (307.414e6, 1400635, "nnzb"),  # k_bsr_spmv<double>, 1.4M blocks
     ("ilu_solve", "fp64"): (60.66e9, 264544907, "subdomain_blocks"),  # k_ilu_solve<double, double, 4, 3, 118>, ILU(2)
-    ("ilu_solve", "mixed"): (33.30e9, 264544907, "subdomain_blocks"),  # k_ilu_solve<float, float, 4, 3, 236>, ILU(2)
+    ("ilu_solve", "mixed"): (42.39e9, 344245751, "subdomain_blocks"),  # k_ilu_solve<float, float, 4, 3, 236>, ILU(3)
 }
 
 # kernel classes with one kernel launch per timed call
