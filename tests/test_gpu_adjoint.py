@@ -54,16 +54,17 @@ def _adjoint(sv, P, **kw):
     return sv.adjoint(P["N"], P["obs_nodes"], P["obs_steps"], P["I_hat"], P["D_hat"], lin_rtol=1e-12, **kw)
 
 
-@pytest.mark.parametrize("coarse", [1, 2])
-def test_gpu_adjoint_matches_oracle_adjoint(coarse):
+@pytest.mark.parametrize("coarse,fill", [(1, 0), (2, 0), (2, 2)])
+def test_gpu_adjoint_matches_oracle_adjoint(coarse, fill):
     """Also with the multiplicative two-grid: the transposed solves then use the
-    two-grid built from J^T (its J Z update included)."""
+    two-grid built from J^T (its J Z update included); and with block ILU(2)
+    factors of J^T on the fill pattern."""
     P = _problem()
     Sx = A.forward_states(P["xy"], P["tri"], P["p"], P["dt"], P["U0"], P["N"], bfield=P["bf"], rtol=1e-13,
                           atol=_floor(P))
     j_ref, g_ref, gb_ref = A.adjoint_gradient(P["xy"], P["tri"], P["p"], P["dt"], Sx, P["obs_nodes"],
                                               P["obs_steps"], P["I_hat"], P["D_hat"], bfield=P["bf"])
-    with _solver(P, coarse=coarse) as sv:
+    with _solver(P, coarse=coarse, ilu_fill=fill) as sv:
         j, g, gb = _adjoint(sv, P)
         U_after = sv.get_state()
     assert abs(j - j_ref) <= 1e-9 * j_ref

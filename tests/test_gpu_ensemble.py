@@ -74,13 +74,13 @@ def test_ensemble_assembly_is_blockwise_the_oracle():
         assert np.abs(val[a:b] - jval).max() <= 1e-12 * np.abs(jval).max(), k
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_ensemble_steps_match_per_sample_oracle(precision):
+@pytest.mark.parametrize("precision,fill", [(0, 0), (1, 0), (0, 1)])
+def test_ensemble_steps_match_per_sample_oracle(precision, fill):
     xy, tri, samples, U0, bf = _problem()
     n = len(xy)
     atol = 1e-14 * np.linalg.norm(O.residual(xy, tri, samples[0], 0.0, np.abs(U0), np.zeros_like(U0)))
     with S.Solver(xy, tri, samples, beta_field=bf, owner=I.box_partition(xy, 2, 2),
-                  **_opts(precision=precision, newton_atol=atol * np.sqrt(len(samples)))) as sv:
+                  **_opts(precision=precision, newton_atol=atol * np.sqrt(len(samples)), ilu_fill=fill)) as sv:
         sv.set_state(np.concatenate([U0] * len(samples)))
         sv.run(3)
         got = sv.get_state()

@@ -570,20 +570,21 @@ def test_autotuned_launch_shapes():
         assert max(rel_l2_per_comp(got, U_ref)) <= (1e-9 if precision == 0 else 1e-6), precision
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_subdomain_solve_batches_give_identical_results(precision):
+@pytest.mark.parametrize("precision,fill", [(0, 0), (1, 0), (0, 2), (1, 3)])
+def test_subdomain_solve_batches_give_identical_results(precision, fill):
     """The subdomain solve's dependency-load batch (1-4 blocks), consumer warps per
     CTA (7 or 3) and factor-ring size (two stages or one), all autotuner choices,
     change only when a row's loads are issued, which warp takes it and how far the
     copies run ahead: every choice forms the same sums in the same order, so the
-    preconditioner apply is bitwise the same for all sixteen."""
+    preconditioner apply is bitwise the same for all sixteen.  With ILU(2) and ILU(3)
+    factors a row spans several batches of every size."""
     wl = WL["irregular3k"]
     r = np.random.default_rng(31).standard_normal(5 * wl.n)
     J = O.jacobian(wl.xy, wl.tri, wl.params, wl.dt, wl.U0, bfield=wl.beta_field)
     rp, col, val = O.to_bsr(J)
-    ref = O.ras_apply(rp, col, val, wl.owner, 2, r, coarse=True, multiplicative=True)
+    ref = O.ras_apply(rp, col, val, wl.owner, 2, r, coarse=True, multiplicative=True, ilu_fill=fill)
     outs = []
-    with solver(wl, overlap=2, coarse=2, precision=precision, autotune=1) as sv:
+    with solver(wl, overlap=2, coarse=2, precision=precision, autotune=1, ilu_fill=fill) as sv:
         sv.jacobian(wl.U0)
         sv.precond_setup()
         sv.set_state(wl.U0)
