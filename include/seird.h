@@ -471,8 +471,7 @@ int seird_setup_check(const seird_mesh* mesh, const seird_options* opt, int64_t*
  * returns SEIRD_ENONFINITE if N <= 0 at a quadrature point.  The first call
  * on a device looks up the scratch array's device address and uploads the
  * quadrature tables (a one-time set-up per device, with that device current,
- * ending in a device synchronisation); make that first call before any
- * stream capture.  Every call shares the one scratch array, whose contents
+ * ending in a device synchronisation).  Every call shares the one scratch array, whose contents
  * are left over from the last call; calls that overlap on the GPU (other
  * streams, other host threads) race on it and must be serialised by the caller. */
 #define SEIRD_NOALLOC_MAX_TRIS 65536
