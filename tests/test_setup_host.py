@@ -78,18 +78,20 @@ def test_bad_mesh_is_reported_not_checked():
         S.setup_check(xy, tri)
 
 
-def test_ensemble_union_mesh():
+@pytest.mark.parametrize("fill", [0, 2])
+def test_ensemble_union_mesh(fill):
     """The union mesh an ensemble is solved on: sample k's copy of the mesh with its
     nodes offset by k n and the per-sample partition shifted by k P (block-diagonal
-    system, no block couples two samples)."""
+    system, no block couples two samples); with fill, no fill block couples two
+    samples either (every sample's schedule is its own)."""
     xy, tri, _ = I.irregular_mesh(4, 800)
     owner = I.box_partition(xy, 2, 2).astype(np.int32)
     n, P, B = len(xy), int(owner.max()) + 1, 3
     uxy = np.concatenate([xy] * B)
     utri = np.concatenate([tri + k * n for k in range(B)]).astype(np.int32)
     uown = np.concatenate([owner + k * P for k in range(B)]).astype(np.int32)
-    st = _check(uxy, utri, owner=uown, overlap=2, coarse=2)
-    one = _check(xy, tri, owner=owner, overlap=2, coarse=2)
+    st = _check(uxy, utri, owner=uown, overlap=2, coarse=2, ilu_fill=fill)
+    one = _check(xy, tri, owner=owner, overlap=2, coarse=2, ilu_fill=fill)
     assert st["n_subdomains"] == B * P and st["nnzb"] == B * one["nnzb"]
     assert st["subdomain_rows"] == B * one["subdomain_rows"]
     assert st["forward_stages"] == B * one["forward_stages"] and st["backward_stages"] == B * one["backward_stages"]
