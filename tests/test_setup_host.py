@@ -1,11 +1,11 @@
 """Host-side set-up invariants (seird_setup_check; no GPU).
 
-The subdomain kernels trust the set-up without checking it: the ILU(0) solve
+The subdomain kernels trust the set-up without checking it: the ILU(k) solve
 streams each stage into fixed shared-memory rings, reads a row's dependencies
 from earlier stages with no synchronisation beyond the stage barrier, and
 writes every owned row of z exactly once.  These tests build the set-up on the
-CPU for the workload generators, geometric and non-geometric partitions and
-every overlap, and require every invariant to hold.
+CPU for the workload generators, geometric and non-geometric partitions, every
+overlap and several levels of fill, and require every invariant to hold.
 """
 import numpy as np
 import pytest
